@@ -1,0 +1,186 @@
+/*
+ * psr.h -- C ABI of libpsr, the GB300 (sm_103a) hot path of PSR-NQS
+ * variational Monte Carlo (parallel-scan recurrent neural quantum states,
+ * arXiv 2605.13807).
+ *
+ * The library evaluates, for many spin configurations at once,
+ *   - the autoregressive log-amplitude log psi(s) of a stack of minGRU layers
+ *     (Sec. II.C, Eq. minGRU) run along the zigzag ordering of the lattice
+ *     (Sec. II.F), with output map x~ = C h + D u, GELU and the residual
+ *     s^(l) = h^(l-1) for l >= 2 (Sec. II.F-G); the recurrence
+ *     h_t = a_t * h_{t-1} + b_t is evaluated as a chunked scan (Sec. II.A);
+ *   - the local energy of the Heisenberg model (Sec. III.C) or the
+ *     transverse-field Ising model (Sec. III.B) over every configuration
+ *     connected to a sample by an off-diagonal term (Sec. II.A, local-energy
+ *     paragraph);
+ *   - the parameter gradient d log psi / d theta per sample (O_k) or its
+ *     weighted sum, as used by the VMC energy-gradient estimator
+ *     (Sec. III.B, optimisation paragraph).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Pointers.  Every array argument may be a device pointer or a host pointer;
+ * the library asks CUDA which it is.  Device arrays are used in place and the
+ * call is asynchronous on the context's stream.  Host inputs are copied to
+ * the device and host outputs are copied back inside the call, which then
+ * synchronises the stream before returning.  The caller owns every array;
+ * the library never frees caller memory.  Scratch memory comes from the
+ * context's workspace, which grows on demand (cudaMalloc) and is released by
+ * psr_context_destroy.
+ *
+ * Spins.  uint8 [n][N] row-major, one byte per site with value 0 (down,
+ * sigma^z = -1) or 1 (up, sigma^z = +1), given in SEQUENCE order: lattice
+ * site (i, j) (column i, row j, 0-based) sits at position
+ *   pos(i, j) = j * Lx + (j even ? i : Lx - 1 - i)
+ * which is the zigzag path of Sec. II.F (predecessor (i - (-1)^j, j)).
+ * For a chain Ly = 1 and pos = i.
+ *
+ * Parameters theta.  float32, P = psr_param_count(n_layers, hidden) values,
+ * for each layer l = 0 .. n_layers-1 with d_in = 2 for l = 0 and hidden
+ * otherwise, row-major:
+ *   W_z[hidden][d_in], b_z[hidden], W_h[hidden][d_in], b_h[hidden],
+ *   C[hidden][hidden], D[hidden][d_in]
+ * followed by the readout W_o[2][hidden], b_o[2].  Layer 0 sees
+ * onehot(s_{t-1}) (the zero vector at t = 0); layer l >= 1 sees the output of
+ * layer l-1.  The conditional of site t is softmax(W_o x_t + b_o) over
+ * s_t in {0, 1}, and log psi = 1/2 sum_t log P(s_t | s_<t).  With n_layers = 3
+ * and hidden = H, P = 9 H^2 + 14 H + 2.
+ *
+ * u1_mask.  When set, once N/2 up (or N/2 down) spins precede site t the
+ * conditional forces the other value (probability one), so log psi is
+ * finite exactly on the zero-magnetisation sector.  Requires N even.
+ *
+ * Precision.  PSR_FP32: every projection in FP32 on CUDA cores (the plain
+ * path).  PSR_BF16: the dense projections of layers >= 1 and the output maps
+ * run on the tensor cores (tcgen05) with BF16 operands and FP32
+ * accumulation; the gates, scan carry, softmax, log-psi sums and every
+ * reduction stay in FP32 (hidden = 128 only).  psr_grad always computes in
+ * FP32.
+ *
+ * Errors.  Every call returns PSR_OK or an error code; nothing traps.
+ * Asynchronous device-side failures (a bounded wait that expired, an
+ * invalid spin value) are recorded in the context's status word and
+ * returned by the next call that synchronises (psr_context_sync or a call
+ * with host buffers).
+ */
+#ifndef PSR_H
+#define PSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PSR_OK = 0,
+    PSR_EINVAL = 1,      /* bad argument: null pointer, size, shape, Hamiltonian */
+    PSR_ENOMEM = 2,      /* device allocation failed */
+    PSR_ECUDA = 3,       /* a CUDA runtime call failed */
+    PSR_ETIMEOUT = 4,    /* a bounded device-side wait expired */
+    PSR_EDEVICE = 5,     /* a device-side check failed (e.g. spin byte not 0/1) */
+    PSR_EUNSUPPORTED = 6 /* valid request the library does not implement */
+};
+
+enum { PSR_FP32 = 0, PSR_BF16 = 1 };
+enum { PSR_HEISENBERG = 0, PSR_TFIM = 1 };
+
+typedef struct psr_context psr_context;
+
+/* Model description.  theta: P floats (host or device), caller-owned. */
+typedef struct {
+    int32_t n_layers;  /* >= 1, <= 8 */
+    int32_t hidden;    /* 32, 64 or 128 (PSR_BF16: 128) */
+    int32_t u1_mask;   /* 0 or 1 */
+    int32_t precision; /* PSR_FP32 or PSR_BF16 */
+    const float *theta;
+    psr_context *ctx;
+} psr_params;
+
+/* Lattice Hamiltonian.  N = Lx * Ly sites.
+ *   PSR_HEISENBERG: H = J sum_<pq> S_p . S_q, S = sigma / 2 (Sec. III.C).
+ *     Diagonal (J/4) sum sigma_p sigma_q; each antiparallel bond (p, q)
+ *     connects s to s with both spins exchanged, element J/2, times -1 when
+ *     marshall = 1 (the Marshall sign of Sec. III.C; bipartite lattices only).
+ *   PSR_TFIM: H = -J sum_<pq> sigma^z_p sigma^z_q - h sum_p sigma^x_p
+ *     (Sec. III.B); every site flip is connected with element -h.
+ * Bonds: nearest neighbours of the Lx x Ly square lattice (a chain when
+ * Ly = 1); with pbc = 1 each dimension of length >= 3 wraps around.
+ * Canonical bond order: lattice sites in row-major order (row j major,
+ * column i minor), for each the bond to (i+1, j) then to (i, j+1); each
+ * stored as (min pos, max pos). */
+typedef struct {
+    int32_t kind;
+    int32_t Lx, Ly;
+    int32_t pbc;
+    int32_t marshall;
+    double J;
+    double h;
+} psr_hamiltonian;
+
+/* Creates a context bound to a CUDA stream (a cudaStream_t passed as
+ * void*; NULL selects the legacy default stream) on the current device.
+ * Returns PSR_EINVAL for a null out pointer, PSR_ECUDA if the device cannot
+ * be queried. */
+int psr_context_create(psr_context **out, void *stream);
+
+/* Synchronises the context's stream, frees its workspace and the context. */
+int psr_context_destroy(psr_context *ctx);
+
+/* Synchronises the context's stream and returns (then clears) the first
+ * device-side error recorded since the last synchronising call. */
+int psr_context_sync(psr_context *ctx);
+
+/* Number of float parameters of the layout described above. */
+int psr_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
+
+/* log psi of n configurations of N = L sites (Sec. III.B: psi = prod_t
+ * sqrt(P(s_t | s_<t)), Sec. II.C recurrence, Sec. II.A scan).
+ * spins: uint8 [n][L]; out: float [n].  n >= 1, L >= 1.
+ * Configurations outside the support (u1_mask) give -inf. */
+int psr_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
+               float *out);
+
+/* Local energy of n samples (Sec. II.A, local-energy paragraph):
+ *   E_loc(s) = diag(s) + sum_{s'} H_{s s'} psi(s') / psi(s)
+ * summed over every connected configuration s' (ragged: Heisenberg has one
+ * per antiparallel bond, TFIM one per site).  Each psi(s')/psi(s) is
+ * exp(log psi(s') - log psi(s)); the forward of s' resumes from the scan
+ * chunk that contains the first changed site, reusing the sample's stored
+ * chunk carries (identical result, fewer site evaluations).
+ * samples: uint8 [n][Lx*Ly]; out: float [n] E_loc; stats: double [3]
+ * {mean, unbiased variance, standard error sqrt(var/n)} accumulated in FP64,
+ * or NULL.  PSR_EINVAL for marshall = 1 on a non-bipartite lattice or a
+ * periodic dimension of length < 3 with more than one site per row. */
+int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                     const psr_hamiltonian *ham, float *out, double *stats);
+
+/* Connected-configuration generator on its own (bit-exact, deterministic):
+ * offsets: int64 [n+1] (CSR over samples), entries: int32 [capacity][3]
+ * rows (sample, p, q) in sample-major then canonical bond order (TFIM: site
+ * order, q = -1), diag: float [n] diagonal energy, total: int64 on the HOST
+ * receiving the number of entries.  capacity must be at least n times the
+ * bond count (Heisenberg) or n * N (TFIM); PSR_EINVAL otherwise.
+ * This call synchronises the stream to report total. */
+int psr_connected(psr_context *ctx, const uint8_t *samples, int64_t n,
+                  const psr_hamiltonian *ham, int64_t *offsets, int32_t *entries,
+                  int64_t capacity, float *diag, int64_t *total);
+
+/* Gradient of log psi (Sec. III.B: stochastic energy-gradient estimates).
+ * dout == NULL: dparams is float [n][P] with row i = O_k(s_i) = d log psi(s_i)
+ *   / d theta (per-sample, e.g. for a covariance / SR solve).
+ * dout != NULL (float [n]): dparams is float [P] = sum_i dout_i O_k(s_i).
+ * The forward is recomputed chunk by chunk from stored chunk-boundary carries
+ * and the recurrence is differentiated by a reverse scan
+ * lambda_t = dL/dh_t + a_{t+1} lambda_{t+1}.  Computed in FP32. */
+int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
+             const float *dout, float *dparams);
+
+/* Static description of an error code. */
+const char *psr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSR_H */

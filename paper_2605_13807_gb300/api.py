@@ -1,0 +1,111 @@
+"""Tensor-level wrappers over the C ABI (allocation and marshalling only).
+
+    logpsi(theta, spins, ...)            -> float32 [n]
+    local_energy(theta, samples, ham)    -> (float32 [n] E_loc, float64 [3] stats)
+    connected(samples, ham)              -> (int64 [n+1], int32 [E, 3], float32 [n])
+    grad(theta, spins, dout=None)        -> float32 [n, P] (O_k) or [P]
+    LogPsi.apply(theta, spins, cfg)      -> differentiable log psi; backward = psr_grad
+
+Outputs live where the inputs live (a CUDA tensor in, CUDA tensors out).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import binding as B
+
+
+@dataclass(frozen=True)
+class ModelConfig:
+    n_layers: int = 3
+    hidden: int = 128
+    u1: bool = False
+    precision: str = "fp32"  # "fp32" or "bf16"
+
+
+def _device_of(*ts):
+    for t in ts:
+        if isinstance(t, torch.Tensor) and t.is_cuda:
+            return t.device
+    return torch.device("cpu")
+
+
+def _ctx():
+    return B.context()
+
+
+def param_count(n_layers: int = 3, hidden: int = 128) -> int:
+    return B.psr_param_count(n_layers, hidden)
+
+
+def logpsi(theta, spins, cfg: ModelConfig, out=None):
+    dev = _device_of(spins, theta)
+    if out is None:
+        out = torch.empty(spins.shape[0], dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    return B.psr_logpsi(p, spins, out)
+
+
+def local_energy(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, out=None, stats=None):
+    dev = _device_of(samples, theta)
+    if out is None:
+        out = torch.empty(samples.shape[0], dtype=torch.float32, device=dev)
+    if stats is None:
+        stats = torch.empty(3, dtype=torch.float64, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_local_energy(p, samples, ham, out, stats)
+    return out, stats
+
+
+def max_entries(ham: B.psr_hamiltonian, n: int) -> int:
+    N = ham.Lx * ham.Ly
+    if ham.kind == B.PSR_TFIM:
+        return n * N
+    wx = 1 if (ham.pbc and ham.Lx >= 3) else 0
+    wy = 1 if (ham.pbc and ham.Ly >= 3) else 0
+    return n * (ham.Ly * (ham.Lx - 1 + wx) + ham.Lx * (ham.Ly - 1 + wy))
+
+
+def connected(samples, ham: B.psr_hamiltonian):
+    n = samples.shape[0]
+    dev = _device_of(samples)
+    cap = max_entries(ham, n)
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    entries = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=dev)
+    diag = torch.empty(n, dtype=torch.float32, device=dev)
+    total = B.psr_connected(_ctx(), samples, ham, offsets, entries, diag)
+    return offsets, entries[:total], diag
+
+
+def grad(theta, spins, cfg: ModelConfig, dout=None, out=None):
+    dev = _device_of(spins, theta)
+    P = param_count(cfg.n_layers, cfg.hidden)
+    if out is None:
+        shape = (P,) if dout is not None else (spins.shape[0], P)
+        out = torch.empty(shape, dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    return B.psr_grad(p, spins, dout, out)
+
+
+def sync():
+    B.psr_context_sync(_ctx())
+
+
+class LogPsi(torch.autograd.Function):
+    """log psi(s; theta) with a backward that calls the reverse-scan adjoint
+    (psr_grad with dout = the incoming gradient)."""
+
+    @staticmethod
+    def forward(ctx, theta, spins, cfg: ModelConfig):
+        ctx.save_for_backward(theta, spins)
+        ctx.cfg = cfg
+        return logpsi(theta.detach().contiguous(), spins, cfg)
+
+    @staticmethod
+    def backward(ctx, g):
+        theta, spins = ctx.saved_tensors
+        dtheta = grad(theta.detach().contiguous(), spins, ctx.cfg,
+                      dout=g.detach().to(torch.float32).contiguous())
+        return dtheta, None, None

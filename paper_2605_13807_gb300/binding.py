@@ -1,0 +1,170 @@
+"""Thin ctypes binding of libpsr (argument marshalling only).
+
+Every function here forwards to the C entry point of the same name declared
+in include/psr.h; no computation happens in Python.  Arrays are torch tensors
+(device or host) or numpy arrays (host); their data pointers are passed as
+is, and the library itself stages host arrays.  If libpsr.so has not been
+built this module raises at import of the library, never falls back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpsr.so")
+
+PSR_OK, PSR_EINVAL, PSR_ENOMEM, PSR_ECUDA, PSR_ETIMEOUT, PSR_EDEVICE, PSR_EUNSUPPORTED = range(7)
+PSR_FP32, PSR_BF16 = 0, 1
+PSR_HEISENBERG, PSR_TFIM = 0, 1
+
+_PRECISION = {"fp32": PSR_FP32, "bf16": PSR_BF16, PSR_FP32: PSR_FP32, PSR_BF16: PSR_BF16}
+
+
+class PsrError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+
+
+class psr_params(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("hidden", C.c_int32), ("u1_mask", C.c_int32),
+                ("precision", C.c_int32), ("theta", C.c_void_p), ("ctx", C.c_void_p)]
+
+
+class psr_hamiltonian(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("Lx", C.c_int32), ("Ly", C.c_int32), ("pbc", C.c_int32),
+                ("marshall", C.c_int32), ("J", C.c_double), ("h", C.c_double)]
+
+
+EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "psr_param_count",
+            "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror")
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libpsr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+                L = C.CDLL(LIB_PATH)
+                vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+                L.psr_context_create.argtypes = [C.POINTER(vp), vp]
+                L.psr_context_destroy.argtypes = [vp]
+                L.psr_context_sync.argtypes = [vp]
+                L.psr_param_count.argtypes = [i32, i32, C.POINTER(i64)]
+                L.psr_logpsi.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp]
+                L.psr_local_energy.argtypes = [C.POINTER(psr_params), vp, i64,
+                                               C.POINTER(psr_hamiltonian), vp, vp]
+                L.psr_connected.argtypes = [vp, vp, i64, C.POINTER(psr_hamiltonian), vp, vp, i64, vp,
+                                            C.POINTER(i64)]
+                L.psr_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
+                L.psr_strerror.argtypes = [C.c_int]
+                L.psr_strerror.restype = C.c_char_p
+                for name in EXPORTED:
+                    if name != "psr_strerror":
+                        getattr(L, name).restype = C.c_int
+                _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().psr_strerror(int(code)).decode()
+
+
+def _check(code, where):
+    if code != PSR_OK:
+        raise PsrError(code, where)
+
+
+# ------------------------------------------------------------------ contexts
+
+_contexts = {}
+
+
+def context(stream=None):
+    """A psr_context bound to a CUDA stream (default: torch's current stream)."""
+    import torch
+    dev = torch.cuda.current_device()
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    handle = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream or 0)
+    key = (dev, handle)
+    ctx = _contexts.get(key)
+    if ctx is None:
+        out = C.c_void_p()
+        _check(lib().psr_context_create(C.byref(out), C.c_void_p(handle)), "psr_context_create")
+        ctx = out.value
+        _contexts[key] = ctx
+    return ctx
+
+
+def psr_context_sync(ctx=None):
+    _check(lib().psr_context_sync(C.c_void_p(ctx if ctx else context())), "psr_context_sync")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return C.c_void_p(a.ctypes.data)
+    assert a.is_contiguous()
+    return C.c_void_p(a.data_ptr())
+
+
+def make_params(theta, n_layers, hidden, u1=False, precision="fp32", ctx=None):
+    return psr_params(int(n_layers), int(hidden), int(bool(u1)), _PRECISION[precision],
+                      _ptr(theta), C.c_void_p(ctx if ctx else context()))
+
+
+def make_hamiltonian(kind, Lx, Ly=1, pbc=False, marshall=True, J=1.0, h=0.0):
+    k = {"heisenberg": PSR_HEISENBERG, "tfim": PSR_TFIM}.get(kind, kind)
+    return psr_hamiltonian(int(k), int(Lx), int(Ly), int(bool(pbc)), int(bool(marshall)),
+                           float(J), float(h))
+
+
+# ------------------------------------------------------------- entry points
+
+def psr_param_count(n_layers, hidden):
+    P = C.c_int64()
+    _check(lib().psr_param_count(int(n_layers), int(hidden), C.byref(P)), "psr_param_count")
+    return int(P.value)
+
+
+def psr_logpsi(params, spins, out):
+    n, L = spins.shape
+    _check(lib().psr_logpsi(C.byref(params), _ptr(spins), int(n), int(L), _ptr(out)), "psr_logpsi")
+    return out
+
+
+def psr_local_energy(params, samples, ham, out, stats=None):
+    n = samples.shape[0]
+    _check(lib().psr_local_energy(C.byref(params), _ptr(samples), int(n), C.byref(ham), _ptr(out),
+                                  _ptr(stats)), "psr_local_energy")
+    return out
+
+
+def psr_connected(ctx, samples, ham, offsets, entries, diag):
+    n = samples.shape[0]
+    total = C.c_int64()
+    _check(lib().psr_connected(C.c_void_p(ctx), _ptr(samples), int(n), C.byref(ham), _ptr(offsets),
+                               _ptr(entries), int(entries.shape[0]), _ptr(diag), C.byref(total)),
+           "psr_connected")
+    return int(total.value)
+
+
+def psr_grad(params, spins, dout, dparams):
+    n, L = spins.shape
+    _check(lib().psr_grad(C.byref(params), _ptr(spins), int(n), int(L), _ptr(dout), _ptr(dparams)),
+           "psr_grad")
+    return dparams

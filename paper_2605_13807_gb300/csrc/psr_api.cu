@@ -1,0 +1,542 @@
+// C ABI of libpsr: argument checks, workspace, host/device staging and the
+// launch sequence of each entry point.  All compute happens in the kernels
+// of psr_fwd_f32.cu, psr_fwd_bf16.cu, psr_ham.cu and psr_bwd.cu.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "psr_internal.cuh"
+
+struct psr_context {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 1;
+    void *ws = nullptr;
+    size_t ws_size = 0;
+    int *status = nullptr;  // device status word
+};
+
+namespace {
+
+using namespace psr;
+
+// Bump allocator over the workspace.  Each entry point runs its carving
+// sequence twice: once with a null base to size it, once for real.
+struct Carver {
+    char *base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T *get(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return PSR_OK;
+    if (e == cudaErrorMemoryAllocation) return PSR_ENOMEM;
+    return PSR_ECUDA;
+}
+
+#define PSR_TRY(expr)                          \
+    do {                                       \
+        int _rc = from_cuda(expr);             \
+        if (_rc != PSR_OK) return _rc;         \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ensure_ws(psr_context *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_size) return PSR_OK;
+    PSR_TRY(cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_size = 0;
+    size_t want = bytes + bytes / 8 + (1u << 20);
+    cudaError_t e = cudaMalloc(&ctx->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return PSR_ENOMEM;
+    }
+    ctx->ws_size = want;
+    return PSR_OK;
+}
+
+// Reads and clears the device status word (synchronises the stream).
+int take_status(psr_context *ctx) {
+    PSR_TRY(cudaStreamSynchronize(ctx->stream));
+    int st = 0;
+    PSR_TRY(cudaMemcpy(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) PSR_TRY(cudaMemset(ctx->status, 0, sizeof(int)));
+    return st;
+}
+
+int check_params(const psr_params *p, int64_t n, int32_t L) {
+    if (!p || !p->ctx || !p->theta) return PSR_EINVAL;
+    if (p->n_layers < 1 || p->n_layers > kMaxLayers) return PSR_EINVAL;
+    if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128) return PSR_EINVAL;
+    if (p->u1_mask != 0 && p->u1_mask != 1) return PSR_EINVAL;
+    if (p->precision != PSR_FP32 && p->precision != PSR_BF16) return PSR_EINVAL;
+    if (n < 1 || L < 1) return PSR_EINVAL;
+    if (n > (int64_t)1 << 31) return PSR_EINVAL;
+    if (p->u1_mask && (L % 2)) return PSR_EINVAL;
+    if (p->precision == PSR_BF16 &&
+        (p->hidden != 128 || p->n_layers != 3 || bf16_packed_bytes() == 0))
+        return PSR_EUNSUPPORTED;
+    return PSR_OK;
+}
+
+int check_ham(const psr_hamiltonian *h) {
+    if (!h) return PSR_EINVAL;
+    if (h->kind != PSR_HEISENBERG && h->kind != PSR_TFIM) return PSR_EINVAL;
+    if (h->Lx < 1 || h->Ly < 1 || (int64_t)h->Lx * h->Ly > (1 << 24)) return PSR_EINVAL;
+    if (h->pbc != 0 && h->pbc != 1) return PSR_EINVAL;
+    if (h->marshall != 0 && h->marshall != 1) return PSR_EINVAL;
+    if (h->kind == PSR_HEISENBERG && h->marshall) {
+        // bipartite unless a wrapped dimension has odd length
+        const bool wx = h->pbc && h->Lx >= 3, wy = h->pbc && h->Ly >= 3;
+        if ((wx && (h->Lx & 1)) || (wy && (h->Ly & 1))) return PSR_EINVAL;
+    }
+    return PSR_OK;
+}
+
+int64_t words_per_row(int N) { return (N + 63) / 64 + 1; }
+
+// Stages an input array: returns the device pointer to use (the caller's own
+// if it is device memory, else a workspace copy filled by an async H2D).
+template <class T>
+int stage_in(const T *src, T *dst_ws, size_t count, bool dev, cudaStream_t st, const T **use) {
+    if (dev) {
+        *use = src;
+        return PSR_OK;
+    }
+    PSR_TRY(cudaMemcpyAsync(dst_ws, src, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    *use = dst_ws;
+    return PSR_OK;
+}
+
+struct ModelDev {
+    const float *theta;
+    float *pk;
+    void *pkb;
+    ThetaLayout tl;
+    F32Layout fl;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *psr_strerror(int code) {
+    switch (code) {
+        case PSR_OK: return "ok";
+        case PSR_EINVAL: return "invalid argument";
+        case PSR_ENOMEM: return "device allocation failed";
+        case PSR_ECUDA: return "CUDA runtime error";
+        case PSR_ETIMEOUT: return "bounded device wait expired";
+        case PSR_EDEVICE: return "device-side check failed";
+        case PSR_EUNSUPPORTED: return "unsupported configuration";
+        default: return "unknown error";
+    }
+}
+
+int psr_param_count(int32_t n_layers, int32_t hidden, int64_t *P) {
+    if (!P || n_layers < 1 || n_layers > kMaxLayers || hidden < 1) return PSR_EINVAL;
+    *P = theta_layout(n_layers, hidden).total;
+    return PSR_OK;
+}
+
+int psr_context_create(psr_context **out, void *stream) {
+    if (!out) return PSR_EINVAL;
+    *out = nullptr;
+    psr_context *ctx = new (std::nothrow) psr_context();
+    if (!ctx) return PSR_ENOMEM;
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    int rc = from_cuda(cudaGetDevice(&ctx->device));
+    if (rc == PSR_OK)
+        rc = from_cuda(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (rc == PSR_OK) rc = from_cuda(cudaMalloc(&ctx->status, sizeof(int)));
+    if (rc == PSR_OK) rc = from_cuda(cudaMemset(ctx->status, 0, sizeof(int)));
+    if (rc != PSR_OK) {
+        if (ctx->status) cudaFree(ctx->status);
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return PSR_OK;
+}
+
+int psr_context_destroy(psr_context *ctx) {
+    if (!ctx) return PSR_EINVAL;
+    int rc = from_cuda(cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->status) cudaFree(ctx->status);
+    delete ctx;
+    return rc;
+}
+
+int psr_context_sync(psr_context *ctx) {
+    if (!ctx) return PSR_EINVAL;
+    return take_status(ctx);
+}
+
+int psr_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, float *out) {
+    int rc = check_params(params, n, L);
+    if (rc != PSR_OK) return rc;
+    if (!spins || !out) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden;
+    const bool bf16 = params->precision == PSR_BF16;
+    const bool d_theta = is_device_ptr(params->theta), d_spins = is_device_ptr(spins),
+               d_out = is_device_ptr(out);
+    const ThetaLayout tl = theta_layout(nL, H);
+    const F32Layout fl = f32_layout(nL, H);
+    const int W = (int)words_per_row(L);
+
+    float *theta_ws = nullptr, *pk = nullptr, *out_ws = nullptr;
+    uint8_t *spins_ws = nullptr;
+    void *pkb = nullptr;
+    uint64_t *bits = nullptr;
+    unsigned long long *counter = nullptr;
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : tl.total);
+        spins_ws = c.get<uint8_t>(d_spins ? 0 : (size_t)n * L);
+        out_ws = c.get<float>(d_out ? 0 : n);
+        pk = c.get<float>(fl.total);
+        pkb = c.get<char>(bf16 ? bf16_packed_bytes() : 0);
+        bits = c.get<uint64_t>((size_t)n * W);
+        counter = c.get<unsigned long long>(1);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, tl.total, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(spins, spins_ws, (size_t)n * L, d_spins, st, &sp)) != PSR_OK) return rc;
+    float *o = d_out ? out : out_ws;
+
+    PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+    if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
+    PSR_TRY(launch_bitpack(sp, n, L, W, bits, ctx->status, st));
+    PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    FwdJobs jb{};
+    jb.mode = 0;
+    jb.N = L;
+    jb.W = W;
+    jb.u1 = params->u1_mask;
+    jb.n_jobs = n;
+    jb.bits = bits;
+    jb.out = o;
+    jb.job_counter = counter;
+    jb.status = ctx->status;
+    if (bf16) PSR_TRY(launch_fwd_bf16(jb, pkb, pk, fl, ctx->num_sms, st));
+    else PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st));
+    if (!d_out) {
+        PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    if (!d_out || !d_spins || !d_theta) return take_status(ctx);
+    return PSR_OK;
+}
+
+// Shared body of psr_connected and the first half of psr_local_energy.
+namespace {
+struct ConnBufs {
+    int32_t *bonds;
+    int64_t *counts;
+    int64_t *offsets;
+    float *diag;
+    int32_t *entries;
+};
+
+int enqueue_connected(psr_context *ctx, const psr_hamiltonian *ham, const uint8_t *sp, int64_t n,
+                      const ConnBufs &b, HamDev &hd) {
+    cudaStream_t st = ctx->stream;
+    const int N = ham->Lx * ham->Ly;
+    hd.kind = ham->kind;
+    hd.N = N;
+    hd.nb = bond_count(ham->Lx, ham->Ly, ham->pbc);
+    hd.bonds = b.bonds;
+    hd.J = (float)ham->J;
+    hd.h = (float)ham->h;
+    hd.coeff = ham->kind == PSR_HEISENBERG ? (float)((ham->marshall ? -0.5 : 0.5) * ham->J)
+                                           : (float)(-ham->h);
+    if (hd.nb > 0) PSR_TRY(launch_bonds(ham->Lx, ham->Ly, ham->pbc, b.bonds, st));
+    PSR_TRY(launch_count_connected(hd, sp, n, b.counts, b.diag, st));
+    PSR_TRY(launch_exclusive_scan(b.counts, n, b.offsets, st));
+    PSR_TRY(launch_fill_connected(hd, sp, n, b.offsets, b.entries, st));
+    return PSR_OK;
+}
+
+int64_t max_entries_per_sample(const psr_hamiltonian *ham) {
+    const int N = ham->Lx * ham->Ly;
+    return ham->kind == PSR_HEISENBERG ? bond_count(ham->Lx, ham->Ly, ham->pbc) : N;
+}
+}  // namespace
+
+int psr_connected(psr_context *ctx, const uint8_t *samples, int64_t n, const psr_hamiltonian *ham,
+                  int64_t *offsets, int32_t *entries, int64_t capacity, float *diag,
+                  int64_t *total) {
+    if (!ctx || !samples || !offsets || !entries || !diag || !total || n < 1) return PSR_EINVAL;
+    int rc = check_ham(ham);
+    if (rc != PSR_OK) return rc;
+    const int N = ham->Lx * ham->Ly;
+    const int64_t cap = n * max_entries_per_sample(ham);
+    if (capacity < cap) return PSR_EINVAL;
+    const bool d_s = is_device_ptr(samples), d_o = is_device_ptr(offsets),
+               d_e = is_device_ptr(entries), d_d = is_device_ptr(diag);
+    const int nb = bond_count(ham->Lx, ham->Ly, ham->pbc);
+    uint8_t *s_ws = nullptr;
+    ConnBufs b{};
+    int64_t *off_ws = nullptr;
+    int32_t *ent_ws = nullptr;
+    float *diag_ws = nullptr;
+    auto carve = [&](Carver &c) {
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        b.bonds = c.get<int32_t>(2 * (size_t)nb + 2);
+        b.counts = c.get<int64_t>(n);
+        off_ws = c.get<int64_t>(d_o ? 0 : n + 1);
+        ent_ws = c.get<int32_t>(d_e ? 0 : 3 * (size_t)cap);
+        diag_ws = c.get<float>(d_d ? 0 : n);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(samples, s_ws, (size_t)n * N, d_s, st, &sp)) != PSR_OK) return rc;
+    b.offsets = d_o ? offsets : off_ws;
+    b.entries = d_e ? entries : ent_ws;
+    b.diag = d_d ? diag : diag_ws;
+    HamDev hd{};
+    if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
+    int64_t tot = 0;
+    PSR_TRY(cudaMemcpyAsync(&tot, b.offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PSR_TRY(cudaStreamSynchronize(st));
+    *total = tot;
+    if (!d_o) PSR_TRY(cudaMemcpyAsync(offsets, off_ws, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (!d_e && tot > 0)
+        PSR_TRY(cudaMemcpyAsync(entries, ent_ws, 3 * (size_t)tot * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (!d_d) PSR_TRY(cudaMemcpyAsync(diag, diag_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    return take_status(ctx);
+}
+
+int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                     const psr_hamiltonian *ham, float *out, double *stats) {
+    int rc = check_ham(ham);
+    if (rc != PSR_OK) return rc;
+    const int N = ham->Lx * ham->Ly;
+    if ((rc = check_params(params, n, N)) != PSR_OK) return rc;
+    if (!samples || !out) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden;
+    const bool bf16 = params->precision == PSR_BF16;
+    const int CH = bf16 ? kChunkBF16 : kChunkF32;
+    const int nch = (N + CH - 1) / CH;
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
+               d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
+    const ThetaLayout tl = theta_layout(nL, H);
+    const F32Layout fl = f32_layout(nL, H);
+    const int W = (int)words_per_row(N);
+    const int nb = bond_count(ham->Lx, ham->Ly, ham->pbc);
+    const int64_t cap = n * max_entries_per_sample(ham);
+
+    float *theta_ws = nullptr, *out_ws = nullptr, *pk = nullptr, *lpsi = nullptr, *logp = nullptr,
+          *carries = nullptr, *delta = nullptr;
+    double *stats_ws = nullptr;
+    uint8_t *s_ws = nullptr;
+    void *pkb = nullptr;
+    uint64_t *bits = nullptr;
+    unsigned long long *counters = nullptr;
+    ConnBufs b{};
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : tl.total);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        out_ws = c.get<float>(d_out ? 0 : n);
+        stats_ws = c.get<double>(d_stats ? 0 : 3);
+        pk = c.get<float>(fl.total);
+        pkb = c.get<char>(bf16 ? bf16_packed_bytes() : 0);
+        bits = c.get<uint64_t>((size_t)n * W);
+        b.bonds = c.get<int32_t>(2 * (size_t)nb + 2);
+        b.counts = c.get<int64_t>(n);
+        b.offsets = c.get<int64_t>(n + 1);
+        b.diag = c.get<float>(n);
+        b.entries = c.get<int32_t>(3 * (size_t)cap);
+        lpsi = c.get<float>(n);
+        logp = c.get<float>((size_t)n * N);
+        carries = c.get<float>((size_t)n * nch * nL * H);
+        delta = c.get<float>(cap);
+        counters = c.get<unsigned long long>(2);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, tl.total, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(samples, s_ws, (size_t)n * N, d_s, st, &sp)) != PSR_OK) return rc;
+    float *o = d_out ? out : out_ws;
+    double *so = stats ? (d_stats ? stats : stats_ws) : nullptr;
+
+    PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+    if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
+    PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));
+    HamDev hd{};
+    if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
+    PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
+
+    FwdJobs js{};
+    js.mode = 0;
+    js.N = N;
+    js.W = W;
+    js.u1 = params->u1_mask;
+    js.n_jobs = n;
+    js.bits = bits;
+    js.out = lpsi;
+    js.logp_out = logp;
+    js.carries_out = carries;
+    js.job_counter = counters;
+    js.status = ctx->status;
+    FwdJobs jc = js;
+    jc.mode = 1;
+    jc.n_jobs = cap;
+    jc.n_jobs_dev = b.offsets + n;
+    jc.entries = b.entries;
+    jc.carries_in = carries;
+    jc.logp_ref = logp;
+    jc.out = delta;
+    jc.logp_out = nullptr;
+    jc.carries_out = nullptr;
+    jc.job_counter = counters + 1;
+    if (bf16) {
+        PSR_TRY(launch_fwd_bf16(js, pkb, pk, fl, ctx->num_sms, st));
+        if (cap > 0) PSR_TRY(launch_fwd_bf16(jc, pkb, pk, fl, ctx->num_sms, st));
+    } else {
+        PSR_TRY(launch_fwd_f32(js, pk, fl, ctx->num_sms, st));
+        if (cap > 0) PSR_TRY(launch_fwd_f32(jc, pk, fl, ctx->num_sms, st));
+    }
+    PSR_TRY(launch_eloc_gather(b.offsets, delta, b.diag, hd.coeff, n, o, st));
+    if (so) PSR_TRY(launch_stats(o, n, so, st));
+    if (!d_out) PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (stats && !d_stats)
+        PSR_TRY(cudaMemcpyAsync(stats, stats_ws, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!d_out || !d_s || !d_theta || !d_stats) return take_status(ctx);
+    return PSR_OK;
+}
+
+int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
+             const float *dout, float *dparams) {
+    int rc = check_params(params, n, L);
+    if (rc != PSR_OK && rc != PSR_EUNSUPPORTED) return rc;
+    if (!spins || !dparams) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden;
+    const ThetaLayout tl = theta_layout(nL, H);
+    const F32Layout fl = f32_layout(nL, H);
+    const int64_t P = tl.total;
+    const int W = (int)words_per_row(L);
+    const int nch = (L + kChunkF32 - 1) / kChunkF32;
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(spins),
+               d_dout = dout ? is_device_ptr(dout) : true, d_g = is_device_ptr(dparams);
+    int per_sm = 1;
+    {
+        int occ = 0;
+        // backward CTA: H threads and bwd_smem_bytes(H) of shared memory
+        int dev_smem = 0;
+        cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+        occ = (int)(dev_smem / (bwd_smem_bytes(H) + 1024));
+        per_sm = occ < 1 ? 1 : (occ > 4 ? 4 : occ);
+    }
+    int64_t grid64 = (int64_t)ctx->num_sms * per_sm;
+    if (grid64 > n) grid64 = n;
+    const int grid = (int)grid64;
+    const size_t grad_rows = dout ? (size_t)grid : (size_t)n;
+
+    float *theta_ws = nullptr, *dout_ws = nullptr, *g_ws = nullptr, *pk = nullptr, *carries = nullptr,
+          *lpsi = nullptr, *tape = nullptr, *partial = nullptr;
+    uint8_t *s_ws = nullptr;
+    uint64_t *bits = nullptr;
+    unsigned long long *counter = nullptr;
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * L);
+        dout_ws = c.get<float>(d_dout ? 0 : n);
+        g_ws = c.get<float>(d_g ? 0 : (dout ? P : (size_t)n * P));
+        pk = c.get<float>(fl.total);
+        bits = c.get<uint64_t>((size_t)n * W);
+        carries = c.get<float>((size_t)n * nch * nL * H);
+        lpsi = c.get<float>(n);
+        tape = c.get<float>((size_t)grid * bwd_tape_floats_per_cta(nL, H));
+        partial = c.get<float>(dout ? grad_rows * P : 0);
+        counter = c.get<unsigned long long>(1);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr;
+    const uint8_t *sp = nullptr;
+    const float *dv = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(spins, s_ws, (size_t)n * L, d_s, st, &sp)) != PSR_OK) return rc;
+    if (dout && (rc = stage_in(dout, dout_ws, n, d_dout, st, &dv)) != PSR_OK) return rc;
+    float *g = d_g ? dparams : g_ws;
+
+    PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+    PSR_TRY(launch_bitpack(sp, n, L, W, bits, ctx->status, st));
+    PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    FwdJobs jb{};
+    jb.mode = 0;
+    jb.N = L;
+    jb.W = W;
+    jb.u1 = params->u1_mask;
+    jb.n_jobs = n;
+    jb.bits = bits;
+    jb.out = lpsi;
+    jb.carries_out = carries;
+    jb.job_counter = counter;
+    jb.status = ctx->status;
+    PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st));
+    float *rows = dout ? partial : g;
+    PSR_TRY(cudaMemsetAsync(rows, 0, grad_rows * P * sizeof(float), st));
+    PSR_TRY(launch_bwd_f32(bits, n, L, W, params->u1_mask, theta, tl, pk, fl, carries, dv, rows, grid,
+                           tape, ctx->status, st));
+    if (dout) PSR_TRY(launch_reduce_rows(partial, grid, P, g, st));
+    if (!d_g)
+        PSR_TRY(cudaMemcpyAsync(dparams, g_ws, (dout ? P : (size_t)n * P) * sizeof(float),
+                                cudaMemcpyDeviceToHost, st));
+    if (!d_g || !d_s || !d_theta || !d_dout) return take_status(ctx);
+    return PSR_OK;
+}
+
+}  // extern "C"

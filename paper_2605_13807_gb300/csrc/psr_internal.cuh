@@ -1,0 +1,120 @@
+// Internal declarations of libpsr (GPU side).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/psr.h"
+
+namespace psr {
+
+constexpr int kMaxLayers = 8;
+constexpr int kChunkF32 = 32;   // scan chunk of the FP32 SIMT path (sites)
+constexpr int kChunkBF16 = 64;  // scan chunk of the tcgen05 path (sites = MMA N)
+
+// Device status word values (first error wins).
+constexpr int kStatusOk = 0;
+
+// Offsets (in elements) of each tensor inside the flat theta vector.
+struct ThetaLayout {
+    int nL, H;
+    int64_t Wz[kMaxLayers], bz[kMaxLayers], Wh[kMaxLayers], bh[kMaxLayers];
+    int64_t C[kMaxLayers], D[kMaxLayers];
+    int64_t Wo, bo;
+    int64_t total;
+};
+ThetaLayout theta_layout(int nL, int H);
+
+// Packed FP32 weights used by the SIMT kernels (offsets in floats).
+//   *T tensors are transposed: WzT[k][j] = W_z[j][k] so that thread j reads
+//   consecutive addresses for a fixed k.
+//   Layer 0 is folded into lookup tables over the input code
+//   (0: t = 0, 1: s_{t-1} = 0, 2: s_{t-1} = 1):
+//     A0[code][j] = sigmoid(W_z u + b_z), B0 = (1 - A0)(W_h u + b_h), DU0 = D u,
+//     CD0 = W_h u + b_h (the candidate, used by the backward).
+//   Readout uses the logit difference wd = W_o[1] - W_o[0], bd = b_o[1] - b_o[0].
+struct F32Layout {
+    int nL, H;
+    int64_t WzT[kMaxLayers], WhT[kMaxLayers], CT[kMaxLayers], DT[kMaxLayers];
+    int64_t bz[kMaxLayers], bh[kMaxLayers];
+    int64_t A0, B0, DU0, CD0;
+    int64_t wd, bd;
+    int64_t total;
+};
+F32Layout f32_layout(int nL, int H);
+
+// One batch of sequence evaluations ("jobs") for the forward kernels.
+//   mode 0: job i evaluates sample i from site 0 (full forward).
+//   mode 1: job e evaluates the connected configuration of entries[e] =
+//           (sample, p, q): the sample with sites p and q (q may be -1)
+//           flipped, resuming from the chunk containing p with the stored
+//           carries; the result is 1/2 sum_{t >= chunk start} (log P'_t -
+//           log P_t(sample)) = log psi(s') - log psi(s).
+struct FwdJobs {
+    int mode;
+    int N;                       // sites
+    int W;                       // 64-bit words per bit-packed row (>= ceil(N/64))
+    int u1;                      // u1 masking
+    int64_t n_jobs;              // number of jobs (mode 0) or capacity (mode 1)
+    const int64_t *n_jobs_dev;   // mode 1: device count of valid jobs
+    const uint64_t *bits;        // [n_samples][W] bit-packed spins
+    const int32_t *entries;      // mode 1: [E][3]
+    const float *carries_in;     // mode 1: [n][nch][nL][H]
+    const float *logp_ref;       // mode 1: [n][N]
+    float *out;                  // mode 0: [n] log psi; mode 1: [E] delta
+    float *logp_out;             // mode 0, optional: [n][N]
+    float *carries_out;          // mode 0, optional: [n][nch][nL][H]
+    unsigned long long *job_counter;  // zeroed before launch
+    int *status;                 // device status word
+};
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `stream` and returns a cudaError_t.
+
+cudaError_t launch_pack_theta_f32(const float *theta, const ThetaLayout &tl, const F32Layout &fl,
+                                  float *packed, cudaStream_t stream);
+cudaError_t launch_bitpack(const uint8_t *spins, int64_t n, int N, int W, uint64_t *bits,
+                           int *status, cudaStream_t stream);
+cudaError_t launch_fwd_f32(const FwdJobs &jobs, const float *packed, const F32Layout &fl,
+                           int num_sms, cudaStream_t stream);
+
+// tcgen05 path (hidden = 128, 3 layers).
+size_t bf16_packed_bytes();
+cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, void *packed,
+                                   cudaStream_t stream);
+cudaError_t launch_fwd_bf16(const FwdJobs &jobs, const void *packed_bf16, const float *packed_f32,
+                            const F32Layout &fl, int num_sms, cudaStream_t stream);
+
+// Hamiltonian side.
+struct HamDev {
+    int kind;
+    int N;
+    int nb;
+    const int32_t *bonds;  // [nb][2]
+    float J, h;
+    float coeff;           // off-diagonal element per entry
+};
+cudaError_t launch_bonds(int Lx, int Ly, int pbc, int32_t *bonds, cudaStream_t stream);
+int bond_count(int Lx, int Ly, int pbc);
+cudaError_t launch_count_connected(const HamDev &hd, const uint8_t *spins, int64_t n,
+                                   int64_t *counts, float *diag, cudaStream_t stream);
+cudaError_t launch_exclusive_scan(const int64_t *counts, int64_t n, int64_t *offsets,
+                                  cudaStream_t stream);
+cudaError_t launch_fill_connected(const HamDev &hd, const uint8_t *spins, int64_t n,
+                                  const int64_t *offsets, int32_t *entries, cudaStream_t stream);
+cudaError_t launch_eloc_gather(const int64_t *offsets, const float *delta, const float *diag,
+                               float coeff, int64_t n, float *eloc, cudaStream_t stream);
+cudaError_t launch_stats(const float *eloc, int64_t n, double *stats, cudaStream_t stream);
+
+// Backward (FP32).
+size_t bwd_tape_floats_per_cta(int nL, int H);
+cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1,
+                           const float *theta, const ThetaLayout &tl, const float *packed,
+                           const F32Layout &fl, const float *carries, const float *dout,
+                           float *grad_rows, int grid, float *tape, int *status,
+                           cudaStream_t stream);
+size_t bwd_smem_bytes(int H);
+cudaError_t launch_reduce_rows(const float *partial, int rows, int64_t P, float *out,
+                               cudaStream_t stream);
+
+}  // namespace psr

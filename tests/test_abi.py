@@ -1,0 +1,70 @@
+"""The C-ABI library loads and exports every symbol declared in include/psr.h
+(no compute calls: these run without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(psr_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpsr():
+    from paper_2605_13807_gb300 import binding
+    if not os.path.exists(binding.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return binding.lib()
+
+
+def test_every_declared_symbol_is_exported(libpsr):
+    declared = _declared()
+    assert "psr_logpsi" in declared and "psr_local_energy" in declared and "psr_grad" in declared
+    for name in declared:
+        assert hasattr(libpsr, name), name
+
+
+def test_param_count_host_only(libpsr):
+    from paper_2605_13807_gb300 import binding, inputs
+    for H in (32, 64, 128):
+        assert binding.psr_param_count(3, H) == 9 * H * H + 14 * H + 2 == inputs.param_count(3, H)
+    P = C.c_int64()
+    assert libpsr.psr_param_count(0, 32, C.byref(P)) == binding.PSR_EINVAL
+    assert libpsr.psr_param_count(3, 32, None) == binding.PSR_EINVAL
+
+
+def test_null_arguments_are_rejected_without_touching_the_device(libpsr):
+    from paper_2605_13807_gb300 import binding
+    assert libpsr.psr_logpsi(None, None, 1, 1, None) == binding.PSR_EINVAL
+    assert libpsr.psr_local_energy(None, None, 1, None, None, None) == binding.PSR_EINVAL
+    assert libpsr.psr_grad(None, None, 1, 1, None, None) == binding.PSR_EINVAL
+    assert libpsr.psr_connected(None, None, 1, None, None, None, 0, None, None) == binding.PSR_EINVAL
+    assert libpsr.psr_context_sync(None) == binding.PSR_EINVAL
+    assert libpsr.psr_context_destroy(None) == binding.PSR_EINVAL
+    assert binding.strerror(binding.PSR_ETIMEOUT) == "bounded device wait expired"
+
+
+def test_library_has_no_oracle_dependency():
+    """The product path must not link or import the oracle."""
+    from paper_2605_13807_gb300 import binding
+    pkg = os.path.join(ROOT, "paper_2605_13807_gb300")
+    for mod in os.listdir(pkg):
+        if mod.endswith(".py"):
+            src = open(os.path.join(pkg, mod)).read()
+            assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), mod
+            assert "liboracle" not in src, mod
+    csrc = os.path.join(ROOT, "paper_2605_13807_gb300", "csrc")
+    for f in os.listdir(csrc):
+        assert "psr_oracle" not in open(os.path.join(csrc, f)).read()
+    assert binding.LIB_PATH.endswith("libpsr.so")
