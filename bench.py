@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Throughput of the PSR-NQS hot path on GB300: log psi forward + reverse-scan
+backward (per-sample O_k) + local energy over every bond-flip-connected
+configuration, 2D Heisenberg 52x52 OBC, hidden 128, 3 layers, 4096 samples,
+BF16 projections with FP32 scan.
+
+One step = psr_logpsi(samples) + psr_grad(samples, O_k per sample)
+         + psr_local_energy(samples) through the C ABI.
+Unit = one (configuration, site) pair of a forward pass, counting the samples
+and every connected configuration with all N sites ("logical"); the sites the
+library actually evaluates (connected forwards resume at the chunk holding
+the first flipped site) are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own 4096 samples on its own GPU (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "configs·sites/s for log psi fwd+bwd+E_loc at 52x52, BF16 vs FP32; % HBM roofline"
+UNIT = "configs·sites/s"
+N_LAYERS, HIDDEN = 3, 128
+MMA_FLOPS_PER_SITE = 2 * HIDDEN * HIDDEN * 9  # nine HxH products per site (BF16 path)
+CHUNK_BF16 = 64
+
+WORKLOADS = {
+    # name: (Lx, Ly, samples)
+    "heisenberg_52x52": (52, 52, 4096),
+    "heisenberg_52x52_small": (52, 52, 64),     # profiling-sized case of the same kernel
+    "heisenberg_10x10": (10, 10, 16384),
+}
+
+# kernels launched per call of each entry point (BF16 precision)
+LAUNCHES = {"logpsi": 4, "grad": 4, "local_energy": 11}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="heisenberg_52x52", choices=sorted(WORKLOADS))
+    ap.add_argument("--fp32-samples", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"psr_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = max((num(r[2]) for r in rows if num(r[2]) is not None), default=None)
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [s for s, p in zip(sm, power) if p is not None and p > 0.3 * max(power)] or sm
+        loaded.sort()
+        return {"sm_mhz": loaded[len(loaded) // 2] if loaded else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_hash():
+    src = os.path.join(ROOT, "paper_2605_13807_gb300", "csrc", "psr_fwd_bf16.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic_per_unit():
+    """DRAM bytes per evaluated config-site of the connected-configuration
+    forward, from the committed ncu summary, if it matches the current kernel."""
+    path = os.path.join(ROOT, "profiles", "fwd_bf16_connected_52x52.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel source sha256/16") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram bytes per evaluated config-site"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------- reference arm
+
+def oracle_rate(Lx, Ly, seconds, threads=None):
+    """The FP64 oracle (sequential recurrence) timed on the host cores: log psi
+    of connected configurations of one sample, the dominant work of E_loc.
+    Returns (config-sites/s, cores, sample description)."""
+    import numpy as np
+
+    from oracle import oracle as orc
+    from paper_2605_13807_gb300 import inputs
+
+    cores = threads or (os.cpu_count() or 1)
+    N = Lx * Ly
+    theta = inputs.glorot_params(N_LAYERS, HIDDEN, seed=0)
+    s = inputs.neel_like_spins(1000, 1, Lx, Ly)
+    offs, ent, _ = orc.connected(orc.HEISENBERG, Lx, Ly, False, s)
+    sp = np.repeat(s, len(ent), axis=0)
+    r = np.arange(len(ent))
+    sp[r, ent[:, 1]] ^= 1
+    sp[r, ent[:, 2]] ^= 1
+    t0 = time.perf_counter()
+    orc.logpsi(theta, N_LAYERS, HIDDEN, sp[:1], u1=True, threads=1)
+    t1 = time.perf_counter() - t0
+    per_core = max(1, int(round(seconds / max(t1, 1e-6))))
+    k = min(len(sp), per_core * cores)
+    t0 = time.perf_counter()
+    orc.logpsi(theta, N_LAYERS, HIDDEN, sp[:k], u1=True, threads=cores)
+    dt = time.perf_counter() - t0
+    desc = (f"FP64 oracle log psi of {k} connected configurations of one {Lx}x{Ly} sample "
+            f"(full sequential forward, {N} sites each), {cores} threads, {dt:.1f} s")
+    return k * N / dt, cores, desc
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    Lx, Ly, n = WORKLOADS[args.workload]
+    per_step = max(1.0, args.cpu_seconds / 3)
+    for _ in range(args.warmup):
+        oracle_rate(Lx, Ly, per_step / 4)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, desc = oracle_rate(Lx, Ly, per_step)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = sum(vals) / len(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"heisenberg_{Lx}x{Ly}_obc", "samples": n, "hidden": HIDDEN,
+                   "layers": N_LAYERS, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_mine(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_13807_gb300 import api, binding as B, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    Lx, Ly, n = WORKLOADS[args.workload]
+    N = Lx * Ly
+    P = api.param_count(N_LAYERS, HIDDEN)
+    ham = B.make_hamiltonian("heisenberg", Lx, Ly, False, True, 1.0, 0.0)
+    cfg = api.ModelConfig(N_LAYERS, HIDDEN, True, "bf16")
+    theta_np = inputs.glorot_params(N_LAYERS, HIDDEN, seed=0)
+    spins_np = inputs.neel_like_spins(1000 + rank, n, Lx, Ly)
+    theta = torch.from_numpy(theta_np).to(dev)
+    spins = torch.from_numpy(spins_np).to(dev)
+    lp = torch.empty(n, dtype=torch.float32, device=dev)
+    el = torch.empty(n, dtype=torch.float32, device=dev)
+    st = torch.empty(3, dtype=torch.float64, device=dev)
+    ok = torch.empty((n, P), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    # work accounting (untimed): connected set of these samples
+    offs, ent, _ = api.connected(spins, ham)
+    E = int(ent.shape[0])
+    p = ent[:, 1].to(torch.int64)
+    evaluated_conn = int((N - (p // CHUNK_BF16) * CHUNK_BF16).sum().item())
+    logical = n * N + E * N
+    evaluated = n * N + evaluated_conn
+    del offs, ent, p
+
+    ctx = B.context()
+    B.psr_context_set_profiling(ctx, True)
+
+    def step():
+        api.logpsi(theta, spins, cfg, out=lp)
+        api.grad(theta, spins, cfg, out=ok)
+        api.local_energy(theta, spins, cfg, ham, out=el, stats=st)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    api.sync()
+
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = Clocks(gpu_id)
+    conn_ms, samp_ms = [], []
+    total_ms = 0.0
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        stages = B.psr_context_stage_ms(ctx)
+        conn_ms.append(stages["fwd_connected"])
+        samp_ms.append(stages["fwd_samples"])
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    api.sync()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * logical / (ms_per_step / 1e3)
+
+    # roofline of the dominant kernel: the connected-configuration forward
+    peaks, peak_src = measured_peaks()
+    conn_avg = sum(conn_ms) / len(conn_ms)
+    flops = evaluated_conn * MMA_FLOPS_PER_SITE
+    achieved = flops / (conn_avg / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    tpu = profiled_traffic_per_unit()
+    roofline = {"kernel": "fwd_bf16_kernel (connected configurations)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                "traffic": (tpu * evaluated_conn if tpu is not None else None),
+                "algorithmic_flops_per_launch": flops, "launch_ms": conn_avg,
+                "units_per_launch": evaluated_conn,
+                "flops_per_unit": MMA_FLOPS_PER_SITE}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded Neel-like S^z=0 configurations, Glorot weights seed 0)",
+        "config": {"workload": f"heisenberg_{Lx}x{Ly}_obc_{n}_samples", "lattice": f"{Lx}x{Ly} OBC",
+                   "samples_per_gpu": n, "hidden": HIDDEN, "layers": N_LAYERS,
+                   "precision": "BF16 tcgen05 projections, FP32 scan/softmax, FP32 backward",
+                   "connected_per_step": E, "logical_units_per_step": logical,
+                   "evaluated_units_per_step": evaluated,
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"dp{world} (independent samples per GPU)"},
+        "evaluated_value": world * evaluated / (ms_per_step / 1e3),
+        "roofline": roofline,
+        "gpu_launches": args.steps * sum(LAUNCHES.values()),
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+        "stages_ms_last_local_energy": B.psr_context_stage_ms(ctx),
+    }
+
+    # plain FP32 path on a bounded subset of the same samples
+    if not args.no_fp32 and rank == 0:
+        m = min(args.fp32_samples, n)
+        cfg32 = api.ModelConfig(N_LAYERS, HIDDEN, True, "fp32")
+        sub = spins[:m].contiguous()
+        o2, e2 = api.connected(sub, ham)[:2]
+        E2 = int(e2.shape[0])
+        ok32 = torch.empty((m, P), dtype=torch.float32, device=dev)
+
+        def step32():
+            api.logpsi(theta, sub, cfg32, out=lp[:m])
+            api.grad(theta, sub, cfg32, out=ok32)
+            api.local_energy(theta, sub, cfg32, ham, out=el[:m], stats=st)
+
+        step32()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        step32()
+        a1.record()
+        a1.synchronize()
+        ms32 = a0.elapsed_time(a1)
+        line["fp32_path"] = {"value": (m * N + E2 * N) / (ms32 / 1e3), "unit": UNIT,
+                             "samples": m, "ms": ms32,
+                             "note": "plain FP32 SIMT path, same workload on a sample subset"}
+        del ok32
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        sp_h = torch.from_numpy(spins_np).pin_memory()
+        th_h = torch.from_numpy(theta_np).pin_memory()
+        lp_h = torch.empty(n, dtype=torch.float32).pin_memory()
+        el_h = torch.empty(n, dtype=torch.float32).pin_memory()
+        st_h = torch.empty(3, dtype=torch.float64).pin_memory()
+        ok_h = torch.empty((n, P), dtype=torch.float32).pin_memory()
+        del ok
+        torch.cuda.empty_cache()
+
+        def step_host():
+            api.logpsi(th_h, sp_h, cfg, out=lp_h)
+            api.grad(th_h, sp_h, cfg, out=ok_h)
+            api.local_energy(th_h, sp_h, cfg, ham, out=el_h, stats=st_h)
+
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_host()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = 3 * (n * N + P * 4)
+        d2h = n * 4 + n * P * 4 + n * 4 + 3 * 8
+        line["e2e"] = {"value": world * logical / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
+
+    if not args.no_cpu and world == 1 and rank == 0:
+        v, cores, desc = oracle_rate(Lx, Ly, args.cpu_seconds / 1.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -150,8 +150,8 @@ int psr_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_
  * chunk carries (identical result, fewer site evaluations).
  * samples: uint8 [n][Lx*Ly]; out: float [n] E_loc; stats: double [3]
  * {mean, unbiased variance, standard error sqrt(var/n)} accumulated in FP64,
- * or NULL.  PSR_EINVAL for marshall = 1 on a non-bipartite lattice or a
- * periodic dimension of length < 3 with more than one site per row. */
+ * or NULL.  PSR_EINVAL for marshall = 1 on a non-bipartite lattice (a
+ * wrapped dimension of odd length). */
 int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
                      const psr_hamiltonian *ham, float *out, double *stats);
 
@@ -175,6 +175,27 @@ int psr_connected(psr_context *ctx, const uint8_t *samples, int64_t n,
  * lambda_t = dL/dh_t + a_{t+1} lambda_{t+1}.  Computed in FP32. */
 int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
              const float *dout, float *dparams);
+
+/* Stages of the launch sequence, for per-stage device timing. */
+enum {
+    PSR_STAGE_PACK = 0,          /* parameter packing and spin bit-packing */
+    PSR_STAGE_GENERATOR = 1,     /* bond list, count, scan, emit (connected set) */
+    PSR_STAGE_FWD_SAMPLES = 2,   /* forward over the samples */
+    PSR_STAGE_FWD_CONNECTED = 3, /* forward over the connected configurations */
+    PSR_STAGE_GATHER = 4,        /* E_loc gather and FP64 statistics */
+    PSR_STAGE_BWD = 5,           /* reverse-scan gradient and its reduction */
+    PSR_STAGE_COUNT = 6
+};
+
+/* Enables (1) or disables (0) per-stage CUDA-event timing on the context's
+ * stream.  When enabled every call records an event pair around each stage;
+ * the cost is a few event records per call. */
+int psr_context_set_profiling(psr_context *ctx, int enable);
+
+/* Device time in milliseconds of one stage of the most recent call on this
+ * context (0 if the stage did not run).  Synchronises on the stage's end
+ * event.  PSR_EINVAL if profiling is off or the stage is out of range. */
+int psr_context_stage_ms(psr_context *ctx, int stage, float *ms);
 
 /* Static description of an error code. */
 const char *psr_strerror(int code);

@@ -41,7 +41,9 @@ class psr_hamiltonian(C.Structure):
 
 
 EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "psr_param_count",
-            "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror")
+            "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror",
+            "psr_context_set_profiling", "psr_context_stage_ms")
+STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd")
 
 _lib = None
 _lock = threading.Lock()
@@ -68,6 +70,8 @@ def lib():
                 L.psr_connected.argtypes = [vp, vp, i64, C.POINTER(psr_hamiltonian), vp, vp, i64, vp,
                                             C.POINTER(i64)]
                 L.psr_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
+                L.psr_context_set_profiling.argtypes = [vp, C.c_int]
+                L.psr_context_stage_ms.argtypes = [vp, C.c_int, C.POINTER(C.c_float)]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -110,6 +114,21 @@ def context(stream=None):
 
 def psr_context_sync(ctx=None):
     _check(lib().psr_context_sync(C.c_void_p(ctx if ctx else context())), "psr_context_sync")
+
+
+def psr_context_set_profiling(ctx, enable=True):
+    _check(lib().psr_context_set_profiling(C.c_void_p(ctx), int(bool(enable))),
+           "psr_context_set_profiling")
+
+
+def psr_context_stage_ms(ctx):
+    """{stage name: ms} of the most recent call on the context."""
+    out = {}
+    for i, name in enumerate(STAGES):
+        ms = C.c_float()
+        _check(lib().psr_context_stage_ms(C.c_void_p(ctx), i, C.byref(ms)), "psr_context_stage_ms")
+        out[name] = float(ms.value)
+    return out
 
 
 def _ptr(a):

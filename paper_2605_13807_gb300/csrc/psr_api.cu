@@ -16,6 +16,10 @@ struct psr_context {
     void *ws = nullptr;
     size_t ws_size = 0;
     int *status = nullptr;  // device status word
+    bool profiling = false;
+    cudaEvent_t ev_begin[PSR_STAGE_COUNT] = {};
+    cudaEvent_t ev_end[PSR_STAGE_COUNT] = {};
+    bool stage_ran[PSR_STAGE_COUNT] = {};
 };
 
 namespace {
@@ -128,13 +132,24 @@ int stage_in(const T *src, T *dst_ws, size_t count, bool dev, cudaStream_t st, c
     return PSR_OK;
 }
 
-struct ModelDev {
-    const float *theta;
-    float *pk;
-    void *pkb;
-    ThetaLayout tl;
-    F32Layout fl;
+// Records the begin/end event of a stage when profiling is on.
+struct StageScope {
+    psr_context *ctx;
+    int stage;
+    StageScope(psr_context *c, int s) : ctx(c), stage(s) {
+        if (ctx->profiling) {
+            cudaEventRecord(ctx->ev_begin[stage], ctx->stream);
+            ctx->stage_ran[stage] = true;
+        }
+    }
+    ~StageScope() {
+        if (ctx->profiling) cudaEventRecord(ctx->ev_end[stage], ctx->stream);
+    }
 };
+
+void reset_stages(psr_context *ctx) {
+    for (int i = 0; i < PSR_STAGE_COUNT; ++i) ctx->stage_ran[i] = false;
+}
 
 }  // namespace
 
@@ -179,9 +194,35 @@ int psr_context_create(psr_context **out, void *stream) {
     return PSR_OK;
 }
 
+int psr_context_set_profiling(psr_context *ctx, int enable) {
+    if (!ctx || (enable != 0 && enable != 1)) return PSR_EINVAL;
+    if (enable && !ctx->ev_begin[0]) {
+        for (int i = 0; i < PSR_STAGE_COUNT; ++i) {
+            PSR_TRY(cudaEventCreate(&ctx->ev_begin[i]));
+            PSR_TRY(cudaEventCreate(&ctx->ev_end[i]));
+        }
+    }
+    ctx->profiling = enable != 0;
+    reset_stages(ctx);
+    return PSR_OK;
+}
+
+int psr_context_stage_ms(psr_context *ctx, int stage, float *ms) {
+    if (!ctx || !ms || !ctx->profiling || stage < 0 || stage >= PSR_STAGE_COUNT) return PSR_EINVAL;
+    *ms = 0.0f;
+    if (!ctx->stage_ran[stage]) return PSR_OK;
+    PSR_TRY(cudaEventSynchronize(ctx->ev_end[stage]));
+    PSR_TRY(cudaEventElapsedTime(ms, ctx->ev_begin[stage], ctx->ev_end[stage]));
+    return PSR_OK;
+}
+
 int psr_context_destroy(psr_context *ctx) {
     if (!ctx) return PSR_EINVAL;
     int rc = from_cuda(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < PSR_STAGE_COUNT; ++i) {
+        if (ctx->ev_begin[i]) cudaEventDestroy(ctx->ev_begin[i]);
+        if (ctx->ev_end[i]) cudaEventDestroy(ctx->ev_end[i]);
+    }
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->status) cudaFree(ctx->status);
     delete ctx;
@@ -234,10 +275,14 @@ int psr_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_
     if ((rc = stage_in(spins, spins_ws, (size_t)n * L, d_spins, st, &sp)) != PSR_OK) return rc;
     float *o = d_out ? out : out_ws;
 
-    PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
-    if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
-    PSR_TRY(launch_bitpack(sp, n, L, W, bits, ctx->status, st));
-    PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+        if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
+        PSR_TRY(launch_bitpack(sp, n, L, W, bits, ctx->status, st));
+        PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    }
     FwdJobs jb{};
     jb.mode = 0;
     jb.N = L;
@@ -248,8 +293,11 @@ int psr_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_
     jb.out = o;
     jb.job_counter = counter;
     jb.status = ctx->status;
-    if (bf16) PSR_TRY(launch_fwd_bf16(jb, pkb, pk, fl, ctx->num_sms, st));
-    else PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st));
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        if (bf16) PSR_TRY(launch_fwd_bf16(jb, pkb, pk, fl, ctx->num_sms, st));
+        else PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st));
+    }
     if (!d_out) {
         PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
     }
@@ -330,7 +378,11 @@ int psr_connected(psr_context *ctx, const uint8_t *samples, int64_t n, const psr
     b.entries = d_e ? entries : ent_ws;
     b.diag = d_d ? diag : diag_ws;
     HamDev hd{};
-    if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_GENERATOR);
+        if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
+    }
     int64_t tot = 0;
     PSR_TRY(cudaMemcpyAsync(&tot, b.offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PSR_TRY(cudaStreamSynchronize(st));
@@ -404,12 +456,19 @@ int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n
     float *o = d_out ? out : out_ws;
     double *so = stats ? (d_stats ? stats : stats_ws) : nullptr;
 
-    PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
-    if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
-    PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+        if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
+        PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));
+        PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
+    }
     HamDev hd{};
-    if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
-    PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
+    {
+        StageScope sc(ctx, PSR_STAGE_GENERATOR);
+        if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
+    }
 
     FwdJobs js{};
     js.mode = 0;
@@ -434,15 +493,21 @@ int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n
     jc.logp_out = nullptr;
     jc.carries_out = nullptr;
     jc.job_counter = counters + 1;
-    if (bf16) {
-        PSR_TRY(launch_fwd_bf16(js, pkb, pk, fl, ctx->num_sms, st));
-        if (cap > 0) PSR_TRY(launch_fwd_bf16(jc, pkb, pk, fl, ctx->num_sms, st));
-    } else {
-        PSR_TRY(launch_fwd_f32(js, pk, fl, ctx->num_sms, st));
-        if (cap > 0) PSR_TRY(launch_fwd_f32(jc, pk, fl, ctx->num_sms, st));
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        if (bf16) PSR_TRY(launch_fwd_bf16(js, pkb, pk, fl, ctx->num_sms, st));
+        else PSR_TRY(launch_fwd_f32(js, pk, fl, ctx->num_sms, st));
     }
-    PSR_TRY(launch_eloc_gather(b.offsets, delta, b.diag, hd.coeff, n, o, st));
-    if (so) PSR_TRY(launch_stats(o, n, so, st));
+    if (cap > 0) {
+        StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
+        if (bf16) PSR_TRY(launch_fwd_bf16(jc, pkb, pk, fl, ctx->num_sms, st));
+        else PSR_TRY(launch_fwd_f32(jc, pk, fl, ctx->num_sms, st));
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_GATHER);
+        PSR_TRY(launch_eloc_gather(b.offsets, delta, b.diag, hd.coeff, n, o, st));
+        if (so) PSR_TRY(launch_stats(o, n, so, st));
+    }
     if (!d_out) PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
     if (stats && !d_stats)
         PSR_TRY(cudaMemcpyAsync(stats, stats_ws, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -512,9 +577,13 @@ int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t 
     if (dout && (rc = stage_in(dout, dout_ws, n, d_dout, st, &dv)) != PSR_OK) return rc;
     float *g = d_g ? dparams : g_ws;
 
-    PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
-    PSR_TRY(launch_bitpack(sp, n, L, W, bits, ctx->status, st));
-    PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+        PSR_TRY(launch_bitpack(sp, n, L, W, bits, ctx->status, st));
+        PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    }
     FwdJobs jb{};
     jb.mode = 0;
     jb.N = L;
@@ -526,12 +595,18 @@ int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t 
     jb.carries_out = carries;
     jb.job_counter = counter;
     jb.status = ctx->status;
-    PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st));
-    float *rows = dout ? partial : g;
-    PSR_TRY(cudaMemsetAsync(rows, 0, grad_rows * P * sizeof(float), st));
-    PSR_TRY(launch_bwd_f32(bits, n, L, W, params->u1_mask, theta, tl, pk, fl, carries, dv, rows, grid,
-                           tape, ctx->status, st));
-    if (dout) PSR_TRY(launch_reduce_rows(partial, grid, P, g, st));
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st));
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_BWD);
+        float *rows = dout ? partial : g;
+        PSR_TRY(cudaMemsetAsync(rows, 0, grad_rows * P * sizeof(float), st));
+        PSR_TRY(launch_bwd_f32(bits, n, L, W, params->u1_mask, theta, tl, pk, fl, carries, dv, rows,
+                               grid, tape, ctx->status, st));
+        if (dout) PSR_TRY(launch_reduce_rows(partial, grid, P, g, st));
+    }
     if (!d_g)
         PSR_TRY(cudaMemcpyAsync(dparams, g_ws, (dout ? P : (size_t)n * P) * sizeof(float),
                                 cudaMemcpyDeviceToHost, st));
