@@ -176,6 +176,27 @@ int psr_connected(psr_context *ctx, const uint8_t *samples, int64_t n,
 int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
              const float *dout, float *dparams);
 
+/* log psi exactly as psr_logpsi computes it, for callers that may not
+ * allocate device memory (the paper has no counterpart; this is a service of
+ * the library).  Such callers include programs whose device memory belongs
+ * to another runtime's pool, latency-critical loops that cannot take the
+ * synchronisation an allocation may imply, and plug-ins that are not given
+ * the allocation API.  Nothing is allocated: all scratch lives in one fixed
+ * 8 MiB array per device inside the library (held from module load until the
+ * process exits).  params->ctx is ignored; the work is queued on `stream`
+ * (a cudaStream_t passed as void*, NULL = legacy default stream) and the call
+ * returns without synchronising.
+ * theta, spins and out must all be device arrays (PSR_EINVAL otherwise).
+ * Any n is accepted (samples are processed in batches that fit the array);
+ * a configuration longer than 33,554,368 sites is rejected with PSR_EINVAL.
+ * The first call on a device, with that device current, performs a one-time
+ * set-up (it looks up the array's device address); make that first call
+ * before any stream capture begins.  Every call shares the array and leaves
+ * its contents behind; calls whose work overlaps on one device race on it.
+ * Device-side checks (a spin byte other than 0/1) are not reported. */
+int psr_logpsi_noalloc(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
+                       float *out, void *stream);
+
 /* Stages of the launch sequence, for per-stage device timing. */
 enum {
     PSR_STAGE_PACK = 0,          /* parameter packing and spin bit-packing */

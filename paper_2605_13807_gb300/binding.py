@@ -42,7 +42,7 @@ class psr_hamiltonian(C.Structure):
 
 EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "psr_param_count",
             "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror",
-            "psr_context_set_profiling", "psr_context_stage_ms")
+            "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd")
 
 _lib = None
@@ -70,6 +70,7 @@ def lib():
                 L.psr_connected.argtypes = [vp, vp, i64, C.POINTER(psr_hamiltonian), vp, vp, i64, vp,
                                             C.POINTER(i64)]
                 L.psr_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
+                L.psr_logpsi_noalloc.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
                 L.psr_context_set_profiling.argtypes = [vp, C.c_int]
                 L.psr_context_stage_ms.argtypes = [vp, C.c_int, C.POINTER(C.c_float)]
                 L.psr_strerror.argtypes = [C.c_int]
@@ -187,3 +188,17 @@ def psr_grad(params, spins, dout, dparams):
     _check(lib().psr_grad(C.byref(params), _ptr(spins), int(n), int(L), _ptr(dout), _ptr(dparams)),
            "psr_grad")
     return dparams
+
+
+def psr_logpsi_noalloc(params, spins, out, stream=None):
+    """log psi with the library's fixed scratch array (no device allocation);
+    queued on `stream` (a torch stream or a raw handle; default: torch's
+    current stream) without synchronising."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream or 0)
+    n, L = spins.shape
+    _check(lib().psr_logpsi_noalloc(C.byref(params), _ptr(spins), int(n), int(L), _ptr(out),
+                                    C.c_void_p(handle)), "psr_logpsi_noalloc")
+    return out
