@@ -16,10 +16,10 @@
 // tables and only its output map C^(0) h is a contraction.  The readout
 // (logit difference, two-way softmax) and log-psi sums are FP32 on CUDA cores.
 //
-// A CTA (one per SM) runs two independent sequence streams, one per
-// warpgroup, each with its own TMEM accumulators, B tiles and mbarrier:
-// while one stream runs its epilogue (gates, scan, GELU) the tensor core
-// works on the other stream's MMAs.  Jobs (full sequences or connected
+// A CTA (one per SM) runs two independent sequence streams, each on two
+// warpgroups that split the 64 sites of a chunk, with its own TMEM
+// accumulators, B tiles and mbarrier: while one stream runs its epilogue
+// (gates, scan, GELU) the tensor core works on the other stream's MMAs.  Jobs (full sequences or connected
 // configurations resumed from a stored chunk carry) come from an atomic
 // counter.  Every mbarrier wait is bounded; on expiry the CTA records
 // PSR_ETIMEOUT, stops issuing work, frees its TMEM and returns.
@@ -36,7 +36,7 @@ namespace {
 constexpr int H = 128;
 constexpr int CH = kChunkBF16;  // 64 sites = MMA N
 constexpr int NL = 3;
-constexpr int kThreads = 256;   // two warpgroups = two streams
+constexpr int kThreads = 512;   // two streams x two warpgroups
 constexpr uint32_t kTileBytes = 16384;     // [K=128 rows][64 sites] bf16
 constexpr uint32_t kMatBytes = 32768;      // 128 x 128 bf16
 constexpr int kSmemMats = 5;               // C0, C1, D1, C2, D2
@@ -104,10 +104,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void named_bar(int id) {
-    asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
-}
-
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -151,28 +147,11 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
         : "memory");
 }
 
-#define PSR_R32(x) \
-    "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]), \
-    "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]),         \
-    "=r"(x[15]), "=r"(x[16]), "=r"(x[17]), "=r"(x[18]), "=r"(x[19]), "=r"(x[20]), "=r"(x[21]),       \
-    "=r"(x[22]), "=r"(x[23]), "=r"(x[24]), "=r"(x[25]), "=r"(x[26]), "=r"(x[27]), "=r"(x[28]),       \
-    "=r"(x[29]), "=r"(x[30]), "=r"(x[31])
 #define PSR_W32(x) \
     "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]),         \
     "r"(x[8]), "r"(x[9]), "r"(x[10]), "r"(x[11]), "r"(x[12]), "r"(x[13]), "r"(x[14]), "r"(x[15]),    \
     "r"(x[16]), "r"(x[17]), "r"(x[18]), "r"(x[19]), "r"(x[20]), "r"(x[21]), "r"(x[22]), "r"(x[23]),  \
     "r"(x[24]), "r"(x[25]), "r"(x[26]), "r"(x[27]), "r"(x[28]), "r"(x[29]), "r"(x[30]), "r"(x[31])
-
-// 32 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : PSR_R32(r)
-        : "r"(taddr)
-        : "memory");
-}
 
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
@@ -195,23 +174,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
-// Writes 32 consecutive sites [32*half, 32*half+32) of row k of an MN-major
-// SW128 B tile: row k is 128 bytes, 16-byte chunk c holds sites 8c..8c+7 and
-// sits at physical chunk c ^ (k & 7).
-__device__ __forceinline__ void tile_store32(uint8_t *tile, int k, int half, const float *v) {
-    uint8_t *row = tile + k * 128;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int c = half * 4 + q;
-        uint4 w;
-        w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-        w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-        w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-        w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
-        *reinterpret_cast<uint4 *>(row + ((c ^ (k & 7)) << 4)) = w;
-    }
-}
-
 struct Misc {
     uint64_t mbar[2];
     long long job[2];
@@ -219,6 +181,85 @@ struct Misc {
     int abort_flag[2];
 };
 static_assert(sizeof(Misc) <= MISC_BYTES, "misc block too large");
+
+// --------------------------------------------------- epilogue arithmetic
+// Approximate-unit forms used only by this BF16 path (every value they
+// produce is rounded to BF16 before the next MMA, except the last layer's
+// output and the scan carry, where the errors below stay far under the BF16
+// rounding of the operands):
+//   sigmoid(x) = 1/2 + 1/2 tanh(x/2) with tanh.approx.f32 (rel. err ~2^-11)
+//   erf(u) for GELU: Abramowitz & Stegun, Handbook of Mathematical Functions,
+//   formula 7.1.28: erf(u) = 1 - (1 + a1 u + ... + a6 u^6)^-16, u >= 0,
+//   |error| <= 3e-7, with one approximate reciprocal.
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// AS7.1.28 coefficients a1..a6
+#define PSR_AS7128_A1 0.0705230784f
+#define PSR_AS7128_A2 0.0422820123f
+#define PSR_AS7128_A3 0.0092705272f
+#define PSR_AS7128_A4 0.0001520143f
+#define PSR_AS7128_A5 0.0002765672f
+#define PSR_AS7128_A6 0.0000430638f
+
+__device__ __forceinline__ float gelu_fast(float x) {
+    const float u = fabsf(x) * 0.70710678118654752f;
+    float p = fmaf(PSR_AS7128_A6, u, PSR_AS7128_A5);
+    p = fmaf(p, u, PSR_AS7128_A4);
+    p = fmaf(p, u, PSR_AS7128_A3);
+    p = fmaf(p, u, PSR_AS7128_A2);
+    p = fmaf(p, u, PSR_AS7128_A1);
+    p = fmaf(p, u, 1.0f);
+    p *= p;
+    p *= p;
+    p *= p;
+    p *= p;                                  // p^16 (inf for huge u -> erf = 1)
+    const float e = 1.0f - rcp_approx(p);    // erf(|x|/sqrt 2)
+    const float hx = 0.5f * x;
+    return fmaf(hx, copysignf(e, x), hx);    // x/2 (1 + erf(x/sqrt 2))
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        : "memory");
+}
+
+// Writes 8 sites (one 16-byte chunk, logical index c) of row k of an
+// MN-major SW128 B tile.
+__device__ __forceinline__ void tile_store8(uint8_t *tile, int k, int c, const float *v) {
+    uint4 w;
+    w.x = pack_bf16(v[0], v[1]);
+    w.y = pack_bf16(v[2], v[3]);
+    w.z = pack_bf16(v[4], v[5]);
+    w.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(tile + k * 128 + ((c ^ (k & 7)) << 4)) = w;
+}
+
+// Address of logical 16-byte chunk c of row k (used as a mailbox before the
+// chunk receives its tile data).
+__device__ __forceinline__ float *tile_slot(uint8_t *tile, int k, int c) {
+    return reinterpret_cast<float *>(tile + k * 128 + ((c ^ (k & 7)) << 4));
+}
 
 }  // namespace
 
@@ -260,6 +301,145 @@ cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, vo
     return cudaGetLastError();
 }
 
+// One dense layer (l = 1 or 2) of one stream half, from the proj MMA to the
+// output epilogue.  h1: layer 1 writes its FP32 h there (the residual of
+// layer 2); layer 2 adds it and overwrites it with the layer output x3.
+template <int L, class WaitF, class PubF, class BarF>
+__device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__restrict__ pk,
+                                            const F32Layout &fl, uint8_t *tileX, uint8_t *tileH,
+                                            uint32_t tX, uint32_t tH, uint32_t wsm, uint32_t aW,
+                                            uint32_t dZ, uint32_t dC, uint32_t accZ, uint32_t accC,
+                                            uint32_t bar, bool issuer, int hf, int j, float &carry,
+                                            float (&h1)[32], WaitF &sync_wait, PubF &publish,
+                                            BarF &sbar) {
+    const uint32_t wz = aW + (L == 1 ? TM_WZ1 : TM_WZ2) * 64;
+    const uint32_t wh = aW + (L == 1 ? TM_WH1 : TM_WH2) * 64;
+    if (issuer) {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) mma_ts(dZ, wz + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) mma_ts(dC, wh + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
+        mma_commit(bar);
+    }
+    if (!sync_wait()) return false;
+    const float hbz = 0.5f * pk[fl.bz[L] + threadIdx.x % 128];
+    const float bh = pk[fl.bh[L] + threadIdx.x % 128];
+    // gates + scan; half 0 from the carry, half 1 as prefix pairs (P, S)
+    float keep[8];
+    float h31 = 0.0f;
+    if (hf == 0) {
+        float h = carry;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint32_t rz[8], rc[8];
+            tmem_ld8(accZ + 8 * g, rz);
+            tmem_ld8(accC + 8 * g, rc);
+            tmem_wait_ld();
+            float hv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float a = fmaf(0.5f, tanh_approx(fmaf(0.5f, __uint_as_float(rz[i]), hbz)), 0.5f);
+                const float cv = __uint_as_float(rc[i]) + bh;
+                h = fmaf(a, h - cv, cv);  // a h + (1 - a) h~
+                hv[i] = h;
+                if (L == 1) h1[8 * g + i] = h;
+            }
+            if (g == 0) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) keep[i] = hv[i];
+            } else {
+                tile_store8(tileH, j, g, hv);
+            }
+        }
+        h31 = h;
+        *tile_slot(tileH, j, 4) = h31;
+    } else {
+        float P = 1.0f, S = 0.0f;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint32_t rz[8], rc[8];
+            tmem_ld8(accZ + 8 * g, rz);
+            tmem_ld8(accC + 8 * g, rc);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float a = fmaf(0.5f, tanh_approx(fmaf(0.5f, __uint_as_float(rz[i]), hbz)), 0.5f);
+                const float cv = __uint_as_float(rc[i]) + bh;
+                S = fmaf(a, S - cv, cv);
+                P *= a;
+                rz[i] = __float_as_uint(S);
+                rc[i] = __float_as_uint(P);
+            }
+            tmem_st8(accZ + 8 * g, rz);
+            tmem_st8(accC + 8 * g, rc);
+        }
+        float *mb = tile_slot(tileH, j, 0);
+        mb[0] = P;
+        mb[1] = S;
+        tmem_wait_st();
+    }
+    sbar();
+    if (hf == 0) {
+        const float *mb = tile_slot(tileH, j, 0);
+        carry = fmaf(mb[0], h31, mb[1]);
+        tile_store8(tileH, j, 0, keep);
+    } else {
+        const float hin = *tile_slot(tileH, j, 4);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint32_t rs[8], rp[8];
+            tmem_ld8(accZ + 8 * g, rs);
+            tmem_ld8(accC + 8 * g, rp);
+            tmem_wait_ld();
+            float hv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                hv[i] = fmaf(__uint_as_float(rp[i]), hin, __uint_as_float(rs[i]));
+                if (L == 1) h1[8 * g + i] = hv[i];
+            }
+            tile_store8(tileH, j, 4 + g, hv);
+        }
+    }
+    publish();
+    constexpr int sC = (L == 1) ? SM_C1 : SM_C2, sD = (L == 1) ? SM_D1 : SM_D2;
+    if (issuer) {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+            mma_ss(dZ, sdesc(wsm + sC * kMatBytes + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
+                   sdesc(tH + kk * 2048, 1024, 1024), kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+            mma_ss(dZ, sdesc(wsm + sD * kMatBytes + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
+                   sdesc(tX + kk * 2048, 1024, 1024), 1);
+        mma_commit(bar);
+    }
+    if (!sync_wait()) return false;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        uint32_t r[8];
+        tmem_ld8(accZ + 8 * g, r);
+        tmem_wait_ld();
+        float xv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float y = __uint_as_float(r[i]);
+            if (L == 2) y += h1[8 * g + i];
+            xv[i] = gelu_fast(y);
+            if (L == 2) h1[8 * g + i] = xv[i];
+        }
+        if (L == 1) tile_store8(tileX, j, 4 * hf + g, xv);
+    }
+    if (L == 1) publish();
+    return true;
+}
+
+// Two streams (independent sequences) per CTA; each stream has two
+// warpgroups that split the 64 sites of a chunk into halves of 32.  The scan
+// across the halves: the first half runs h_t = a_t h_{t-1} + b_t from the
+// carry; the second half composes its 32 affine maps into prefix pairs
+// (P_t, S_t) (h_t = P_t h_31 + S_t), parked in its own TMEM columns.  The
+// halves swap h_31 and (P_63, S_63) through mailboxes inside the B tile, then
+// each writes its part of the tile.
 __global__ void __launch_bounds__(kThreads, 1)
 fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__restrict__ pk,
                 F32Layout fl) {
@@ -269,16 +449,20 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
     Misc &M = *reinterpret_cast<Misc *>(smem + OFF_MISC);
 
     const int tid = threadIdx.x;
-    const int g = tid >> 7;          // stream (warpgroup)
+    const int wg = tid >> 7;         // warpgroup
+    const int s = wg >> 1;           // stream
+    const int hf = wg & 1;           // half of the chunk (sites 32*hf .. 32*hf+31)
     const int j = tid & 127;         // hidden unit = TMEM lane
     const int warp = tid >> 5;
+    const int lane = tid & 31;
     const int lane_base = (warp & 3) * 32;
+    const bool issuer = (hf == 0 && j == 0);
 
-    uint8_t *tileX = smem + OFF_TILES + (2 * g) * kTileBytes;
+    uint8_t *tileX = smem + OFF_TILES + (2 * s) * kTileBytes;
     uint8_t *tileH = tileX + kTileBytes;
     const uint32_t wsm = smem_u32(smem + OFF_W);
     const uint32_t tX = smem_u32(tileX), tH = smem_u32(tileH);
-    const uint32_t bar = smem_u32(&M.mbar[g]);
+    const uint32_t bar = smem_u32(&M.mbar[s]);
 
     // ------------------------------------------------------------- set-up
     if (warp == 0) {
@@ -295,7 +479,6 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
         M.abort_flag[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // shared-memory weight images (plain 16-byte copies)
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(pkb + PK_SMEM);
         uint4 *dst = reinterpret_cast<uint4 *>(smem + OFF_W);
@@ -306,18 +489,17 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
     __syncthreads();
     tc_after();
     const uint32_t tmem = M.tmem_base;
-    // TMEM weight images: warpgroup 0, lane j = row j
-    if (g == 0) {
+    if (wg == 0) {
 #pragma unroll 1
         for (int m = 0; m < kTmemMats; ++m) {
             const uint32_t *row =
                 reinterpret_cast<const uint32_t *>(pkb + PK_TMEM + (size_t)m * kMatBytes + j * 256);
 #pragma unroll 1
-            for (int half = 0; half < 2; ++half) {
+            for (int part = 0; part < 2; ++part) {
                 uint32_t r[32];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) r[q] = row[half * 32 + q];
-                tmem_st32(tmem + ((uint32_t)lane_base << 16) + kTmemWeightCol + m * 64 + half * 32, r);
+                for (int q = 0; q < 32; ++q) r[q] = row[part * 32 + q];
+                tmem_st32(tmem + ((uint32_t)lane_base << 16) + kTmemWeightCol + m * 64 + part * 32, r);
             }
         }
         tmem_wait_st();
@@ -326,55 +508,46 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
     __syncthreads();
     tc_after();
 
-    // per-thread constants (FP32)
-    const float a0_0 = pk[fl.A0 + j], a0_1 = pk[fl.A0 + H + j], a0_2 = pk[fl.A0 + 2 * H + j];
-    const float b0_0 = pk[fl.B0 + j], b0_1 = pk[fl.B0 + H + j], b0_2 = pk[fl.B0 + 2 * H + j];
-    const float d0_0 = pk[fl.DU0 + j], d0_1 = pk[fl.DU0 + H + j], d0_2 = pk[fl.DU0 + 2 * H + j];
-    const float bz1 = pk[fl.bz[1] + j], bh1 = pk[fl.bh[1] + j];
-    const float bz2 = pk[fl.bz[2] + j], bh2 = pk[fl.bh[2] + j];
-    const float wdj = pk[fl.wd + j];
-    const float bd = pk[fl.bd];
-
     const uint32_t lane_off = (uint32_t)lane_base << 16;
-    const uint32_t accZ = tmem + lane_off + 128 * g;       // this thread's lane, Z columns
-    const uint32_t accC = accZ + 64;
-    const uint32_t dZ = tmem + 128 * g;                    // MMA destination (lane 0)
+    const uint32_t accZ = tmem + lane_off + 128 * s + 32 * hf;  // this half's Z columns
+    const uint32_t accC = accZ + 64;                              // this half's C columns
+    const uint32_t dZ = tmem + 128 * s;
     const uint32_t dC = dZ + 64;
-    const uint32_t aW = tmem + kTmemWeightCol;             // TMEM weights (lane 0)
+    const uint32_t aW = tmem + kTmemWeightCol;
 
     const int N = jb.N;
     const int nch = (N + CH - 1) / CH;
     const long long njobs = jb.mode == 1 ? (long long)*jb.n_jobs_dev : (long long)jb.n_jobs;
-    const int bar_id = 1 + g;
+    const int bar_id = 1 + s;
     uint32_t phase = 0;
     bool aborted = false;
+    float *red = reinterpret_cast<float *>(tileX);        // readout scratch [2][4][32]
+    float *red2 = red + 2 * 4 * 32;                       // per-half site sums [2]
 
-    // Issues the MMAs of one step (thread j == 0 of the stream) and waits.
-    // Returns false if the wait expired (the whole stream then stops).
+    auto sbar = [&]() { asm volatile("bar.sync %0, 256;" ::"r"(bar_id) : "memory"); };
     auto sync_wait = [&]() -> bool {
         bool ok = mbar_wait(bar, phase);
         phase ^= 1u;
         if (!ok) {
-            M.abort_flag[g] = 1;
+            M.abort_flag[s] = 1;
             set_status(jb.status, PSR_ETIMEOUT);
         }
-        named_bar(bar_id);
+        sbar();
         tc_after();
-        return M.abort_flag[g] == 0;
+        return M.abort_flag[s] == 0;
     };
-    // generic smem writes + TMEM loads done -> visible to the MMA issuer
     auto publish = [&]() {
         fence_proxy_async();
         tc_before();
-        named_bar(bar_id);
+        sbar();
         tc_after();
     };
 
     for (;;) {
-        if (j == 0) M.job[g] = (long long)atomicAdd(jb.job_counter, 1ull);
-        named_bar(bar_id);
-        const long long job = M.job[g];
-        named_bar(bar_id);
+        if (issuer) M.job[s] = (long long)atomicAdd(jb.job_counter, 1ull);
+        sbar();
+        const long long job = M.job[s];
+        sbar();
         if (job >= njobs) break;
 
         int sample, p = -1, q = -1, c0 = 0;
@@ -388,23 +561,23 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
             c0 = p / CH;
         }
         const uint64_t *row = jb.bits + (int64_t)sample * jb.W;
-        float hc0 = 0.0f, hc1 = 0.0f, hc2 = 0.0f;
-        if (c0 > 0) {
+        float cr[NL] = {0.0f, 0.0f, 0.0f};  // scan carries (used by half 0)
+        if (hf == 0 && c0 > 0) {
             const float *cin = jb.carries_in + (((int64_t)sample * nch + c0) * NL) * H + j;
-            hc0 = cin[0];
-            hc1 = cin[H];
-            hc2 = cin[2 * H];
+            cr[0] = cin[0];
+            cr[1] = cin[H];
+            cr[2] = cin[2 * H];
         }
         int n_up = jb.u1 ? count_up_before(row, c0 * CH) : 0;
         float acc = 0.0f;
 
         for (int c = c0; c < nch && !aborted; ++c) {
             const int t0 = c * CH;
-            if (jb.carries_out) {
+            if (hf == 0 && jb.carries_out) {
                 float *co = jb.carries_out + (((int64_t)sample * nch + c) * NL) * H + j;
-                co[0] = hc0;
-                co[H] = hc1;
-                co[2 * H] = hc2;
+                co[0] = cr[0];
+                co[H] = cr[1];
+                co[2 * H] = cr[2];
             }
             uint64_t cur = row[c];
             uint32_t prev = (c > 0) ? (uint32_t)(row[c - 1] >> 63) : 0u;
@@ -416,26 +589,85 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
             }
             const int nvalid = min(CH, N - t0);
             if (nvalid < 64) cur &= (1ull << nvalid) - 1ull;
-            const uint64_t prevbits = (cur << 1) | prev;  // bit t = s_{t0+t-1}
+            // bit i = s_{t-1} for site t = t0 + 32 hf + i
+            const uint32_t inbits = (uint32_t)(((cur << 1) | prev) >> (32 * hf));
+            const bool seq_start = (t0 == 0 && hf == 0);  // site 0 has no predecessor
 
-            // ---------------- layer 0: lookup gates + scan -> h0 (B tile H)
+            float h1[32];  // FP32 h of layer 1 (residual of layer 2); becomes x3
+
+            // ---------------- layer 0: lookup gates, scan -> tile H
+            {
+                const float a0_0 = pk[fl.A0 + j], a0_1 = pk[fl.A0 + H + j], a0_2 = pk[fl.A0 + 2 * H + j];
+                const float b0_0 = pk[fl.B0 + j], b0_1 = pk[fl.B0 + H + j], b0_2 = pk[fl.B0 + 2 * H + j];
+                float keep[8];  // half 0: sites 0..7, written after the mailbox swap
+                float h31 = 0.0f;
+                if (hf == 0) {
+                    float h = cr[0];
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                float hv[32];
+                    for (int g = 0; g < 4; ++g) {
+                        float hv[8];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int t = half * 32 + i;
-                    const bool first = (t0 + t == 0);
-                    const bool sb = (prevbits >> t) & 1ull;
-                    const float a = first ? a0_0 : (sb ? a0_2 : a0_1);
-                    const float b = first ? b0_0 : (sb ? b0_2 : b0_1);
-                    hc0 = a * hc0 + b;
-                    hv[i] = hc0;
+                        for (int i = 0; i < 8; ++i) {
+                            const bool sb = (inbits >> (8 * g + i)) & 1u;
+                            float a = sb ? a0_2 : a0_1, b = sb ? b0_2 : b0_1;
+                            if (g == 0 && i == 0 && seq_start) { a = a0_0; b = b0_0; }
+                            h = fmaf(a, h, b);
+                            hv[i] = h;
+                        }
+                        if (g == 0) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) keep[i] = hv[i];
+                        } else {
+                            tile_store8(tileH, j, g, hv);
+                        }
+                    }
+                    h31 = h;
+                    *tile_slot(tileH, j, 4) = h31;
+                } else {
+                    float P = 1.0f, S = 0.0f;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        uint32_t rs[8], rp[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const bool sb = (inbits >> (8 * g + i)) & 1u;
+                            const float a = sb ? a0_2 : a0_1, b = sb ? b0_2 : b0_1;
+                            S = fmaf(a, S, b);
+                            P *= a;
+                            rs[i] = __float_as_uint(S);
+                            rp[i] = __float_as_uint(P);
+                        }
+                        tmem_st8(accZ + 8 * g, rs);
+                        tmem_st8(accC + 8 * g, rp);
+                    }
+                    float *mb = tile_slot(tileH, j, 0);
+                    mb[0] = P;
+                    mb[1] = S;
+                    tmem_wait_st();
                 }
-                tile_store32(tileH, j, half, hv);
+                sbar();
+                if (hf == 0) {
+                    const float *mb = tile_slot(tileH, j, 0);
+                    cr[0] = fmaf(mb[0], h31, mb[1]);
+                    tile_store8(tileH, j, 0, keep);
+                } else {
+                    const float hin = *tile_slot(tileH, j, 4);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        uint32_t rs[8], rp[8];
+                        tmem_ld8(accZ + 8 * g, rs);
+                        tmem_ld8(accC + 8 * g, rp);
+                        tmem_wait_ld();
+                        float hv[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            hv[i] = fmaf(__uint_as_float(rp[i]), hin, __uint_as_float(rs[i]));
+                        tile_store8(tileH, j, 4 + g, hv);
+                    }
+                }
             }
             publish();
-            if (j == 0) {
+            if (issuer) {
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk)
                     mma_ss(dZ, sdesc(wsm + SM_C0 * kMatBytes + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
@@ -443,105 +675,45 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
                 mma_commit(bar);
             }
             if (!sync_wait()) { aborted = true; break; }
-            // epilogue: x1 = GELU(C0 h0 + D0 u) -> B tile X
+            // epilogue: x1 = GELU(C0 h0 + D0 u) -> tile X
+            const float d0_0 = pk[fl.DU0 + j], d0_1 = pk[fl.DU0 + H + j], d0_2 = pk[fl.DU0 + 2 * H + j];
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                uint32_t r[32];
-                tmem_ld32(accZ + half * 32, r);
+            for (int g = 0; g < 4; ++g) {
+                uint32_t r[8];
+                tmem_ld8(accZ + 8 * g, r);
                 tmem_wait_ld();
-                float xv[32];
+                float xv[8];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int t = half * 32 + i;
-                    const bool first = (t0 + t == 0);
-                    const bool sb = (prevbits >> t) & 1ull;
-                    const float du = first ? d0_0 : (sb ? d0_2 : d0_1);
-                    xv[i] = gelu_f(__uint_as_float(r[i]) + du);
+                for (int i = 0; i < 8; ++i) {
+                    const bool sb = (inbits >> (8 * g + i)) & 1u;
+                    float du = sb ? d0_2 : d0_1;
+                    if (g == 0 && i == 0 && seq_start) du = d0_0;
+                    xv[i] = gelu_fast(__uint_as_float(r[i]) + du);
                 }
-                tile_store32(tileX, j, half, xv);
+                tile_store8(tileX, j, 4 * hf + g, xv);
             }
             publish();
 
             // ---------------- layers 1 and 2
-            float h1[CH];
-            float x3[CH];
-#pragma unroll
-            for (int l = 1; l <= 2; ++l) {
-                const uint32_t wz = aW + (l == 1 ? TM_WZ1 : TM_WZ2) * 64;
-                const uint32_t wh = aW + (l == 1 ? TM_WH1 : TM_WH2) * 64;
-                if (j == 0) {
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-                        mma_ts(dZ, wz + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-                        mma_ts(dC, wh + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
-                    mma_commit(bar);
-                }
-                if (!sync_wait()) { aborted = true; break; }
-                const float bz = (l == 1) ? bz1 : bz2, bh = (l == 1) ? bh1 : bh2;
-                float hc = (l == 1) ? hc1 : hc2;
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    uint32_t rz[32], rc[32];
-                    tmem_ld32(accZ + half * 32, rz);
-                    tmem_ld32(accC + half * 32, rc);
-                    tmem_wait_ld();
-                    float hv[32];
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float a = sigmoid_f(__uint_as_float(rz[i]) + bz);
-                        hc = a * hc + (1.0f - a) * (__uint_as_float(rc[i]) + bh);
-                        hv[i] = hc;
-                        if (l == 1) h1[half * 32 + i] = hc;
-                    }
-                    tile_store32(tileH, j, half, hv);
-                }
-                if (l == 1) hc1 = hc; else hc2 = hc;
-                publish();
-                const int sC = (l == 1) ? SM_C1 : SM_C2, sD = (l == 1) ? SM_D1 : SM_D2;
-                if (j == 0) {
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-                        mma_ss(dZ, sdesc(wsm + sC * kMatBytes + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-                               sdesc(tH + kk * 2048, 1024, 1024), kk > 0);
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-                        mma_ss(dZ, sdesc(wsm + sD * kMatBytes + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-                               sdesc(tX + kk * 2048, 1024, 1024), 1);
-                    mma_commit(bar);
-                }
-                if (!sync_wait()) { aborted = true; break; }
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    uint32_t r[32];
-                    tmem_ld32(accZ + half * 32, r);
-                    tmem_wait_ld();
-                    float xv[32];
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        float y = __uint_as_float(r[i]);
-                        if (l == 2) y += h1[half * 32 + i];
-                        xv[i] = gelu_f(y);
-                        if (l == 2) x3[half * 32 + i] = xv[i];
-                    }
-                    if (l == 1) tile_store32(tileX, j, half, xv);
-                }
-                if (l == 1) publish();
-            }
-            if (aborted) break;
-            tc_before();  // TMEM reads of this chunk are done before the next MMA
+            if (!dense_layer<1>(jb, pk, fl, tileX, tileH, tX, tH, wsm, aW, dZ, dC, accZ, accC, bar,
+                                issuer, hf, j, cr[1], h1, sync_wait, publish, sbar))
+                { aborted = true; break; }
+            if (!dense_layer<2>(jb, pk, fl, tileX, tileH, tX, tH, wsm, aW, dZ, dC, accZ, accC, bar,
+                                issuer, hf, j, cr[2], h1, sync_wait, publish, sbar))
+                { aborted = true; break; }
+            float (&xo)[32] = h1;  // layer-2 output (x3) of this half
 
-            // ---------------- readout: d_t = wd . x3_t + bd, reduced over units
+            // ---------------- readout: d_t = wd . x3_t + bd over the 128 units
             {
-                float v[CH];
+                const float wdj = pk[fl.wd + j];
+                const float bd = pk[fl.bd];
+                float v[32];
 #pragma unroll
-                for (int t = 0; t < CH; ++t) v[t] = wdj * x3[t];
-                const int lane = tid & 31;
+                for (int i = 0; i < 32; ++i) v[i] = wdj * xo[i];
 #pragma unroll
-                for (int s = 0; s < 5; ++s) {
-                    const int m = 16 >> s;
-                    const int half = 32 >> s;
+                for (int st = 0; st < 5; ++st) {
+                    const int m = 16 >> st;
+                    const int half = 16 >> st;
                     const bool upper = (lane & m) != 0;
 #pragma unroll
                     for (int i = 0; i < half; ++i) {
@@ -550,37 +722,33 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
                         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
                     }
                 }
-                // lane L now holds sites 2L and 2L+1 summed over its warp's units
-                float *red = reinterpret_cast<float *>(tileX);  // [4 warps][64]
-                const int w4 = warp & 3;
-                red[w4 * CH + 2 * lane] = v[0];
-                red[w4 * CH + 2 * lane + 1] = v[1];
-                named_bar(bar_id);
-                float sv = 0.0f;
-                if (j < CH) {
-                    const int t = j;
-                    const float d = bd + red[t] + red[CH + t] + red[2 * CH + t] + red[3 * CH + t];
+                // lane L holds site L of this half, summed over its warp's units
+                red[(hf * 4 + (warp & 3)) * 32 + lane] = v[0];
+                sbar();
+                if ((warp & 3) == 0) {
+                    const int t = 32 * hf + lane;
+                    const float d = bd + red[(hf * 4 + 0) * 32 + lane] + red[(hf * 4 + 1) * 32 + lane] +
+                                    red[(hf * 4 + 2) * 32 + lane] + red[(hf * 4 + 3) * 32 + lane];
                     const int tt = t0 + t;
+                    float sv = 0.0f;
                     if (tt < N) {
-                        const int s = (int)((cur >> t) & 1ull);
+                        const int sbit = (int)((cur >> t) & 1ull);
                         const int nu = n_up + __popcll(cur & ((1ull << t) - 1ull));
-                        const float lp = site_logp(d, s, u1_forced(jb.u1, N, tt, nu));
+                        const float lp = site_logp(d, sbit, u1_forced(jb.u1, N, tt, nu));
                         if (jb.logp_out) jb.logp_out[(int64_t)sample * N + tt] = lp;
                         sv = (jb.mode == 1) ? lp - jb.logp_ref[(int64_t)sample * N + tt] : lp;
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                    if (lane == 0) red2[hf] = sv;
                 }
-                named_bar(bar_id);  // red[] reads done
-                if (j < CH && (j & 31) == 0) red[j >> 5] = sv;
-                named_bar(bar_id);
-                if (j == 0) acc += red[0] + red[1];
+                sbar();
+                if (issuer) acc += red2[0] + red2[1];
                 n_up += __popcll(cur);
-                named_bar(bar_id);  // scratch reads done before the next chunk writes X
             }
         }
         if (aborted) break;
-        if (j == 0) jb.out[job] = 0.5f * acc;
+        if (issuer) jb.out[job] = 0.5f * acc;
     }
 
     // ------------------------------------------------------------ teardown
