@@ -211,21 +211,37 @@ __device__ __forceinline__ float rcp_approx(float x) {
 #define PSR_AS7128_A5 0.0002765672f
 #define PSR_AS7128_A6 0.0000430638f
 
-__device__ __forceinline__ float gelu_fast(float x) {
-    const float u = fabsf(x) * 0.70710678118654752f;
-    float p = fmaf(PSR_AS7128_A6, u, PSR_AS7128_A5);
-    p = fmaf(p, u, PSR_AS7128_A4);
-    p = fmaf(p, u, PSR_AS7128_A3);
-    p = fmaf(p, u, PSR_AS7128_A2);
-    p = fmaf(p, u, PSR_AS7128_A1);
-    p = fmaf(p, u, 1.0f);
-    p *= p;
-    p *= p;
-    p *= p;
-    p *= p;                                  // p^16 (inf for huge u -> erf = 1)
-    const float e = 1.0f - rcp_approx(p);    // erf(|x|/sqrt 2)
-    const float hx = 0.5f * x;
-    return fmaf(hx, copysignf(e, x), hx);    // x/2 (1 + erf(x/sqrt 2))
+// Packed two-site forms (FP32x2: each lane is an IEEE FP32 operation, so the
+// results equal the scalar ones; one instruction serves two sites).
+__device__ __forceinline__ float2 gelu_fast2(float2 x) {
+    const float2 k = make_float2(0.70710678118654752f, 0.70710678118654752f);
+    const float2 u = __fmul2_rn(make_float2(fabsf(x.x), fabsf(x.y)), k);
+    float2 p = __ffma2_rn(make_float2(PSR_AS7128_A6, PSR_AS7128_A6), u,
+                          make_float2(PSR_AS7128_A5, PSR_AS7128_A5));
+    p = __ffma2_rn(p, u, make_float2(PSR_AS7128_A4, PSR_AS7128_A4));
+    p = __ffma2_rn(p, u, make_float2(PSR_AS7128_A3, PSR_AS7128_A3));
+    p = __ffma2_rn(p, u, make_float2(PSR_AS7128_A2, PSR_AS7128_A2));
+    p = __ffma2_rn(p, u, make_float2(PSR_AS7128_A1, PSR_AS7128_A1));
+    p = __ffma2_rn(p, u, make_float2(1.0f, 1.0f));
+    p = __fmul2_rn(p, p);
+    p = __fmul2_rn(p, p);
+    p = __fmul2_rn(p, p);
+    p = __fmul2_rn(p, p);
+    const float2 e = make_float2(copysignf(1.0f - rcp_approx(p.x), x.x),
+                                 copysignf(1.0f - rcp_approx(p.y), x.y));
+    const float2 hx = __fmul2_rn(make_float2(0.5f, 0.5f), x);
+    return __ffma2_rn(hx, e, hx);
+}
+
+// Gate a = sigmoid(z + b_z) = 1/2 + 1/2 tanh((z + b_z)/2) and the scan input
+// b = (1 - a)(h~ + b_h) for two sites; hbz2 = (b_z/2, b_z/2).
+__device__ __forceinline__ void gates2(float2 z, float2 c, float2 hbz2, float2 bh2, float2 &a,
+                                       float2 &b) {
+    const float2 zz = __ffma2_rn(make_float2(0.5f, 0.5f), z, hbz2);
+    const float2 t = make_float2(tanh_approx(zz.x), tanh_approx(zz.y));
+    a = __ffma2_rn(make_float2(0.5f, 0.5f), t, make_float2(0.5f, 0.5f));
+    const float2 cv = __fadd2_rn(c, bh2);
+    b = __ffma2_rn(make_float2(-a.x, -a.y), cv, cv);
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
@@ -324,6 +340,7 @@ __device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__re
     if (!sync_wait()) return false;
     const float hbz = 0.5f * pk[fl.bz[L] + threadIdx.x % 128];
     const float bh = pk[fl.bh[L] + threadIdx.x % 128];
+    const float2 hbz2 = make_float2(hbz, hbz), bh2 = make_float2(bh, bh);
     // gates + scan; half 0 from the carry, half 1 as prefix pairs (P, S)
     float keep[8];
     float h31 = 0.0f;
@@ -337,12 +354,18 @@ __device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__re
             tmem_wait_ld();
             float hv[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float a = fmaf(0.5f, tanh_approx(fmaf(0.5f, __uint_as_float(rz[i]), hbz)), 0.5f);
-                const float cv = __uint_as_float(rc[i]) + bh;
-                h = fmaf(a, h - cv, cv);  // a h + (1 - a) h~
+            for (int i = 0; i < 8; i += 2) {
+                float2 a, b;
+                gates2(make_float2(__uint_as_float(rz[i]), __uint_as_float(rz[i + 1])),
+                       make_float2(__uint_as_float(rc[i]), __uint_as_float(rc[i + 1])), hbz2, bh2, a, b);
+                h = fmaf(a.x, h, b.x);  // h_t = a_t h_{t-1} + (1 - a_t) h~_t
                 hv[i] = h;
-                if (L == 1) h1[8 * g + i] = h;
+                h = fmaf(a.y, h, b.y);
+                hv[i + 1] = h;
+            }
+            if (L == 1) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) h1[8 * g + i] = hv[i];
             }
             if (g == 0) {
 #pragma unroll
@@ -362,13 +385,18 @@ __device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__re
             tmem_ld8(accC + 8 * g, rc);
             tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float a = fmaf(0.5f, tanh_approx(fmaf(0.5f, __uint_as_float(rz[i]), hbz)), 0.5f);
-                const float cv = __uint_as_float(rc[i]) + bh;
-                S = fmaf(a, S - cv, cv);
-                P *= a;
+            for (int i = 0; i < 8; i += 2) {
+                float2 a, b;
+                gates2(make_float2(__uint_as_float(rz[i]), __uint_as_float(rz[i + 1])),
+                       make_float2(__uint_as_float(rc[i]), __uint_as_float(rc[i + 1])), hbz2, bh2, a, b);
+                S = fmaf(a.x, S, b.x);
+                P *= a.x;
                 rz[i] = __float_as_uint(S);
                 rc[i] = __float_as_uint(P);
+                S = fmaf(a.y, S, b.y);
+                P *= a.y;
+                rz[i + 1] = __float_as_uint(S);
+                rc[i + 1] = __float_as_uint(P);
             }
             tmem_st8(accZ + 8 * g, rz);
             tmem_st8(accC + 8 * g, rc);
@@ -393,9 +421,16 @@ __device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__re
             tmem_wait_ld();
             float hv[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                hv[i] = fmaf(__uint_as_float(rp[i]), hin, __uint_as_float(rs[i]));
-                if (L == 1) h1[8 * g + i] = hv[i];
+            for (int i = 0; i < 8; i += 2) {
+                const float2 v = __ffma2_rn(make_float2(__uint_as_float(rp[i]), __uint_as_float(rp[i + 1])),
+                                            make_float2(hin, hin),
+                                            make_float2(__uint_as_float(rs[i]), __uint_as_float(rs[i + 1])));
+                hv[i] = v.x;
+                hv[i + 1] = v.y;
+            }
+            if (L == 1) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) h1[8 * g + i] = hv[i];
             }
             tile_store8(tileH, j, 4 + g, hv);
         }
@@ -421,11 +456,16 @@ __device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__re
         tmem_wait_ld();
         float xv[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            float y = __uint_as_float(r[i]);
-            if (L == 2) y += h1[8 * g + i];
-            xv[i] = gelu_fast(y);
-            if (L == 2) h1[8 * g + i] = xv[i];
+        for (int i = 0; i < 8; i += 2) {
+            float2 y = make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1]));
+            if (L == 2) y = __fadd2_rn(y, make_float2(h1[8 * g + i], h1[8 * g + i + 1]));
+            const float2 x = gelu_fast2(y);
+            xv[i] = x.x;
+            xv[i + 1] = x.y;
+            if (L == 2) {
+                h1[8 * g + i] = x.x;
+                h1[8 * g + i + 1] = x.y;
+            }
         }
         if (L == 1) tile_store8(tileX, j, 4 * hf + g, xv);
     }
@@ -684,11 +724,14 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
                 tmem_wait_ld();
                 float xv[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const bool sb = (inbits >> (8 * g + i)) & 1u;
-                    float du = sb ? d0_2 : d0_1;
-                    if (g == 0 && i == 0 && seq_start) du = d0_0;
-                    xv[i] = gelu_fast(__uint_as_float(r[i]) + du);
+                for (int i = 0; i < 8; i += 2) {
+                    float du0 = ((inbits >> (8 * g + i)) & 1u) ? d0_2 : d0_1;
+                    const float du1 = ((inbits >> (8 * g + i + 1)) & 1u) ? d0_2 : d0_1;
+                    if (g == 0 && i == 0 && seq_start) du0 = d0_0;
+                    const float2 x = gelu_fast2(__fadd2_rn(
+                        make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1])), make_float2(du0, du1)));
+                    xv[i] = x.x;
+                    xv[i + 1] = x.y;
                 }
                 tile_store8(tileX, j, 4 * hf + g, xv);
             }
@@ -709,7 +752,11 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
                 const float bd = pk[fl.bd];
                 float v[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = wdj * xo[i];
+                for (int i = 0; i < 32; i += 2) {
+                    const float2 w = __fmul2_rn(make_float2(wdj, wdj), make_float2(xo[i], xo[i + 1]));
+                    v[i] = w.x;
+                    v[i + 1] = w.y;
+                }
 #pragma unroll
                 for (int st = 0; st < 5; ++st) {
                     const int m = 16 >> st;
