@@ -565,16 +565,19 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
     float *red2 = red + 2 * 4 * 32;                       // per-half site sums [2]
 
     auto sbar = [&]() { asm volatile("bar.sync %0, 256;" ::"r"(bar_id) : "memory"); };
+    // Waits for this stream's MMAs.  A wait that expires records
+    // PSR_ETIMEOUT and the stream's abort flag but keeps the control flow
+    // of every thread identical (all later waits are bounded too); the flag
+    // is acted on at the end of the chunk, after a stream-wide barrier.
     auto sync_wait = [&]() -> bool {
-        bool ok = mbar_wait(bar, phase);
+        const bool ok = mbar_wait(bar, phase);
         phase ^= 1u;
         if (!ok) {
             M.abort_flag[s] = 1;
             set_status(jb.status, PSR_ETIMEOUT);
         }
-        sbar();
         tc_after();
-        return M.abort_flag[s] == 0;
+        return true;
     };
     auto publish = [&]() {
         fence_proxy_async();
@@ -792,6 +795,7 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
                 sbar();
                 if (issuer) acc += red2[0] + red2[1];
                 n_up += __popcll(cur);
+                if (M.abort_flag[s]) aborted = true;  // uniform: read after the barrier
             }
         }
         if (aborted) break;
