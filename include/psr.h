@@ -166,6 +166,35 @@ int psr_connected(psr_context *ctx, const uint8_t *samples, int64_t n,
                   const psr_hamiltonian *ham, int64_t *offsets, int32_t *entries,
                   int64_t capacity, float *diag, int64_t *total);
 
+/* One sample set of a mixed batch: its own lattice, size and Hamiltonian,
+ * the model shared with the other items. */
+typedef struct {
+    const uint8_t *samples; /* uint8 [n][Lx*Ly] in sequence order, host or device */
+    int64_t n;              /* >= 1 */
+    psr_hamiltonian ham;
+    int32_t u1_mask;        /* zero-magnetisation masking for this item (params->u1_mask is ignored) */
+    float *out;             /* float [n]: E_loc */
+    double *stats;          /* double [3] {mean, variance, standard error} or NULL */
+} psr_batch_item;
+
+/* Local energy of up to 8 sample sets that share one model (e.g. several
+ * lattice sizes and both Hamiltonians).  Each item gets exactly what
+ * psr_local_energy would give it, but the sample forwards of all items run
+ * in one launch and the connected configurations of all items (ragged over
+ * samples and lattices) in one persistent launch.  When graphs are enabled
+ * on the context (psr_context_set_graphs), the context's stream is not the
+ * legacy default stream and every array is a device array, the launch
+ * sequence is captured into a CUDA graph on the first call and replayed by
+ * later calls with the same arguments (same pointers and sizes; the arrays'
+ * contents may change).  PSR_EINVAL for n_items outside 1..8 or any item
+ * psr_local_energy would reject. */
+int psr_local_energy_batch(const psr_params *params, const psr_batch_item *items,
+                           int32_t n_items);
+
+/* Enables (1) or disables (0) CUDA-graph capture and replay of
+ * psr_local_energy_batch on this context. */
+int psr_context_set_graphs(psr_context *ctx, int enable);
+
 /* Gradient of log psi (Sec. III.B: stochastic energy-gradient estimates).
  * dout == NULL: dparams is float [n][P] with row i = O_k(s_i) = d log psi(s_i)
  *   / d theta (per-sample, e.g. for a covariance / SR solve).

@@ -59,6 +59,19 @@ def local_energy(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, out=N
     return out, stats
 
 
+def local_energy_batch(theta, batch, cfg: ModelConfig, outs=None, stats=None):
+    """batch: list of (samples, hamiltonian, u1_mask).  Returns lists of E_loc
+    and stats tensors; all items run in one persistent launch."""
+    dev = _device_of(theta, *[b[0] for b in batch])
+    if outs is None:
+        outs = [torch.empty(b[0].shape[0], dtype=torch.float32, device=dev) for b in batch]
+    if stats is None:
+        stats = [torch.empty(3, dtype=torch.float64, device=dev) for _ in batch]
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_local_energy_batch(p, [(s, h, u1, o, st) for (s, h, u1), o, st in zip(batch, outs, stats)])
+    return outs, stats
+
+
 def max_entries(ham: B.psr_hamiltonian, n: int) -> int:
     N = ham.Lx * ham.Ly
     if ham.kind == B.PSR_TFIM:

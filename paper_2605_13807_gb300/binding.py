@@ -40,9 +40,15 @@ class psr_hamiltonian(C.Structure):
                 ("marshall", C.c_int32), ("J", C.c_double), ("h", C.c_double)]
 
 
+class psr_batch_item(C.Structure):
+    _fields_ = [("samples", C.c_void_p), ("n", C.c_int64), ("ham", psr_hamiltonian),
+                ("u1_mask", C.c_int32), ("out", C.c_void_p), ("stats", C.c_void_p)]
+
+
 EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "psr_param_count",
             "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror",
-            "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc")
+            "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc",
+            "psr_local_energy_batch", "psr_context_set_graphs")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd")
 
 _lib = None
@@ -71,6 +77,8 @@ def lib():
                                             C.POINTER(i64)]
                 L.psr_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
                 L.psr_logpsi_noalloc.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
+                L.psr_local_energy_batch.argtypes = [C.POINTER(psr_params), C.POINTER(psr_batch_item), i32]
+                L.psr_context_set_graphs.argtypes = [vp, C.c_int]
                 L.psr_context_set_profiling.argtypes = [vp, C.c_int]
                 L.psr_context_stage_ms.argtypes = [vp, C.c_int, C.POINTER(C.c_float)]
                 L.psr_strerror.argtypes = [C.c_int]
@@ -202,3 +210,20 @@ def psr_logpsi_noalloc(params, spins, out, stream=None):
     _check(lib().psr_logpsi_noalloc(C.byref(params), _ptr(spins), int(n), int(L), _ptr(out),
                                     C.c_void_p(handle)), "psr_logpsi_noalloc")
     return out
+
+
+def psr_context_set_graphs(ctx, enable=True):
+    _check(lib().psr_context_set_graphs(C.c_void_p(ctx), int(bool(enable))), "psr_context_set_graphs")
+
+
+def psr_local_energy_batch(params, items):
+    """items: sequence of (samples, hamiltonian, u1_mask, out, stats-or-None)."""
+    arr = (psr_batch_item * len(items))()
+    for k, (samples, ham, u1, out, stats) in enumerate(items):
+        arr[k].samples = _ptr(samples)
+        arr[k].n = int(samples.shape[0])
+        arr[k].ham = ham
+        arr[k].u1_mask = int(bool(u1))
+        arr[k].out = _ptr(out)
+        arr[k].stats = _ptr(stats)
+    _check(lib().psr_local_energy_batch(C.byref(params), arr, len(items)), "psr_local_energy_batch")

@@ -177,6 +177,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 struct Misc {
     uint64_t mbar[2];
     long long job[2];
+    long long base[kMaxGroups + 1];  // first job of each group
     uint32_t tmem_base;
     int abort_flag[2];
 };
@@ -481,8 +482,8 @@ __device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__re
 // halves swap h_31 and (P_63, S_63) through mailboxes inside the B tile, then
 // each writes its part of the tile.
 __global__ void __launch_bounds__(kThreads, 1)
-fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__restrict__ pk,
-                F32Layout fl) {
+fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ pkb,
+                const float *__restrict__ pk, F32Layout fl) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -517,6 +518,12 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
         mbar_init(smem_u32(&M.mbar[1]), 1);
         M.abort_flag[0] = 0;
         M.abort_flag[1] = 0;
+        long long b = 0;
+        M.base[0] = 0;
+        for (int i = 0; i < jb.n_groups; ++i) {
+            b += jb.mode == 1 ? (long long)*jb.g[i].n_jobs_dev : (long long)jb.g[i].n_jobs;
+            M.base[i + 1] = b;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     {
@@ -555,9 +562,7 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
     const uint32_t dC = dZ + 64;
     const uint32_t aW = tmem + kTmemWeightCol;
 
-    const int N = jb.N;
-    const int nch = (N + CH - 1) / CH;
-    const long long njobs = jb.mode == 1 ? (long long)*jb.n_jobs_dev : (long long)jb.n_jobs;
+    const long long njobs = M.base[jb.n_groups];
     const int bar_id = 1 + s;
     uint32_t phase = 0;
     bool aborted = false;
@@ -592,32 +597,38 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
         const long long job = M.job[s];
         sbar();
         if (job >= njobs) break;
+        int gi = 0;
+        while (gi + 1 < jb.n_groups && job >= M.base[gi + 1]) ++gi;
+        const FwdGroup &G = jb.g[gi];
+        const long long lj = job - M.base[gi];
+        const int N = G.N;
+        const int nch = (N + CH - 1) / CH;
 
         int sample, p = -1, q = -1, c0 = 0;
         if (jb.mode == 0) {
-            sample = (int)job;
+            sample = (int)lj;
         } else {
-            const int32_t *e = jb.entries + 3 * job;
+            const int32_t *e = G.entries + 3 * lj;
             sample = e[0];
             p = e[1];
             q = e[2];
             c0 = p / CH;
         }
-        const uint64_t *row = jb.bits + (int64_t)sample * jb.W;
+        const uint64_t *row = G.bits + (int64_t)sample * G.W;
         float cr[NL] = {0.0f, 0.0f, 0.0f};  // scan carries (used by half 0)
         if (hf == 0 && c0 > 0) {
-            const float *cin = jb.carries_in + (((int64_t)sample * nch + c0) * NL) * H + j;
+            const float *cin = G.carries_in + (((int64_t)sample * nch + c0) * NL) * H + j;
             cr[0] = cin[0];
             cr[1] = cin[H];
             cr[2] = cin[2 * H];
         }
-        int n_up = jb.u1 ? count_up_before(row, c0 * CH) : 0;
+        int n_up = G.u1 ? count_up_before(row, c0 * CH) : 0;
         float acc = 0.0f;
 
         for (int c = c0; c < nch && !aborted; ++c) {
             const int t0 = c * CH;
-            if (hf == 0 && jb.carries_out) {
-                float *co = jb.carries_out + (((int64_t)sample * nch + c) * NL) * H + j;
+            if (hf == 0 && G.carries_out) {
+                float *co = G.carries_out + (((int64_t)sample * nch + c) * NL) * H + j;
                 co[0] = cr[0];
                 co[H] = cr[1];
                 co[2 * H] = cr[2];
@@ -784,9 +795,9 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
                     if (tt < N) {
                         const int sbit = (int)((cur >> t) & 1ull);
                         const int nu = n_up + __popcll(cur & ((1ull << t) - 1ull));
-                        const float lp = site_logp(d, sbit, u1_forced(jb.u1, N, tt, nu));
-                        if (jb.logp_out) jb.logp_out[(int64_t)sample * N + tt] = lp;
-                        sv = (jb.mode == 1) ? lp - jb.logp_ref[(int64_t)sample * N + tt] : lp;
+                        const float lp = site_logp(d, sbit, u1_forced(G.u1, N, tt, nu));
+                        if (G.logp_out) G.logp_out[(int64_t)sample * N + tt] = lp;
+                        sv = (jb.mode == 1) ? lp - G.logp_ref[(int64_t)sample * N + tt] : lp;
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
@@ -799,7 +810,7 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
             }
         }
         if (aborted) break;
-        if (issuer) jb.out[job] = 0.5f * acc;
+        if (issuer) G.out[lj] = 0.5f * acc;
     }
 
     // ------------------------------------------------------------ teardown
@@ -813,14 +824,25 @@ fwd_bf16_kernel(FwdJobs jb, const uint8_t *__restrict__ pkb, const float *__rest
     }
 }
 
+cudaError_t prepare_fwd_bf16() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(fwd_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
 cudaError_t launch_fwd_bf16(const FwdJobs &jobs, const void *packed_bf16, const float *packed_f32,
                             const F32Layout &fl, int num_sms, cudaStream_t stream) {
     if (fl.H != H || fl.nL != NL) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fwd_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+    cudaError_t e = prepare_fwd_bf16();
     if (e != cudaSuccess) return e;
     int64_t grid = num_sms;
-    const int64_t max_jobs_streams = (jobs.n_jobs + 1) / 2;
+    const int64_t max_jobs_streams = (max_jobs(jobs) + 1) / 2;
     if (grid > max_jobs_streams) grid = max_jobs_streams;
     if (grid < 1) grid = 1;
     fwd_bf16_kernel<<<(int)grid, kThreads, kSmemBytes, stream>>>(

@@ -151,8 +151,8 @@ cudaError_t launch_bitpack(const uint8_t *spins, int64_t n, int N, int W, uint64
 }
 
 template <int H>
-__global__ void __launch_bounds__(H) fwd_f32_kernel(FwdJobs jb, const float *__restrict__ pk,
-                                                   F32Layout fl) {
+__global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJobs jb,
+                                                   const float *__restrict__ pk, F32Layout fl) {
     constexpr int CH = kChunkF32;
     constexpr int LD = CH + 4;  // padded row: conflict-free float4 row writes
     extern __shared__ __align__(16) float smem[];
@@ -160,12 +160,20 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(FwdJobs jb, const float *__r
     float *hs = xs + H * LD;       // [H][LD] hidden states of the chunk
     float *hcar = hs + H * LD;     // [kMaxLayers][H] scan carries
     __shared__ long long s_job;
+    __shared__ long long s_base[kMaxGroups + 1];
 
     const int j = threadIdx.x;
     const int nL = fl.nL;
-    const int N = jb.N;
-    const int nch = (N + CH - 1) / CH;
-    const long long njobs = jb.mode == 1 ? (long long)*jb.n_jobs_dev : (long long)jb.n_jobs;
+    if (j == 0) {
+        long long b = 0;
+        s_base[0] = 0;
+        for (int i = 0; i < jb.n_groups; ++i) {
+            b += jb.mode == 1 ? (long long)*jb.g[i].n_jobs_dev : (long long)jb.g[i].n_jobs;
+            s_base[i + 1] = b;
+        }
+    }
+    __syncthreads();
+    const long long njobs = s_base[jb.n_groups];
 
     const float a0_0 = pk[fl.A0 + j], a0_1 = pk[fl.A0 + H + j], a0_2 = pk[fl.A0 + 2 * H + j];
     const float b0_0 = pk[fl.B0 + j], b0_1 = pk[fl.B0 + H + j], b0_2 = pk[fl.B0 + 2 * H + j];
@@ -178,29 +186,35 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(FwdJobs jb, const float *__r
         const long long job = s_job;
         __syncthreads();
         if (job >= njobs) break;
+        int gi = 0;
+        while (gi + 1 < jb.n_groups && job >= s_base[gi + 1]) ++gi;
+        const FwdGroup &G = jb.g[gi];
+        const long long lj = job - s_base[gi];
+        const int N = G.N;
+        const int nch = (N + CH - 1) / CH;
 
         int sample, p = -1, q = -1, c0 = 0;
         if (jb.mode == 0) {
-            sample = (int)job;
+            sample = (int)lj;
         } else {
-            const int32_t *e = jb.entries + 3 * job;
+            const int32_t *e = G.entries + 3 * lj;
             sample = e[0];
             p = e[1];
             q = e[2];
             c0 = p / CH;
         }
-        const uint64_t *row = jb.bits + (int64_t)sample * jb.W;
+        const uint64_t *row = G.bits + (int64_t)sample * G.W;
         for (int l = 0; l < nL; ++l)
             hcar[l * H + j] = (c0 == 0) ? 0.0f
-                : jb.carries_in[(((int64_t)sample * nch + c0) * nL + l) * H + j];
-        int n_up = jb.u1 ? count_up_before(row, c0 * CH) : 0;
+                : G.carries_in[(((int64_t)sample * nch + c0) * nL + l) * H + j];
+        int n_up = G.u1 ? count_up_before(row, c0 * CH) : 0;
         float acc = 0.0f;
 
         for (int c = c0; c < nch; ++c) {
             const int t0 = c * CH;
-            if (jb.carries_out)
+            if (G.carries_out)
                 for (int l = 0; l < nL; ++l)
-                    jb.carries_out[(((int64_t)sample * nch + c) * nL + l) * H + j] = hcar[l * H + j];
+                    G.carries_out[(((int64_t)sample * nch + c) * nL + l) * H + j] = hcar[l * H + j];
             uint32_t cur, prev;
             chunk_bits32(row, t0, p, q, cur, prev);
             const int nvalid = min(CH, N - t0);
@@ -323,9 +337,9 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(FwdJobs jb, const float *__r
                 if (tt < N) {
                     const int s = (cur >> t) & 1u;
                     const int nu = n_up + __popc(cur & ((1u << t) - 1u));
-                    const float lp = site_logp(d, s, u1_forced(jb.u1, N, tt, nu));
-                    if (jb.logp_out) jb.logp_out[(int64_t)sample * N + tt] = lp;
-                    v = (jb.mode == 1) ? lp - jb.logp_ref[(int64_t)sample * N + tt] : lp;
+                    const float lp = site_logp(d, s, u1_forced(G.u1, N, tt, nu));
+                    if (G.logp_out) G.logp_out[(int64_t)sample * N + tt] = lp;
+                    v = (jb.mode == 1) ? lp - G.logp_ref[(int64_t)sample * N + tt] : lp;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -334,7 +348,7 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(FwdJobs jb, const float *__r
             n_up += __popc(cur);
             __syncthreads();
         }
-        if (j == 0) jb.out[job] = 0.5f * acc;
+        if (j == 0) G.out[lj] = 0.5f * acc;
     }
 }
 
@@ -347,7 +361,8 @@ static cudaError_t launch_fwd_f32_h(const FwdJobs &jobs, const float *packed, co
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
-    if (jobs.n_jobs < grid) grid = jobs.n_jobs;
+    const int64_t nj = max_jobs(jobs);
+    if (nj < grid) grid = nj;
     if (grid < 1) grid = 1;
     fwd_f32_kernel<H><<<(int)grid, H, smem, stream>>>(jobs, packed, fl);
     return cudaGetLastError();

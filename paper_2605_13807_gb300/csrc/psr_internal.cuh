@@ -43,19 +43,22 @@ struct F32Layout {
 };
 F32Layout f32_layout(int nL, int H);
 
-// One batch of sequence evaluations ("jobs") for the forward kernels.
-//   mode 0: job i evaluates sample i from site 0 (full forward).
+// Sequence evaluations ("jobs") for the forward kernels, in up to
+// kMaxGroups groups (one per lattice / sample set).  Jobs are numbered
+// across the groups in order; a kernel maps a job to its group with the
+// group sizes (read on the device in mode 1).
+//   mode 0: job i of a group evaluates sample i from site 0 (full forward).
 //   mode 1: job e evaluates the connected configuration of entries[e] =
 //           (sample, p, q): the sample with sites p and q (q may be -1)
 //           flipped, resuming from the chunk containing p with the stored
 //           carries; the result is 1/2 sum_{t >= chunk start} (log P'_t -
 //           log P_t(sample)) = log psi(s') - log psi(s).
-struct FwdJobs {
-    int mode;
+constexpr int kMaxGroups = 8;
+struct FwdGroup {
     int N;                       // sites
-    int W;                       // 64-bit words per bit-packed row (>= ceil(N/64))
-    int u1;                      // u1 masking
-    int64_t n_jobs;              // number of jobs (mode 0) or capacity (mode 1)
+    int u1;                      // zero-magnetisation masking
+    int W;                       // 64-bit words per bit-packed row (>= ceil(N/64) + 1)
+    int64_t n_jobs;              // mode 0: number of samples; mode 1: capacity
     const int64_t *n_jobs_dev;   // mode 1: device count of valid jobs
     const uint64_t *bits;        // [n_samples][W] bit-packed spins
     const int32_t *entries;      // mode 1: [E][3]
@@ -64,9 +67,21 @@ struct FwdJobs {
     float *out;                  // mode 0: [n] log psi; mode 1: [E] delta
     float *logp_out;             // mode 0, optional: [n][N]
     float *carries_out;          // mode 0, optional: [n][nch][nL][H]
+};
+struct FwdJobs {
+    int mode;
+    int n_groups;
+    FwdGroup g[kMaxGroups];
     unsigned long long *job_counter;  // zeroed before launch
     int *status;                 // device status word
 };
+
+// Upper bound of the job count (mode 1 uses capacities).
+inline int64_t max_jobs(const FwdJobs &jb) {
+    int64_t n = 0;
+    for (int i = 0; i < jb.n_groups; ++i) n += jb.g[i].n_jobs;
+    return n;
+}
 
 // ---------------------------------------------------------------- launchers
 // Every launcher enqueues on `stream` and returns a cudaError_t.
@@ -84,6 +99,8 @@ cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, vo
                                    cudaStream_t stream);
 cudaError_t launch_fwd_bf16(const FwdJobs &jobs, const void *packed_bf16, const float *packed_f32,
                             const F32Layout &fl, int num_sms, cudaStream_t stream);
+// Sets the kernel's shared-memory attribute on the current device (once).
+cudaError_t prepare_fwd_bf16();
 
 // Hamiltonian side.
 struct HamDev {

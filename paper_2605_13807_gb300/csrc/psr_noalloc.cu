@@ -146,12 +146,13 @@ extern "C" int psr_logpsi_noalloc(const psr_params *params, const uint8_t *spins
             return rc;
         FwdJobs jb{};
         jb.mode = 0;
-        jb.N = L;
-        jb.W = (int)W;
-        jb.u1 = params->u1_mask;
-        jb.n_jobs = cnt;
-        jb.bits = bits;
-        jb.out = out + first;
+        jb.n_groups = 1;
+        jb.g[0].u1 = params->u1_mask;
+        jb.g[0].N = L;
+        jb.g[0].W = (int)W;
+        jb.g[0].n_jobs = cnt;
+        jb.g[0].bits = bits;
+        jb.g[0].out = out + first;
         jb.job_counter = counter;
         jb.status = status;
         rc = to_rc(bf16 ? launch_fwd_bf16(jb, pkb, pk, fl, dev->num_sms, st)
