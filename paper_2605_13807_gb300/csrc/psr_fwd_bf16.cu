@@ -23,6 +23,7 @@
 // configurations resumed from a stored chunk carry) come from an atomic
 // counter.  Every mbarrier wait is bounded; on expiry the CTA records
 // PSR_ETIMEOUT, stops issuing work, frees its TMEM and returns.
+#include <cstddef>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -182,6 +183,7 @@ struct Misc {
     int abort_flag[2];
 };
 static_assert(sizeof(Misc) <= MISC_BYTES, "misc block too large");
+static_assert(offsetof(Misc, mbar) == 0, "mbarriers open the misc block");
 
 // --------------------------------------------------- epilogue arithmetic
 // Approximate-unit forms used only by this BF16 path (every value they
@@ -212,6 +214,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
 #define PSR_AS7128_A5 0.0002765672f
 #define PSR_AS7128_A6 0.0000430638f
 
+// log P(s | .) from the logit difference with the fast exponential and
+// logarithm (absolute error ~1e-7, far below the BF16 path's tolerance).
+__device__ __forceinline__ float site_logp_fast(float d, int s, int forced) {
+    if (forced >= 0) return (s == forced) ? 0.0f : -INFINITY;
+    const float x = s ? -d : d;  // log P = -softplus(x)
+    return -(fmaxf(x, 0.0f) + __logf(1.0f + __expf(-fabsf(x))));
+}
+
 // Packed two-site forms (FP32x2: each lane is an IEEE FP32 operation, so the
 // results equal the scalar ones; one instruction serves two sites).
 __device__ __forceinline__ float2 gelu_fast2(float2 x) {
@@ -232,6 +242,26 @@ __device__ __forceinline__ float2 gelu_fast2(float2 x) {
                                  copysignf(1.0f - rcp_approx(p.y), x.y));
     const float2 hx = __fmul2_rn(make_float2(0.5f, 0.5f), x);
     return __ffma2_rn(hx, e, hx);
+}
+
+// GELU for outputs that are rounded to BF16 right away (layers 0 and 1):
+// GELU(x) ~= x/2 (1 + tanh(x (g1 + g3 s + g5 s^2))), s = min(x^2, 36), with
+// (g1, g3, g5) fitted here to minimise the maximum error against the exact erf
+// GELU (2.6e-5 in FP32 arithmetic; tanh.approx adds at most ~2.5e-4 |x|,
+// below the BF16 rounding step 2^-8 |x| of an activation of that size).
+#define PSR_GELU_G1 7.975078843e-01f
+#define PSR_GELU_G3 3.700564602e-02f
+#define PSR_GELU_G5 -3.515167885e-04f
+
+__device__ __forceinline__ float2 gelu_bf16out2(float2 x) {
+    float2 sq = __fmul2_rn(x, x);
+    sq = make_float2(fminf(sq.x, 36.0f), fminf(sq.y, 36.0f));
+    float2 p = __ffma2_rn(make_float2(PSR_GELU_G5, PSR_GELU_G5), sq, make_float2(PSR_GELU_G3, PSR_GELU_G3));
+    p = __ffma2_rn(p, sq, make_float2(PSR_GELU_G1, PSR_GELU_G1));
+    const float2 arg = __fmul2_rn(p, x);
+    const float2 t = make_float2(tanh_approx(arg.x), tanh_approx(arg.y));
+    const float2 hx = __fmul2_rn(make_float2(0.5f, 0.5f), x);
+    return __ffma2_rn(hx, t, hx);
 }
 
 // Gate a = sigmoid(z + b_z) = 1/2 + 1/2 tanh((z + b_z)/2) and the scan input
@@ -318,29 +348,65 @@ cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, vo
     return cudaGetLastError();
 }
 
+// MMA issue for stream S.  Every operand is a compile-time offset from two
+// warp-uniform bases -- the CTA's shared-memory window (sbase) and TMEM
+// column 0 (the kernel owns all 512 columns, so its allocation starts
+// there) -- so the tensor-core descriptors stay in uniform registers.
+template <int S>
+__device__ __forceinline__ void issue_l0(uint32_t sbase) {
+    const uint32_t tH = sbase + OFF_TILES + (2 * S + 1) * kTileBytes;
+    const uint32_t wC = sbase + OFF_W + SM_C0 * kMatBytes;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+        mma_ss(128 * S, sdesc(wC + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
+               sdesc(tH + kk * 2048, 1024, 1024), kk > 0);
+    mma_commit(sbase + OFF_MISC + 8 * S);
+}
+
+template <int S, int L>
+__device__ __forceinline__ void issue_proj(uint32_t sbase) {
+    const uint32_t tX = sbase + OFF_TILES + (2 * S) * kTileBytes;
+    const uint32_t wz = kTmemWeightCol + (L == 1 ? TM_WZ1 : TM_WZ2) * 64;
+    const uint32_t wh = kTmemWeightCol + (L == 1 ? TM_WH1 : TM_WH2) * 64;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) mma_ts(128 * S, wz + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+        mma_ts(128 * S + 64, wh + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
+    mma_commit(sbase + OFF_MISC + 8 * S);
+}
+
+template <int S, int L>
+__device__ __forceinline__ void issue_out(uint32_t sbase) {
+    const uint32_t tX = sbase + OFF_TILES + (2 * S) * kTileBytes;
+    const uint32_t tH = tX + kTileBytes;
+    const uint32_t wC = sbase + OFF_W + (L == 1 ? SM_C1 : SM_C2) * kMatBytes;
+    const uint32_t wD = sbase + OFF_W + (L == 1 ? SM_D1 : SM_D2) * kMatBytes;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+        mma_ss(128 * S, sdesc(wC + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
+               sdesc(tH + kk * 2048, 1024, 1024), kk > 0);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+        mma_ss(128 * S, sdesc(wD + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
+               sdesc(tX + kk * 2048, 1024, 1024), 1);
+    mma_commit(sbase + OFF_MISC + 8 * S);
+}
+
 // One dense layer (l = 1 or 2) of one stream half, from the proj MMA to the
 // output epilogue.  h1: layer 1 writes its FP32 h there (the residual of
 // layer 2); layer 2 adds it and overwrites it with the layer output x3.
 template <int L, class WaitF, class PubF, class BarF>
-__device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__restrict__ pk,
-                                            const F32Layout &fl, uint8_t *tileX, uint8_t *tileH,
-                                            uint32_t tX, uint32_t tH, uint32_t wsm, uint32_t aW,
-                                            uint32_t dZ, uint32_t dC, uint32_t accZ, uint32_t accC,
-                                            uint32_t bar, bool issuer, int hf, int j, float &carry,
-                                            float (&h1)[32], WaitF &sync_wait, PubF &publish,
-                                            BarF &sbar) {
-    const uint32_t wz = aW + (L == 1 ? TM_WZ1 : TM_WZ2) * 64;
-    const uint32_t wh = aW + (L == 1 ? TM_WH1 : TM_WH2) * 64;
+__device__ __forceinline__ bool dense_layer(float hbz, float bh,
+                                            uint8_t *tileX, uint8_t *tileH, uint32_t sbase, int s,
+                                            uint32_t accZ, uint32_t accC, bool issuer, int hf, int j,
+                                            float &carry, float (&h1)[32], WaitF &sync_wait,
+                                            PubF &publish, BarF &sbar) {
     if (issuer) {
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_ts(dZ, wz + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_ts(dC, wh + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
-        mma_commit(bar);
+        if (s == 0) issue_proj<0, L>(sbase);
+        else issue_proj<1, L>(sbase);
     }
     if (!sync_wait()) return false;
-    const float hbz = 0.5f * pk[fl.bz[L] + threadIdx.x % 128];
-    const float bh = pk[fl.bh[L] + threadIdx.x % 128];
     const float2 hbz2 = make_float2(hbz, hbz), bh2 = make_float2(bh, bh);
     // gates + scan; half 0 from the carry, half 1 as prefix pairs (P, S)
     float keep[8];
@@ -437,17 +503,9 @@ __device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__re
         }
     }
     publish();
-    constexpr int sC = (L == 1) ? SM_C1 : SM_C2, sD = (L == 1) ? SM_D1 : SM_D2;
     if (issuer) {
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-            mma_ss(dZ, sdesc(wsm + sC * kMatBytes + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-                   sdesc(tH + kk * 2048, 1024, 1024), kk > 0);
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-            mma_ss(dZ, sdesc(wsm + sD * kMatBytes + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-                   sdesc(tX + kk * 2048, 1024, 1024), 1);
-        mma_commit(bar);
+        if (s == 0) issue_out<0, L>(sbase);
+        else issue_out<1, L>(sbase);
     }
     if (!sync_wait()) return false;
 #pragma unroll
@@ -460,7 +518,7 @@ __device__ __forceinline__ bool dense_layer(const FwdJobs &jb, const float *__re
         for (int i = 0; i < 8; i += 2) {
             float2 y = make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1]));
             if (L == 2) y = __fadd2_rn(y, make_float2(h1[8 * g + i], h1[8 * g + i + 1]));
-            const float2 x = gelu_fast2(y);
+            const float2 x = (L == 1) ? gelu_bf16out2(y) : gelu_fast2(y);
             xv[i] = x.x;
             xv[i + 1] = x.y;
             if (L == 2) {
@@ -501,8 +559,7 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
 
     uint8_t *tileX = smem + OFF_TILES + (2 * s) * kTileBytes;
     uint8_t *tileH = tileX + kTileBytes;
-    const uint32_t wsm = smem_u32(smem + OFF_W);
-    const uint32_t tX = smem_u32(tileX), tH = smem_u32(tileH);
+    const uint32_t sbase = smem_u32(smem);
     const uint32_t bar = smem_u32(&M.mbar[s]);
 
     // ------------------------------------------------------------- set-up
@@ -535,7 +592,7 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
     tc_before();
     __syncthreads();
     tc_after();
-    const uint32_t tmem = M.tmem_base;
+    const uint32_t tmem = M.tmem_base;  // 0: the kernel owns all 512 columns
     if (wg == 0) {
 #pragma unroll 1
         for (int m = 0; m < kTmemMats; ++m) {
@@ -555,14 +612,24 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
     __syncthreads();
     tc_after();
 
-    const uint32_t lane_off = (uint32_t)lane_base << 16;
-    const uint32_t accZ = tmem + lane_off + 128 * s + 32 * hf;  // this half's Z columns
-    const uint32_t accC = accZ + 64;                              // this half's C columns
-    const uint32_t dZ = tmem + 128 * s;
-    const uint32_t dC = dZ + 64;
-    const uint32_t aW = tmem + kTmemWeightCol;
+    // per-unit constants, read once (shared memory holds no room for them and
+    // the L1 left beside 227 KB of shared memory does not keep them)
+    const float a0_0 = pk[fl.A0 + j], a0_1 = pk[fl.A0 + H + j], a0_2 = pk[fl.A0 + 2 * H + j];
+    const float b0_0 = pk[fl.B0 + j], b0_1 = pk[fl.B0 + H + j], b0_2 = pk[fl.B0 + 2 * H + j];
+    const float d0_0 = pk[fl.DU0 + j], d0_1 = pk[fl.DU0 + H + j], d0_2 = pk[fl.DU0 + 2 * H + j];
+    const float hbz1 = 0.5f * pk[fl.bz[1] + j], bh1 = pk[fl.bh[1] + j];
+    const float hbz2 = 0.5f * pk[fl.bz[2] + j], bh2 = pk[fl.bh[2] + j];
+    const float wdj = pk[fl.wd + j];
+    const float bd = pk[fl.bd];
 
-    const long long njobs = M.base[jb.n_groups];
+    const uint32_t lane_off = (uint32_t)lane_base << 16;
+    const uint32_t accZ = lane_off + 128 * s + 32 * hf;  // this half's Z columns
+    const uint32_t accC = accZ + 64;                     // this half's C columns
+
+    // all 512 columns belong to this CTA, so the allocation starts at column 0;
+    // anything else is reported and no work is done
+    const long long njobs = (tmem == 0) ? M.base[jb.n_groups] : 0;
+    if (tmem != 0 && tid == 0) set_status(jb.status, PSR_EDEVICE);
     const int bar_id = 1 + s;
     uint32_t phase = 0;
     bool aborted = false;
@@ -624,6 +691,8 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
         }
         int n_up = G.u1 ? count_up_before(row, c0 * CH) : 0;
         float acc = 0.0f;
+        uint64_t next_word = row[c0];
+        uint32_t next_prev = (c0 > 0) ? (uint32_t)(row[c0 - 1] >> 63) : 0u;
 
         for (int c = c0; c < nch && !aborted; ++c) {
             const int t0 = c * CH;
@@ -633,8 +702,15 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
                 co[H] = cr[1];
                 co[2 * H] = cr[2];
             }
-            uint64_t cur = row[c];
-            uint32_t prev = (c > 0) ? (uint32_t)(row[c - 1] >> 63) : 0u;
+            uint64_t cur = next_word;
+            uint32_t prev = next_prev;
+            // next chunk's spins and this chunk's reference log P are fetched now,
+            // long before they are needed
+            next_prev = (uint32_t)(cur >> 63);
+            if (c + 1 < nch) next_word = row[c + 1];
+            float lp_ref = 0.0f;
+            if (jb.mode == 1 && (warp & 3) == 0 && t0 + 32 * hf + lane < N)
+                lp_ref = G.logp_ref[(int64_t)sample * N + t0 + 32 * hf + lane];
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const int x = f ? q : p;
@@ -651,8 +727,6 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
 
             // ---------------- layer 0: lookup gates, scan -> tile H
             {
-                const float a0_0 = pk[fl.A0 + j], a0_1 = pk[fl.A0 + H + j], a0_2 = pk[fl.A0 + 2 * H + j];
-                const float b0_0 = pk[fl.B0 + j], b0_1 = pk[fl.B0 + H + j], b0_2 = pk[fl.B0 + 2 * H + j];
                 float keep[8];  // half 0: sites 0..7, written after the mailbox swap
                 float h31 = 0.0f;
                 if (hf == 0) {
@@ -722,15 +796,11 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
             }
             publish();
             if (issuer) {
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk)
-                    mma_ss(dZ, sdesc(wsm + SM_C0 * kMatBytes + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-                           sdesc(tH + kk * 2048, 1024, 1024), kk > 0);
-                mma_commit(bar);
+                if (s == 0) issue_l0<0>(sbase);
+                else issue_l0<1>(sbase);
             }
             if (!sync_wait()) { aborted = true; break; }
             // epilogue: x1 = GELU(C0 h0 + D0 u) -> tile X
-            const float d0_0 = pk[fl.DU0 + j], d0_1 = pk[fl.DU0 + H + j], d0_2 = pk[fl.DU0 + 2 * H + j];
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
                 uint32_t r[8];
@@ -742,7 +812,7 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
                     float du0 = ((inbits >> (8 * g + i)) & 1u) ? d0_2 : d0_1;
                     const float du1 = ((inbits >> (8 * g + i + 1)) & 1u) ? d0_2 : d0_1;
                     if (g == 0 && i == 0 && seq_start) du0 = d0_0;
-                    const float2 x = gelu_fast2(__fadd2_rn(
+                    const float2 x = gelu_bf16out2(__fadd2_rn(
                         make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1])), make_float2(du0, du1)));
                     xv[i] = x.x;
                     xv[i + 1] = x.y;
@@ -752,18 +822,16 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
             publish();
 
             // ---------------- layers 1 and 2
-            if (!dense_layer<1>(jb, pk, fl, tileX, tileH, tX, tH, wsm, aW, dZ, dC, accZ, accC, bar,
-                                issuer, hf, j, cr[1], h1, sync_wait, publish, sbar))
+            if (!dense_layer<1>(hbz1, bh1, tileX, tileH, sbase, s, accZ, accC, issuer, hf, j, cr[1], h1,
+                                sync_wait, publish, sbar))
                 { aborted = true; break; }
-            if (!dense_layer<2>(jb, pk, fl, tileX, tileH, tX, tH, wsm, aW, dZ, dC, accZ, accC, bar,
-                                issuer, hf, j, cr[2], h1, sync_wait, publish, sbar))
+            if (!dense_layer<2>(hbz2, bh2, tileX, tileH, sbase, s, accZ, accC, issuer, hf, j, cr[2], h1,
+                                sync_wait, publish, sbar))
                 { aborted = true; break; }
             float (&xo)[32] = h1;  // layer-2 output (x3) of this half
 
             // ---------------- readout: d_t = wd . x3_t + bd over the 128 units
             {
-                const float wdj = pk[fl.wd + j];
-                const float bd = pk[fl.bd];
                 float v[32];
 #pragma unroll
                 for (int i = 0; i < 32; i += 2) {
@@ -795,9 +863,9 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
                     if (tt < N) {
                         const int sbit = (int)((cur >> t) & 1ull);
                         const int nu = n_up + __popcll(cur & ((1ull << t) - 1ull));
-                        const float lp = site_logp(d, sbit, u1_forced(G.u1, N, tt, nu));
+                        const float lp = site_logp_fast(d, sbit, u1_forced(G.u1, N, tt, nu));
                         if (G.logp_out) G.logp_out[(int64_t)sample * N + tt] = lp;
-                        sv = (jb.mode == 1) ? lp - G.logp_ref[(int64_t)sample * N + tt] : lp;
+                        sv = (jb.mode == 1) ? lp - lp_ref : lp;
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);

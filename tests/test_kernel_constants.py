@@ -15,6 +15,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "paper_2605_13807_gb300", "csrc", "psr_fwd_bf16.cu")
 
 
+def _gelu_fit():
+    src = open(SRC).read()
+    vals = {k: float(v) for k, v in re.findall(r"#define PSR_GELU_(G\d) ([0-9.eE+-]+)f", src)}
+    assert sorted(vals) == ["G1", "G3", "G5"]
+    return vals["G1"], vals["G3"], vals["G5"]
+
+
 def _coeffs():
     src = open(SRC).read()
     vals = {int(k): float(v) for k, v in re.findall(r"#define PSR_AS7128_A(\d) ([0-9.eE+-]+)f", src)}
@@ -39,3 +46,22 @@ def test_gelu_from_as7128_is_close_to_exact_gelu():
     gelu = 0.5 * x * (1.0 + np.sign(x) * e)
     exact = 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))
     assert np.max(np.abs(gelu - exact)) <= 3.0e-7 * 0.5 * 12.0
+
+
+def test_fitted_tanh_gelu_error_is_far_below_bf16_rounding():
+    """The layer-0/1 GELU form (outputs rounded to BF16 at once) stays within
+    3e-5 of the exact GELU in FP32 arithmetic; a 2^-11 relative error in tanh
+    adds at most 2.5e-4 |x|, under the BF16 rounding step (2^-8 |x|) of an
+    activation of the same magnitude."""
+    g1, g3, g5 = (np.float32(v) for v in _gelu_fit())
+    x = np.linspace(-16.0, 16.0, 320001).astype(np.float32)
+    s = np.minimum(x * x, np.float32(36.0))
+    arg = x * ((g5 * s + g3) * s + g1)
+    t = np.tanh(arg.astype(np.float64))
+    exact = 0.5 * x.astype(np.float64) * (1.0 + erf(x.astype(np.float64) / np.sqrt(2.0)))
+    approx = 0.5 * x * (1.0 + t.astype(np.float32))
+    assert np.max(np.abs(approx - exact)) <= 3.0e-5
+    for sgn in (1.0, -1.0):
+        tt = t * (1.0 + sgn * 2.0 ** -10.987)
+        worst = np.abs(0.5 * x * (1.0 + tt) - exact)
+        assert np.all(worst <= 2.5e-4 * np.abs(x) + 3.0e-5)
