@@ -16,7 +16,10 @@
 // lambda_t and a_{t+1} cross chunk boundaries in shared memory.  Thread j owns
 // hidden unit j for the per-unit work and input unit k = j for the
 // weight-gradient rows, which makes every parameter update a coalesced
-// read-modify-write by exactly one thread (deterministic, no atomics).
+// reduction issued by exactly one thread.  The updates are fire-and-forget
+// global reductions (no value returned, so the warp does not wait on memory);
+// a single writer per address adds in program order, so the sums are
+// deterministic.
 #include <cuda_runtime.h>
 
 #include "psr_device.cuh"
@@ -120,6 +123,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                 }
                 __syncthreads();
                 const float *Ct = pk + fl.CT[0];
+                #pragma unroll 4
                 for (int k = 0; k < H; ++k) {
                     const float w = Ct[k * H + j];
                     const float4 *src = reinterpret_cast<const float4 *>(S.hs + k * LD);
@@ -148,6 +152,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                 }
                 const float *Wz = pk + fl.WzT[l];
                 const float *Wh = pk + fl.WhT[l];
+                #pragma unroll 4
                 for (int k = 0; k < H; ++k) {
                     const float wz = Wz[k * H + j], wh = Wh[k * H + j];
                     const float4 *src = reinterpret_cast<const float4 *>(S.xs + k * LD);
@@ -182,6 +187,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                 for (int t = 0; t < CH; ++t) y[t] = (l >= 2) ? hprevl[t] : 0.0f;
                 const float *Ct = pk + fl.CT[l];
                 const float *Dt = pk + fl.DT[l];
+                #pragma unroll 4
                 for (int k = 0; k < H; ++k) {
                     const float wc = Ct[k * H + j], wd = Dt[k * H + j];
                     const float4 *sh = reinterpret_cast<const float4 *>(S.hs + k * LD);
@@ -238,11 +244,11 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                     gw += S.g1[t] * S.xl[t * (H + 1) + j];
                     gb += S.g1[t];
                 }
-                G[tl.Wo + H + j] += gw;
-                G[tl.Wo + j] -= gw;
+                atomicAdd(&G[tl.Wo + H + j], gw);
+                atomicAdd(&G[tl.Wo + j], -(gw));
                 if (j == 0) {
-                    G[tl.bo + 1] += gb;
-                    G[tl.bo] -= gb;
+                    atomicAdd(&G[tl.bo + 1], gb);
+                    atomicAdd(&G[tl.bo], -(gb));
                 }
             }
             // ------------------------------------------------ layers, top down
@@ -272,9 +278,16 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                 }
                 const float *Cw = theta + tl.C[l];
                 const float *Dw = theta + tl.D[l];
+                // weights of the next jj are fetched one iteration ahead
+                float cjk_n = Cw[j];
+                float djk_n = (l >= 1) ? Dw[j] : 0.0f;
                 for (int jj = 0; jj < H; ++jj) {
-                    const float cjk = Cw[(int64_t)jj * H + j];
-                    const float djk = (l >= 1) ? Dw[(int64_t)jj * H + j] : 0.0f;
+                    const float cjk = cjk_n;
+                    const float djk = djk_n;
+                    if (jj + 1 < H) {
+                        cjk_n = Cw[(int64_t)(jj + 1) * H + j];
+                        djk_n = (l >= 1) ? Dw[(int64_t)(jj + 1) * H + j] : 0.0f;
+                    }
                     float ac = 0.0f, ad = 0.0f;
 #pragma unroll
                     for (int t = 0; t < CH; ++t) {
@@ -284,8 +297,8 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                         ac += g * hk[t];
                         ad += g * uk[t];
                     }
-                    G[tl.C[l] + (int64_t)jj * H + j] += ac;
-                    if (l >= 1) G[tl.D[l] + (int64_t)jj * H + j] += ad;
+                    atomicAdd(&G[tl.C[l] + (int64_t)jj * H + j], ac);
+                    if (l >= 1) atomicAdd(&G[tl.D[l] + (int64_t)jj * H + j], ad);
                 }
                 if (l == 0) {
                     float d0 = 0.0f, d1 = 0.0f;
@@ -294,8 +307,8 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                         if (cd == 1) d0 += gy[t];
                         if (cd == 2) d1 += gy[t];
                     }
-                    G[tl.D[0] + 2 * j] += d0;
-                    G[tl.D[0] + 2 * j + 1] += d1;
+                    atomicAdd(&G[tl.D[0] + 2 * j], d0);
+                    atomicAdd(&G[tl.D[0] + 2 * j + 1], d1);
                 }
                 // reverse scan (thread j = hidden unit j)
                 {
@@ -329,9 +342,14 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                     float gn[CH];
 #pragma unroll
                     for (int t = 0; t < CH; ++t) gn[t] = gud[t];
+                    float wz_n = Wzw[j], wh_n = Whw[j];
                     for (int jj = 0; jj < H; ++jj) {
-                        const float wz = Wzw[(int64_t)jj * H + j];
-                        const float wh = Whw[(int64_t)jj * H + j];
+                        const float wz = wz_n;
+                        const float wh = wh_n;
+                        if (jj + 1 < H) {
+                            wz_n = Wzw[(int64_t)(jj + 1) * H + j];
+                            wh_n = Whw[(int64_t)(jj + 1) * H + j];
+                        }
                         float az = 0.0f, ah = 0.0f;
 #pragma unroll
                         for (int t = 0; t < CH; ++t) {
@@ -340,8 +358,8 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                             az += gzv * uk[t];
                             ah += gcv * uk[t];
                         }
-                        G[tl.Wz[l] + (int64_t)jj * H + j] += az;
-                        G[tl.Wh[l] + (int64_t)jj * H + j] += ah;
+                        atomicAdd(&G[tl.Wz[l] + (int64_t)jj * H + j], az);
+                        atomicAdd(&G[tl.Wh[l] + (int64_t)jj * H + j], ah);
                     }
 #pragma unroll
                     for (int t = 0; t < CH; ++t) {
@@ -356,18 +374,18 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                         if (cd == 1) { z0 += gzv; c0v += gcv; }
                         if (cd == 2) { z1 += gzv; c1v += gcv; }
                     }
-                    G[tl.Wz[0] + 2 * j] += z0;
-                    G[tl.Wz[0] + 2 * j + 1] += z1;
-                    G[tl.Wh[0] + 2 * j] += c0v;
-                    G[tl.Wh[0] + 2 * j + 1] += c1v;
+                    atomicAdd(&G[tl.Wz[0] + 2 * j], z0);
+                    atomicAdd(&G[tl.Wz[0] + 2 * j + 1], z1);
+                    atomicAdd(&G[tl.Wh[0] + 2 * j], c0v);
+                    atomicAdd(&G[tl.Wh[0] + 2 * j + 1], c1v);
                 }
                 (void)din;
                 __syncthreads();
             }
         }
         for (int l = 0; l < nL; ++l) {
-            G[tl.bz[l] + j] += gbz[l];
-            G[tl.bh[l] + j] += gbh[l];
+            atomicAdd(&G[tl.bz[l] + j], gbz[l]);
+            atomicAdd(&G[tl.bh[l] + j], gbh[l]);
         }
         __syncthreads();
     }

@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
             __syncthreads();
             {
                 const float *Ct = pk + fl.CT[0];
+                #pragma unroll 4
                 for (int k = 0; k < H; ++k) {
                     const float w = Ct[k * H + j];
                     const float4 *src = reinterpret_cast<const float4 *>(hs + k * LD);
@@ -270,6 +271,7 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                 for (int t = 0; t < CH; ++t) { z[t] = bz; y[t] = bh; }
                 const float *Wz = pk + fl.WzT[l];
                 const float *Wh = pk + fl.WhT[l];
+                #pragma unroll 4
                 for (int k = 0; k < H; ++k) {
                     const float wz = Wz[k * H + j], wh = Wh[k * H + j];
                     const float4 *src = reinterpret_cast<const float4 *>(xs + k * LD);
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                 for (int t = 0; t < CH; ++t) y[t] = (l >= 2) ? hl[t] : 0.0f;
                 const float *Ct = pk + fl.CT[l];
                 const float *Dt = pk + fl.DT[l];
+                #pragma unroll 4
                 for (int k = 0; k < H; ++k) {
                     const float wc = Ct[k * H + j], wd = Dt[k * H + j];
                     const float4 *sh = reinterpret_cast<const float4 *>(hs + k * LD);

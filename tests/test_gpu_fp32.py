@@ -218,3 +218,21 @@ def test_argument_errors():
     with pytest.raises(B.PsrError) as ei:
         api.local_energy(theta, _dev(inputs.random_spins(1, 4, 5)), api.ModelConfig(3, 64), ham)
     assert ei.value.code == B.PSR_EINVAL
+
+
+def test_gradient_is_deterministic():
+    """Gradient updates are reductions with one writer per address, so two
+    runs give identical bits (per-sample rows and the dout-weighted sum)."""
+    n_layers, H, N, n = 3, 128, 70, 12
+    theta = _dev(inputs.random_params(n_layers, H, seed=50, scale=1.0))
+    spins = _dev(inputs.random_spins(51, n, N))
+    dout = _dev((inputs.uniform(52, (n,)) - 0.5).astype(np.float32))
+    cfg = api.ModelConfig(n_layers, H, False, "fp32")
+    a = api.grad(theta, spins, cfg).clone()
+    b = api.grad(theta, spins, cfg)
+    api.sync()
+    assert torch.equal(a, b)
+    c = api.grad(theta, spins, cfg, dout=dout).clone()
+    d = api.grad(theta, spins, cfg, dout=dout)
+    api.sync()
+    assert torch.equal(c, d)
