@@ -57,6 +57,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-scan", action="store_true")
+    ap.add_argument("--scan-only", action="store_true",
+                    help="only the standalone scan measurement (profiling runs)")
+    ap.add_argument("--scan-n", type=int, default=0,
+                    help="sequences of the scan-only run (default: the workload's samples)")
+    ap.add_argument("--scan-tile", default="",
+                    help="units,chunk: fixed tile shape of the scan-only run (default: autotuned)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -135,15 +142,16 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def kernel_hash():
-    src = os.path.join(ROOT, "paper_2605_13807_gb300", "csrc", "psr_fwd_bf16.cu")
+def kernel_hash(src_name="psr_fwd_bf16.cu"):
+    src = os.path.join(ROOT, "paper_2605_13807_gb300", "csrc", src_name)
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic_per_unit():
-    """DRAM bytes per evaluated config-site of the connected-configuration
-    forward, from the committed ncu summary, if it matches the current kernel."""
-    path = os.path.join(ROOT, "profiles", "fwd_bf16_connected_52x52.md")
+def profiled_traffic_per_unit(profile="fwd_bf16_connected_52x52.md", src_name="psr_fwd_bf16.cu",
+                              key="dram bytes per evaluated config-site"):
+    """DRAM bytes per unit of work of a kernel, from its committed ncu
+    summary, if the summary was taken of the current kernel source."""
+    path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -151,10 +159,10 @@ def profiled_traffic_per_unit():
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel source sha256/16") != kernel_hash():
+    if vals.get("kernel source sha256/16") != kernel_hash(src_name):
         return None
     try:
-        return float(vals["dram bytes per evaluated config-site"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -223,6 +231,64 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+
+def scan_leg(args, n, N, dev, reps=5):
+    """The standalone chunked scan (psr_scan) over one layer's worth of the
+    workload: n sequences x N sites x 128 units, FP32 a, b -> h (12 bytes per
+    element from HBM; 17 GB per launch at 52x52, far above L2).  The tile
+    shape is picked by the context's autotuner on the first call."""
+    import torch
+
+    from paper_2605_13807_gb300 import api, binding as B, inputs
+    ctx = B.context()
+    B.psr_context_set_profiling(ctx, True)
+    a, b, h0 = inputs.scan_inputs_device(7, n, N, HIDDEN, dev)
+    h = torch.empty_like(a)
+    forced = tuple(int(x) for x in args.scan_tile.split(",")) if args.scan_tile else None
+    if forced is None:
+        B.psr_context_set_autotune(ctx, True)
+        api.scan(a, b, h0, out=h)
+        B.psr_context_set_autotune(ctx, False)
+        tile, tuned = B.psr_scan_tile_for(ctx, n, N, HIDDEN)
+    else:
+        tile, tuned = forced, False
+    for _ in range(3):
+        api.scan(a, b, h0, tile=forced, out=h)
+    ms = []
+    for _ in range(reps):
+        api.scan(a, b, h0, tile=forced, out=h)
+        ms.append(B.psr_context_stage_ms(ctx)["scan"])
+    api.sync()
+    elems = n * N * HIDDEN
+    algo = 12 * elems + 4 * n * HIDDEN
+    avg = sum(ms) / len(ms)
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs"))
+    achieved = algo / (avg / 1e3) / 1e9
+    tpe = profiled_traffic_per_unit("scan_52x52_layer.md", "psr_scan.cu",
+                                    "dram bytes per element")
+    del a, b, h0, h
+    torch.cuda.empty_cache()
+    return {"kernel": "scan_kernel (psr_scan, standalone chunked scan)",
+            "shape": [n, N, HIDDEN], "tile": {"units": tile[0], "chunk": tile[1]},
+            "tuned": tuned, "ms": avg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"hbm_gbs of {src}",
+                         "traffic": (tpe * elems if tpe is not None else None),
+                         "algorithmic_bytes_per_launch": algo, "bytes_per_unit": 12}}
+
+
+def run_scan_only(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    Lx, Ly, n = WORKLOADS[args.workload]
+    n = args.scan_n or n
+    torch.cuda.set_device(0)
+    print(json.dumps({"scan": scan_leg(args, n, Lx * Ly, torch.device("cuda", 0))}), flush=True)
+    return 0
+
 
 def run_mine(args):
     import numpy as np
@@ -378,6 +444,9 @@ def run_mine(args):
                              "note": "plain FP32 SIMT path, same workload on a sample subset"}
         del ok32
 
+    if not args.no_scan and rank == 0:
+        line["scan"] = scan_leg(args, n, N, dev)
+
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
         sp_h = torch.from_numpy(spins_np).pin_memory()
@@ -426,6 +495,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.scan_only:
+        return run_scan_only(args)
     return run_mine(args)
 
 

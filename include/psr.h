@@ -226,6 +226,45 @@ int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t 
 int psr_logpsi_noalloc(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
                        float *out, void *stream);
 
+/* Standalone scan of the diagonal linear recurrence at the heart of the
+ * minGRU layer (Eq. minGRU with a_t = 1 - z_t, b_t = z_t h~_t), evaluated as
+ * a chunked parallel scan (Sec. II.A, parallel-scan paragraph):
+ *     h_t = a_t * h_{t-1} + b_t,  t = 0 .. N-1,  h_{-1} = h0 (zero if NULL),
+ * element-wise over H units, independently for each of n sequences.
+ * a, b, h: float [n][N][H] row-major (H contiguous); h0: float [n][H] or
+ * NULL.  Host or device arrays (device arrays must be 16-byte aligned);
+ * h may alias a or b.  The kernel reads a and b and writes h once each
+ * (12 bytes per element from HBM); between chunks of one sequence the carry
+ * is passed through a look-back array in the workspace.
+ * PSR_EINVAL: null a, b or h, n < 1, N outside 1 .. 2^30, H not a positive
+ * multiple of 4, or a misaligned device array. */
+typedef struct {
+    int32_t units; /* units per tile: 4, 16, 32 or 128, dividing H */
+    int32_t chunk; /* sites per tile (>= N: one chunk per sequence) */
+} psr_scan_tile;
+
+int psr_scan(psr_context *ctx, const float *a, const float *b, const float *h0, int64_t n,
+             int32_t N, int32_t H, float *h);
+
+/* psr_scan with an explicit tile shape (PSR_EINVAL for an invalid one). */
+int psr_scan_tiled(psr_context *ctx, const float *a, const float *b, const float *h0, int64_t n,
+                   int32_t N, int32_t H, float *h, const psr_scan_tile *tile);
+
+/* The tile shape psr_scan will use for (n, N, H) on this context: the
+ * autotuned one if (n, N, H) has been tuned (*tuned = 1), else the built-in
+ * default (*tuned = 0).  tuned may be NULL. */
+int psr_scan_tile_for(psr_context *ctx, int64_t n, int32_t N, int32_t H, psr_scan_tile *tile,
+                      int32_t *tuned);
+
+/* Enables (1) or disables (0) the autotuner of this context.  While enabled,
+ * the first psr_scan of a shape (n, N, H) that is not being captured into a
+ * graph times every candidate tile shape (unit-block width x chunk length)
+ * on its own inputs with CUDA events, keeps the fastest for the context's
+ * lifetime and then computes its result with it; that first call
+ * synchronises the stream.  Every tile shape computes the same recurrence;
+ * results differ only by FP32 rounding of the composed maps. */
+int psr_context_set_autotune(psr_context *ctx, int enable);
+
 /* Stages of the launch sequence, for per-stage device timing. */
 enum {
     PSR_STAGE_PACK = 0,          /* parameter packing and spin bit-packing */
@@ -234,7 +273,8 @@ enum {
     PSR_STAGE_FWD_CONNECTED = 3, /* forward over the connected configurations */
     PSR_STAGE_GATHER = 4,        /* E_loc gather and FP64 statistics */
     PSR_STAGE_BWD = 5,           /* reverse-scan gradient and its reduction */
-    PSR_STAGE_COUNT = 6
+    PSR_STAGE_SCAN = 6,          /* psr_scan / psr_scan_tiled kernel */
+    PSR_STAGE_COUNT = 7
 };
 
 /* Enables (1) or disables (0) per-stage CUDA-event timing on the context's

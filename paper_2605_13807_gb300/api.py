@@ -3,6 +3,7 @@
     logpsi(theta, spins, ...)            -> float32 [n]
     local_energy(theta, samples, ham)    -> (float32 [n] E_loc, float64 [3] stats)
     connected(samples, ham)              -> (int64 [n+1], int32 [E, 3], float32 [n])
+    scan(a, b, h0=None)                  -> float32 [n, N, H], h_t = a_t h_{t-1} + b_t
     grad(theta, spins, dout=None)        -> float32 [n, P] (O_k) or [P]
     LogPsi.apply(theta, spins, cfg)      -> differentiable log psi; backward = psr_grad
 
@@ -100,6 +101,17 @@ def grad(theta, spins, cfg: ModelConfig, dout=None, out=None):
         out = torch.empty(shape, dtype=torch.float32, device=dev)
     p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
     return B.psr_grad(p, spins, dout, out)
+
+
+def scan(a, b, h0=None, tile=None, out=None):
+    """h_t = a_t h_{t-1} + b_t over float32 [n, N, H] tensors (psr_scan)."""
+    if out is None:
+        out = torch.empty_like(a)
+    return B.psr_scan(_ctx(), a, b, out, h0=h0, tile=tile)
+
+
+def set_autotune(enable=True):
+    B.psr_context_set_autotune(_ctx(), enable)
 
 
 def sync():

@@ -40,6 +40,10 @@ class psr_hamiltonian(C.Structure):
                 ("marshall", C.c_int32), ("J", C.c_double), ("h", C.c_double)]
 
 
+class psr_scan_tile(C.Structure):
+    _fields_ = [("units", C.c_int32), ("chunk", C.c_int32)]
+
+
 class psr_batch_item(C.Structure):
     _fields_ = [("samples", C.c_void_p), ("n", C.c_int64), ("ham", psr_hamiltonian),
                 ("u1_mask", C.c_int32), ("out", C.c_void_p), ("stats", C.c_void_p)]
@@ -48,8 +52,9 @@ class psr_batch_item(C.Structure):
 EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "psr_param_count",
             "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror",
             "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc",
-            "psr_local_energy_batch", "psr_context_set_graphs")
-STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd")
+            "psr_local_energy_batch", "psr_context_set_graphs", "psr_scan", "psr_scan_tiled",
+            "psr_scan_tile_for", "psr_context_set_autotune")
+STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan")
 
 _lib = None
 _lock = threading.Lock()
@@ -81,6 +86,11 @@ def lib():
                 L.psr_context_set_graphs.argtypes = [vp, C.c_int]
                 L.psr_context_set_profiling.argtypes = [vp, C.c_int]
                 L.psr_context_stage_ms.argtypes = [vp, C.c_int, C.POINTER(C.c_float)]
+                L.psr_scan.argtypes = [vp, vp, vp, vp, i64, i32, i32, vp]
+                L.psr_scan_tiled.argtypes = [vp, vp, vp, vp, i64, i32, i32, vp, C.POINTER(psr_scan_tile)]
+                L.psr_scan_tile_for.argtypes = [vp, i64, i32, i32, C.POINTER(psr_scan_tile),
+                                                C.POINTER(i32)]
+                L.psr_context_set_autotune.argtypes = [vp, C.c_int]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -227,3 +237,31 @@ def psr_local_energy_batch(params, items):
         arr[k].out = _ptr(out)
         arr[k].stats = _ptr(stats)
     _check(lib().psr_local_energy_batch(C.byref(params), arr, len(items)), "psr_local_energy_batch")
+
+
+def psr_scan(ctx, a, b, h, h0=None, tile=None):
+    """h_t = a_t h_{t-1} + b_t over [n, N, H] arrays; tile = (units, chunk)
+    forces a tile shape (psr_scan_tiled), None lets the context choose."""
+    n, N, H = a.shape
+    if tile is None:
+        _check(lib().psr_scan(C.c_void_p(ctx), _ptr(a), _ptr(b), _ptr(h0), int(n), int(N), int(H),
+                              _ptr(h)), "psr_scan")
+    else:
+        t = psr_scan_tile(int(tile[0]), int(tile[1]))
+        _check(lib().psr_scan_tiled(C.c_void_p(ctx), _ptr(a), _ptr(b), _ptr(h0), int(n), int(N),
+                                    int(H), _ptr(h), C.byref(t)), "psr_scan_tiled")
+    return h
+
+
+def psr_scan_tile_for(ctx, n, N, H):
+    """((units, chunk), tuned) that psr_scan would use for this shape."""
+    t = psr_scan_tile()
+    tuned = C.c_int32()
+    _check(lib().psr_scan_tile_for(C.c_void_p(ctx), int(n), int(N), int(H), C.byref(t),
+                                   C.byref(tuned)), "psr_scan_tile_for")
+    return (int(t.units), int(t.chunk)), bool(tuned.value)
+
+
+def psr_context_set_autotune(ctx, enable=True):
+    _check(lib().psr_context_set_autotune(C.c_void_p(ctx), int(bool(enable))),
+           "psr_context_set_autotune")

@@ -3,6 +3,7 @@
 // of psr_fwd_f32.cu, psr_fwd_bf16.cu, psr_ham.cu and psr_bwd.cu.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -27,6 +28,17 @@ struct psr_context {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<unsigned char> graph_key;  // arguments the cached graph was built for
     uint64_t graph_ws_generation = 0;
+    // Autotuner: measured choices per (operation, shape), kept for the
+    // context's lifetime.
+    bool autotune = false;
+    struct Tuned {
+        int op;
+        int64_t k0, k1, k2;
+        int32_t v0, v1;
+        float ms;
+    };
+    std::vector<Tuned> tuned;
+    cudaEvent_t tune_ev[2] = {};
 };
 
 namespace {
@@ -238,6 +250,8 @@ int psr_context_destroy(psr_context *ctx) {
         if (ctx->ev_begin[i]) cudaEventDestroy(ctx->ev_begin[i]);
         if (ctx->ev_end[i]) cudaEventDestroy(ctx->ev_end[i]);
     }
+    for (int i = 0; i < 2; ++i)
+        if (ctx->tune_ev[i]) cudaEventDestroy(ctx->tune_ev[i]);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->status) cudaFree(ctx->status);
     delete ctx;
@@ -849,6 +863,222 @@ int psr_local_energy_batch(const psr_params *params, const psr_batch_item *items
     }
     if (rc != PSR_OK) return rc;
     if (!all_device) return take_status(ctx);
+    return PSR_OK;
+}
+
+// ------------------------------------------------------------------ scan
+
+namespace {
+
+enum { kTuneScan = 1 };
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+const psr_context::Tuned *find_tuned(const psr_context *ctx, int op, int64_t k0, int64_t k1,
+                                     int64_t k2) {
+    for (const auto &t : ctx->tuned)
+        if (t.op == op && t.k0 == k0 && t.k1 == k1 && t.k2 == k2) return &t;
+    return nullptr;
+}
+
+// Tile shape used without measurement: the widest unit block that still
+// gives every resident warp a column, and enough chunks per column to give
+// each resident warp about two tiles when columns are scarce.
+psr_scan_tile scan_default_tile(const psr_context *ctx, int64_t n, int N, int H) {
+    const int64_t resident = (int64_t)ctx->num_sms * 32;  // warps at 4 CTAs of 8 warps per SM
+    int units = 4;
+    const int widths[4] = {128, 32, 16, 4};
+    for (int w : widths)
+        if (H % w == 0 && n * (H / w) >= resident) {
+            units = w;
+            break;
+        }
+    const int64_t cols = n * (H / units);
+    int chunk = N;
+    if (cols < 2 * resident) {
+        const int64_t per_col = (2 * resident + cols - 1) / cols;
+        int64_t c = (N + per_col - 1) / per_col;
+        c = (c + 31) / 32 * 32;
+        if (c < 256) c = 256;
+        if (c < N) chunk = (int)c;
+    }
+    return psr_scan_tile{units, chunk};
+}
+
+// Candidate tile shapes measured by the autotuner.
+std::vector<psr_scan_tile> scan_candidates(const psr_context *ctx, int64_t n, int N, int H) {
+    std::vector<psr_scan_tile> out;
+    const int widths[4] = {4, 16, 32, 128};
+    const int chunks[4] = {256, 1024, 4096, 0};  // 0: whole sequence
+    for (int w : widths) {
+        if (H % w) continue;
+        for (int c : chunks) {
+            const int ch = c == 0 ? N : c;
+            if (c != 0 && ch >= N) continue;
+            out.push_back(psr_scan_tile{w, ch});
+        }
+    }
+    const psr_scan_tile d = scan_default_tile(ctx, n, N, H);
+    bool have = false;
+    for (const auto &t : out) have = have || (t.units == d.units && t.chunk == d.chunk);
+    if (!have) out.push_back(d);
+    return out;
+}
+
+int enqueue_scan(psr_context *ctx, const float *a, const float *b, const float *h0, int64_t n,
+                 int N, int H, float *h, psr_scan_tile tile, unsigned long long *counter,
+                 int *flags, float *desc) {
+    cudaStream_t st = ctx->stream;
+    ScanArgs g{};
+    g.a = a;
+    g.b = b;
+    g.h0 = h0;
+    g.h = h;
+    g.N = N;
+    g.H = H;
+    scan_geometry(n, N, H, tile.units, tile.chunk, &g.nch, &g.n_tiles);
+    g.C = tile.chunk >= N ? N : tile.chunk;
+    g.nub = H / tile.units;
+    g.counter = counter;
+    g.flags = flags;
+    g.desc = desc;
+    g.status = ctx->status;
+    PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    if (g.nch > 1) PSR_TRY(cudaMemsetAsync(flags, 0, (size_t)g.n_tiles * sizeof(int), st));
+    PSR_TRY(launch_scan(g, tile.units, ctx->num_sms, st));
+    return PSR_OK;
+}
+
+int scan_impl(psr_context *ctx, const float *a, const float *b, const float *h0, int64_t n,
+              int32_t N, int32_t H, float *h, const psr_scan_tile *forced) {
+    if (!ctx || !a || !b || !h) return PSR_EINVAL;
+    if (n < 1 || N < 1 || N > (1 << 30) || H < 4 || (H % 4) != 0) return PSR_EINVAL;
+    if (forced && !scan_tile_valid(H, forced->units, forced->chunk)) return PSR_EINVAL;
+    const bool d_a = is_device_ptr(a), d_b = is_device_ptr(b), d_h = is_device_ptr(h),
+               d_h0 = h0 ? is_device_ptr(h0) : true;
+    if ((d_a && !aligned16(a)) || (d_b && !aligned16(b)) || (d_h && !aligned16(h)) ||
+        (h0 && d_h0 && !aligned16(h0)))
+        return PSR_EINVAL;
+    const size_t count = (size_t)n * N * H;
+
+    // The tile: forced, tuned (cached or measured now), or the default.
+    std::vector<psr_scan_tile> cands;
+    psr_scan_tile tile = scan_default_tile(ctx, n, N, H);
+    bool tune_now = false;
+    if (forced) {
+        tile = *forced;
+    } else if (const psr_context::Tuned *t = find_tuned(ctx, kTuneScan, n, N, H)) {
+        tile = psr_scan_tile{t->v0, t->v1};
+    } else if (ctx->autotune && !ctx->capturing) {
+        cands = scan_candidates(ctx, n, N, H);
+        tune_now = true;
+    }
+    // Look-back arrays sized for the smallest chunk that may run.
+    int64_t max_tiles = 0;
+    size_t max_desc = 0;
+    {
+        std::vector<psr_scan_tile> all = cands;
+        all.push_back(tile);
+        for (const auto &t : all) {
+            int nch;
+            int64_t nt;
+            scan_geometry(n, N, H, t.units, t.chunk, &nch, &nt);
+            if (nch > 1) {
+                if (nt > max_tiles) max_tiles = nt;
+                const size_t d = (size_t)nt * 3 * t.units;
+                if (d > max_desc) max_desc = d;
+            }
+        }
+    }
+
+    float *a_ws = nullptr, *b_ws = nullptr, *h_ws = nullptr, *h0_ws = nullptr, *desc = nullptr;
+    unsigned long long *counter = nullptr;
+    int *flags = nullptr;
+    auto carve = [&](Carver &c) {
+        a_ws = c.get<float>(d_a ? 0 : count);
+        b_ws = c.get<float>(d_b ? 0 : count);
+        h_ws = c.get<float>(d_h ? 0 : count);
+        h0_ws = c.get<float>(d_h0 ? 0 : (size_t)n * H);
+        counter = c.get<unsigned long long>(1);
+        flags = c.get<int>((size_t)max_tiles);
+        desc = c.get<float>(max_desc);
+    };
+    Carver sz;
+    carve(sz);
+    int rc = ensure_ws(ctx, sz.off);
+    if (rc != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *ua = nullptr, *ub = nullptr, *uh0 = nullptr;
+    if ((rc = stage_in(a, a_ws, count, d_a, st, &ua)) != PSR_OK) return rc;
+    if ((rc = stage_in(b, b_ws, count, d_b, st, &ub)) != PSR_OK) return rc;
+    if (h0 && (rc = stage_in(h0, h0_ws, (size_t)n * H, d_h0, st, &uh0)) != PSR_OK) return rc;
+    float *uh = d_h ? h : h_ws;
+
+    if (tune_now) {
+        // Time every candidate on these inputs (second of two runs each),
+        // keep the fastest; the run below then produces the result.
+        if (!ctx->tune_ev[0]) {
+            PSR_TRY(cudaEventCreate(&ctx->tune_ev[0]));
+            PSR_TRY(cudaEventCreate(&ctx->tune_ev[1]));
+        }
+        float best = -1.0f;
+        for (const auto &t : cands) {
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                PSR_TRY(cudaEventRecord(ctx->tune_ev[0], st));
+                if ((rc = enqueue_scan(ctx, ua, ub, uh0, n, N, H, uh, t, counter, flags, desc)) != PSR_OK)
+                    return rc;
+                PSR_TRY(cudaEventRecord(ctx->tune_ev[1], st));
+                PSR_TRY(cudaEventSynchronize(ctx->tune_ev[1]));
+                PSR_TRY(cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
+            }
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                tile = t;
+            }
+        }
+        ctx->tuned.push_back(psr_context::Tuned{kTuneScan, n, N, H, tile.units, tile.chunk, best});
+    }
+
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_SCAN);
+        if ((rc = enqueue_scan(ctx, ua, ub, uh0, n, N, H, uh, tile, counter, flags, desc)) != PSR_OK)
+            return rc;
+    }
+    if (!d_h) PSR_TRY(cudaMemcpyAsync(h, h_ws, count * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (!d_a || !d_b || !d_h || !d_h0) return take_status(ctx);
+    return PSR_OK;
+}
+
+}  // namespace
+
+int psr_context_set_autotune(psr_context *ctx, int enable) {
+    if (!ctx || (enable != 0 && enable != 1)) return PSR_EINVAL;
+    ctx->autotune = enable != 0;
+    return PSR_OK;
+}
+
+int psr_scan(psr_context *ctx, const float *a, const float *b, const float *h0, int64_t n,
+             int32_t N, int32_t H, float *h) {
+    return scan_impl(ctx, a, b, h0, n, N, H, h, nullptr);
+}
+
+int psr_scan_tiled(psr_context *ctx, const float *a, const float *b, const float *h0, int64_t n,
+                   int32_t N, int32_t H, float *h, const psr_scan_tile *tile) {
+    if (!tile) return PSR_EINVAL;
+    return scan_impl(ctx, a, b, h0, n, N, H, h, tile);
+}
+
+int psr_scan_tile_for(psr_context *ctx, int64_t n, int32_t N, int32_t H, psr_scan_tile *tile,
+                      int32_t *tuned) {
+    if (!ctx || !tile || n < 1 || N < 1 || H < 4 || (H % 4) != 0) return PSR_EINVAL;
+    const psr_context::Tuned *t = find_tuned(ctx, kTuneScan, n, N, H);
+    *tile = t ? psr_scan_tile{t->v0, t->v1} : scan_default_tile(ctx, n, N, H);
+    if (tuned) *tuned = t ? 1 : 0;
     return PSR_OK;
 }
 

@@ -123,6 +123,27 @@ cudaError_t launch_eloc_gather(const int64_t *offsets, const float *delta, const
                                float coeff, int64_t n, float *eloc, cudaStream_t stream);
 cudaError_t launch_stats(const float *eloc, int64_t n, double *stats, cudaStream_t stream);
 
+// Standalone chunked scan h_t = a_t h_{t-1} + b_t over [n][N][H] FP32 arrays
+// (psr_scan.cu).  Tile = (sequence, `units` units, `chunk` sites); flags and
+// desc are the look-back arrays of n_tiles entries (flags zeroed before the
+// launch; only touched when nch > 1).
+struct ScanArgs {
+    const float *a, *b, *h0;
+    float *h;
+    int N, H;
+    int C;                // chunk length in sites (<= N)
+    int nch;              // chunks per column
+    int nub;              // unit blocks per sequence (H / units)
+    int64_t n_tiles;
+    unsigned long long *counter;  // zeroed before launch
+    int *flags;           // [n_tiles]
+    float *desc;          // [n_tiles][3][units]
+    int *status;
+};
+bool scan_tile_valid(int H, int units, int chunk);
+void scan_geometry(int64_t n, int N, int H, int units, int chunk, int *nch, int64_t *n_tiles);
+cudaError_t launch_scan(const ScanArgs &g, int units, int num_sms, cudaStream_t stream);
+
 // Backward (FP32).
 size_t bwd_tape_floats_per_cta(int nL, int H);
 cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1,

@@ -154,3 +154,28 @@ def neel_like_spins(seed: int, n: int, Lx: int, Ly: int, anti_fraction: float = 
         out[rows, ups[ku]] = 0
         out[rows, dns[kd]] = 1
     return out
+
+
+def scan_inputs(seed: int, n: int, N: int, H: int):
+    """Coefficients of a diagonal linear recurrence h_t = a_t h_{t-1} + b_t
+    shaped like a minGRU layer's gates: a in (0.001, 1) with many values
+    close to 1 (long memory), b and h0 uniform in (-1, 1).  float32
+    [n, N, H], [n, N, H], [n, H]."""
+    u = uniform(seed, (3, n * N * H + n * H))
+    a = (1.0 - 0.999 * u[0, : n * N * H] ** 2).astype(np.float32).reshape(n, N, H)
+    b = (2.0 * u[1, : n * N * H] - 1.0).astype(np.float32).reshape(n, N, H)
+    h0 = (2.0 * u[2, n * N * H:] - 1.0).astype(np.float32).reshape(n, H)
+    return a, b, h0
+
+
+def scan_inputs_device(seed: int, n: int, N: int, H: int, device):
+    """The distribution of scan_inputs drawn on the device with torch's seeded
+    generator (for sizes where host generation is too slow)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    a = torch.rand((n, N, H), generator=g, device=device, dtype=torch.float32)
+    a.pow_(2).mul_(-0.999).add_(1.0)
+    b = torch.rand((n, N, H), generator=g, device=device, dtype=torch.float32).mul_(2.0).sub_(1.0)
+    h0 = torch.rand((n, H), generator=g, device=device, dtype=torch.float32).mul_(2.0).sub_(1.0)
+    return a, b, h0
