@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-scan", action="store_true")
+    ap.add_argument("--no-sample", action="store_true")
     ap.add_argument("--scan-only", action="store_true",
                     help="only the standalone scan measurement (profiling runs)")
     ap.add_argument("--scan-n", type=int, default=0,
@@ -278,6 +279,47 @@ def scan_leg(args, n, N, dev, reps=5):
                          "algorithmic_bytes_per_launch": algo, "bytes_per_unit": 12}}
 
 
+# FP32 CUDA-core peak derived from unit counts and clock: 152 SMs x 128 FP32
+# lanes x 2 flops per FMA x 2.07 GHz (maximum SM clock).
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def sample_leg(theta, n, N, dev, reps=2):
+    """The exact autoregressive sampler (psr_sample) drawing n samples of N
+    sites from the caller's uniforms; samples per CTA picked by the
+    autotuner on the first call.  FP32 on CUDA cores: 18 H^2 flops per
+    sample-site (the forward's products), against the derived FP32 peak."""
+    import torch
+
+    from paper_2605_13807_gb300 import api, binding as B, inputs
+    ctx = B.context()
+    B.psr_context_set_profiling(ctx, True)
+    g = torch.Generator(device=dev)
+    g.manual_seed(3)
+    u = torch.rand((n, N), generator=g, device=dev, dtype=torch.float32)
+    cfg = api.ModelConfig(N_LAYERS, HIDDEN, True, "fp32")
+    api.set_autotune(True)
+    s, lp = api.sample(theta, u, cfg)
+    api.set_autotune(False)
+    per_cta, tuned = B.psr_sample_tile_for(ctx, n, N, N_LAYERS, HIDDEN)
+    ms = []
+    for _ in range(reps):
+        api.sample(theta, u, cfg, spins=s, logpsi=lp)
+        ms.append(B.psr_context_stage_ms(ctx)["sample"])
+    api.sync()
+    avg = sum(ms) / len(ms)
+    flops = n * N * MMA_FLOPS_PER_SITE
+    achieved = flops / (avg / 1e3) / 1e12
+    del u, s, lp
+    return {"kernel": "sample_kernel (psr_sample, exact autoregressive sampler, FP32)",
+            "samples": n, "sites": N, "samples_per_cta": per_cta, "tuned": tuned, "ms": avg,
+            "value": n * N / (avg / 1e3), "unit": "sample-sites/s",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                         "traffic": None, "flops_per_unit": MMA_FLOPS_PER_SITE}}
+
+
 def run_scan_only(args):
     import torch
 
@@ -446,6 +488,8 @@ def run_mine(args):
 
     if not args.no_scan and rank == 0:
         line["scan"] = scan_leg(args, n, N, dev)
+    if not args.no_sample and rank == 0:
+        line["sample"] = sample_leg(theta, n, N, dev)
 
     # end to end through the C ABI with host buffers
     if not args.no_e2e:

@@ -256,13 +256,35 @@ int psr_scan_tiled(psr_context *ctx, const float *a, const float *b, const float
 int psr_scan_tile_for(psr_context *ctx, int64_t n, int32_t N, int32_t H, psr_scan_tile *tile,
                       int32_t *tuned);
 
+/* Exact autoregressive sampling (Sec. II.A and Sec. III.B: the conditionals
+ * P(s_t | s_<t) of the model are drawn site by site along the zigzag
+ * sequence, so the n samples are exact and independent).  The caller
+ * supplies the random numbers: uniforms float [n][L] in [0, 1), and site t
+ * of sample i is s_t = 1 iff uniforms[i][t] < P(s_t = 1 | s_<t) (with
+ * u1_mask, the forced value where the mask forces one).  spins: uint8
+ * [n][L] output in sequence order; logpsi: float [n] output (log psi of the
+ * drawn sample) or NULL.  Computed in FP32 for both precisions.  The result
+ * does not depend on how samples are grouped into CTAs (a tile shape the
+ * autotuner chooses), so equal uniforms give equal samples.
+ * PSR_EINVAL: what psr_logpsi rejects, or null uniforms / spins. */
+int psr_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t L,
+               uint8_t *spins, float *logpsi);
+
+/* Samples per CTA psr_sample will use for (n, L, n_layers, hidden) on this
+ * context: the autotuned value if that shape has been tuned (*tuned = 1),
+ * else the default 8 (*tuned = 0).  tuned may be NULL. */
+int psr_sample_tile_for(psr_context *ctx, int64_t n, int32_t L, int32_t n_layers, int32_t hidden,
+                        int32_t *per_cta, int32_t *tuned);
+
 /* Enables (1) or disables (0) the autotuner of this context.  While enabled,
- * the first psr_scan of a shape (n, N, H) that is not being captured into a
- * graph times every candidate tile shape (unit-block width x chunk length)
- * on its own inputs with CUDA events, keeps the fastest for the context's
- * lifetime and then computes its result with it; that first call
- * synchronises the stream.  Every tile shape computes the same recurrence;
- * results differ only by FP32 rounding of the composed maps. */
+ * the first call of psr_scan or psr_sample for a shape it has not seen
+ * (scan: n, N, H; sample: n, L, layers, hidden), when not being captured
+ * into a graph, times every candidate tile shape (scan: unit-block width x
+ * chunk length; sample: samples per CTA) on its own inputs with CUDA events,
+ * keeps the fastest for the context's lifetime and then computes its result
+ * with it; that first call synchronises the stream.  Every scan tile
+ * computes the same recurrence (results differ only by FP32 rounding of the
+ * composed maps); every sampler tile gives identical samples. */
 int psr_context_set_autotune(psr_context *ctx, int enable);
 
 /* Stages of the launch sequence, for per-stage device timing. */
@@ -274,7 +296,8 @@ enum {
     PSR_STAGE_GATHER = 4,        /* E_loc gather and FP64 statistics */
     PSR_STAGE_BWD = 5,           /* reverse-scan gradient and its reduction */
     PSR_STAGE_SCAN = 6,          /* psr_scan / psr_scan_tiled kernel */
-    PSR_STAGE_COUNT = 7
+    PSR_STAGE_SAMPLE = 7,        /* psr_sample kernel */
+    PSR_STAGE_COUNT = 8
 };
 
 /* Enables (1) or disables (0) per-stage CUDA-event timing on the context's

@@ -4,6 +4,7 @@
     local_energy(theta, samples, ham)    -> (float32 [n] E_loc, float64 [3] stats)
     connected(samples, ham)              -> (int64 [n+1], int32 [E, 3], float32 [n])
     scan(a, b, h0=None)                  -> float32 [n, N, H], h_t = a_t h_{t-1} + b_t
+    sample(theta, uniforms, cfg)         -> (uint8 [n, L] exact samples, float32 [n] log psi)
     grad(theta, spins, dout=None)        -> float32 [n, P] (O_k) or [P]
     LogPsi.apply(theta, spins, cfg)      -> differentiable log psi; backward = psr_grad
 
@@ -108,6 +109,20 @@ def scan(a, b, h0=None, tile=None, out=None):
     if out is None:
         out = torch.empty_like(a)
     return B.psr_scan(_ctx(), a, b, out, h0=h0, tile=tile)
+
+
+def sample(theta, uniforms, cfg: ModelConfig, spins=None, logpsi=None):
+    """Exact autoregressive samples from the caller's uniforms [n, L]:
+    (uint8 spins [n, L] in sequence order, float32 log psi [n])."""
+    dev = _device_of(uniforms, theta)
+    n, L = uniforms.shape
+    if spins is None:
+        spins = torch.empty((n, L), dtype=torch.uint8, device=dev)
+    if logpsi is None:
+        logpsi = torch.empty(n, dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_sample(p, uniforms, spins, logpsi)
+    return spins, logpsi
 
 
 def set_autotune(enable=True):

@@ -53,8 +53,8 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror",
             "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc",
             "psr_local_energy_batch", "psr_context_set_graphs", "psr_scan", "psr_scan_tiled",
-            "psr_scan_tile_for", "psr_context_set_autotune")
-STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan")
+            "psr_scan_tile_for", "psr_context_set_autotune", "psr_sample", "psr_sample_tile_for")
+STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
 _lock = threading.Lock()
@@ -91,6 +91,8 @@ def lib():
                 L.psr_scan_tile_for.argtypes = [vp, i64, i32, i32, C.POINTER(psr_scan_tile),
                                                 C.POINTER(i32)]
                 L.psr_context_set_autotune.argtypes = [vp, C.c_int]
+                L.psr_sample.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
+                L.psr_sample_tile_for.argtypes = [vp, i64, i32, i32, i32, C.POINTER(i32), C.POINTER(i32)]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -265,3 +267,20 @@ def psr_scan_tile_for(ctx, n, N, H):
 def psr_context_set_autotune(ctx, enable=True):
     _check(lib().psr_context_set_autotune(C.c_void_p(ctx), int(bool(enable))),
            "psr_context_set_autotune")
+
+
+def psr_sample(params, uniforms, spins, logpsi=None):
+    """Exact autoregressive samples: spins[i, t] = 1 iff uniforms[i, t] < P(up)."""
+    n, L = uniforms.shape
+    _check(lib().psr_sample(C.byref(params), _ptr(uniforms), int(n), int(L), _ptr(spins),
+                            _ptr(logpsi)), "psr_sample")
+    return spins
+
+
+def psr_sample_tile_for(ctx, n, L, n_layers, hidden):
+    """(samples per CTA, tuned) that psr_sample would use for this shape."""
+    per = C.c_int32()
+    tuned = C.c_int32()
+    _check(lib().psr_sample_tile_for(C.c_void_p(ctx), int(n), int(L), int(n_layers), int(hidden),
+                                     C.byref(per), C.byref(tuned)), "psr_sample_tile_for")
+    return int(per.value), bool(tuned.value)

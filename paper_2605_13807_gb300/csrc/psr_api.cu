@@ -866,11 +866,44 @@ int psr_local_energy_batch(const psr_params *params, const psr_batch_item *items
     return PSR_OK;
 }
 
+}  // extern "C"
+
 // ------------------------------------------------------------------ scan
 
 namespace {
 
-enum { kTuneScan = 1 };
+enum { kTuneScan = 1, kTuneSample = 2 };
+
+// Times run(i) for every candidate i on the context's stream with CUDA
+// events (two runs each when a run is short, the second counted) and
+// returns the index of the fastest.  Synchronises the stream.
+template <class Run>
+int measure_candidates(psr_context *ctx, int count, Run run, int *best, float *best_ms) {
+    if (!ctx->tune_ev[0]) {
+        PSR_TRY(cudaEventCreate(&ctx->tune_ev[0]));
+        PSR_TRY(cudaEventCreate(&ctx->tune_ev[1]));
+    }
+    cudaStream_t st = ctx->stream;
+    *best = 0;
+    *best_ms = -1.0f;
+    for (int i = 0; i < count; ++i) {
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {
+            PSR_TRY(cudaEventRecord(ctx->tune_ev[0], st));
+            int rc = run(i);
+            if (rc != PSR_OK) return rc;
+            PSR_TRY(cudaEventRecord(ctx->tune_ev[1], st));
+            PSR_TRY(cudaEventSynchronize(ctx->tune_ev[1]));
+            PSR_TRY(cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
+            if (ms > 50.0f) break;  // long runs: the first is representative
+        }
+        if (*best_ms < 0.0f || ms < *best_ms) {
+            *best_ms = ms;
+            *best = i;
+        }
+    }
+    return PSR_OK;
+}
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -1018,28 +1051,15 @@ int scan_impl(psr_context *ctx, const float *a, const float *b, const float *h0,
     float *uh = d_h ? h : h_ws;
 
     if (tune_now) {
-        // Time every candidate on these inputs (second of two runs each),
-        // keep the fastest; the run below then produces the result.
-        if (!ctx->tune_ev[0]) {
-            PSR_TRY(cudaEventCreate(&ctx->tune_ev[0]));
-            PSR_TRY(cudaEventCreate(&ctx->tune_ev[1]));
-        }
-        float best = -1.0f;
-        for (const auto &t : cands) {
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {
-                PSR_TRY(cudaEventRecord(ctx->tune_ev[0], st));
-                if ((rc = enqueue_scan(ctx, ua, ub, uh0, n, N, H, uh, t, counter, flags, desc)) != PSR_OK)
-                    return rc;
-                PSR_TRY(cudaEventRecord(ctx->tune_ev[1], st));
-                PSR_TRY(cudaEventSynchronize(ctx->tune_ev[1]));
-                PSR_TRY(cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
-            }
-            if (best < 0.0f || ms < best) {
-                best = ms;
-                tile = t;
-            }
-        }
+        // Time every candidate on these inputs and keep the fastest; the
+        // run below then produces the result.
+        int bi = 0;
+        float best = 0.0f;
+        rc = measure_candidates(ctx, (int)cands.size(), [&](int i) {
+            return enqueue_scan(ctx, ua, ub, uh0, n, N, H, uh, cands[i], counter, flags, desc);
+        }, &bi, &best);
+        if (rc != PSR_OK) return rc;
+        tile = cands[bi];
         ctx->tuned.push_back(psr_context::Tuned{kTuneScan, n, N, H, tile.units, tile.chunk, best});
     }
 
@@ -1055,6 +1075,8 @@ int scan_impl(psr_context *ctx, const float *a, const float *b, const float *h0,
 }
 
 }  // namespace
+
+extern "C" {
 
 int psr_context_set_autotune(psr_context *ctx, int enable) {
     if (!ctx || (enable != 0 && enable != 1)) return PSR_EINVAL;
@@ -1078,6 +1100,86 @@ int psr_scan_tile_for(psr_context *ctx, int64_t n, int32_t N, int32_t H, psr_sca
     if (!ctx || !tile || n < 1 || N < 1 || H < 4 || (H % 4) != 0) return PSR_EINVAL;
     const psr_context::Tuned *t = find_tuned(ctx, kTuneScan, n, N, H);
     *tile = t ? psr_scan_tile{t->v0, t->v1} : scan_default_tile(ctx, n, N, H);
+    if (tuned) *tuned = t ? 1 : 0;
+    return PSR_OK;
+}
+
+// --------------------------------------------------------------- sampler
+
+int psr_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t L,
+               uint8_t *spins, float *logpsi) {
+    int rc = check_params(params, n, L);
+    if (rc == PSR_EUNSUPPORTED && params->precision == PSR_BF16) rc = PSR_OK;  // FP32 either way
+    if (rc != PSR_OK) return rc;
+    if (!uniforms || !spins) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden;
+    const bool d_theta = is_device_ptr(params->theta), d_u = is_device_ptr(uniforms),
+               d_s = is_device_ptr(spins), d_lp = logpsi ? is_device_ptr(logpsi) : true;
+    const ThetaLayout tl = theta_layout(nL, H);
+    const F32Layout fl = f32_layout(nL, H);
+    const size_t cells = (size_t)n * L;
+
+    float *theta_ws = nullptr, *u_ws = nullptr, *lp_ws = nullptr, *pk = nullptr;
+    uint8_t *s_ws = nullptr;
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : tl.total);
+        u_ws = c.get<float>(d_u ? 0 : cells);
+        s_ws = c.get<uint8_t>(d_s ? 0 : cells);
+        lp_ws = c.get<float>(d_lp ? 0 : n);
+        pk = c.get<float>(fl.total);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr, *uu = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, tl.total, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(uniforms, u_ws, cells, d_u, st, &uu)) != PSR_OK) return rc;
+    uint8_t *so = d_s ? spins : s_ws;
+    float *lo = logpsi ? (d_lp ? logpsi : lp_ws) : nullptr;
+
+    // samples per CTA: forced by nothing, tuned, or the default
+    const int64_t key2 = (int64_t)nL * 1024 + H;
+    int per_cta = 8;
+    bool tune_now = false;
+    if (const psr_context::Tuned *t = find_tuned(ctx, kTuneSample, n, L, key2)) per_cta = t->v0;
+    else if (ctx->autotune && !ctx->capturing) tune_now = true;
+
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+    }
+    if (tune_now) {
+        const int cands[4] = {4, 8, 16, 32};
+        int bi = 0;
+        float best = 0.0f;
+        rc = measure_candidates(ctx, 4, [&](int i) {
+            return from_cuda(launch_sample(cands[i], pk, fl, uu, n, L, params->u1_mask, so, lo, st));
+        }, &bi, &best);
+        if (rc != PSR_OK) return rc;
+        per_cta = cands[bi];
+        ctx->tuned.push_back(psr_context::Tuned{kTuneSample, n, L, key2, per_cta, 0, best});
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_SAMPLE);
+        PSR_TRY(launch_sample(per_cta, pk, fl, uu, n, L, params->u1_mask, so, lo, st));
+    }
+    if (!d_s) PSR_TRY(cudaMemcpyAsync(spins, s_ws, cells, cudaMemcpyDeviceToHost, st));
+    if (logpsi && !d_lp) PSR_TRY(cudaMemcpyAsync(logpsi, lp_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (!d_theta || !d_u || !d_s || !d_lp) return take_status(ctx);
+    return PSR_OK;
+}
+
+int psr_sample_tile_for(psr_context *ctx, int64_t n, int32_t L, int32_t n_layers, int32_t hidden,
+                        int32_t *per_cta, int32_t *tuned) {
+    if (!ctx || !per_cta || n < 1 || L < 1) return PSR_EINVAL;
+    const psr_context::Tuned *t = find_tuned(ctx, kTuneSample, n, L, (int64_t)n_layers * 1024 + hidden);
+    *per_cta = t ? t->v0 : 8;
     if (tuned) *tuned = t ? 1 : 0;
     return PSR_OK;
 }

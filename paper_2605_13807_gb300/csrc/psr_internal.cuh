@@ -144,6 +144,12 @@ bool scan_tile_valid(int H, int units, int chunk);
 void scan_geometry(int64_t n, int N, int H, int units, int chunk, int *nch, int64_t *n_tiles);
 cudaError_t launch_scan(const ScanArgs &g, int units, int num_sms, cudaStream_t stream);
 
+// Exact autoregressive sampler (psr_sample.cu), FP32; per_cta samples per
+// CTA: 4, 8, 16 or 32.  unif: [n][N] uniforms in [0, 1).
+cudaError_t launch_sample(int per_cta, const float *packed, const F32Layout &fl, const float *unif,
+                          int64_t n, int N, int u1, uint8_t *out, float *logpsi,
+                          cudaStream_t stream);
+
 // Backward (FP32).
 size_t bwd_tape_floats_per_cta(int nL, int H);
 cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1,
