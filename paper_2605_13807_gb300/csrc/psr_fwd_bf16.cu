@@ -555,7 +555,9 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int lane_base = (warp & 3) * 32;
-    const bool issuer = (hf == 0 && j == 0);
+    // one MMA-issuing thread per stream, on different SM sub-partitions
+    // (warp 0 and warp 10)
+    const bool issuer = (hf == 0 && j == (s == 0 ? 0 : 64));
 
     uint8_t *tileX = smem + OFF_TILES + (2 * s) * kTileBytes;
     uint8_t *tileH = tileX + kTileBytes;
