@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "psr_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "psr_oracle2d.c"))
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 
@@ -27,9 +28,10 @@ TFIM = 1
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (no architecture-specific flags)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(x) for x in _SRCS)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -72,6 +74,12 @@ def lib():
         _lib.psro_scan_sequential.argtypes = [vp, vp, i, d, vp]
         _lib.psro_scan_blelloch.restype = None
         _lib.psro_scan_blelloch.argtypes = [vp, vp, i, d, vp]
+        _lib.psro2d_param_count.restype = l
+        _lib.psro2d_param_count.argtypes = [i, i]
+        _lib.psro2d_logpsi.restype = d
+        _lib.psro2d_logpsi.argtypes = [vp, i, i, i, i, i, vp, vp]
+        _lib.psro2d_sample.restype = None
+        _lib.psro2d_sample.argtypes = [vp, i, i, i, i, i, l, vp, vp, vp]
     return _lib
 
 
@@ -253,3 +261,66 @@ def _map(fn, n, threads):
         return
     with ThreadPoolExecutor(max_workers=t) as ex:
         list(ex.map(fn, range(n)))
+
+
+# --------------------------------------------- two-dimensional patched minGRU
+
+def param_count2d(n_layers: int, hidden: int) -> int:
+    return int(lib().psro2d_param_count(n_layers, hidden))
+
+
+def logpsi2d(theta, n_layers, hidden, Lx, Ly, spins, u1=False, threads=None, per_site=False):
+    """log psi of the 2D patched minGRU for every row of spins [n, Lx*Ly]
+    (sequence order); optionally the per-patch log P [n, Lx*Ly/4]."""
+    th = _theta64(theta)
+    s = _spins(spins)
+    n, N = s.shape
+    assert N == Lx * Ly
+    Np = (Lx // 2) * (Ly // 2)
+    out = np.empty(n)
+    lp = np.empty((n, Np)) if per_site else None
+    L = lib()
+
+    def one(i):
+        row = np.ascontiguousarray(s[i])
+        buf = np.empty(Np) if per_site else None
+        out[i] = L.psro2d_logpsi(_p(th), n_layers, hidden, int(u1), Lx, Ly, _p(row),
+                                 _p(buf) if per_site else None)
+        if per_site:
+            lp[i] = buf
+
+    _map(one, n, threads)
+    return (out, lp) if per_site else out
+
+
+def sample2d(theta, n_layers, hidden, Lx, Ly, uniforms, u1=False):
+    """Exact samples of the 2D model from uniforms [n, Lx*Ly/4] (one per patch)."""
+    th = _theta64(theta)
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    n = u.shape[0]
+    out = np.empty((n, Lx * Ly), dtype=np.uint8)
+    lps = np.empty(n)
+    lib().psro2d_sample(_p(th), n_layers, hidden, int(u1), Lx, Ly, n, _p(u), _p(out), _p(lps))
+    return out, lps
+
+
+def local_energy2d(theta, n_layers, hidden, spins, kind, Lx, Ly, pbc=False, marshall=True,
+                   J=1.0, h=0.0, u1=False, threads=None):
+    """E_loc of the 2D model: the connected configurations of the bond /
+    site flips, each evaluated by a full forward, combined with the diagonal
+    energy (the same steps as the one-dimensional E_loc)."""
+    s = _spins(spins)
+    n, N = s.shape
+    offsets, ent, diag = connected(kind, Lx, Ly, pbc, s, J=J)
+    flipped = np.repeat(s, np.diff(offsets), axis=0)
+    rows = np.arange(flipped.shape[0])
+    if flipped.shape[0]:
+        flipped[rows, ent[:, 1]] ^= 1
+        has_q = ent[:, 2] >= 0
+        flipped[rows[has_q], ent[has_q, 2]] ^= 1
+    lp_s = logpsi2d(theta, n_layers, hidden, Lx, Ly, s, u1=u1, threads=threads)
+    lp_sp = logpsi2d(theta, n_layers, hidden, Lx, Ly, flipped, u1=u1, threads=threads) \
+        if flipped.shape[0] else np.empty(0)
+    c = offdiag_coeff(kind, J=J, h=h, marshall=marshall)
+    return np.array([eloc_combine(diag[i], c, lp_s[i], lp_sp[offsets[i]:offsets[i + 1]])
+                     for i in range(n)])
