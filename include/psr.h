@@ -287,6 +287,42 @@ int psr_sample_tile_for(psr_context *ctx, int64_t n, int32_t L, int32_t n_layers
  * composed maps); every sampler tile gives identical samples. */
 int psr_context_set_autotune(psr_context *ctx, int enable);
 
+/* ---------------------------------------------------------------------
+ * The paper's two-dimensional patched minGRU (Sec. II.F, two-dimensional
+ * recurrences; Sec. II.G, residual connections).  The Lx x Ly spin lattice
+ * (Lx, Ly even) is cut into 2 x 2 patches; patch (i, j) holds the spins
+ * (2i + dx, 2j + dy) and takes the value v = sum s 2^(2 dy + dx) in 0..15.
+ * Patches are visited along the zigzag path of the patch lattice (row j left
+ * to right when j is even) with causal predecessors H = (i - (-1)^j, j) and
+ * V = (i, j - 1) (zero outside the lattice).  Layer input u_0 =
+ * (onehot16(v_H), onehot16(v_V)), u_l = x_l for l >= 1;
+ *   z = sigma(W_z u + b_z),  h~ = W_h [u, h_V] + b_h,  h = z h_H + (1 - z) h~,
+ *   x_{l+1} = GELU(C h + D u + s_l),  s_l = h_{l-1} for l >= 2, else 0;
+ * the conditional of a patch is softmax(W_o x_{nL} + b_o) over its 16
+ * values (with u1_mask: over the values that keep both the up and the down
+ * count at most N/2), log psi = 1/2 sum log P.
+ * Spins are uint8 [n][Lx * Ly] in the sequence order of the SPIN lattice,
+ * as for the calls above.  theta: float, per layer l (din = 32 at l = 0,
+ * else hidden) W_z[hidden][din], b_z[hidden], W_h[hidden][din + hidden]
+ * (the last hidden columns act on h_V), b_h[hidden], C[hidden][hidden],
+ * D[hidden][din]; then W_o[16][hidden], b_o[16]; psr2d_param_count gives
+ * the length (12 H^2 + 118 H + 16 for three layers).
+ * Computed in FP32 on CUDA cores, row by row: within a patch row all sites
+ * share one batched projection and one scan (the row starts from h_H = 0).
+ * PSR_EUNSUPPORTED for precision PSR_BF16 or Lx > 64 (more than 32 patches
+ * per row); PSR_EINVAL for odd Lx or Ly and what psr_logpsi rejects. */
+int psr2d_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
+
+int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
+                 float *out);
+
+/* Local energy of the 2D model over every connected configuration, as
+ * psr_local_energy computes it for the chain model; a connected
+ * configuration is resumed at the patch row of its first flipped spin from
+ * the sample's stored row states. */
+int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                       const psr_hamiltonian *hamiltonian, float *out, double *stats);
+
 /* Stages of the launch sequence, for per-stage device timing. */
 enum {
     PSR_STAGE_PACK = 0,          /* parameter packing and spin bit-packing */

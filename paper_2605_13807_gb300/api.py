@@ -5,6 +5,7 @@
     connected(samples, ham)              -> (int64 [n+1], int32 [E, 3], float32 [n])
     scan(a, b, h0=None)                  -> float32 [n, N, H], h_t = a_t h_{t-1} + b_t
     sample(theta, uniforms, cfg)         -> (uint8 [n, L] exact samples, float32 [n] log psi)
+    logpsi2d / local_energy2d            -> the 2D patched minGRU (Lx, Ly even)
     grad(theta, spins, dout=None)        -> float32 [n, P] (O_k) or [P]
     LogPsi.apply(theta, spins, cfg)      -> differentiable log psi; backward = psr_grad
 
@@ -123,6 +124,30 @@ def sample(theta, uniforms, cfg: ModelConfig, spins=None, logpsi=None):
     p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
     B.psr_sample(p, uniforms, spins, logpsi)
     return spins, logpsi
+
+
+def param_count2d(n_layers: int = 3, hidden: int = 128) -> int:
+    return B.psr2d_param_count(n_layers, hidden)
+
+
+def logpsi2d(theta, spins, cfg: ModelConfig, Lx: int, Ly: int, out=None):
+    """log psi of the 2D patched minGRU (spins [n, Lx*Ly] in sequence order)."""
+    dev = _device_of(spins, theta)
+    if out is None:
+        out = torch.empty(spins.shape[0], dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    return B.psr2d_logpsi(p, spins, Lx, Ly, out)
+
+
+def local_energy2d(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, out=None, stats=None):
+    dev = _device_of(samples, theta)
+    if out is None:
+        out = torch.empty(samples.shape[0], dtype=torch.float32, device=dev)
+    if stats is None:
+        stats = torch.empty(3, dtype=torch.float64, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr2d_local_energy(p, samples, ham, out, stats)
+    return out, stats
 
 
 def set_autotune(enable=True):

@@ -53,7 +53,8 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror",
             "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc",
             "psr_local_energy_batch", "psr_context_set_graphs", "psr_scan", "psr_scan_tiled",
-            "psr_scan_tile_for", "psr_context_set_autotune", "psr_sample", "psr_sample_tile_for")
+            "psr_scan_tile_for", "psr_context_set_autotune", "psr_sample", "psr_sample_tile_for",
+            "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -93,6 +94,10 @@ def lib():
                 L.psr_context_set_autotune.argtypes = [vp, C.c_int]
                 L.psr_sample.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
                 L.psr_sample_tile_for.argtypes = [vp, i64, i32, i32, i32, C.POINTER(i32), C.POINTER(i32)]
+                L.psr2d_param_count.argtypes = [i32, i32, C.POINTER(i64)]
+                L.psr2d_logpsi.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp]
+                L.psr2d_local_energy.argtypes = [C.POINTER(psr_params), vp, i64,
+                                                 C.POINTER(psr_hamiltonian), vp, vp]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -284,3 +289,23 @@ def psr_sample_tile_for(ctx, n, L, n_layers, hidden):
     _check(lib().psr_sample_tile_for(C.c_void_p(ctx), int(n), int(L), int(n_layers), int(hidden),
                                      C.byref(per), C.byref(tuned)), "psr_sample_tile_for")
     return int(per.value), bool(tuned.value)
+
+
+def psr2d_param_count(n_layers, hidden):
+    P = C.c_int64()
+    _check(lib().psr2d_param_count(int(n_layers), int(hidden), C.byref(P)), "psr2d_param_count")
+    return int(P.value)
+
+
+def psr2d_logpsi(params, spins, Lx, Ly, out):
+    n = spins.shape[0]
+    _check(lib().psr2d_logpsi(C.byref(params), _ptr(spins), int(n), int(Lx), int(Ly), _ptr(out)),
+           "psr2d_logpsi")
+    return out
+
+
+def psr2d_local_energy(params, samples, ham, out, stats=None):
+    n = samples.shape[0]
+    _check(lib().psr2d_local_energy(C.byref(params), _ptr(samples), int(n), C.byref(ham), _ptr(out),
+                                    _ptr(stats)), "psr2d_local_energy")
+    return out

@@ -150,6 +150,47 @@ cudaError_t launch_sample(int per_cta, const float *packed, const F32Layout &fl,
                           int64_t n, int N, int u1, uint8_t *out, float *logpsi,
                           cudaStream_t stream);
 
+// Two-dimensional patched minGRU (psr_fwd2d.cu), FP32.  Packed transposed
+// weights: for layer l (din = 32 at l = 0, else H) WzT, WhxT, DT [din][H],
+// WhvT, CT [H][H] (h_V and C parts), bz, bh [H]; readout Wo [16][H], bo [16].
+struct F2Layout {
+    int nL, H;
+    int64_t WzT[kMaxLayers], WhxT[kMaxLayers], WhvT[kMaxLayers], CT[kMaxLayers], DT[kMaxLayers];
+    int64_t bz[kMaxLayers], bh[kMaxLayers];
+    int64_t Wo, bo;
+    int64_t total;
+};
+F2Layout f2_layout(int nL, int H);
+int64_t param_count2d(int nL, int H);
+// Jobs of the 2D forward.  mode 0: sample i from the first patch row, writing
+// out[i] = log psi, optionally logp_out [n][Np] and the row checkpoints
+// carries_out [n][Py][fwd2d_checkpoint_floats]; mode 1: entry e = (sample,
+// p, q) resumed at the patch row of spin p from carries_in, writing
+// out[e] = log psi(s') - log psi(s) from logp_ref.
+struct Fwd2Group {
+    int Lx, Ly, u1;
+    int64_t n_jobs;              // mode 0: samples; mode 1: capacity
+    const int64_t *n_jobs_dev;   // mode 1: device count
+    const uint8_t *spins;        // [n][Lx*Ly] sequence order
+    const int32_t *entries;      // mode 1: [E][3]
+    const float *carries_in;
+    const float *logp_ref;
+    float *out;
+    float *logp_out;
+    float *carries_out;
+};
+struct Fwd2Jobs {
+    int mode;
+    Fwd2Group g;
+    unsigned long long *job_counter;
+    int *status;
+};
+size_t fwd2d_checkpoint_floats(int nL, int H);
+cudaError_t launch_pack_theta_f2(const float *theta, const F2Layout &f, float *packed,
+                                 cudaStream_t stream);
+cudaError_t launch_fwd2d_f32(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f,
+                             int num_sms, cudaStream_t stream);
+
 // Backward (FP32).
 size_t bwd_tape_floats_per_cta(int nL, int H);
 cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1,

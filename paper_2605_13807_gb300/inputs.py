@@ -75,6 +75,35 @@ def glorot_params(n_layers: int, hidden: int, seed: int = 0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
+def param_shapes2d(n_layers: int, hidden: int):
+    """(name, shape, is_weight) in the flat parameter order of the 2D patched
+    model (layer-0 input: two 16-value one-hots; W_h also acts on h_V)."""
+    out = []
+    for l in range(n_layers):
+        din = 32 if l == 0 else hidden
+        out += [(f"W_z{l}", (hidden, din), True), (f"b_z{l}", (hidden,), False),
+                (f"W_h{l}", (hidden, din + hidden), True), (f"b_h{l}", (hidden,), False),
+                (f"C{l}", (hidden, hidden), True), (f"D{l}", (hidden, din), True)]
+    out += [("W_o", (16, hidden), True), ("b_o", (16,), False)]
+    return out
+
+
+def glorot_params2d(n_layers: int, hidden: int, seed: int = 0) -> np.ndarray:
+    """Glorot-uniform weights, zero biases, for the 2D patched model; FP32."""
+    parts = []
+    off = 0
+    for _, shape, is_w in param_shapes2d(n_layers, hidden):
+        n = int(np.prod(shape))
+        if is_w:
+            fan_out, fan_in = shape
+            lim = np.sqrt(6.0 / (fan_in + fan_out))
+            parts.append((2.0 * uniform(seed, (n,), offset=off) - 1.0) * lim)
+        else:
+            parts.append(np.zeros(n))
+        off += n
+    return np.concatenate(parts).astype(np.float32)
+
+
 def random_params(n_layers: int, hidden: int, seed: int, scale: float = 0.5) -> np.ndarray:
     """Every entry (biases included) uniform in +-scale/sqrt(fan_in); FP32.
     Used by tests to exercise every parameter."""

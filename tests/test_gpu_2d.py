@@ -1,0 +1,122 @@
+"""GPU 2D patched minGRU (psr2d_logpsi, psr2d_local_energy) against the FP64
+oracle of the same model.
+
+Tolerances as for the chain model's FP32 path: |d log psi| <= 1e-5 +
+1e-6 |log psi|; E_loc error <= 1e-3 of |diag| + |E_loc - diag|.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2605_13807_gb300 import api, binding as B, inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    yield
+
+
+def _theta(oracle_mod, nL, H, seed, scale):
+    P = oracle_mod.param_count2d(nL, H)
+    assert P == api.param_count2d(nL, H)
+    # uniform entries of size scale / sqrt(fan-in) keep activations O(1)
+    return (scale * (2.0 * inputs.uniform(seed, (P,)) - 1.0) / np.sqrt(H)).astype(np.float32)
+
+
+def _spins(seed, n, Lx, Ly, u1):
+    N = Lx * Ly
+    return inputs.zero_magnetisation_spins(seed, n, N) if u1 else inputs.random_spins(seed, n, N)
+
+
+@pytest.mark.parametrize("Lx,Ly,H,nL,u1", [(4, 4, 32, 3, False), (6, 4, 64, 2, True),
+                                           (10, 10, 128, 3, True), (8, 6, 32, 1, False),
+                                           (64, 4, 32, 2, False), (2, 8, 64, 3, True)])
+def test_logpsi_matches_oracle(oracle_mod, Lx, Ly, H, nL, u1):
+    theta = _theta(oracle_mod, nL, H, seed=400 + Lx + Ly + H, scale=2.0)
+    s = _spins(401 + Lx, 40, Lx, Ly, u1)
+    cfg = api.ModelConfig(nL, H, u1, "fp32")
+    got = api.logpsi2d(torch.from_numpy(theta).cuda(), torch.from_numpy(s).cuda(), cfg, Lx, Ly)
+    api.sync()
+    ref = oracle_mod.logpsi2d(theta.astype(np.float64), nL, H, Lx, Ly, s, u1=u1)
+    got = got.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got) == np.isfinite(ref))
+    fin = np.isfinite(ref)
+    assert np.all(np.abs(got[fin] - ref[fin]) <= 1e-5 + 1e-6 * np.abs(ref[fin]))
+
+
+@pytest.mark.parametrize("kind,Lx,Ly,H,u1,hf", [(0, 4, 4, 32, True, 0.0), (0, 6, 6, 64, True, 0.0),
+                                                (1, 4, 6, 32, False, 3.044),
+                                                (0, 10, 10, 128, True, 0.0)])
+def test_local_energy_matches_oracle(oracle_mod, kind, Lx, Ly, H, u1, hf):
+    nL = 3
+    theta = _theta(oracle_mod, nL, H, seed=410 + Lx * Ly + kind, scale=2.0)
+    n = 4 if Lx * Ly >= 100 else 12
+    s = (inputs.neel_like_spins(411, n, Lx, Ly) if kind == 0 else inputs.random_spins(411, n, Lx * Ly))
+    ham = B.make_hamiltonian(kind, Lx, Ly, False, True, 1.0, hf)
+    cfg = api.ModelConfig(nL, H, u1, "fp32")
+    e, st = api.local_energy2d(torch.from_numpy(theta).cuda(), torch.from_numpy(s).cuda(), cfg, ham)
+    api.sync()
+    ref = oracle_mod.local_energy2d(theta.astype(np.float64), nL, H, s, kind, Lx, Ly, pbc=False,
+                                    marshall=True, J=1.0, h=hf, u1=u1)
+    _, _, diag = oracle_mod.connected(kind, Lx, Ly, False, s)
+    scale = np.abs(diag) + np.abs(ref - diag)
+    assert np.all(np.abs(e.cpu().numpy() - ref) <= 1e-3 * scale)
+    m, v, se = oracle_mod.stats(e.cpu().numpy().astype(np.float64))
+    assert abs(st[0].item() - m) <= 1e-9 * max(1.0, abs(m))
+
+
+def test_rejected_shapes_and_precision():
+    theta = torch.zeros(api.param_count2d(3, 32), device="cuda")
+    s = torch.zeros((2, 5 * 4), dtype=torch.uint8, device="cuda")
+    out = torch.empty(2, device="cuda")
+    with pytest.raises(B.PsrError) as ei:  # odd Lx
+        B.psr2d_logpsi(B.make_params(theta, 3, 32), s, 5, 4, out)
+    assert ei.value.code == B.PSR_EINVAL
+    s2 = torch.zeros((2, 66 * 2), dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.PsrError) as ei:  # 33 patches in a row
+        B.psr2d_logpsi(B.make_params(theta, 3, 32), s2, 66, 2, out)
+    assert ei.value.code == B.PSR_EUNSUPPORTED
+    s3 = torch.zeros((2, 16), dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.PsrError) as ei:
+        B.psr2d_logpsi(B.make_params(theta, 3, 32, False, "bf16"), s3, 4, 4, out)
+    assert ei.value.code == B.PSR_EUNSUPPORTED
+
+
+def test_52x52_resume_equals_full_forwards(oracle_mod):
+    """52x52, hidden 128, three layers, zero magnetisation: E_loc of two
+    samples (connected configurations resumed at their patch row) equals the
+    combination of full forwards of every connected configuration, and
+    sampled log psi values agree with the oracle."""
+    Lx = Ly = 52
+    nL, H = 3, 128
+    theta = inputs.glorot_params2d(nL, H, seed=0)
+    assert theta.size == oracle_mod.param_count2d(nL, H)
+    s = inputs.neel_like_spins(421, 2, Lx, Ly)
+    ham = B.make_hamiltonian("heisenberg", Lx, Ly, False, True, 1.0, 0.0)
+    cfg = api.ModelConfig(nL, H, True, "fp32")
+    th = torch.from_numpy(theta).cuda()
+    e, _ = api.local_energy2d(th, torch.from_numpy(s).cuda(), cfg, ham)
+    offsets, entries, diag = oracle_mod.connected(0, Lx, Ly, False, s)
+    flipped = np.repeat(s, np.diff(offsets), axis=0)
+    rows = np.arange(flipped.shape[0])
+    flipped[rows, entries[:, 1]] ^= 1
+    flipped[rows, entries[:, 2]] ^= 1
+    lp_s = api.logpsi2d(th, torch.from_numpy(s).cuda(), cfg, Lx, Ly).cpu().numpy().astype(np.float64)
+    lp_f = api.logpsi2d(th, torch.from_numpy(flipped).cuda(), cfg, Lx, Ly).cpu().numpy().astype(np.float64)
+    api.sync()
+    full = np.array([diag[i] - 0.5 * np.sum(np.exp(lp_f[offsets[i]:offsets[i + 1]] - lp_s[i]))
+                     for i in range(2)])
+    scale = np.abs(diag) + np.abs(full - diag)
+    assert np.all(np.abs(e.cpu().numpy() - full) <= 1e-4 * scale)
+    pick = np.random.default_rng(0).choice(flipped.shape[0], 6, replace=False)
+    ref = oracle_mod.logpsi2d(theta.astype(np.float64), nL, H, Lx, Ly,
+                              np.concatenate([s, flipped[pick]]), u1=True)
+    got = np.concatenate([lp_s, lp_f[pick]])
+    assert np.all(np.abs(got - ref) <= 1e-5 + 1e-6 * np.abs(ref))
