@@ -561,7 +561,7 @@ int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t 
     const F32Layout fl = f32_layout(nL, H);
     const int64_t P = tl.total;
     const int W = (int)words_per_row(L);
-    const int nch = (L + kChunkF32 - 1) / kChunkF32;
+    const int nch = (L + kChunkGrad - 1) / kChunkGrad;
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(spins),
                d_dout = dout ? is_device_ptr(dout) : true, d_g = is_device_ptr(dparams);
     int per_sm = 1;
@@ -633,7 +633,7 @@ int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t 
     jb.status = ctx->status;
     {
         StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
-        PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st));
+        PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st, kChunkGrad));
     }
     {
         StageScope sc(ctx, PSR_STAGE_BWD);

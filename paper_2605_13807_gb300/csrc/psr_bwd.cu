@@ -28,7 +28,7 @@
 namespace psr {
 
 namespace {
-constexpr int CH = kChunkF32;
+constexpr int CH = kChunkGrad;
 constexpr int LD = CH + 4;
 enum { TQ_U = 0, TQ_A = 1, TQ_C = 2, TQ_H = 3, TQ_Y = 4, TQ_N = 5 };
 }  // namespace
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
             uint32_t cur, prev;
             chunk_bits32(row, t0, -1, -1, cur, prev);
             const int nvalid = min(CH, N - t0);
-            if (nvalid < 32) cur &= (1u << nvalid) - 1u;
+            cur &= (1u << nvalid) - 1u;
             const uint32_t prevbits = (cur << 1) | prev;
             if (j < CH) S.code[j] = (t0 + j == 0) ? 0 : 1 + (int)((prevbits >> j) & 1u);
             float hprevl[CH];

@@ -150,10 +150,10 @@ cudaError_t launch_bitpack(const uint8_t *spins, int64_t n, int N, int W, uint64
     return cudaGetLastError();
 }
 
-template <int H>
+template <int H, int CH>
 __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJobs jb,
                                                    const float *__restrict__ pk, F32Layout fl) {
-    constexpr int CH = kChunkF32;
+    static_assert(CH == 16 || CH == 32, "chunk of 16 or 32 sites");
     constexpr int LD = CH + 4;  // padded row: conflict-free float4 row writes
     extern __shared__ __align__(16) float smem[];
     float *xs = smem;              // [H][LD] layer input / output
@@ -329,15 +329,15 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                 __syncthreads();
             }
 
-            // readout: thread t < 32 handles site t0 + t
-            if (j < CH) {
+            // readout: thread t < CH handles site t0 + t (warp 0 reduces)
+            if (j < 32) {
                 const int t = j;
-                float d = bd;
-                const float *wd = pk + fl.wd;
-                for (int k = 0; k < H; ++k) d += wd[k] * xs[k * LD + t];
                 float v = 0.0f;
                 const int tt = t0 + t;
-                if (tt < N) {
+                if (t < CH && tt < N) {
+                    float d = bd;
+                    const float *wd = pk + fl.wd;
+                    for (int k = 0; k < H; ++k) d += wd[k] * xs[k * LD + t];
                     const int s = (cur >> t) & 1u;
                     const int nu = n_up + __popc(cur & ((1u << t) - 1u));
                     const float lp = site_logp(d, s, u1_forced(G.u1, N, tt, nu));
@@ -355,28 +355,37 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
     }
 }
 
-template <int H>
+template <int H, int CH>
 static cudaError_t launch_fwd_f32_h(const FwdJobs &jobs, const float *packed, const F32Layout &fl,
                                     int num_sms, cudaStream_t stream) {
-    const size_t smem = (size_t)(2 * H * (kChunkF32 + 4) + kMaxLayers * H) * sizeof(float);
+    const size_t smem = (size_t)(2 * H * (CH + 4) + kMaxLayers * H) * sizeof(float);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_f32_kernel<H>, H, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_f32_kernel<H, CH>, H, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
     const int64_t nj = max_jobs(jobs);
     if (nj < grid) grid = nj;
     if (grid < 1) grid = 1;
-    fwd_f32_kernel<H><<<(int)grid, H, smem, stream>>>(jobs, packed, fl);
+    fwd_f32_kernel<H, CH><<<(int)grid, H, smem, stream>>>(jobs, packed, fl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_f32(const FwdJobs &jobs, const float *packed, const F32Layout &fl,
-                           int num_sms, cudaStream_t stream) {
+                           int num_sms, cudaStream_t stream, int chunk) {
+    if (chunk == kChunkGrad) {
+        switch (fl.H) {
+            case 32: return launch_fwd_f32_h<32, kChunkGrad>(jobs, packed, fl, num_sms, stream);
+            case 64: return launch_fwd_f32_h<64, kChunkGrad>(jobs, packed, fl, num_sms, stream);
+            case 128: return launch_fwd_f32_h<128, kChunkGrad>(jobs, packed, fl, num_sms, stream);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (chunk != kChunkF32) return cudaErrorInvalidValue;
     switch (fl.H) {
-        case 32: return launch_fwd_f32_h<32>(jobs, packed, fl, num_sms, stream);
-        case 64: return launch_fwd_f32_h<64>(jobs, packed, fl, num_sms, stream);
-        case 128: return launch_fwd_f32_h<128>(jobs, packed, fl, num_sms, stream);
+        case 32: return launch_fwd_f32_h<32, kChunkF32>(jobs, packed, fl, num_sms, stream);
+        case 64: return launch_fwd_f32_h<64, kChunkF32>(jobs, packed, fl, num_sms, stream);
+        case 128: return launch_fwd_f32_h<128, kChunkF32>(jobs, packed, fl, num_sms, stream);
         default: return cudaErrorInvalidValue;
     }
 }

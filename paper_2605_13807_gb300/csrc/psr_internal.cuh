@@ -10,6 +10,7 @@ namespace psr {
 
 constexpr int kMaxLayers = 8;
 constexpr int kChunkF32 = 32;   // scan chunk of the FP32 SIMT path (sites)
+constexpr int kChunkGrad = 16;  // chunk of the gradient path (carries, recompute)
 constexpr int kChunkBF16 = 64;  // scan chunk of the tcgen05 path (sites = MMA N)
 
 // Device status word values (first error wins).
@@ -90,8 +91,9 @@ cudaError_t launch_pack_theta_f32(const float *theta, const ThetaLayout &tl, con
                                   float *packed, cudaStream_t stream);
 cudaError_t launch_bitpack(const uint8_t *spins, int64_t n, int N, int W, uint64_t *bits,
                            int *status, cudaStream_t stream);
+// chunk: kChunkF32 (log psi, E_loc) or kChunkGrad (carries for psr_grad)
 cudaError_t launch_fwd_f32(const FwdJobs &jobs, const float *packed, const F32Layout &fl,
-                           int num_sms, cudaStream_t stream);
+                           int num_sms, cudaStream_t stream, int chunk = kChunkF32);
 
 // tcgen05 path (hidden = 128, 3 layers).
 size_t bf16_packed_bytes();
