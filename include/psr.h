@@ -276,6 +276,16 @@ int psr_sample(const psr_params *params, const float *uniforms, int64_t n, int32
 int psr_sample_tile_for(psr_context *ctx, int64_t n, int32_t L, int32_t n_layers, int32_t hidden,
                         int32_t *per_cta, int32_t *tuned);
 
+/* Self-test of the bounded device waits (failure detection without a GPU
+ * fault).  Runs a two-chunk scan of one short sequence whose first chunk is
+ * deliberately left unprocessed, so the second chunk's look-back wait finds
+ * a flag that nothing sets and gives up at its 2 s limit.  Returns
+ * PSR_ETIMEOUT (read from, and cleared in, the context's status word) when
+ * the bound works; the context stays usable afterwards.  elapsed_ms (may be
+ * NULL) receives the device time of the scan.  Synchronises the stream.
+ * PSR_EINVAL during stream capture.  The paper has no counterpart. */
+int psr_selftest_wait_timeout(psr_context *ctx, float *elapsed_ms);
+
 /* Enables (1) or disables (0) the autotuner of this context.  While enabled,
  * the first call of psr_scan or psr_sample for a shape it has not seen
  * (scan: n, N, H; sample: n, L, layers, hidden), when not being captured

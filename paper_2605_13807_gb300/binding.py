@@ -54,7 +54,7 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc",
             "psr_local_energy_batch", "psr_context_set_graphs", "psr_scan", "psr_scan_tiled",
             "psr_scan_tile_for", "psr_context_set_autotune", "psr_sample", "psr_sample_tile_for",
-            "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy")
+            "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy", "psr_selftest_wait_timeout")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -98,6 +98,7 @@ def lib():
                 L.psr2d_logpsi.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp]
                 L.psr2d_local_energy.argtypes = [C.POINTER(psr_params), vp, i64,
                                                  C.POINTER(psr_hamiltonian), vp, vp]
+                L.psr_selftest_wait_timeout.argtypes = [vp, C.POINTER(C.c_float)]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -309,3 +310,11 @@ def psr2d_local_energy(params, samples, ham, out, stats=None):
     _check(lib().psr2d_local_energy(C.byref(params), _ptr(samples), int(n), C.byref(ham), _ptr(out),
                                     _ptr(stats)), "psr2d_local_energy")
     return out
+
+
+def psr_selftest_wait_timeout(ctx):
+    """(return code, device ms) of the bounded-wait self-test; the code is
+    PSR_ETIMEOUT when the bound works."""
+    ms = C.c_float()
+    rc = lib().psr_selftest_wait_timeout(C.c_void_p(ctx), C.byref(ms))
+    return int(rc), float(ms.value)

@@ -958,9 +958,11 @@ std::vector<psr_scan_tile> scan_candidates(const psr_context *ctx, int64_t n, in
     return out;
 }
 
+// first_ticket > 0 leaves the tiles before it unprocessed (used only by the
+// bounded-wait self-test: their look-back flags are never set).
 int enqueue_scan(psr_context *ctx, const float *a, const float *b, const float *h0, int64_t n,
                  int N, int H, float *h, psr_scan_tile tile, unsigned long long *counter,
-                 int *flags, float *desc) {
+                 int *flags, float *desc, int first_ticket = 0) {
     cudaStream_t st = ctx->stream;
     ScanArgs g{};
     g.a = a;
@@ -977,6 +979,8 @@ int enqueue_scan(psr_context *ctx, const float *a, const float *b, const float *
     g.desc = desc;
     g.status = ctx->status;
     PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    if (first_ticket > 0 && first_ticket < 256)
+        PSR_TRY(cudaMemsetAsync(counter, first_ticket, 1, st));  // low byte (little endian)
     if (g.nch > 1) PSR_TRY(cudaMemsetAsync(flags, 0, (size_t)g.n_tiles * sizeof(int), st));
     PSR_TRY(launch_scan(g, tile.units, ctx->num_sms, st));
     return PSR_OK;
@@ -1077,6 +1081,49 @@ int scan_impl(psr_context *ctx, const float *a, const float *b, const float *h0,
 }  // namespace
 
 extern "C" {
+
+int psr_selftest_wait_timeout(psr_context *ctx, float *elapsed_ms) {
+    if (!ctx || ctx->capturing) return PSR_EINVAL;
+    // one sequence, 64 sites, 4 units, two chunks of 32: tile 0 is skipped,
+    // so tile 1 waits for a flag that nothing sets
+    const int N = 64, H = 4;
+    float *a = nullptr, *b = nullptr, *h = nullptr, *desc = nullptr;
+    unsigned long long *counter = nullptr;
+    int *flags = nullptr;
+    auto carve = [&](Carver &c) {
+        a = c.get<float>((size_t)N * H);
+        b = c.get<float>((size_t)N * H);
+        h = c.get<float>((size_t)N * H);
+        counter = c.get<unsigned long long>(1);
+        flags = c.get<int>(2);
+        desc = c.get<float>(2 * 3 * 4);
+    };
+    Carver sz;
+    carve(sz);
+    int rc = ensure_ws(ctx, sz.off);
+    if (rc != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    if ((rc = take_status(ctx)) != PSR_OK) return rc;  // start from a clean status word
+    PSR_TRY(cudaMemsetAsync(a, 0, (size_t)N * H * sizeof(float), st));
+    PSR_TRY(cudaMemsetAsync(b, 0, (size_t)N * H * sizeof(float), st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PSR_TRY(cudaEventCreate(&e0));
+    PSR_TRY(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    rc = enqueue_scan(ctx, a, b, nullptr, 1, N, H, h, psr_scan_tile{4, 32}, counter, flags, desc, 1);
+    cudaEventRecord(e1, st);
+    const int status = take_status(ctx);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (elapsed_ms) *elapsed_ms = ms;
+    if (rc != PSR_OK) return rc;
+    return status;
+}
 
 int psr_context_set_autotune(psr_context *ctx, int enable) {
     if (!ctx || (enable != 0 && enable != 1)) return PSR_EINVAL;

@@ -154,3 +154,19 @@ def test_full_size_sampled_columns(oracle_mod):
     b_s = b_c[:, None, :].transpose(0, 2, 1)
     sub = [(k, 0) for k in range(len(cols))]
     _check(oracle_mod, a_s, b_s, h0_c[:, None], h_c[:, :, None], sub)
+
+
+def test_bounded_wait_expires_and_context_recovers(oracle_mod):
+    """A look-back wait on a flag that nothing sets gives up after its limit,
+    reports PSR_ETIMEOUT through the status word and leaves the context
+    usable (failure detection without a GPU fault)."""
+    ctx = B.context()
+    rc, ms = B.psr_selftest_wait_timeout(ctx)
+    assert rc == B.PSR_ETIMEOUT
+    assert 1500.0 <= ms <= 20000.0, ms
+    B.psr_context_sync(ctx)  # the status word was cleared
+    a, b, h0 = inputs.scan_inputs(16, 2, 300, 16)
+    ta, tb, th0 = (torch.from_numpy(x).cuda() for x in (a, b, h0))
+    h = api.scan(ta, tb, th0, tile=(16, 64))
+    api.sync()
+    _check(oracle_mod, a, b, h0, h.cpu().numpy())
