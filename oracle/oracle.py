@@ -17,7 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "psr_oracle.c")
-_SRCS = (_SRC, os.path.join(_HERE, "psr_oracle2d.c"))
+_SRCS = (_SRC, os.path.join(_HERE, "psr_oracle2d.c"), os.path.join(_HERE, "psr_oracle_lru.c"))
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 
@@ -80,6 +80,12 @@ def lib():
         _lib.psro2d_logpsi.argtypes = [vp, i, i, i, i, i, vp, vp]
         _lib.psro2d_sample.restype = None
         _lib.psro2d_sample.argtypes = [vp, i, i, i, i, i, l, vp, vp, vp]
+        _lib.psro_lru_param_count.restype = l
+        _lib.psro_lru_param_count.argtypes = [i, i]
+        _lib.psro_lru_logpsi.restype = d
+        _lib.psro_lru_logpsi.argtypes = [vp, i, i, i, vp, i, vp]
+        _lib.psro_lru_sample.restype = None
+        _lib.psro_lru_sample.argtypes = [vp, i, i, i, i, l, vp, vp, vp]
     return _lib
 
 
@@ -320,6 +326,65 @@ def local_energy2d(theta, n_layers, hidden, spins, kind, Lx, Ly, pbc=False, mars
         flipped[rows[has_q], ent[has_q, 2]] ^= 1
     lp_s = logpsi2d(theta, n_layers, hidden, Lx, Ly, s, u1=u1, threads=threads)
     lp_sp = logpsi2d(theta, n_layers, hidden, Lx, Ly, flipped, u1=u1, threads=threads) \
+        if flipped.shape[0] else np.empty(0)
+    c = offdiag_coeff(kind, J=J, h=h, marshall=marshall)
+    return np.array([eloc_combine(diag[i], c, lp_s[i], lp_sp[offsets[i]:offsets[i + 1]])
+                     for i in range(n)])
+
+
+# --------------------------------------------------------- deep 1D LRU model
+
+def param_count_lru(n_layers: int, hidden: int) -> int:
+    return int(lib().psro_lru_param_count(n_layers, hidden))
+
+
+def logpsi_lru(theta, n_layers, hidden, spins, u1=False, threads=None, per_site=False):
+    """log psi of the deep LRU for every row of spins [n, N]; optionally the
+    per-site log P [n, N]."""
+    th = _theta64(theta)
+    s = _spins(spins)
+    n, N = s.shape
+    out = np.empty(n)
+    lp = np.empty((n, N)) if per_site else None
+    L = lib()
+
+    def one(i):
+        row = np.ascontiguousarray(s[i])
+        buf = np.empty(N) if per_site else None
+        out[i] = L.psro_lru_logpsi(_p(th), n_layers, hidden, int(u1), _p(row), N,
+                                   _p(buf) if per_site else None)
+        if per_site:
+            lp[i] = buf
+
+    _map(one, n, threads)
+    return (out, lp) if per_site else out
+
+
+def sample_lru(theta, n_layers, hidden, N, uniforms, u1=False):
+    th = _theta64(theta)
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    n = u.shape[0]
+    out = np.empty((n, N), dtype=np.uint8)
+    lps = np.empty(n)
+    lib().psro_lru_sample(_p(th), n_layers, hidden, int(u1), N, n, _p(u), _p(out), _p(lps))
+    return out, lps
+
+
+def local_energy_lru(theta, n_layers, hidden, spins, kind, Lx, Ly, pbc=False, marshall=True,
+                     J=1.0, h=0.0, u1=False, threads=None):
+    """E_loc of the deep LRU: connected configurations evaluated by full
+    forwards and combined with the diagonal energy."""
+    s = _spins(spins)
+    n, N = s.shape
+    offsets, ent, diag = connected(kind, Lx, Ly, pbc, s, J=J)
+    flipped = np.repeat(s, np.diff(offsets), axis=0)
+    rows = np.arange(flipped.shape[0])
+    if flipped.shape[0]:
+        flipped[rows, ent[:, 1]] ^= 1
+        has_q = ent[:, 2] >= 0
+        flipped[rows[has_q], ent[has_q, 2]] ^= 1
+    lp_s = logpsi_lru(theta, n_layers, hidden, s, u1=u1, threads=threads)
+    lp_sp = logpsi_lru(theta, n_layers, hidden, flipped, u1=u1, threads=threads) \
         if flipped.shape[0] else np.empty(0)
     c = offdiag_coeff(kind, J=J, h=h, marshall=marshall)
     return np.array([eloc_combine(diag[i], c, lp_s[i], lp_sp[offsets[i]:offsets[i + 1]])
