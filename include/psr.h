@@ -333,6 +333,31 @@ int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int3
 int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
                        const psr_hamiltonian *hamiltonian, float *out, double *stats);
 
+/* ---------------------------------------------------------------------
+ * The paper's deep 1D LRU ansatz (Sec. II.B Eq. lru; Sec. II.G 1D residual;
+ * Sec. III.B: each layer an LRU followed by a single-layer GLU feed-forward
+ * network).  With d = d_h = hidden and layer input u_t (onehot(s_{t-1}) at
+ * layer 0, zero at t = 0; x_t of the layer below otherwise):
+ *   h_t = lambda h_{t-1} + e^gamma (B u_t),  lambda = exp(-e^nu + i e^theta),
+ *   y_t = Re(C h_t) + D u_t,
+ *   x_t = (W_a y_t + b_a) sigmoid(W_g y_t + b_g) + [layer >= 1] u_t,
+ * with complex B, C; D is a hidden x 2 matrix at layer 0 (one-hot input) and
+ * diagonal (hidden entries) above.  Readout, u1_mask and spins as for
+ * psr_logpsi.  theta: float, per layer nu[H], theta[H], gamma[H],
+ * B_re[H][din], B_im[H][din], C_re[H][H], C_im[H][H], D ([H][2] at layer 0,
+ * else [H]), W_a[H][H], b_a[H], W_g[H][H], b_g[H] (din = 2 at layer 0, else
+ * H), then W_o[2][H], b_o[2]; 16 H^2 + 25 H + 2 values for three layers.
+ * Computed in FP32 on CUDA cores (PSR_EUNSUPPORTED for PSR_BF16). */
+int psr_lru_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
+
+int psr_lru_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, float *out);
+
+/* Local energy of the LRU ansatz over every connected configuration
+ * (connected configurations resume at their first flipped site's chunk from
+ * the sample's complex chunk carries), as psr_local_energy. */
+int psr_lru_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                         const psr_hamiltonian *hamiltonian, float *out, double *stats);
+
 /* Stages of the launch sequence, for per-stage device timing. */
 enum {
     PSR_STAGE_PACK = 0,          /* parameter packing and spin bit-packing */

@@ -6,6 +6,7 @@
     scan(a, b, h0=None)                  -> float32 [n, N, H], h_t = a_t h_{t-1} + b_t
     sample(theta, uniforms, cfg)         -> (uint8 [n, L] exact samples, float32 [n] log psi)
     logpsi2d / local_energy2d            -> the 2D patched minGRU (Lx, Ly even)
+    logpsi_lru / local_energy_lru        -> the deep 1D LRU ansatz
     grad(theta, spins, dout=None)        -> float32 [n, P] (O_k) or [P]
     LogPsi.apply(theta, spins, cfg)      -> differentiable log psi; backward = psr_grad
 
@@ -147,6 +148,30 @@ def local_energy2d(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, out
         stats = torch.empty(3, dtype=torch.float64, device=dev)
     p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
     B.psr2d_local_energy(p, samples, ham, out, stats)
+    return out, stats
+
+
+def param_count_lru(n_layers: int = 3, hidden: int = 64) -> int:
+    return B.psr_lru_param_count(n_layers, hidden)
+
+
+def logpsi_lru(theta, spins, cfg: ModelConfig, out=None):
+    """log psi of the deep 1D LRU ansatz (spins [n, L] in sequence order)."""
+    dev = _device_of(spins, theta)
+    if out is None:
+        out = torch.empty(spins.shape[0], dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    return B.psr_lru_logpsi(p, spins, out)
+
+
+def local_energy_lru(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, out=None, stats=None):
+    dev = _device_of(samples, theta)
+    if out is None:
+        out = torch.empty(samples.shape[0], dtype=torch.float32, device=dev)
+    if stats is None:
+        stats = torch.empty(3, dtype=torch.float64, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_lru_local_energy(p, samples, ham, out, stats)
     return out, stats
 
 

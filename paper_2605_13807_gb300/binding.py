@@ -54,7 +54,8 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc",
             "psr_local_energy_batch", "psr_context_set_graphs", "psr_scan", "psr_scan_tiled",
             "psr_scan_tile_for", "psr_context_set_autotune", "psr_sample", "psr_sample_tile_for",
-            "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy", "psr_selftest_wait_timeout")
+            "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy", "psr_selftest_wait_timeout",
+            "psr_lru_param_count", "psr_lru_logpsi", "psr_lru_local_energy")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -99,6 +100,10 @@ def lib():
                 L.psr2d_local_energy.argtypes = [C.POINTER(psr_params), vp, i64,
                                                  C.POINTER(psr_hamiltonian), vp, vp]
                 L.psr_selftest_wait_timeout.argtypes = [vp, C.POINTER(C.c_float)]
+                L.psr_lru_param_count.argtypes = [i32, i32, C.POINTER(i64)]
+                L.psr_lru_logpsi.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp]
+                L.psr_lru_local_energy.argtypes = [C.POINTER(psr_params), vp, i64,
+                                                   C.POINTER(psr_hamiltonian), vp, vp]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -318,3 +323,23 @@ def psr_selftest_wait_timeout(ctx):
     ms = C.c_float()
     rc = lib().psr_selftest_wait_timeout(C.c_void_p(ctx), C.byref(ms))
     return int(rc), float(ms.value)
+
+
+def psr_lru_param_count(n_layers, hidden):
+    P = C.c_int64()
+    _check(lib().psr_lru_param_count(int(n_layers), int(hidden), C.byref(P)), "psr_lru_param_count")
+    return int(P.value)
+
+
+def psr_lru_logpsi(params, spins, out):
+    n, L = spins.shape
+    _check(lib().psr_lru_logpsi(C.byref(params), _ptr(spins), int(n), int(L), _ptr(out)),
+           "psr_lru_logpsi")
+    return out
+
+
+def psr_lru_local_energy(params, samples, ham, out, stats=None):
+    n = samples.shape[0]
+    _check(lib().psr_lru_local_energy(C.byref(params), _ptr(samples), int(n), C.byref(ham), _ptr(out),
+                                      _ptr(stats)), "psr_lru_local_energy")
+    return out

@@ -193,6 +193,26 @@ cudaError_t launch_pack_theta_f2(const float *theta, const F2Layout &f, float *p
 cudaError_t launch_fwd2d_f32(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f,
                              int num_sms, cudaStream_t stream);
 
+// Deep 1D LRU (psr_lru.cu), FP32.  Packed: per layer lambda (Re, Im) and
+// e^gamma [H], B^T (Re, Im) [din][H], C^T (Re, Im) [H][H], D ([2][H] at
+// layer 0, else [H]), W_a^T, W_g^T [H][H], b_a, b_g [H]; readout as the logit
+// difference wd [H], bd.  Jobs use FwdJobs (carries [n][nch][nL][2][H]).
+struct LruLayout {
+    int nL, H;
+    int64_t lre[kMaxLayers], lim[kMaxLayers], gam[kMaxLayers];
+    int64_t BreT[kMaxLayers], BimT[kMaxLayers], CreT[kMaxLayers], CimT[kMaxLayers], D[kMaxLayers];
+    int64_t WaT[kMaxLayers], ba[kMaxLayers], WgT[kMaxLayers], bg[kMaxLayers];
+    int64_t wd, bd;
+    int64_t total;
+};
+LruLayout lru_layout(int nL, int H);
+int64_t param_count_lru(int nL, int H);
+constexpr int kChunkLru = 32;
+cudaError_t launch_pack_theta_lru(const float *theta, const LruLayout &f, float *packed,
+                                  cudaStream_t stream);
+cudaError_t launch_lru_f32(const FwdJobs &jobs, const float *packed, const LruLayout &f, int num_sms,
+                           cudaStream_t stream);
+
 // Backward (FP32).
 size_t bwd_tape_floats_per_cta(int nL, int H);
 cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1,

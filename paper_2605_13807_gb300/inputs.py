@@ -208,3 +208,46 @@ def scan_inputs_device(seed: int, n: int, N: int, H: int, device):
     b = torch.rand((n, N, H), generator=g, device=device, dtype=torch.float32).mul_(2.0).sub_(1.0)
     h0 = torch.rand((n, H), generator=g, device=device, dtype=torch.float32).mul_(2.0).sub_(1.0)
     return a, b, h0
+
+
+def param_shapes_lru(n_layers: int, hidden: int):
+    """(name, shape) in the flat parameter order of the deep 1D LRU."""
+    out = []
+    for l in range(n_layers):
+        din = 2 if l == 0 else hidden
+        out += [(f"nu{l}", (hidden,)), (f"theta{l}", (hidden,)), (f"gamma{l}", (hidden,)),
+                (f"B_re{l}", (hidden, din)), (f"B_im{l}", (hidden, din)),
+                (f"C_re{l}", (hidden, hidden)), (f"C_im{l}", (hidden, hidden)),
+                (f"D{l}", (hidden, 2) if l == 0 else (hidden,)),
+                (f"W_a{l}", (hidden, hidden)), (f"b_a{l}", (hidden,)),
+                (f"W_g{l}", (hidden, hidden)), (f"b_g{l}", (hidden,))]
+    out += [("W_o", (2, hidden)), ("b_o", (2,))]
+    return out
+
+
+def lru_params(n_layers: int, hidden: int, seed: int = 0) -> np.ndarray:
+    """Seeded LRU parameters in the usual ring initialisation: |lambda| =
+    exp(-e^nu) uniform in [0.9, 0.999], phase e^theta uniform in
+    [0.01, 0.1 * 2 pi], gamma = log sqrt(1 - |lambda|^2) (unit-variance
+    states); matrices U(+-1/sqrt(fan_in)), biases 0; FP32."""
+    parts = []
+    off = 0
+    for name, shape in param_shapes_lru(n_layers, hidden):
+        n = int(np.prod(shape))
+        u = uniform(seed, (n,), offset=off)
+        off += n
+        base = name.rstrip("0123456789")
+        if base == "nu":
+            r = 0.9 + 0.099 * u
+            parts.append(np.log(-np.log(r)))
+            r_last = r
+        elif base == "theta":
+            parts.append(np.log(0.01 + (0.2 * np.pi - 0.01) * u))
+        elif base == "gamma":
+            parts.append(np.log(np.sqrt(1.0 - r_last ** 2)))
+        elif base in ("b_a", "b_g", "b_o"):
+            parts.append(np.zeros(n))
+        else:
+            fan_in = shape[1] if len(shape) == 2 else 1
+            parts.append((2.0 * u - 1.0) / np.sqrt(fan_in))
+    return np.concatenate(parts).astype(np.float32)
