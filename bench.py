@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-scan", action="store_true")
     ap.add_argument("--no-sample", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--no-lru", action="store_true")
     ap.add_argument("--samples-2d", type=int, default=64,
                     help="samples of the 2D patched-model leg (52x52, FP32)")
     ap.add_argument("--scan-only", action="store_true",
@@ -409,6 +410,62 @@ def model2d_leg(Lx, Ly, n, dev, reps=2):
                          "launch_ms": conn_ms}}
 
 
+# FLOPs per evaluated site of the deep LRU (3 layers, hidden H): layer 0:
+# Re(C h) and the two GLU products (2 x 2H^2 + 2 x 2H^2); layers 1, 2: also
+# the complex B u (2 x 2H^2), so 12 H^2 each.
+def lru_flops_per_site(H):
+    return 8 * H * H + 2 * 12 * H * H
+
+
+def lru_leg(dev, N=256, H=64, n=1024, reps=3):
+    """The paper's deep 1D LRU on the 1D TFIM (Table IV configuration: 3
+    layers, d = d_h = 64, N = 256 OBC, 1024 samples, h = 1): log psi + E_loc
+    over every site flip, FP32 CUDA cores."""
+    import torch
+
+    from paper_2605_13807_gb300 import api, binding as B, inputs
+    ham = B.make_hamiltonian("tfim", N, 1, False, True, 1.0, 1.0)
+    cfg = api.ModelConfig(N_LAYERS, H, False, "fp32")
+    theta = torch.from_numpy(inputs.lru_params(N_LAYERS, H, seed=0)).to(dev)
+    spins = torch.from_numpy(inputs.random_spins(2000, n, N)).to(dev)
+    lp = torch.empty(n, dtype=torch.float32, device=dev)
+    el = torch.empty(n, dtype=torch.float32, device=dev)
+    st = torch.empty(3, dtype=torch.float64, device=dev)
+    E = n * N
+
+    def step():
+        api.logpsi_lru(theta, spins, cfg, out=lp)
+        api.local_energy_lru(theta, spins, cfg, ham, out=el, stats=st)
+
+    step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        step()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx = B.context()
+    B.psr_context_set_profiling(ctx, True)
+    api.local_energy_lru(theta, spins, cfg, ham, out=el, stats=st)
+    conn_ms = B.psr_context_stage_ms(ctx)["fwd_connected"]
+    # sites evaluated by the connected forward: each flip at p resumes at its chunk
+    p = torch.arange(N, device=dev)
+    conn_sites = n * int((N - (p // 32) * 32).sum().item())
+    achieved = conn_sites * lru_flops_per_site(H) / (conn_ms / 1e3) / 1e12
+    return {"model": "deep 1D LRU (complex diagonal recurrence + GLU), FP32 CUDA cores",
+            "workload": f"tfim_chain_{N}_obc_{n}_samples", "hidden": H, "connected": E,
+            "value": (n + E) * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "roofline": {"kernel": "lru_f32_kernel (connected configurations)", "bound": "alu",
+                         "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_SIMT_TFLOPS,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                         "traffic": None, "flops_per_unit": lru_flops_per_site(H),
+                         "launch_ms": conn_ms}}
+
+
 def run_scan_only(args):
     import torch
 
@@ -577,6 +634,8 @@ def run_mine(args):
         line["sample"] = sample_leg(theta, n, N, dev)
     if not args.no_2d and rank == 0:
         line["model2d"] = model2d_leg(Lx, Ly, min(args.samples_2d, n), dev)
+    if not args.no_lru and rank == 0:
+        line["lru"] = lru_leg(dev)
 
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
