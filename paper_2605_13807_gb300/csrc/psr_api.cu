@@ -570,7 +570,7 @@ int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t 
         // backward CTA: H threads and bwd_smem_bytes(H) of shared memory
         int dev_smem = 0;
         cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
-        occ = (int)(dev_smem / (bwd_smem_bytes(H) + 1024));
+        occ = (int)(dev_smem / (bwd_smem_bytes(H, nL) + 1024));
         per_sm = occ < 1 ? 1 : (occ > 4 ? 4 : occ);
     }
     int64_t grid64 = (int64_t)ctx->num_sms * per_sm;

@@ -36,24 +36,22 @@ enum { TQ_U = 0, TQ_A = 1, TQ_C = 2, TQ_H = 3, TQ_Y = 4, TQ_N = 5 };
 __host__ __device__ inline size_t tape_floats(int nL, int H) { return (size_t)nL * TQ_N * CH * H; }
 size_t bwd_tape_floats_per_cta(int nL, int H) { return tape_floats(nL, H); }
 
+// Shared memory of one CTA.  The per-layer carries that follow the struct
+// (hc0, hcar, lam, anext: [nL][H] each) are sized by the layer count.
 template <int H>
 struct BwdSmem {
     float xs[H * LD];        // forward recompute: layer input tile [k][t]
     float hs[H * LD];        // forward recompute: hidden tile [k][t]
     float gy[CH * H];        // [t][j]
-    float gz[CH * H];        // [t][j]
-    float gc[CH * H];        // [t][j]
-    float xl[CH * (H + 1)];  // last-layer output [t][k] (padded)
-    float hc0[kMaxLayers * H];   // carry at chunk start (= h_{t0-1})
-    float hcar[kMaxLayers * H];  // running carry during recompute
-    float lam[kMaxLayers * H];   // adjoint carry lambda_{t0+CH}
-    float anext[kMaxLayers * H]; // a_{t0+CH} of the later chunk
+    float gzc[2 * CH * H];   // gz, gc [t][j] in the layer loop; before it the
+                             // last-layer output xl [t][k] (padded rows)
     float g1[CH];
     int code[CH];
 };
+static_assert(CH * (128 + 1) <= 2 * CH * 128, "xl fits in the gz / gc storage");
 
 template <int H>
-__global__ void __launch_bounds__(H) bwd_f32_kernel(
+__global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
     const uint64_t *__restrict__ bits, int64_t n, int N, int W, int u1,
     const float *__restrict__ theta, ThetaLayout tl, const float *__restrict__ pk, F32Layout fl,
     const float *__restrict__ carries, const float *__restrict__ dout, float *__restrict__ grad_rows,
@@ -62,6 +60,19 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
     BwdSmem<H> &S = *reinterpret_cast<BwdSmem<H> *>(smem_raw);
     const int j = threadIdx.x;
     const int nL = tl.nL;
+    struct {
+        float *hc0, *hcar, *lam, *anext, *gz, *gc, *xl;
+    } V;
+    {
+        float *tail = reinterpret_cast<float *>(smem_raw + sizeof(BwdSmem<H>));
+        V.hc0 = tail;               // carry at chunk start (= h_{t0-1})
+        V.hcar = tail + nL * H;     // running carry during recompute
+        V.lam = tail + 2 * nL * H;  // adjoint carry lambda_{t0+CH}
+        V.anext = tail + 3 * nL * H;  // a_{t0+CH} of the later chunk
+        V.gz = S.gzc;
+        V.gc = S.gzc + CH * H;
+        V.xl = S.gzc;
+    }
     const int nch = (N + CH - 1) / CH;
     const int64_t P = tl.total;
     float *tape = tape_all + (size_t)blockIdx.x * tape_floats(nL, H);
@@ -81,8 +92,8 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
         const float scale = dout ? dout[s] : 1.0f;
         float *G = dout ? grad_rows + (size_t)blockIdx.x * P : grad_rows + (size_t)s * P;
         for (int l = 0; l < nL; ++l) {
-            S.lam[l * H + j] = 0.0f;
-            S.anext[l * H + j] = 0.0f;
+            V.lam[l * H + j] = 0.0f;
+            V.anext[l * H + j] = 0.0f;
         }
         float gbz[kMaxLayers], gbh[kMaxLayers];
 #pragma unroll
@@ -93,8 +104,8 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
             // ------------------------------------------------ recompute chunk
             for (int l = 0; l < nL; ++l) {
                 const float v = carries[(((int64_t)s * nch + c) * nL + l) * H + j];
-                S.hc0[l * H + j] = v;
-                S.hcar[l * H + j] = v;
+                V.hc0[l * H + j] = v;
+                V.hcar[l * H + j] = v;
             }
             uint32_t cur, prev;
             chunk_bits32(row, t0, -1, -1, cur, prev);
@@ -104,7 +115,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
             if (j < CH) S.code[j] = (t0 + j == 0) ? 0 : 1 + (int)((prevbits >> j) & 1u);
             float hprevl[CH];
             {
-                float hv = S.hcar[j];
+                float hv = V.hcar[j];
                 float y[CH];
 #pragma unroll
                 for (int t = 0; t < CH; ++t) {
@@ -167,7 +178,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                 }
                 float hn[CH];
                 {
-                    float hv = S.hcar[l * H + j];
+                    float hv = V.hcar[l * H + j];
 #pragma unroll
                     for (int t = 0; t < CH; ++t) {
                         const float a = sigmoid_f(z[t]);
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                         T(l, TQ_C, t)[j] = y[t];
                         T(l, TQ_H, t)[j] = hv;
                     }
-                    S.hcar[l * H + j] = hv;
+                    V.hcar[l * H + j] = hv;
                 }
                 __syncthreads();  // everyone done reading hs of the previous layer
 #pragma unroll
@@ -211,13 +222,13 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                 __syncthreads();
             }
             // ------------------------------------------------ readout adjoint
-            for (int t = 0; t < CH; ++t) S.xl[t * (H + 1) + j] = S.xs[j * LD + t];
+            for (int t = 0; t < CH; ++t) V.xl[t * (H + 1) + j] = S.xs[j * LD + t];
             __syncthreads();
             if (j < CH) {
                 const int t = j;
                 float d = bd;
                 const float *wd = pk + fl.wd;
-                for (int k = 0; k < H; ++k) d += wd[k] * S.xl[t * (H + 1) + k];
+                for (int k = 0; k < H; ++k) d += wd[k] * V.xl[t * (H + 1) + k];
                 float g = 0.0f;
                 const int tt = t0 + t;
                 if (tt < N) {
@@ -241,7 +252,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
             {
                 float gw = 0.0f, gb = 0.0f;
                 for (int t = 0; t < CH; ++t) {
-                    gw += S.g1[t] * S.xl[t * (H + 1) + j];
+                    gw += S.g1[t] * V.xl[t * (H + 1) + j];
                     gb += S.g1[t];
                 }
                 atomicAdd(&G[tl.Wo + H + j], gw);
@@ -312,26 +323,26 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                 }
                 // reverse scan (thread j = hidden unit j)
                 {
-                    float lam = S.lam[l * H + j];
-                    float an = S.anext[l * H + j];
+                    float lam = V.lam[l * H + j];
+                    float an = V.anext[l * H + j];
                     float sz = 0.0f, sc = 0.0f;
 #pragma unroll
                     for (int t = CH - 1; t >= 0; --t) {
                         lam = ghd[t] + an * lam;
                         const float a = T(l, TQ_A, t)[j];
                         const float cd = T(l, TQ_C, t)[j];
-                        const float hp = (t > 0) ? hk[t - 1] : S.hc0[l * H + j];
+                        const float hp = (t > 0) ? hk[t - 1] : V.hc0[l * H + j];
                         const float ga = lam * (hp - cd);
                         const float gcv = lam * (1.0f - a);
                         const float gzv = ga * a * (1.0f - a);
-                        S.gz[t * H + j] = gzv;
-                        S.gc[t * H + j] = gcv;
+                        V.gz[t * H + j] = gzv;
+                        V.gc[t * H + j] = gcv;
                         sz += gzv;
                         sc += gcv;
                         an = a;
                     }
-                    S.lam[l * H + j] = lam;
-                    S.anext[l * H + j] = an;
+                    V.lam[l * H + j] = lam;
+                    V.anext[l * H + j] = an;
                     gbz[l] += sz;
                     gbh[l] += sc;
                 }
@@ -353,7 +364,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                         float az = 0.0f, ah = 0.0f;
 #pragma unroll
                         for (int t = 0; t < CH; ++t) {
-                            const float gzv = S.gz[t * H + jj], gcv = S.gc[t * H + jj];
+                            const float gzv = V.gz[t * H + jj], gcv = V.gc[t * H + jj];
                             gn[t] += wz * gzv + wh * gcv;
                             az += gzv * uk[t];
                             ah += gcv * uk[t];
@@ -370,7 +381,7 @@ __global__ void __launch_bounds__(H) bwd_f32_kernel(
                     float z0 = 0.0f, z1 = 0.0f, c0v = 0.0f, c1v = 0.0f;
                     for (int t = 0; t < CH; ++t) {
                         const int cd = S.code[t];
-                        const float gzv = S.gz[t * H + j], gcv = S.gc[t * H + j];
+                        const float gzv = V.gz[t * H + j], gcv = V.gc[t * H + j];
                         if (cd == 1) { z0 += gzv; c0v += gcv; }
                         if (cd == 2) { z1 += gzv; c1v += gcv; }
                     }
@@ -398,7 +409,7 @@ static cudaError_t launch_bwd_h(const uint64_t *bits, int64_t n, int N, int W, i
                                 const F32Layout &fl, const float *carries, const float *dout,
                                 float *grad_rows, int grid, float *tape, int *status,
                                 cudaStream_t stream) {
-    const size_t smem = sizeof(BwdSmem<H>);
+    const size_t smem = sizeof(BwdSmem<H>) + 4 * (size_t)tl.nL * H * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(bwd_f32_kernel<H>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -420,11 +431,12 @@ cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1
     }
 }
 
-size_t bwd_smem_bytes(int H) {
+size_t bwd_smem_bytes(int H, int nL) {
+    const size_t tail = 4 * (size_t)nL * H * sizeof(float);
     switch (H) {
-        case 32: return sizeof(BwdSmem<32>);
-        case 64: return sizeof(BwdSmem<64>);
-        default: return sizeof(BwdSmem<128>);
+        case 32: return sizeof(BwdSmem<32>) + tail;
+        case 64: return sizeof(BwdSmem<64>) + tail;
+        default: return sizeof(BwdSmem<128>) + tail;
     }
 }
 

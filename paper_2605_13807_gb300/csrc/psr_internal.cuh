@@ -220,7 +220,7 @@ cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1
                            const F32Layout &fl, const float *carries, const float *dout,
                            float *grad_rows, int grid, float *tape, int *status,
                            cudaStream_t stream);
-size_t bwd_smem_bytes(int H);
+size_t bwd_smem_bytes(int H, int nL);
 cudaError_t launch_reduce_rows(const float *partial, int rows, int64_t P, float *out,
                                cudaStream_t stream);
 
