@@ -44,6 +44,18 @@ def test_param_count_host_only(libpsr):
     assert libpsr.psr_param_count(3, 32, None) == binding.PSR_EINVAL
 
 
+def test_param_counts_of_the_other_models(libpsr):
+    from paper_2605_13807_gb300 import binding, inputs
+    for H in (32, 64, 128):
+        assert binding.psr2d_param_count(3, H) == 12 * H * H + 118 * H + 16
+        assert binding.psr2d_param_count(3, H) == inputs.glorot_params2d(3, H).size
+        assert binding.psr_lru_param_count(3, H) == 16 * H * H + 25 * H + 2
+        assert binding.psr_lru_param_count(3, H) == inputs.lru_params(3, H).size
+    P = C.c_int64()
+    assert libpsr.psr2d_param_count(9, 32, C.byref(P)) == binding.PSR_EINVAL
+    assert libpsr.psr_lru_param_count(3, 32, None) == binding.PSR_EINVAL
+
+
 def test_null_arguments_are_rejected_without_touching_the_device(libpsr):
     from paper_2605_13807_gb300 import binding
     assert libpsr.psr_logpsi(None, None, 1, 1, None) == binding.PSR_EINVAL
@@ -51,6 +63,11 @@ def test_null_arguments_are_rejected_without_touching_the_device(libpsr):
     assert libpsr.psr_grad(None, None, 1, 1, None, None) == binding.PSR_EINVAL
     assert libpsr.psr_connected(None, None, 1, None, None, None, 0, None, None) == binding.PSR_EINVAL
     assert libpsr.psr_context_sync(None) == binding.PSR_EINVAL
+    assert libpsr.psr2d_logpsi(None, None, 1, 4, 4, None) == binding.PSR_EINVAL
+    assert libpsr.psr_lru_logpsi(None, None, 1, 4, None) == binding.PSR_EINVAL
+    assert libpsr.psr_sample(None, None, 1, 4, None, None) == binding.PSR_EINVAL
+    assert libpsr.psr_scan(None, None, None, None, 1, 4, 4, None) == binding.PSR_EINVAL
+    assert libpsr.psr_selftest_wait_timeout(None, None) == binding.PSR_EINVAL
     assert libpsr.psr_context_destroy(None) == binding.PSR_EINVAL
     assert binding.strerror(binding.PSR_ETIMEOUT) == "bounded device wait expired"
 
