@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-sample", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--no-lru", action="store_true")
-    ap.add_argument("--samples-2d", type=int, default=64,
+    ap.add_argument("--samples-2d", type=int, default=32,
                     help="samples of the 2D patched-model leg (52x52, FP32)")
     ap.add_argument("--scan-only", action="store_true",
                     help="only the standalone scan measurement (profiling runs)")
@@ -355,19 +355,21 @@ def sample_leg(theta, n, N, dev, reps=2):
 # FLOPs per evaluated patch of the 2D patched minGRU (3 layers, hidden H):
 # layer 0: W_h h_V and C h (2 x 2H^2); layers 1, 2: W_z x, W_h x, W_h h_V,
 # C h, D x (5 x 2H^2 each).
-FLOPS_PER_PATCH_2D = 2 * HIDDEN * HIDDEN * 12
+def flops_per_patch_2d(H):
+    return 2 * H * H * 12
 
 
-def model2d_leg(Lx, Ly, n, dev, reps=2):
-    """The paper's 2D patched minGRU (FP32 CUDA cores): log psi of n samples
-    plus E_loc over all their connected configurations at Lx x Ly, in the
-    headline metric's unit (configuration x spin site, logical)."""
+def model2d_leg(Lx, Ly, n, dev, reps=2, H=256):
+    """The paper's 2D patched minGRU at its 52x52 configuration (3 layers,
+    d_h = 256, 2x2 patches; FP32 CUDA cores): log psi of n samples plus E_loc
+    over all their connected configurations, in the headline metric's unit
+    (configuration x spin site, logical)."""
     import torch
 
     from paper_2605_13807_gb300 import api, binding as B, inputs
     ham = B.make_hamiltonian("heisenberg", Lx, Ly, False, True, 1.0, 0.0)
-    cfg = api.ModelConfig(N_LAYERS, HIDDEN, True, "fp32")
-    theta = torch.from_numpy(inputs.glorot_params2d(N_LAYERS, HIDDEN, seed=0)).to(dev)
+    cfg = api.ModelConfig(N_LAYERS, H, True, "fp32")
+    theta = torch.from_numpy(inputs.glorot_params2d(N_LAYERS, H, seed=0)).to(dev)
     spins = torch.from_numpy(rank_samples(0, n, Lx, Ly)).to(dev)
     N, Px, Py = Lx * Ly, Lx // 2, Ly // 2
     _, ent, _ = api.connected(spins, ham)
@@ -397,16 +399,17 @@ def model2d_leg(Lx, Ly, n, dev, reps=2):
     api.local_energy2d(theta, spins, cfg, ham, out=el, stats=st)
     conn_ms = B.psr_context_stage_ms(ctx)["fwd_connected"]
     conn_patches = evaluated - n * Px * Py
-    achieved = conn_patches * FLOPS_PER_PATCH_2D / (conn_ms / 1e3) / 1e12
+    achieved = conn_patches * flops_per_patch_2d(H) / (conn_ms / 1e3) / 1e12
     return {"model": "2D patched minGRU (2x2 patches, vertical h_V coupling), FP32 CUDA cores",
-            "lattice": f"{Lx}x{Ly} OBC", "samples": n, "connected": E,
+            "lattice": f"{Lx}x{Ly} OBC", "hidden": H, "layers": N_LAYERS, "samples": n,
+            "connected": E,
             "value": (n + E) * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "evaluated_patches_per_step": evaluated,
             "roofline": {"kernel": "fwd2d_f32_kernel (connected configurations)", "bound": "alu",
                          "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_SIMT_TFLOPS,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                         "traffic": None, "flops_per_unit": FLOPS_PER_PATCH_2D,
+                         "traffic": None, "flops_per_unit": flops_per_patch_2d(H),
                          "launch_ms": conn_ms}}
 
 

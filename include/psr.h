@@ -319,8 +319,10 @@ int psr_context_set_autotune(psr_context *ctx, int enable);
  * the length (12 H^2 + 118 H + 16 for three layers).
  * Computed in FP32 on CUDA cores, row by row: within a patch row all sites
  * share one batched projection and one scan (the row starts from h_H = 0).
- * PSR_EUNSUPPORTED for precision PSR_BF16 or Lx > 64 (more than 32 patches
- * per row); PSR_EINVAL for odd Lx or Ly and what psr_logpsi rejects. */
+ * hidden may also be 256 (the paper's 52 x 52 model) with at most 4 layers.
+ * PSR_EUNSUPPORTED for precision PSR_BF16, Lx > 64 (more than 32 patches
+ * per row) or hidden 256 with more than 4 layers; PSR_EINVAL for odd Lx or
+ * Ly and what psr_logpsi rejects. */
 int psr2d_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
 
 int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,

@@ -1240,7 +1240,8 @@ namespace {
 int check_params2d(const psr_params *p, int64_t n, int Lx, int Ly) {
     if (!p || !p->ctx || !p->theta) return PSR_EINVAL;
     if (p->n_layers < 1 || p->n_layers > kMaxLayers) return PSR_EINVAL;
-    if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128) return PSR_EINVAL;
+    if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128 && p->hidden != 256) return PSR_EINVAL;
+    if (p->hidden == 256 && p->n_layers > 4) return PSR_EUNSUPPORTED;  // shared memory
     if (p->u1_mask != 0 && p->u1_mask != 1) return PSR_EINVAL;
     if (p->precision != PSR_FP32 && p->precision != PSR_BF16) return PSR_EINVAL;
     if (n < 1 || n > (int64_t)1 << 31) return PSR_EINVAL;

@@ -421,6 +421,7 @@ cudaError_t launch_fwd2d_f32(const Fwd2Jobs &jobs, const float *packed, const F2
         case 32: return launch_fwd2d_h<32>(jobs, packed, f, num_sms, stream);
         case 64: return launch_fwd2d_h<64>(jobs, packed, f, num_sms, stream);
         case 128: return launch_fwd2d_h<128>(jobs, packed, f, num_sms, stream);
+        case 256: return launch_fwd2d_h<256>(jobs, packed, f, num_sms, stream);
         default: return cudaErrorInvalidValue;
     }
 }
