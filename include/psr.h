@@ -360,6 +360,58 @@ int psr_lru_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, in
 int psr_lru_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
                          const psr_hamiltonian *hamiltonian, float *out, double *stats);
 
+/* ---------------------------------------------------------------------
+ * c4v symmetrisation (the point-group symmetry the paper imposes on its 2D
+ * runs, Sec. III.C, in the form of the RNN wave-function work it cites):
+ *   psi_sym(s) = sqrt(1/8 sum_g psi(g s)^2)
+ * over the 8 operations g of c4v on an L x L lattice (identity, rotations by
+ * 90, 180, 270 degrees, reflections in x, in y and in both diagonals), image
+ * g of a configuration being (g s)(g(x)) = s(x).  Model, parameters and
+ * precision as psr_logpsi (chain minGRU along the zigzag path); every call
+ * evaluates the 8 images (8 x the work).  PSR_EINVAL unless Lx == Ly. */
+int psr_sym_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
+                   float *out);
+
+/* E_loc of psi_sym: E_loc(s) = diag(s) + sum_e c_e psi_sym(s'_e) / psi_sym(s).
+ * The images of a connected configuration are connected configurations of
+ * the sample's images (sites g(p), g(q) flipped), so each resumes from the
+ * stored carries of its image sample.  Otherwise as psr_local_energy;
+ * PSR_EINVAL unless Lx == Ly. */
+int psr_sym_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                         const psr_hamiltonian *hamiltonian, float *out, double *stats);
+
+/* Adam state (Sec. III.B; Kingma and Ba): m = beta1 m + (1 - beta1) g,
+ * v = beta2 v + (1 - beta2) g^2, theta -= lr m^ / (sqrt(v^) + eps) with the
+ * bias corrections m^ = m / (1 - beta1^step), v^ = v / (1 - beta2^step).
+ * m, v: device float [P], zero before the first step, updated in place. */
+typedef struct {
+    float lr, beta1, beta2, eps;
+    int32_t step; /* 1-based count of this update */
+    float *m, *v;
+} psr_adam;
+
+/* One VMC step on the device (Sec. III.B: exact sampling, local energy,
+ * stochastic energy gradient, Adam):
+ *   1. n exact samples s_i of |psi|^2 from uniforms [n][N] (psr_sample); with
+ *      symmetrize = 1, sample i is replaced by its c4v image
+ *      g_i = floor(8 sym_uniforms[i]), which makes it a sample of |psi_sym|^2;
+ *   2. E_loc (psr_local_energy or psr_sym_local_energy) and its FP64 mean,
+ *      variance and standard error;
+ *   3. the energy gradient 2/n sum_i (E_loc(s_i) - mean) d log psi / d theta
+ *      (for psi_sym: d log psi_sym = sum_g w_g d log psi(g s), w_g the
+ *      images' normalised weights psi(g s)^2), by the FP32 reverse scan;
+ *   4. theta_out = the Adam update of params->theta (theta_out may alias it).
+ * Every array is a device array: uniforms, sym_uniforms (float [n], only with
+ * symmetrize), theta_out [P], adam->m, adam->v; optional outputs (NULL to
+ * skip): spins_out uint8 [n][N] (the samples used), eloc_out float [n],
+ * stats_out double [3], grad_out float [P].  Asynchronous on the context's
+ * stream.  PSR_EINVAL for host arrays, a non-square lattice with
+ * symmetrize, step < 1 or out-of-range Adam constants. */
+int psr_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, int32_t symmetrize,
+                 const float *uniforms, const float *sym_uniforms, int64_t n, const psr_adam *adam,
+                 float *theta_out, uint8_t *spins_out, float *eloc_out, double *stats_out,
+                 float *grad_out);
+
 /* Stages of the launch sequence, for per-stage device timing. */
 enum {
     PSR_STAGE_PACK = 0,          /* parameter packing and spin bit-packing */

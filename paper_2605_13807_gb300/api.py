@@ -7,6 +7,8 @@
     sample(theta, uniforms, cfg)         -> (uint8 [n, L] exact samples, float32 [n] log psi)
     logpsi2d / local_energy2d            -> the 2D patched minGRU (Lx, Ly even)
     logpsi_lru / local_energy_lru        -> the deep 1D LRU ansatz
+    sym_logpsi / sym_local_energy        -> c4v-symmetrised amplitude and its E_loc
+    vmc_step(theta, cfg, ham, u, adam)   -> one on-device VMC step (sample, E_loc, gradient, Adam)
     grad(theta, spins, dout=None)        -> float32 [n, P] (O_k) or [P]
     LogPsi.apply(theta, spins, cfg)      -> differentiable log psi; backward = psr_grad
 
@@ -173,6 +175,61 @@ def local_energy_lru(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, o
     p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
     B.psr_lru_local_energy(p, samples, ham, out, stats)
     return out, stats
+
+
+def sym_logpsi(theta, spins, cfg: ModelConfig, L: int, out=None):
+    """c4v-symmetrised log psi on an L x L lattice."""
+    dev = _device_of(spins, theta)
+    if out is None:
+        out = torch.empty(spins.shape[0], dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    return B.psr_sym_logpsi(p, spins, L, L, out)
+
+
+def sym_local_energy(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, out=None, stats=None):
+    dev = _device_of(samples, theta)
+    if out is None:
+        out = torch.empty(samples.shape[0], dtype=torch.float32, device=dev)
+    if stats is None:
+        stats = torch.empty(3, dtype=torch.float64, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_sym_local_energy(p, samples, ham, out, stats)
+    return out, stats
+
+
+class Adam:
+    """Adam moments for psr_vmc_step (device tensors, updated in place)."""
+
+    def __init__(self, P, device, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.m = torch.zeros(P, dtype=torch.float32, device=device)
+        self.v = torch.zeros(P, dtype=torch.float32, device=device)
+        self.lr, self.beta1, self.beta2, self.eps = lr, beta1, beta2, eps
+        self.step = 0
+
+    def state(self):
+        return B.psr_adam(self.lr, self.beta1, self.beta2, self.eps, self.step, B._ptr(self.m),
+                          B._ptr(self.v))
+
+
+def vmc_step(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: Adam,
+             symmetrize=False, sym_uniforms=None, theta_out=None):
+    """One VMC step on the device: exact samples from `uniforms` [n, N],
+    E_loc, energy gradient, Adam update.  Returns a dict with the updated
+    parameters, the samples, E_loc, FP64 statistics and the gradient."""
+    n, N = uniforms.shape
+    dev = uniforms.device
+    if theta_out is None:
+        theta_out = torch.empty_like(theta)
+    out = {"theta": theta_out,
+           "spins": torch.empty((n, N), dtype=torch.uint8, device=dev),
+           "eloc": torch.empty(n, dtype=torch.float32, device=dev),
+           "stats": torch.empty(3, dtype=torch.float64, device=dev),
+           "grad": torch.empty_like(theta)}
+    adam.step += 1
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_vmc_step(p, ham, symmetrize, uniforms, sym_uniforms, adam.state(), theta_out,
+                   out["spins"], out["eloc"], out["stats"], out["grad"])
+    return out
 
 
 def set_autotune(enable=True):

@@ -44,6 +44,11 @@ class psr_scan_tile(C.Structure):
     _fields_ = [("units", C.c_int32), ("chunk", C.c_int32)]
 
 
+class psr_adam(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32), ("m", C.c_void_p), ("v", C.c_void_p)]
+
+
 class psr_batch_item(C.Structure):
     _fields_ = [("samples", C.c_void_p), ("n", C.c_int64), ("ham", psr_hamiltonian),
                 ("u1_mask", C.c_int32), ("out", C.c_void_p), ("stats", C.c_void_p)]
@@ -55,7 +60,8 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_local_energy_batch", "psr_context_set_graphs", "psr_scan", "psr_scan_tiled",
             "psr_scan_tile_for", "psr_context_set_autotune", "psr_sample", "psr_sample_tile_for",
             "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy", "psr_selftest_wait_timeout",
-            "psr_lru_param_count", "psr_lru_logpsi", "psr_lru_local_energy")
+            "psr_lru_param_count", "psr_lru_logpsi", "psr_lru_local_energy", "psr_sym_logpsi",
+            "psr_sym_local_energy", "psr_vmc_step")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -104,6 +110,11 @@ def lib():
                 L.psr_lru_logpsi.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp]
                 L.psr_lru_local_energy.argtypes = [C.POINTER(psr_params), vp, i64,
                                                    C.POINTER(psr_hamiltonian), vp, vp]
+                L.psr_sym_logpsi.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp]
+                L.psr_sym_local_energy.argtypes = [C.POINTER(psr_params), vp, i64,
+                                                   C.POINTER(psr_hamiltonian), vp, vp]
+                L.psr_vmc_step.argtypes = [C.POINTER(psr_params), C.POINTER(psr_hamiltonian), i32, vp, vp,
+                                           i64, C.POINTER(psr_adam), vp, vp, vp, vp, vp]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -343,3 +354,27 @@ def psr_lru_local_energy(params, samples, ham, out, stats=None):
     _check(lib().psr_lru_local_energy(C.byref(params), _ptr(samples), int(n), C.byref(ham), _ptr(out),
                                       _ptr(stats)), "psr_lru_local_energy")
     return out
+
+
+def psr_sym_logpsi(params, spins, Lx, Ly, out):
+    n = spins.shape[0]
+    _check(lib().psr_sym_logpsi(C.byref(params), _ptr(spins), int(n), int(Lx), int(Ly), _ptr(out)),
+           "psr_sym_logpsi")
+    return out
+
+
+def psr_sym_local_energy(params, samples, ham, out, stats=None):
+    n = samples.shape[0]
+    _check(lib().psr_sym_local_energy(C.byref(params), _ptr(samples), int(n), C.byref(ham), _ptr(out),
+                                      _ptr(stats)), "psr_sym_local_energy")
+    return out
+
+
+def psr_vmc_step(params, ham, symmetrize, uniforms, sym_uniforms, adam, theta_out, spins_out=None,
+                 eloc_out=None, stats_out=None, grad_out=None):
+    n = uniforms.shape[0]
+    _check(lib().psr_vmc_step(C.byref(params), C.byref(ham), int(bool(symmetrize)), _ptr(uniforms),
+                              _ptr(sym_uniforms), int(n), C.byref(adam), _ptr(theta_out),
+                              _ptr(spins_out), _ptr(eloc_out), _ptr(stats_out), _ptr(grad_out)),
+           "psr_vmc_step")
+    return theta_out

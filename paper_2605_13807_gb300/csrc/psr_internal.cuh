@@ -213,6 +213,21 @@ cudaError_t launch_pack_theta_lru(const float *theta, const LruLayout &f, float 
 cudaError_t launch_lru_f32(const FwdJobs &jobs, const float *packed, const LruLayout &f, int num_sms,
                            cudaStream_t stream);
 
+// c4v symmetrisation and VMC-step kernels (psr_vmc.cu).
+cudaError_t launch_c4v_images(const uint8_t *s, int64_t n, int L, uint8_t *out, cudaStream_t st);
+cudaError_t launch_c4v_pick(const uint8_t *s, const float *u, int64_t n, int L, uint8_t *out,
+                            cudaStream_t st);
+cudaError_t launch_c4v_entries(const int32_t *entries, const int64_t *count, int64_t cap, int L,
+                               int32_t *out, cudaStream_t st);
+cudaError_t launch_sym_logpsi(const float *lp8, int64_t n, float *out, cudaStream_t st);
+cudaError_t launch_sym_delta(const int32_t *entries, const int64_t *count, int64_t cap,
+                             const float *lp8, int64_t n, const float *delta8, float *out,
+                             cudaStream_t st);
+cudaError_t launch_vmc_dout(const float *eloc, const double *stats, const float *lp8, int64_t n,
+                            int n_img, float *dout, cudaStream_t st);
+cudaError_t launch_adam(const float *theta, const float *grad, int64_t P, float lr, float b1, float b2,
+                        float eps, int step, float *m, float *v, float *out, cudaStream_t st);
+
 // Backward (FP32).
 size_t bwd_tape_floats_per_cta(int nL, int H);
 cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1,
