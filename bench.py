@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-sample", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--no-lru", action="store_true")
+    ap.add_argument("--no-vmc", action="store_true")
     ap.add_argument("--samples-2d", type=int, default=32,
                     help="samples of the 2D patched-model leg (52x52, FP32)")
     ap.add_argument("--scan-only", action="store_true",
@@ -469,6 +470,43 @@ def lru_leg(dev, N=256, H=64, n=1024, reps=3):
                          "launch_ms": conn_ms}}
 
 
+def vmc_leg(dev, L=10, n=1024, reps=3):
+    """One full on-device VMC step (exact sampling, E_loc, energy gradient,
+    Adam; the paper's definition of a training step, Sec. III.A) for the
+    chain model on the 10x10 Heisenberg lattice (hidden 128, 3 layers, BF16
+    E_loc, FP32 sampling and gradient), without and with c4v
+    symmetrisation (8 images per configuration)."""
+    import torch
+
+    from paper_2605_13807_gb300 import api, binding as B, inputs
+    N = L * L
+    ham = B.make_hamiltonian("heisenberg", L, L, False, True, 1.0, 0.0)
+    cfg = api.ModelConfig(N_LAYERS, HIDDEN, True, "bf16")
+    theta = torch.from_numpy(inputs.glorot_params(N_LAYERS, HIDDEN, seed=0)).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    u = torch.rand((n, N), generator=g, device=dev)
+    us = torch.rand(n, generator=g, device=dev)
+    res = {"workload": f"heisenberg_{L}x{L}_obc_{n}_samples", "hidden": HIDDEN,
+           "layers": N_LAYERS, "precision": "BF16 E_loc, FP32 sampling and gradient"}
+    for sym in (False, True):
+        adam = api.Adam(theta.numel(), dev, lr=1e-3)
+        th = theta.clone()  # updated in place by every step
+        out = api.vmc_step(th, cfg, ham, u, adam, symmetrize=sym, sym_uniforms=us, theta_out=th)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = api.vmc_step(th, cfg, ham, u, adam, symmetrize=sym, sym_uniforms=us, theta_out=th)
+        e1.record()
+        e1.synchronize()
+        key = "c4v" if sym else "plain"
+        res[key] = {"ms_per_step": e0.elapsed_time(e1) / reps,
+                    "energy_per_site": float(out["stats"][0].item()) / N}
+    return res
+
+
 def run_scan_only(args):
     import torch
 
@@ -639,6 +677,8 @@ def run_mine(args):
         line["model2d"] = model2d_leg(Lx, Ly, min(args.samples_2d, n), dev)
     if not args.no_lru and rank == 0:
         line["lru"] = lru_leg(dev)
+    if not args.no_vmc and rank == 0:
+        line["vmc_step"] = vmc_leg(dev)
 
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
