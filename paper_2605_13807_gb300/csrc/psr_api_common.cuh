@@ -1,0 +1,255 @@
+// Internal helpers of the C ABI shared by the psr_api*.cu files: the
+// context object, workspace carving, host/device staging, argument checks,
+// per-stage events, the connected-configuration generator sequence and the
+// autotuner's measurement loop.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "psr_internal.cuh"
+
+struct psr_context {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 1;
+    void *ws = nullptr;
+    size_t ws_size = 0;
+    int *status = nullptr;  // device status word
+    bool profiling = false;
+    bool capturing = false;  // a CUDA graph is being captured on the stream
+    cudaEvent_t ev_begin[PSR_STAGE_COUNT] = {};
+    cudaEvent_t ev_end[PSR_STAGE_COUNT] = {};
+    bool stage_ran[PSR_STAGE_COUNT] = {};
+    uint64_t ws_generation = 0;  // bumped whenever the workspace moves
+    bool graphs = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<unsigned char> graph_key;  // arguments the cached graph was built for
+    uint64_t graph_ws_generation = 0;
+    // Autotuner: measured choices per (operation, shape), kept for the
+    // context's lifetime.
+    bool autotune = false;
+    struct Tuned {
+        int op;
+        int64_t k0, k1, k2;
+        int32_t v0, v1;
+        float ms;
+    };
+    std::vector<Tuned> tuned;
+    cudaEvent_t tune_ev[2] = {};
+    // second workspace: arrays psr_vmc_step keeps across the calls it makes
+    void *ws2 = nullptr;
+    size_t ws2_size = 0;
+};
+
+namespace psr {
+namespace apiutil {
+
+// Bump allocator over the workspace.  Each entry point runs its carving
+// sequence twice: once with a null base to size it, once for real.
+struct Carver {
+    char *base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T *get(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+inline int from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return PSR_OK;
+    if (e == cudaErrorMemoryAllocation) return PSR_ENOMEM;
+    return PSR_ECUDA;
+}
+
+#define PSR_TRY(expr)                          \
+    do {                                       \
+        int _rc = from_cuda(expr);             \
+        if (_rc != PSR_OK) return _rc;         \
+    } while (0)
+
+inline bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int ensure_ws(psr_context *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_size) return PSR_OK;
+    PSR_TRY(cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_size = 0;
+    size_t want = bytes + bytes / 8 + (1u << 20);
+    cudaError_t e = cudaMalloc(&ctx->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return PSR_ENOMEM;
+    }
+    ctx->ws_size = want;
+    ctx->ws_generation++;
+    return PSR_OK;
+}
+
+// Reads and clears the device status word (synchronises the stream).
+inline int take_status(psr_context *ctx) {
+    PSR_TRY(cudaStreamSynchronize(ctx->stream));
+    int st = 0;
+    PSR_TRY(cudaMemcpy(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) PSR_TRY(cudaMemset(ctx->status, 0, sizeof(int)));
+    return st;
+}
+
+inline int check_params(const psr_params *p, int64_t n, int32_t L) {
+    if (!p || !p->ctx || !p->theta) return PSR_EINVAL;
+    if (p->n_layers < 1 || p->n_layers > kMaxLayers) return PSR_EINVAL;
+    if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128) return PSR_EINVAL;
+    if (p->u1_mask != 0 && p->u1_mask != 1) return PSR_EINVAL;
+    if (p->precision != PSR_FP32 && p->precision != PSR_BF16) return PSR_EINVAL;
+    if (n < 1 || L < 1) return PSR_EINVAL;
+    if (n > (int64_t)1 << 31) return PSR_EINVAL;
+    if (p->u1_mask && (L % 2)) return PSR_EINVAL;
+    if (p->precision == PSR_BF16 &&
+        (p->hidden != 128 || p->n_layers != 3 || bf16_packed_bytes() == 0))
+        return PSR_EUNSUPPORTED;
+    return PSR_OK;
+}
+
+inline int check_ham(const psr_hamiltonian *h) {
+    if (!h) return PSR_EINVAL;
+    if (h->kind != PSR_HEISENBERG && h->kind != PSR_TFIM) return PSR_EINVAL;
+    if (h->Lx < 1 || h->Ly < 1 || (int64_t)h->Lx * h->Ly > (1 << 24)) return PSR_EINVAL;
+    if (h->pbc != 0 && h->pbc != 1) return PSR_EINVAL;
+    if (h->marshall != 0 && h->marshall != 1) return PSR_EINVAL;
+    if (h->kind == PSR_HEISENBERG && h->marshall) {
+        // bipartite unless a wrapped dimension has odd length
+        const bool wx = h->pbc && h->Lx >= 3, wy = h->pbc && h->Ly >= 3;
+        if ((wx && (h->Lx & 1)) || (wy && (h->Ly & 1))) return PSR_EINVAL;
+    }
+    return PSR_OK;
+}
+
+inline int64_t words_per_row(int N) { return (N + 63) / 64 + 1; }
+
+// Stages an input array: returns the device pointer to use (the caller's own
+// if it is device memory, else a workspace copy filled by an async H2D).
+template <class T>
+inline int stage_in(const T *src, T *dst_ws, size_t count, bool dev, cudaStream_t st, const T **use) {
+    if (dev) {
+        *use = src;
+        return PSR_OK;
+    }
+    PSR_TRY(cudaMemcpyAsync(dst_ws, src, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    *use = dst_ws;
+    return PSR_OK;
+}
+
+// Records the begin/end event of a stage when profiling is on.
+struct StageScope {
+    psr_context *ctx;
+    int stage;
+    StageScope(psr_context *c, int s) : ctx(c), stage(s) {
+        if (ctx->profiling && !ctx->capturing) {
+            cudaEventRecord(ctx->ev_begin[stage], ctx->stream);
+            ctx->stage_ran[stage] = true;
+        }
+    }
+    ~StageScope() {
+        if (ctx->profiling && !ctx->capturing) cudaEventRecord(ctx->ev_end[stage], ctx->stream);
+    }
+};
+
+inline void reset_stages(psr_context *ctx) {
+    for (int i = 0; i < PSR_STAGE_COUNT; ++i) ctx->stage_ran[i] = false;
+}
+
+// Shared body of psr_connected and the first half of every local-energy call.
+struct ConnBufs {
+    int32_t *bonds;
+    int64_t *counts;
+    int64_t *offsets;
+    float *diag;
+    int32_t *entries;
+};
+
+inline int enqueue_connected(psr_context *ctx, const psr_hamiltonian *ham, const uint8_t *sp, int64_t n,
+                      const ConnBufs &b, HamDev &hd) {
+    cudaStream_t st = ctx->stream;
+    const int N = ham->Lx * ham->Ly;
+    hd.kind = ham->kind;
+    hd.N = N;
+    hd.nb = bond_count(ham->Lx, ham->Ly, ham->pbc);
+    hd.bonds = b.bonds;
+    hd.J = (float)ham->J;
+    hd.h = (float)ham->h;
+    hd.coeff = ham->kind == PSR_HEISENBERG ? (float)((ham->marshall ? -0.5 : 0.5) * ham->J)
+                                           : (float)(-ham->h);
+    if (hd.nb > 0) PSR_TRY(launch_bonds(ham->Lx, ham->Ly, ham->pbc, b.bonds, st));
+    PSR_TRY(launch_count_connected(hd, sp, n, b.counts, b.diag, st));
+    PSR_TRY(launch_exclusive_scan(b.counts, n, b.offsets, st));
+    PSR_TRY(launch_fill_connected(hd, sp, n, b.offsets, b.entries, st));
+    return PSR_OK;
+}
+
+inline int64_t max_entries_per_sample(const psr_hamiltonian *ham) {
+    const int N = ham->Lx * ham->Ly;
+    return ham->kind == PSR_HEISENBERG ? bond_count(ham->Lx, ham->Ly, ham->pbc) : N;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+enum { kTuneScan = 1, kTuneSample = 2 };
+
+// Times run(i) for every candidate i on the context's stream with CUDA
+// events (two runs each when a run is short, the second counted) and
+// returns the index of the fastest.  Synchronises the stream.
+template <class Run>
+int measure_candidates(psr_context *ctx, int count, Run run, int *best, float *best_ms) {
+    if (!ctx->tune_ev[0]) {
+        PSR_TRY(cudaEventCreate(&ctx->tune_ev[0]));
+        PSR_TRY(cudaEventCreate(&ctx->tune_ev[1]));
+    }
+    cudaStream_t st = ctx->stream;
+    *best = 0;
+    *best_ms = -1.0f;
+    for (int i = 0; i < count; ++i) {
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {
+            PSR_TRY(cudaEventRecord(ctx->tune_ev[0], st));
+            int rc = run(i);
+            if (rc != PSR_OK) return rc;
+            PSR_TRY(cudaEventRecord(ctx->tune_ev[1], st));
+            PSR_TRY(cudaEventSynchronize(ctx->tune_ev[1]));
+            PSR_TRY(cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
+            if (ms > 50.0f) break;  // long runs: the first is representative
+        }
+        if (*best_ms < 0.0f || ms < *best_ms) {
+            *best_ms = ms;
+            *best = i;
+        }
+    }
+    return PSR_OK;
+}
+
+inline const psr_context::Tuned *find_tuned(const psr_context *ctx, int op, int64_t k0, int64_t k1,
+                                     int64_t k2) {
+    for (const auto &t : ctx->tuned)
+        if (t.op == op && t.k0 == k0 && t.k1 == k1 && t.k2 == k2) return &t;
+    return nullptr;
+}
+
+}  // namespace apiutil
+}  // namespace psr

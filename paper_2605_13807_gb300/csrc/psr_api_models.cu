@@ -1,0 +1,364 @@
+// C ABI: the paper's two-dimensional patched minGRU and deep 1D LRU models.
+#include "psr_api_common.cuh"
+
+using namespace psr;
+using namespace psr::apiutil;
+
+// ------------------------------------------- two-dimensional patched minGRU
+
+namespace {
+
+int check_params2d(const psr_params *p, int64_t n, int Lx, int Ly) {
+    if (!p || !p->ctx || !p->theta) return PSR_EINVAL;
+    if (p->n_layers < 1 || p->n_layers > kMaxLayers) return PSR_EINVAL;
+    if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128 && p->hidden != 256) return PSR_EINVAL;
+    if (p->hidden == 256 && p->n_layers > 4) return PSR_EUNSUPPORTED;  // shared memory
+    if (p->u1_mask != 0 && p->u1_mask != 1) return PSR_EINVAL;
+    if (p->precision != PSR_FP32 && p->precision != PSR_BF16) return PSR_EINVAL;
+    if (n < 1 || n > (int64_t)1 << 31) return PSR_EINVAL;
+    if (Lx < 2 || Ly < 2 || (Lx % 2) || (Ly % 2) || (int64_t)Lx * Ly > (1 << 24)) return PSR_EINVAL;
+    if (Lx > 64) return PSR_EUNSUPPORTED;  // at most 32 patches per row
+    if (p->precision != PSR_FP32) return PSR_EUNSUPPORTED;
+    return PSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psr2d_param_count(int32_t n_layers, int32_t hidden, int64_t *P) {
+    if (!P || n_layers < 1 || n_layers > kMaxLayers || hidden < 1) return PSR_EINVAL;
+    *P = param_count2d(n_layers, hidden);
+    return PSR_OK;
+}
+
+int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
+                 float *out) {
+    int rc = check_params2d(params, n, Lx, Ly);
+    if (rc != PSR_OK) return rc;
+    if (!spins || !out) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden, N = Lx * Ly;
+    const int64_t P = param_count2d(nL, H);
+    const F2Layout f = f2_layout(nL, H);
+    const int W = (int)words_per_row(N);
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(spins),
+               d_out = is_device_ptr(out);
+    float *theta_ws = nullptr, *out_ws = nullptr, *pk = nullptr;
+    uint8_t *s_ws = nullptr;
+    uint64_t *bits = nullptr;
+    unsigned long long *counter = nullptr;
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        out_ws = c.get<float>(d_out ? 0 : n);
+        pk = c.get<float>(f.total);
+        bits = c.get<uint64_t>((size_t)n * W);
+        counter = c.get<unsigned long long>(1);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(spins, s_ws, (size_t)n * N, d_s, st, &sp)) != PSR_OK) return rc;
+    float *o = d_out ? out : out_ws;
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
+        PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));  // spin-byte check
+        PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    }
+    Fwd2Jobs jb{};
+    jb.mode = 0;
+    jb.g.Lx = Lx;
+    jb.g.Ly = Ly;
+    jb.g.u1 = params->u1_mask;
+    jb.g.n_jobs = n;
+    jb.g.spins = sp;
+    jb.g.out = o;
+    jb.job_counter = counter;
+    jb.status = ctx->status;
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        PSR_TRY(launch_fwd2d_f32(jb, pk, f, ctx->num_sms, st));
+    }
+    if (!d_out) PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (!d_out || !d_s || !d_theta) return take_status(ctx);
+    return PSR_OK;
+}
+
+int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                       const psr_hamiltonian *ham, float *out, double *stats) {
+    int rc = check_ham(ham);
+    if (rc != PSR_OK) return rc;
+    if ((rc = check_params2d(params, n, ham->Lx, ham->Ly)) != PSR_OK) return rc;
+    if (!samples || !out) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden, Lx = ham->Lx, Ly = ham->Ly;
+    const int N = Lx * Ly, Py = Ly / 2, Np = (Lx / 2) * Py;
+    const int64_t P = param_count2d(nL, H);
+    const F2Layout f = f2_layout(nL, H);
+    const int W = (int)words_per_row(N);
+    const int nb = bond_count(Lx, Ly, ham->pbc);
+    const int64_t cap = n * max_entries_per_sample(ham);
+    const size_t ckpt = fwd2d_checkpoint_floats(nL, H);
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
+               d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
+
+    float *theta_ws = nullptr, *out_ws = nullptr, *pk = nullptr, *lpsi = nullptr, *logp = nullptr,
+          *carries = nullptr, *delta = nullptr;
+    double *stats_ws = nullptr;
+    uint8_t *s_ws = nullptr;
+    uint64_t *bits = nullptr;
+    unsigned long long *counters = nullptr;
+    ConnBufs b{};
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        out_ws = c.get<float>(d_out ? 0 : n);
+        stats_ws = c.get<double>(d_stats ? 0 : 3);
+        pk = c.get<float>(f.total);
+        bits = c.get<uint64_t>((size_t)n * W);
+        b.bonds = c.get<int32_t>(2 * (size_t)nb + 2);
+        b.counts = c.get<int64_t>(n);
+        b.offsets = c.get<int64_t>(n + 1);
+        b.diag = c.get<float>(n);
+        b.entries = c.get<int32_t>(3 * (size_t)cap);
+        lpsi = c.get<float>(n);
+        logp = c.get<float>((size_t)n * Np);
+        carries = c.get<float>((size_t)n * Py * ckpt);
+        delta = c.get<float>(cap);
+        counters = c.get<unsigned long long>(2);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(samples, s_ws, (size_t)n * N, d_s, st, &sp)) != PSR_OK) return rc;
+    float *o = d_out ? out : out_ws;
+    double *so = stats ? (d_stats ? stats : stats_ws) : nullptr;
+
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
+        PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));  // spin-byte check
+        PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
+    }
+    HamDev hd{};
+    {
+        StageScope sc(ctx, PSR_STAGE_GENERATOR);
+        if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
+    }
+    Fwd2Jobs js{};
+    js.mode = 0;
+    js.g.Lx = Lx;
+    js.g.Ly = Ly;
+    js.g.u1 = params->u1_mask;
+    js.g.n_jobs = n;
+    js.g.spins = sp;
+    js.g.out = lpsi;
+    js.g.logp_out = logp;
+    js.g.carries_out = carries;
+    js.job_counter = counters;
+    js.status = ctx->status;
+    Fwd2Jobs jc = js;
+    jc.mode = 1;
+    jc.g.n_jobs = cap;
+    jc.g.n_jobs_dev = b.offsets + n;
+    jc.g.entries = b.entries;
+    jc.g.carries_in = carries;
+    jc.g.logp_ref = logp;
+    jc.g.out = delta;
+    jc.g.logp_out = nullptr;
+    jc.g.carries_out = nullptr;
+    jc.job_counter = counters + 1;
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        PSR_TRY(launch_fwd2d_f32(js, pk, f, ctx->num_sms, st));
+    }
+    if (cap > 0) {
+        StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
+        PSR_TRY(launch_fwd2d_f32(jc, pk, f, ctx->num_sms, st));
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_GATHER);
+        PSR_TRY(launch_eloc_gather(b.offsets, delta, b.diag, hd.coeff, n, o, st));
+        if (so) PSR_TRY(launch_stats(o, n, so, st));
+    }
+    if (!d_out) PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (stats && !d_stats)
+        PSR_TRY(cudaMemcpyAsync(stats, stats_ws, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!d_out || !d_s || !d_theta || !d_stats) return take_status(ctx);
+    return PSR_OK;
+}
+
+// ------------------------------------------------------ deep 1D LRU model
+
+}  // extern "C"
+
+namespace {
+
+int check_params_lru(const psr_params *p, int64_t n, int32_t L) {
+    if (!p || !p->ctx || !p->theta) return PSR_EINVAL;
+    if (p->n_layers < 1 || p->n_layers > kMaxLayers) return PSR_EINVAL;
+    if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128) return PSR_EINVAL;
+    if (p->u1_mask != 0 && p->u1_mask != 1) return PSR_EINVAL;
+    if (p->precision != PSR_FP32 && p->precision != PSR_BF16) return PSR_EINVAL;
+    if (n < 1 || L < 1 || n > (int64_t)1 << 31) return PSR_EINVAL;
+    if (p->u1_mask && (L % 2)) return PSR_EINVAL;
+    if (p->precision != PSR_FP32) return PSR_EUNSUPPORTED;
+    return PSR_OK;
+}
+
+// Shared body of psr_lru_logpsi (ham == nullptr) and psr_lru_local_energy.
+int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t L,
+            const psr_hamiltonian *ham, float *out, double *stats) {
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden, N = L;
+    const int64_t P = param_count_lru(nL, H);
+    const LruLayout f = lru_layout(nL, H);
+    const int W = (int)words_per_row(N);
+    const int nch = (N + kChunkLru - 1) / kChunkLru;
+    const bool eloc = ham != nullptr;
+    const int nb = eloc ? bond_count(ham->Lx, ham->Ly, ham->pbc) : 0;
+    const int64_t cap = eloc ? n * max_entries_per_sample(ham) : 0;
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
+               d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
+    float *theta_ws = nullptr, *out_ws = nullptr, *pk = nullptr, *lpsi = nullptr, *logp = nullptr,
+          *carries = nullptr, *delta = nullptr;
+    double *stats_ws = nullptr;
+    uint8_t *s_ws = nullptr;
+    uint64_t *bits = nullptr;
+    unsigned long long *counters = nullptr;
+    ConnBufs b{};
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        out_ws = c.get<float>(d_out ? 0 : n);
+        stats_ws = c.get<double>(d_stats ? 0 : 3);
+        pk = c.get<float>(f.total);
+        bits = c.get<uint64_t>((size_t)n * W);
+        counters = c.get<unsigned long long>(2);
+        if (eloc) {
+            b.bonds = c.get<int32_t>(2 * (size_t)nb + 2);
+            b.counts = c.get<int64_t>(n);
+            b.offsets = c.get<int64_t>(n + 1);
+            b.diag = c.get<float>(n);
+            b.entries = c.get<int32_t>(3 * (size_t)cap);
+            lpsi = c.get<float>(n);
+            logp = c.get<float>((size_t)n * N);
+            carries = c.get<float>((size_t)n * nch * nL * 2 * H);
+            delta = c.get<float>(cap);
+        }
+    };
+    Carver sz;
+    carve(sz);
+    int rc = ensure_ws(ctx, sz.off);
+    if (rc != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(samples, s_ws, (size_t)n * N, d_s, st, &sp)) != PSR_OK) return rc;
+    float *o = d_out ? out : out_ws;
+    double *so = stats ? (d_stats ? stats : stats_ws) : nullptr;
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_lru(theta, f, pk, st));
+        PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));
+        PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
+    }
+    HamDev hd{};
+    if (eloc) {
+        StageScope sc(ctx, PSR_STAGE_GENERATOR);
+        if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
+    }
+    FwdJobs js{};
+    js.mode = 0;
+    js.n_groups = 1;
+    js.g[0].u1 = params->u1_mask;
+    js.g[0].N = N;
+    js.g[0].W = W;
+    js.g[0].n_jobs = n;
+    js.g[0].bits = bits;
+    js.g[0].out = eloc ? lpsi : o;
+    js.g[0].logp_out = logp;
+    js.g[0].carries_out = carries;
+    js.job_counter = counters;
+    js.status = ctx->status;
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        PSR_TRY(launch_lru_f32(js, pk, f, ctx->num_sms, st));
+    }
+    if (eloc) {
+        FwdJobs jc = js;
+        jc.mode = 1;
+        jc.g[0].n_jobs = cap;
+        jc.g[0].n_jobs_dev = b.offsets + n;
+        jc.g[0].entries = b.entries;
+        jc.g[0].carries_in = carries;
+        jc.g[0].logp_ref = logp;
+        jc.g[0].out = delta;
+        jc.g[0].logp_out = nullptr;
+        jc.g[0].carries_out = nullptr;
+        jc.job_counter = counters + 1;
+        if (cap > 0) {
+            StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
+            PSR_TRY(launch_lru_f32(jc, pk, f, ctx->num_sms, st));
+        }
+        StageScope sc(ctx, PSR_STAGE_GATHER);
+        PSR_TRY(launch_eloc_gather(b.offsets, delta, b.diag, hd.coeff, n, o, st));
+        if (so) PSR_TRY(launch_stats(o, n, so, st));
+    }
+    if (!d_out) PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (stats && !d_stats)
+        PSR_TRY(cudaMemcpyAsync(stats, stats_ws, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!d_out || !d_s || !d_theta || !d_stats) return take_status(ctx);
+    return PSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psr_lru_param_count(int32_t n_layers, int32_t hidden, int64_t *P) {
+    if (!P || n_layers < 1 || n_layers > kMaxLayers || hidden < 1) return PSR_EINVAL;
+    *P = param_count_lru(n_layers, hidden);
+    return PSR_OK;
+}
+
+int psr_lru_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, float *out) {
+    int rc = check_params_lru(params, n, L);
+    if (rc != PSR_OK) return rc;
+    if (!spins || !out) return PSR_EINVAL;
+    return lru_run(params, spins, n, L, nullptr, out, nullptr);
+}
+
+int psr_lru_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                         const psr_hamiltonian *ham, float *out, double *stats) {
+    int rc = check_ham(ham);
+    if (rc != PSR_OK) return rc;
+    if ((rc = check_params_lru(params, n, ham->Lx * ham->Ly)) != PSR_OK) return rc;
+    if (!samples || !out) return PSR_EINVAL;
+    return lru_run(params, samples, n, ham->Lx * ham->Ly, ham, out, stats);
+}
+
+}  // extern "C"
