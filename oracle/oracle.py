@@ -80,6 +80,8 @@ def lib():
         _lib.psro2d_logpsi.argtypes = [vp, i, i, i, i, i, vp, vp]
         _lib.psro2d_sample.restype = None
         _lib.psro2d_sample.argtypes = [vp, i, i, i, i, i, l, vp, vp, vp]
+        _lib.psro2d_conditionals.restype = None
+        _lib.psro2d_conditionals.argtypes = [vp, i, i, i, i, i, vp, vp]
         _lib.psro_lru_param_count.restype = l
         _lib.psro_lru_param_count.argtypes = [i, i]
         _lib.psro_lru_logpsi.restype = d
@@ -308,6 +310,25 @@ def sample2d(theta, n_layers, hidden, Lx, Ly, uniforms, u1=False):
     lps = np.empty(n)
     lib().psro2d_sample(_p(th), n_layers, hidden, int(u1), Lx, Ly, n, _p(u), _p(out), _p(lps))
     return out, lps
+
+
+def conditionals2d(theta, n_layers, hidden, Lx, Ly, spins, u1=False, threads=None):
+    """[n, Np, 16] conditional distributions of every patch (path order)."""
+    th = _theta64(theta)
+    s = _spins(spins)
+    n = s.shape[0]
+    Np = (Lx // 2) * (Ly // 2)
+    out = np.empty((n, Np, 16))
+    L = lib()
+
+    def one(i):
+        row = np.ascontiguousarray(s[i])
+        buf = np.empty((Np, 16))
+        L.psro2d_conditionals(_p(th), n_layers, hidden, int(u1), Lx, Ly, _p(row), _p(buf))
+        out[i] = buf
+
+    _map(one, n, threads)
+    return out
 
 
 def local_energy2d(theta, n_layers, hidden, spins, kind, Lx, Ly, pbc=False, marshall=True,

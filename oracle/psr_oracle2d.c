@@ -275,3 +275,33 @@ ORC_EXPORT void psro2d_sample(const double *theta, int nL, int H, int u1, int Lx
     o2_free(&S);
     free(vals);
 }
+
+/* The 16-way conditional of every patch of one configuration, in path
+ * order: probs[t][v] = P(v_t = v | v_<t) under the mask (0 for values the
+ * mask excludes). */
+ORC_EXPORT void psro2d_conditionals(const double *theta, int nL, int H, int u1, int Lx, int Ly,
+                                    const uint8_t *s, double *probs) {
+    const int Px = Lx / 2, Py = Ly / 2, N = Lx * Ly;
+    o2_state S;
+    int *vals = malloc(sizeof(int) * (size_t)Px * Py);
+    if (!vals || o2_alloc(&S, Px, Py, nL, H)) {
+        free(vals);
+        return;
+    }
+    for (int pj = 0; pj < Py; ++pj)
+        for (int pi = 0; pi < Px; ++pi) vals[pj * Px + pi] = o2_patch_value(s, Lx, pi, pj);
+    double logits[16];
+    int n_up = 0, n_down = 0, allowed[16];
+    for (int t = 0; t < Px * Py; ++t) {
+        int pi, pj;
+        o2_patch_at(Px, t, &pi, &pj);
+        o2_patch(theta, &S, vals, pi, pj, logits);
+        o2_mask(u1, N, n_up, n_down, allowed);
+        for (int v = 0; v < 16; ++v) probs[(size_t)t * 16 + v] = exp(o2_logp(logits, allowed, v));
+        const int v = vals[pj * Px + pi];
+        n_up += o2_popcount4(v);
+        n_down += 4 - o2_popcount4(v);
+    }
+    o2_free(&S);
+    free(vals);
+}

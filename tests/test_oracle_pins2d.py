@@ -240,3 +240,18 @@ def test_sampler_respects_u1(oracle_mod):
     s, lps = oracle_mod.sample2d(theta, 2, 4, Lx, Ly, inputs.uniform(363, (500, 4)), u1=True)
     assert np.all(s.sum(axis=1) == 8)
     assert np.all(np.isfinite(lps))
+
+
+def test_conditionals_are_the_log_probabilities(oracle_mod):
+    """The 16-way conditionals sum to one, vanish on masked values, and at the
+    configuration's own values reproduce its per-patch log P."""
+    Lx, Ly, H = 6, 4, 4
+    theta = _random_theta(oracle_mod, 2, H, seed=370, scale=1.2)
+    s = inputs.zero_magnetisation_spins(371, 5, Lx * Ly)
+    probs = oracle_mod.conditionals2d(theta, 2, H, Lx, Ly, s, u1=True)
+    assert np.allclose(probs.sum(axis=2), 1.0, atol=1e-13)
+    _, lp = oracle_mod.logpsi2d(theta, 2, H, Lx, Ly, s, u1=True, per_site=True)
+    vals = np.array([_patch_values(x, Lx, Ly) for x in s])
+    own = np.take_along_axis(probs, vals[:, :, None], axis=2)[:, :, 0]
+    assert np.max(np.abs(np.log(own) - lp)) < 1e-12
+    assert np.any(probs == 0.0)  # the mask removes values near the end
