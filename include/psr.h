@@ -328,6 +328,16 @@ int psr2d_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
 int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
                  float *out);
 
+/* Exact samples of the 2D model (Sec. III.B): patch t of sample i takes the
+ * smallest value v whose cumulative conditional probability (values in
+ * increasing order, masked ones skipped) exceeds uniforms[i][t]; uniforms
+ * float [n][Np], Np = (Lx/2)(Ly/2), in path order.  spins: uint8 [n][Lx*Ly]
+ * output in sequence order; logpsi: float [n] or NULL.  FP32; the result
+ * does not depend on how samples are grouped into CTAs (a tile shape the
+ * autotuner chooses).  Requirements as psr2d_logpsi. */
+int psr2d_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t Lx, int32_t Ly,
+                 uint8_t *spins, float *logpsi);
+
 /* Local energy of the 2D model over every connected configuration, as
  * psr_local_energy computes it for the chain model; a connected
  * configuration is resumed at the patch row of its first flipped spin from

@@ -153,6 +153,19 @@ def local_energy2d(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, out
     return out, stats
 
 
+def sample2d(theta, uniforms, cfg: ModelConfig, Lx: int, Ly: int, spins=None, logpsi=None):
+    """Exact samples of the 2D patched minGRU from uniforms [n, Np]."""
+    dev = _device_of(uniforms, theta)
+    n = uniforms.shape[0]
+    if spins is None:
+        spins = torch.empty((n, Lx * Ly), dtype=torch.uint8, device=dev)
+    if logpsi is None:
+        logpsi = torch.empty(n, dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr2d_sample(p, uniforms, Lx, Ly, spins, logpsi)
+    return spins, logpsi
+
+
 def param_count_lru(n_layers: int = 3, hidden: int = 64) -> int:
     return B.psr_lru_param_count(n_layers, hidden)
 

@@ -94,6 +94,76 @@ int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int3
     return PSR_OK;
 }
 
+int psr2d_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t Lx, int32_t Ly,
+                 uint8_t *spins, float *logpsi) {
+    int rc = check_params2d(params, n, Lx, Ly);
+    if (rc != PSR_OK) return rc;
+    if (!uniforms || !spins) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden, N = Lx * Ly;
+    const int64_t Np = (int64_t)(Lx / 2) * (Ly / 2);
+    const int64_t P = param_count2d(nL, H);
+    const F2Layout f = f2_layout(nL, H);
+    const bool d_theta = is_device_ptr(params->theta), d_u = is_device_ptr(uniforms),
+               d_s = is_device_ptr(spins), d_lp = logpsi ? is_device_ptr(logpsi) : true;
+    // samples per CTA: the candidates that fit (a thread per logit, shared memory)
+    std::vector<int> cands;
+    for (int b : {1, 2, 4, 8})
+        if (b * 16 <= H && sample2d_smem_bytes(b, nL, H, Lx) <= 220 * 1024) cands.push_back(b);
+    if (cands.empty()) return PSR_EUNSUPPORTED;
+    float *theta_ws = nullptr, *u_ws = nullptr, *lp_ws = nullptr, *pk = nullptr;
+    uint8_t *s_ws = nullptr;
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        u_ws = c.get<float>(d_u ? 0 : (size_t)n * Np);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        lp_ws = c.get<float>(d_lp ? 0 : n);
+        pk = c.get<float>(f.total);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr, *uu = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(uniforms, u_ws, (size_t)n * Np, d_u, st, &uu)) != PSR_OK) return rc;
+    uint8_t *so = d_s ? spins : s_ws;
+    float *lo = logpsi ? (d_lp ? logpsi : lp_ws) : nullptr;
+    const int64_t key2 = (int64_t)nL * 1024 + H;
+    int per_cta = cands.size() > 2 ? cands[2] : cands.back();  // 4 where it fits
+    bool tune_now = false;
+    if (const psr_context::Tuned *t = find_tuned(ctx, kTuneSample2d, n, (int64_t)Lx * 65536 + Ly, key2))
+        per_cta = t->v0;
+    else if (ctx->autotune && !ctx->capturing) tune_now = true;
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
+    }
+    if (tune_now) {
+        int bi = 0;
+        float best = 0.0f;
+        rc = measure_candidates(ctx, (int)cands.size(), [&](int i) {
+            return from_cuda(launch_sample2d(cands[i], pk, f, uu, n, Lx, Ly, params->u1_mask, so, lo, st));
+        }, &bi, &best);
+        if (rc != PSR_OK) return rc;
+        per_cta = cands[bi];
+        ctx->tuned.push_back(psr_context::Tuned{kTuneSample2d, n, (int64_t)Lx * 65536 + Ly, key2, per_cta, 0,
+                                                best});
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_SAMPLE);
+        PSR_TRY(launch_sample2d(per_cta, pk, f, uu, n, Lx, Ly, params->u1_mask, so, lo, st));
+    }
+    if (!d_s) PSR_TRY(cudaMemcpyAsync(spins, s_ws, (size_t)n * N, cudaMemcpyDeviceToHost, st));
+    if (logpsi && !d_lp) PSR_TRY(cudaMemcpyAsync(logpsi, lp_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (!d_theta || !d_u || !d_s || !d_lp) return take_status(ctx);
+    return PSR_OK;
+}
+
 int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
                        const psr_hamiltonian *ham, float *out, double *stats) {
     int rc = check_ham(ham);

@@ -193,6 +193,13 @@ cudaError_t launch_pack_theta_f2(const float *theta, const F2Layout &f, float *p
 cudaError_t launch_fwd2d_f32(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f,
                              int num_sms, cudaStream_t stream);
 
+// Exact sampler of the 2D patched minGRU (psr_sample2d.cu); per_cta: 1, 2,
+// 4 (hidden >= 64) or 8 (hidden >= 128) samples per CTA.  unif: [n][Np].
+size_t sample2d_smem_bytes(int per_cta, int nL, int H, int Lx);
+cudaError_t launch_sample2d(int per_cta, const float *packed, const F2Layout &f, const float *unif,
+                            int64_t n, int Lx, int Ly, int u1, uint8_t *out, float *logpsi,
+                            cudaStream_t stream);
+
 // Deep 1D LRU (psr_lru.cu), FP32.  Packed: per layer lambda (Re, Im) and
 // e^gamma [H], B^T (Re, Im) [din][H], C^T (Re, Im) [H][H], D ([2][H] at
 // layer 0, else [H]), W_a^T, W_g^T [H][H], b_a, b_g [H]; readout as the logit

@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(H) sample_kernel(const float *__restrict__ pk,
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 const float a = sigmoid_f(z[b]);
-                const float h = a * hcl[b * H + j] + (1.0f - a) * y[b];
+                // explicit rounding order: identical for every samples-per-CTA instance
+                const float h = fmaf(a, hcl[b * H + j], __fmul_rn(1.0f - a, y[b]));
                 hcl[b * H + j] = h;
                 hs[b * H + j] = h;
             }
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(H) sample_kernel(const float *__restrict__ pk,
             for (int k = 0; k < H; ++k) {
                 const float wc = Ct[k * H + j], wd = Dt[k * H + j];
 #pragma unroll
-                for (int b = 0; b < B; ++b) y[b] += wc * hs[b * H + k] + wd * xs[b * H + k];
+                for (int b = 0; b < B; ++b) y[b] = fmaf(wd, xs[b * H + k], fmaf(wc, hs[b * H + k], y[b]));
             }
             __syncthreads();
 #pragma unroll

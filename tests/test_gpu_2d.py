@@ -122,3 +122,81 @@ def test_52x52_resume_equals_full_forwards(oracle_mod):
                               np.concatenate([s, flipped[pick]]), u1=True)
     got = np.concatenate([lp_s, lp_f[pick]])
     assert np.all(np.abs(got - ref) <= 1e-5 + 1e-6 * np.abs(ref))
+
+
+def _patch_vals(s, Lx, Ly):
+    """[n, Np] patch values in path order (value bit 2 dy + dx)."""
+    Px, Py = Lx // 2, Ly // 2
+    out = np.zeros((s.shape[0], Px * Py), dtype=np.int64)
+    t = 0
+    for pj in range(Py):
+        for k in range(Px):
+            pi = k if pj % 2 == 0 else Px - 1 - k
+            for dy in range(2):
+                for dx in range(2):
+                    out[:, t] |= s[:, inputs.seq_pos(Lx, 2 * pi + dx, 2 * pj + dy)].astype(np.int64) << (2 * dy + dx)
+            t += 1
+    return out
+
+
+@pytest.mark.parametrize("Lx,Ly,H,nL,u1", [(6, 4, 32, 3, True), (8, 6, 64, 2, False),
+                                           (10, 10, 128, 3, True), (8, 8, 256, 3, True)])
+def test_sampler_follows_oracle_conditionals(oracle_mod, Lx, Ly, H, nL, u1):
+    """Each patch's value is the first whose cumulative oracle probability
+    exceeds its uniform, except within 1e-4 of a boundary (FP32 rounding);
+    log psi of the draw matches the oracle."""
+    theta = _theta(oracle_mod, nL, H, seed=430 + H, scale=2.0)
+    n, Np = 120, (Lx // 2) * (Ly // 2)
+    u = inputs.uniform(431, (n, Np)).astype(np.float32)
+    cfg = api.ModelConfig(nL, H, u1, "fp32")
+    s, lp = api.sample2d(torch.from_numpy(theta).cuda(), torch.from_numpy(u).cuda(), cfg, Lx, Ly)
+    api.sync()
+    s = s.cpu().numpy()
+    if u1:
+        assert np.all(s.sum(axis=1) == Lx * Ly // 2)
+    probs = oracle_mod.conditionals2d(theta.astype(np.float64), nL, H, Lx, Ly, s, u1=u1)
+    cdf = np.cumsum(probs, axis=2)
+    v = _patch_vals(s, Lx, Ly)
+    lo = np.where(v > 0, np.take_along_axis(cdf, np.maximum(v - 1, 0)[:, :, None], axis=2)[:, :, 0], 0.0)
+    hi = np.take_along_axis(cdf, v[:, :, None], axis=2)[:, :, 0]
+    u64 = u.astype(np.float64)
+    inside = (u64 >= lo) & (u64 < hi)
+    near = np.minimum(np.abs(u64 - lo), np.abs(u64 - hi)) <= 1e-4
+    assert np.all(inside | near)
+    assert np.count_nonzero(~inside) <= max(2, 1e-3 * inside.size)
+    assert np.all(np.take_along_axis(probs, v[:, :, None], axis=2) > 0)  # never a masked value
+    ref = oracle_mod.logpsi2d(theta.astype(np.float64), nL, H, Lx, Ly, s, u1=u1)
+    assert np.all(np.abs(lp.cpu().numpy() - ref) <= 1e-5 + 1e-6 * np.abs(ref))
+
+
+def test_sampler_frequencies_chi2(oracle_mod):
+    from scipy.stats import chi2
+    Lx, Ly, nL, H, n = 4, 2, 2, 32, 40000
+    theta = _theta(oracle_mod, nL, H, seed=440, scale=3.0)
+    u = inputs.uniform(441, (n, 2)).astype(np.float32)
+    s, _ = api.sample2d(torch.from_numpy(theta).cuda(), torch.from_numpy(u).cuda(),
+                        api.ModelConfig(nL, H, False, "fp32"), Lx, Ly)
+    api.sync()
+    s = s.cpu().numpy()
+    cfg = ((np.arange(256)[:, None] >> (7 - np.arange(8))[None, :]) & 1).astype(np.uint8)
+    p = np.exp(2 * oracle_mod.logpsi2d(theta.astype(np.float64), nL, H, Lx, Ly, cfg))
+    idx = (s.astype(np.int64) << (7 - np.arange(8))).sum(axis=1)
+    obs = np.bincount(idx, minlength=256)
+    keep = p * n > 1e-9
+    stat = np.sum((obs[keep] - p[keep] * n) ** 2 / (p[keep] * n))
+    assert chi2.sf(stat, df=int(keep.sum()) - 1) > 1e-4
+
+
+def test_sampler_tuned_tile_draws_identical_samples(oracle_mod):
+    Lx, Ly, nL, H = 8, 8, 3, 128
+    theta = torch.from_numpy(_theta(oracle_mod, nL, H, seed=450, scale=2.0)).cuda()
+    u = torch.from_numpy(inputs.uniform(451, (50, 16)).astype(np.float32)).cuda()
+    cfg = api.ModelConfig(nL, H, True, "fp32")
+    s0, lp0 = api.sample2d(theta, u, cfg, Lx, Ly)
+    api.set_autotune(True)
+    try:
+        s1, lp1 = api.sample2d(theta, u, cfg, Lx, Ly)
+    finally:
+        api.set_autotune(False)
+    api.sync()
+    assert torch.equal(s0, s1) and torch.equal(lp0, lp1)
