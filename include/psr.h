@@ -338,6 +338,16 @@ int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int3
 int psr2d_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t Lx, int32_t Ly,
                  uint8_t *spins, float *logpsi);
 
+/* Gradient of log psi of the 2D model, as psr_grad for the chain model:
+ * dout == NULL gives per-sample O_k rows [n][P], otherwise the dout-weighted
+ * sum [P].  Rows of patches are recomputed from the forward's row
+ * checkpoints and differentiated from the last row to the first, the
+ * adjoint of each row's states reaching the row above through
+ * W_h^T (the h_V columns).  FP32; hidden up to 128 (PSR_EUNSUPPORTED
+ * above). */
+int psr2d_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
+               const float *dout, float *dparams);
+
 /* Local energy of the 2D model over every connected configuration, as
  * psr_local_energy computes it for the chain model; a connected
  * configuration is resumed at the patch row of its first flipped spin from

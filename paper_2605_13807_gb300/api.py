@@ -166,6 +166,17 @@ def sample2d(theta, uniforms, cfg: ModelConfig, Lx: int, Ly: int, spins=None, lo
     return spins, logpsi
 
 
+def grad2d(theta, spins, cfg: ModelConfig, Lx: int, Ly: int, dout=None, out=None):
+    """d log psi / d theta of the 2D model: [n, P] per sample, or [P] with dout."""
+    dev = _device_of(spins, theta)
+    P = param_count2d(cfg.n_layers, cfg.hidden)
+    if out is None:
+        shape = (P,) if dout is not None else (spins.shape[0], P)
+        out = torch.empty(shape, dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    return B.psr2d_grad(p, spins, Lx, Ly, dout, out)
+
+
 def param_count_lru(n_layers: int = 3, hidden: int = 64) -> int:
     return B.psr_lru_param_count(n_layers, hidden)
 

@@ -61,7 +61,7 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_scan_tile_for", "psr_context_set_autotune", "psr_sample", "psr_sample_tile_for",
             "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy", "psr_selftest_wait_timeout",
             "psr_lru_param_count", "psr_lru_logpsi", "psr_lru_local_energy", "psr_sym_logpsi",
-            "psr_sym_local_energy", "psr_vmc_step", "psr2d_sample")
+            "psr_sym_local_energy", "psr_vmc_step", "psr2d_sample", "psr2d_grad")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -116,6 +116,7 @@ def lib():
                 L.psr_vmc_step.argtypes = [C.POINTER(psr_params), C.POINTER(psr_hamiltonian), i32, vp, vp,
                                            i64, C.POINTER(psr_adam), vp, vp, vp, vp, vp]
                 L.psr2d_sample.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp, vp]
+                L.psr2d_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp, vp]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -386,3 +387,10 @@ def psr2d_sample(params, uniforms, Lx, Ly, spins, logpsi=None):
     _check(lib().psr2d_sample(C.byref(params), _ptr(uniforms), int(n), int(Lx), int(Ly), _ptr(spins),
                               _ptr(logpsi)), "psr2d_sample")
     return spins
+
+
+def psr2d_grad(params, spins, Lx, Ly, dout, dparams):
+    n = spins.shape[0]
+    _check(lib().psr2d_grad(C.byref(params), _ptr(spins), int(n), int(Lx), int(Ly), _ptr(dout),
+                            _ptr(dparams)), "psr2d_grad")
+    return dparams

@@ -164,6 +164,97 @@ int psr2d_sample(const psr_params *params, const float *uniforms, int64_t n, int
     return PSR_OK;
 }
 
+int psr2d_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
+               const float *dout, float *dparams) {
+    int rc = check_params2d(params, n, Lx, Ly);
+    if (rc != PSR_OK) return rc;
+    if (!spins || !dparams) return PSR_EINVAL;
+    if (params->hidden > 128) return PSR_EUNSUPPORTED;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden, N = Lx * Ly, Py = Ly / 2;
+    const int64_t P = param_count2d(nL, H);
+    const F2Layout f = f2_layout(nL, H);
+    const T2Layout tl = t2_layout(nL, H);
+    const int W = (int)words_per_row(N);
+    const size_t ckpt = fwd2d_checkpoint_floats(nL, H);
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+    int per_sm = (int)(dev_smem / (bwd2d_smem_bytes(nL, H) + 1024));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    int64_t grid64 = (int64_t)ctx->num_sms * per_sm;
+    if (grid64 > n) grid64 = n;
+    const int grid = (int)grid64;
+    const size_t rows = dout ? (size_t)grid : (size_t)n;
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(spins),
+               d_dout = dout ? is_device_ptr(dout) : true, d_g = is_device_ptr(dparams);
+    float *theta_ws = nullptr, *dout_ws = nullptr, *g_ws = nullptr, *pk = nullptr, *lpsi = nullptr,
+          *carries = nullptr, *scratch = nullptr, *partial = nullptr;
+    uint8_t *s_ws = nullptr;
+    uint64_t *bits = nullptr;
+    unsigned long long *counter = nullptr;
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        dout_ws = c.get<float>(d_dout ? 0 : n);
+        g_ws = c.get<float>(d_g ? 0 : (dout ? P : (size_t)n * P));
+        pk = c.get<float>(f.total);
+        bits = c.get<uint64_t>((size_t)n * W);
+        lpsi = c.get<float>(n);
+        carries = c.get<float>((size_t)n * Py * ckpt);
+        scratch = c.get<float>((size_t)grid * bwd2d_scratch_floats_per_cta(nL, H));
+        partial = c.get<float>(dout ? rows * P : 0);
+        counter = c.get<unsigned long long>(1);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr, *dv = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(spins, s_ws, (size_t)n * N, d_s, st, &sp)) != PSR_OK) return rc;
+    if (dout && (rc = stage_in(dout, dout_ws, n, d_dout, st, &dv)) != PSR_OK) return rc;
+    float *g = d_g ? dparams : g_ws;
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
+        PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));  // spin-byte check
+        PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    }
+    Fwd2Jobs jb{};
+    jb.mode = 0;
+    jb.g.Lx = Lx;
+    jb.g.Ly = Ly;
+    jb.g.u1 = params->u1_mask;
+    jb.g.n_jobs = n;
+    jb.g.spins = sp;
+    jb.g.out = lpsi;
+    jb.g.carries_out = carries;
+    jb.job_counter = counter;
+    jb.status = ctx->status;
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        PSR_TRY(launch_fwd2d_f32(jb, pk, f, ctx->num_sms, st));
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_BWD);
+        float *out_rows = dout ? partial : g;
+        PSR_TRY(cudaMemsetAsync(out_rows, 0, rows * P * sizeof(float), st));
+        PSR_TRY(launch_bwd2d(sp, n, Lx, Ly, params->u1_mask, theta, tl, pk, f, carries, dv, out_rows, grid,
+                             scratch, st));
+        if (dout) PSR_TRY(launch_reduce_rows(partial, grid, P, g, st));
+    }
+    if (!d_g)
+        PSR_TRY(cudaMemcpyAsync(dparams, g_ws, (dout ? P : (size_t)n * P) * sizeof(float),
+                                cudaMemcpyDeviceToHost, st));
+    if (!d_g || !d_s || !d_theta || !d_dout) return take_status(ctx);
+    return PSR_OK;
+}
+
 int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
                        const psr_hamiltonian *ham, float *out, double *stats) {
     int rc = check_ham(ham);

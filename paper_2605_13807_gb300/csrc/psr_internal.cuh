@@ -193,6 +193,25 @@ cudaError_t launch_pack_theta_f2(const float *theta, const F2Layout &f, float *p
 cudaError_t launch_fwd2d_f32(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f,
                              int num_sms, cudaStream_t stream);
 
+// Offsets of the 2D model's tensors in the flat theta (psr_bwd2d.cu).
+struct T2Layout {
+    int nL, H;
+    int64_t Wz[kMaxLayers], bz[kMaxLayers], Wh[kMaxLayers], bh[kMaxLayers];
+    int64_t C[kMaxLayers], D[kMaxLayers];
+    int64_t Wo, bo;
+    int64_t total;
+};
+T2Layout t2_layout(int nL, int H);
+// Reverse-mode gradient of the 2D model over n samples from the forward's
+// row checkpoints; grad_rows: [n][P] (dout == NULL) or [grid][P] partial
+// sums of dout_i O_k(s_i).  scratch: grid * bwd2d_scratch_floats_per_cta.
+size_t bwd2d_scratch_floats_per_cta(int nL, int H);
+size_t bwd2d_smem_bytes(int nL, int H);
+cudaError_t launch_bwd2d(const uint8_t *spins, int64_t n, int Lx, int Ly, int u1, const float *theta,
+                         const T2Layout &tl, const float *packed, const F2Layout &f, const float *carries,
+                         const float *dout, float *grad_rows, int grid, float *scratch,
+                         cudaStream_t stream);
+
 // Exact sampler of the 2D patched minGRU (psr_sample2d.cu); per_cta: 1, 2,
 // 4 (hidden >= 64) or 8 (hidden >= 128) samples per CTA.  unif: [n][Np].
 size_t sample2d_smem_bytes(int per_cta, int nL, int H, int Lx);

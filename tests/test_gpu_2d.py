@@ -200,3 +200,52 @@ def test_sampler_tuned_tile_draws_identical_samples(oracle_mod):
         api.set_autotune(False)
     api.sync()
     assert torch.equal(s0, s1) and torch.equal(lp0, lp1)
+
+
+@pytest.mark.parametrize("Lx,Ly,H,nL,u1", [(6, 6, 32, 3, True), (8, 4, 64, 2, False),
+                                           (4, 8, 32, 1, False), (6, 4, 128, 3, True)])
+def test_gradient_matches_oracle_finite_differences(oracle_mod, Lx, Ly, H, nL, u1):
+    """Per-sample O_k against central differences of the FP64 oracle's
+    log psi: 80 sampled components (|dO_k| <= 1e-3 max|O|) and 3 random
+    directions (|dO.d| <= 1e-3 ||O|| ||d||)."""
+    theta = _theta(oracle_mod, nL, H, seed=460 + H + Lx, scale=2.0)
+    th64 = theta.astype(np.float64)
+    n = 3
+    s = _spins(461, n, Lx, Ly, u1)
+    cfg = api.ModelConfig(nL, H, u1, "fp32")
+    ok = api.grad2d(torch.from_numpy(theta).cuda(), torch.from_numpy(s).cuda(), cfg, Lx, Ly)
+    api.sync()
+    ok = ok.cpu().numpy().astype(np.float64)
+    P = theta.size
+    rng = np.random.default_rng(462)
+    eps = 1e-5
+
+    def lp(t):
+        return oracle_mod.logpsi2d(t, nL, H, Lx, Ly, s, u1=u1)
+
+    for k in rng.choice(P, 80, replace=False):
+        tp, tm = th64.copy(), th64.copy()
+        tp[k] += eps
+        tm[k] -= eps
+        fd = (lp(tp) - lp(tm)) / (2 * eps)
+        assert np.all(np.abs(ok[:, k] - fd) <= 1e-3 * np.max(np.abs(ok), axis=1) + 1e-6), k
+    for _ in range(3):
+        d = rng.standard_normal(P)
+        fd = (lp(th64 + eps * d) - lp(th64 - eps * d)) / (2 * eps)
+        assert np.all(np.abs(ok @ d - fd) <= 1e-3 * np.linalg.norm(ok, axis=1) * np.linalg.norm(d))
+
+
+def test_gradient_weighted_sum_and_determinism(oracle_mod):
+    Lx, Ly, H, nL = 6, 6, 64, 3
+    theta = torch.from_numpy(_theta(oracle_mod, nL, H, seed=470, scale=2.0)).cuda()
+    s = torch.from_numpy(_spins(471, 40, Lx, Ly, True)).cuda()
+    cfg = api.ModelConfig(nL, H, True, "fp32")
+    rows = api.grad2d(theta, s, cfg, Lx, Ly)
+    w = torch.from_numpy(inputs.uniform(472, (40,)).astype(np.float32) - 0.5).cuda()
+    tot = api.grad2d(theta, s, cfg, Lx, Ly, dout=w)
+    tot2 = api.grad2d(theta, s, cfg, Lx, Ly, dout=w)
+    rows2 = api.grad2d(theta, s, cfg, Lx, Ly)
+    api.sync()
+    ref = (w[:, None].double() * rows.double()).sum(0)
+    assert torch.allclose(tot.double(), ref, rtol=1e-4, atol=1e-5 * ref.abs().max().item())
+    assert torch.equal(tot, tot2) and torch.equal(rows, rows2)
