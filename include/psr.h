@@ -432,6 +432,14 @@ int psr_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, i
                  float *theta_out, uint8_t *spins_out, float *eloc_out, double *stats_out,
                  float *grad_out);
 
+/* One VMC step of the 2D patched minGRU on the device, as psr_vmc_step
+ * without symmetrisation: exact samples from uniforms [n][Np] (Np patches
+ * in path order, psr2d_sample), E_loc (psr2d_local_energy), the energy
+ * gradient by psr2d_grad, Adam.  Same array rules as psr_vmc_step. */
+int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, const float *uniforms,
+                   int64_t n, const psr_adam *adam, float *theta_out, uint8_t *spins_out,
+                   float *eloc_out, double *stats_out, float *grad_out);
+
 /* Stages of the launch sequence, for per-stage device timing. */
 enum {
     PSR_STAGE_PACK = 0,          /* parameter packing and spin bit-packing */

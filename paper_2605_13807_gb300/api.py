@@ -256,6 +256,25 @@ def vmc_step(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: Ad
     return out
 
 
+def vmc_step2d(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: Adam, theta_out=None):
+    """One on-device VMC step of the 2D patched minGRU (uniforms [n, Np])."""
+    n = uniforms.shape[0]
+    dev = uniforms.device
+    N = ham.Lx * ham.Ly
+    if theta_out is None:
+        theta_out = torch.empty_like(theta)
+    out = {"theta": theta_out,
+           "spins": torch.empty((n, N), dtype=torch.uint8, device=dev),
+           "eloc": torch.empty(n, dtype=torch.float32, device=dev),
+           "stats": torch.empty(3, dtype=torch.float64, device=dev),
+           "grad": torch.empty_like(theta)}
+    adam.step += 1
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr2d_vmc_step(p, ham, uniforms, adam.state(), theta_out, out["spins"], out["eloc"], out["stats"],
+                     out["grad"])
+    return out
+
+
 def set_autotune(enable=True):
     B.psr_context_set_autotune(_ctx(), enable)
 

@@ -145,3 +145,34 @@ def test_vmc_step_rejects_host_arrays_and_bad_constants():
         B.psr_vmc_step(p, sym_ham, True, torch.zeros((8, 8), device="cuda"),
                        torch.zeros(8, device="cuda"), adam.state(), out)
     assert ei.value.code == B.PSR_EINVAL
+
+
+def test_vmc_step_of_the_2d_model(oracle_mod):
+    """psr2d_vmc_step: its E_loc match the oracle on the drawn samples, its
+    gradient is the centred estimator over the per-sample O_k of psr2d_grad
+    (themselves checked against finite differences), and its update is Adam."""
+    Lx = Ly = 6
+    nL, H, n = 3, 32, 64
+    N, Np = Lx * Ly, (Lx // 2) * (Ly // 2)
+    P = oracle_mod.param_count2d(nL, H)
+    theta = ((2.0 * inputs.uniform(840, (P,)) - 1.0) * 2.0 / np.sqrt(H)).astype(np.float32)
+    th = torch.from_numpy(theta).cuda()
+    ham = B.make_hamiltonian("heisenberg", Lx, Ly, False, True, 1.0, 0.0)
+    cfg = api.ModelConfig(nL, H, True, "fp32")
+    u = torch.from_numpy(inputs.uniform(841, (n, Np)).astype(np.float32)).cuda()
+    adam = api.Adam(P, "cuda", lr=1e-2)
+    out = api.vmc_step2d(th, cfg, ham, u, adam)
+    api.sync()
+    s = out["spins"].cpu().numpy()
+    assert np.all(s.sum(axis=1) == N // 2)
+    e = out["eloc"].cpu().numpy().astype(np.float64)
+    ref_e = oracle_mod.local_energy2d(theta.astype(np.float64), nL, H, s, 0, Lx, Ly, u1=True)
+    _, _, diag = oracle_mod.connected(0, Lx, Ly, False, s)
+    assert np.all(np.abs(e - ref_e) <= 1e-3 * (np.abs(diag) + np.abs(ref_e - diag)))
+    ok = api.grad2d(th, out["spins"], cfg, Lx, Ly)
+    api.sync()
+    ref_g, _ = vmc.energy_gradient(e, ok.cpu().numpy().astype(np.float64))
+    g = out["grad"].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
+    t1, _, _ = vmc.adam(theta, g, np.zeros(P), np.zeros(P), 1, 1e-2)
+    assert np.max(np.abs(out["theta"].cpu().numpy() - t1)) <= 1e-6 + 1e-6 * np.max(np.abs(t1))
