@@ -504,6 +504,23 @@ def vmc_leg(dev, L=10, n=1024, reps=3):
         key = "c4v" if sym else "plain"
         res[key] = {"ms_per_step": e0.elapsed_time(e1) / reps,
                     "energy_per_site": float(out["stats"][0].item()) / N}
+    # the paper's 2D patched minGRU (hidden 128 here: its gradient kernel
+    # keeps a row's tiles in shared memory up to that width)
+    cfg2 = api.ModelConfig(N_LAYERS, HIDDEN, True, "fp32")
+    th2 = torch.from_numpy(inputs.glorot_params2d(N_LAYERS, HIDDEN, seed=0)).to(dev)
+    u2 = torch.rand((n, N // 4), generator=g, device=dev)
+    adam = api.Adam(th2.numel(), dev, lr=1e-3)
+    out = api.vmc_step2d(th2, cfg2, ham, u2, adam, theta_out=th2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        out = api.vmc_step2d(th2, cfg2, ham, u2, adam, theta_out=th2)
+    e1.record()
+    e1.synchronize()
+    res["model2d"] = {"ms_per_step": e0.elapsed_time(e1) / reps, "precision": "FP32",
+                      "energy_per_site": float(out["stats"][0].item()) / N}
     return res
 
 
