@@ -380,6 +380,24 @@ int psr_lru_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, in
 int psr_lru_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
                          const psr_hamiltonian *hamiltonian, float *out, double *stats);
 
+/* Exact samples of |psi|^2 of the LRU ansatz from uniforms [n][L] (float,
+ * host or device): s_t = 1 iff u_t < P(s_t = 1 | s_<t), the forced value at
+ * sites the zero-magnetisation mask fixes (Sec. II.A).  spins: uint8 [n][L]
+ * out; logpsi: float [n] out (NULL to skip).  FP32; the result does not
+ * depend on how samples are grouped into CTAs.  Requirements as
+ * psr_lru_logpsi. */
+int psr_lru_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t L, uint8_t *spins,
+                   float *logpsi);
+
+/* Gradient of log psi of the LRU ansatz, as psr_grad for the chain model:
+ * dout == NULL gives per-sample O_k rows [n][P] (P = psr_lru_param_count),
+ * otherwise the dout-weighted sum [P].  Chunks of 32 sites are recomputed
+ * from the forward's complex chunk carries and differentiated from the last
+ * to the first; the complex recurrence's adjoint runs backwards as
+ * mu_t = dL/dh_t + conj(lambda) mu_{t+1}.  FP32. */
+int psr_lru_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, const float *dout,
+                 float *dparams);
+
 /* ---------------------------------------------------------------------
  * c4v symmetrisation (the point-group symmetry the paper imposes on its 2D
  * runs, Sec. III.C, in the form of the RNN wave-function work it cites):
@@ -439,6 +457,14 @@ int psr_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, i
 int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, const float *uniforms,
                    int64_t n, const psr_adam *adam, float *theta_out, uint8_t *spins_out,
                    float *eloc_out, double *stats_out, float *grad_out);
+
+/* One VMC step of the LRU ansatz on the device, as psr_vmc_step without
+ * symmetrisation: exact samples from uniforms [n][N] (psr_lru_sample),
+ * E_loc (psr_lru_local_energy), the energy gradient by psr_lru_grad, Adam.
+ * Same array rules as psr_vmc_step. */
+int psr_lru_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, const float *uniforms,
+                     int64_t n, const psr_adam *adam, float *theta_out, uint8_t *spins_out,
+                     float *eloc_out, double *stats_out, float *grad_out);
 
 /* Stages of the launch sequence, for per-stage device timing. */
 enum {

@@ -201,6 +201,30 @@ def local_energy_lru(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, o
     return out, stats
 
 
+def sample_lru(theta, uniforms, cfg: ModelConfig, spins=None, logpsi=None):
+    """Exact samples of the LRU ansatz from uniforms [n, L]."""
+    dev = _device_of(uniforms, theta)
+    n, L = uniforms.shape
+    if spins is None:
+        spins = torch.empty((n, L), dtype=torch.uint8, device=dev)
+    if logpsi is None:
+        logpsi = torch.empty(n, dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_lru_sample(p, uniforms, spins, logpsi)
+    return spins, logpsi
+
+
+def grad_lru(theta, spins, cfg: ModelConfig, dout=None, out=None):
+    """d log psi / d theta of the LRU ansatz: [n, P] per sample, or [P] with dout."""
+    dev = _device_of(spins, theta)
+    P = param_count_lru(cfg.n_layers, cfg.hidden)
+    if out is None:
+        shape = (P,) if dout is not None else (spins.shape[0], P)
+        out = torch.empty(shape, dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    return B.psr_lru_grad(p, spins, dout, out)
+
+
 def sym_logpsi(theta, spins, cfg: ModelConfig, L: int, out=None):
     """c4v-symmetrised log psi on an L x L lattice."""
     dev = _device_of(spins, theta)
@@ -272,6 +296,25 @@ def vmc_step2d(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: 
     p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
     B.psr2d_vmc_step(p, ham, uniforms, adam.state(), theta_out, out["spins"], out["eloc"], out["stats"],
                      out["grad"])
+    return out
+
+
+def vmc_step_lru(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: Adam, theta_out=None):
+    """One on-device VMC step of the LRU ansatz (uniforms [n, N])."""
+    n = uniforms.shape[0]
+    dev = uniforms.device
+    N = ham.Lx * ham.Ly
+    if theta_out is None:
+        theta_out = torch.empty_like(theta)
+    out = {"theta": theta_out,
+           "spins": torch.empty((n, N), dtype=torch.uint8, device=dev),
+           "eloc": torch.empty(n, dtype=torch.float32, device=dev),
+           "stats": torch.empty(3, dtype=torch.float64, device=dev),
+           "grad": torch.empty_like(theta)}
+    adam.step += 1
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_lru_vmc_step(p, ham, uniforms, adam.state(), theta_out, out["spins"], out["eloc"], out["stats"],
+                       out["grad"])
     return out
 
 

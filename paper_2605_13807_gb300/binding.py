@@ -61,7 +61,8 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_scan_tile_for", "psr_context_set_autotune", "psr_sample", "psr_sample_tile_for",
             "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy", "psr_selftest_wait_timeout",
             "psr_lru_param_count", "psr_lru_logpsi", "psr_lru_local_energy", "psr_sym_logpsi",
-            "psr_sym_local_energy", "psr_vmc_step", "psr2d_sample", "psr2d_grad", "psr2d_vmc_step")
+            "psr_sym_local_energy", "psr_vmc_step", "psr2d_sample", "psr2d_grad", "psr2d_vmc_step",
+            "psr_lru_sample", "psr_lru_grad", "psr_lru_vmc_step")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -119,6 +120,10 @@ def lib():
                 L.psr2d_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp, vp]
                 L.psr2d_vmc_step.argtypes = [C.POINTER(psr_params), C.POINTER(psr_hamiltonian), vp, i64,
                                              C.POINTER(psr_adam), vp, vp, vp, vp, vp]
+                L.psr_lru_sample.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
+                L.psr_lru_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
+                L.psr_lru_vmc_step.argtypes = [C.POINTER(psr_params), C.POINTER(psr_hamiltonian), vp, i64,
+                                               C.POINTER(psr_adam), vp, vp, vp, vp, vp]
                 L.psr_strerror.argtypes = [C.c_int]
                 L.psr_strerror.restype = C.c_char_p
                 for name in EXPORTED:
@@ -404,4 +409,27 @@ def psr2d_vmc_step(params, ham, uniforms, adam, theta_out, spins_out=None, eloc_
     _check(lib().psr2d_vmc_step(C.byref(params), C.byref(ham), _ptr(uniforms), int(n), C.byref(adam),
                                 _ptr(theta_out), _ptr(spins_out), _ptr(eloc_out), _ptr(stats_out),
                                 _ptr(grad_out)), "psr2d_vmc_step")
+    return theta_out
+
+
+def psr_lru_sample(params, uniforms, spins, logpsi=None):
+    n, L = uniforms.shape
+    _check(lib().psr_lru_sample(C.byref(params), _ptr(uniforms), int(n), int(L), _ptr(spins), _ptr(logpsi)),
+           "psr_lru_sample")
+    return spins
+
+
+def psr_lru_grad(params, spins, dout, dparams):
+    n, L = spins.shape
+    _check(lib().psr_lru_grad(C.byref(params), _ptr(spins), int(n), int(L), _ptr(dout), _ptr(dparams)),
+           "psr_lru_grad")
+    return dparams
+
+
+def psr_lru_vmc_step(params, ham, uniforms, adam, theta_out, spins_out=None, eloc_out=None,
+                     stats_out=None, grad_out=None):
+    n = uniforms.shape[0]
+    _check(lib().psr_lru_vmc_step(C.byref(params), C.byref(ham), _ptr(uniforms), int(n), C.byref(adam),
+                                  _ptr(theta_out), _ptr(spins_out), _ptr(eloc_out), _ptr(stats_out),
+                                  _ptr(grad_out)), "psr_lru_vmc_step")
     return theta_out

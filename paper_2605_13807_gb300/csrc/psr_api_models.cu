@@ -522,4 +522,150 @@ int psr_lru_local_energy(const psr_params *params, const uint8_t *samples, int64
     return lru_run(params, samples, n, ham->Lx * ham->Ly, ham, out, stats);
 }
 
+int psr_lru_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t L, uint8_t *spins,
+                   float *logpsi) {
+    int rc = check_params_lru(params, n, L);
+    if (rc != PSR_OK) return rc;
+    if (!uniforms || !spins) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden, N = L;
+    const int64_t P = param_count_lru(nL, H);
+    const LruLayout f = lru_layout(nL, H);
+    const bool d_theta = is_device_ptr(params->theta), d_u = is_device_ptr(uniforms),
+               d_s = is_device_ptr(spins), d_lp = logpsi ? is_device_ptr(logpsi) : true;
+    float *theta_ws = nullptr, *u_ws = nullptr, *lp_ws = nullptr, *pk = nullptr;
+    uint8_t *s_ws = nullptr;
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        u_ws = c.get<float>(d_u ? 0 : (size_t)n * N);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        lp_ws = c.get<float>(d_lp ? 0 : n);
+        pk = c.get<float>(f.total);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr, *uu = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(uniforms, u_ws, (size_t)n * N, d_u, st, &uu)) != PSR_OK) return rc;
+    uint8_t *so = d_s ? spins : s_ws;
+    float *lo = logpsi ? (d_lp ? logpsi : lp_ws) : nullptr;
+    // samples per CTA: the most that still gives every SM a CTA (weights are
+    // read once per CTA and site, so more samples per CTA read less)
+    int per_cta = 4;
+    for (int b : {16, 8})
+        if ((n + b - 1) / b >= ctx->num_sms && sample_lru_smem_bytes(b, nL, H) <= 220 * 1024) {
+            per_cta = b;
+            break;
+        }
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_lru(theta, f, pk, st));
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_SAMPLE);
+        PSR_TRY(launch_sample_lru(per_cta, pk, f, uu, n, N, params->u1_mask, so, lo, st));
+    }
+    if (!d_s) PSR_TRY(cudaMemcpyAsync(spins, s_ws, (size_t)n * N, cudaMemcpyDeviceToHost, st));
+    if (logpsi && !d_lp) PSR_TRY(cudaMemcpyAsync(logpsi, lp_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (!d_theta || !d_u || !d_s || !d_lp) return take_status(ctx);
+    return PSR_OK;
+}
+
+int psr_lru_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, const float *dout,
+                 float *dparams) {
+    int rc = check_params_lru(params, n, L);
+    if (rc != PSR_OK) return rc;
+    if (!spins || !dparams) return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden, N = L;
+    const int64_t P = param_count_lru(nL, H);
+    const LruLayout f = lru_layout(nL, H);
+    const TLruLayout tl = tlru_layout(nL, H);
+    const int W = (int)words_per_row(N);
+    const int nch = (N + kChunkLru - 1) / kChunkLru;
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+    int per_sm = (int)(dev_smem / (bwd_lru_smem_bytes(H) + 1024));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    int64_t grid64 = (int64_t)ctx->num_sms * per_sm;
+    if (grid64 > n) grid64 = n;
+    const int grid = (int)grid64;
+    const size_t rows = dout ? (size_t)grid : (size_t)n;
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(spins),
+               d_dout = dout ? is_device_ptr(dout) : true, d_g = is_device_ptr(dparams);
+    float *theta_ws = nullptr, *dout_ws = nullptr, *g_ws = nullptr, *pk = nullptr, *lpsi = nullptr,
+          *carries = nullptr, *scratch = nullptr, *partial = nullptr;
+    uint8_t *s_ws = nullptr;
+    uint64_t *bits = nullptr;
+    unsigned long long *counter = nullptr;
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        dout_ws = c.get<float>(d_dout ? 0 : n);
+        g_ws = c.get<float>(d_g ? 0 : (dout ? P : (size_t)n * P));
+        pk = c.get<float>(f.total);
+        bits = c.get<uint64_t>((size_t)n * W);
+        lpsi = c.get<float>(n);
+        carries = c.get<float>((size_t)n * nch * nL * 2 * H);
+        scratch = c.get<float>((size_t)grid * bwd_lru_scratch_floats_per_cta(nL, H));
+        partial = c.get<float>(dout ? rows * P : 0);
+        counter = c.get<unsigned long long>(1);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr, *dv = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(spins, s_ws, (size_t)n * N, d_s, st, &sp)) != PSR_OK) return rc;
+    if (dout && (rc = stage_in(dout, dout_ws, n, d_dout, st, &dv)) != PSR_OK) return rc;
+    float *g = d_g ? dparams : g_ws;
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_lru(theta, f, pk, st));
+        PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));  // spin-byte check
+        PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    }
+    FwdJobs js{};
+    js.mode = 0;
+    js.n_groups = 1;
+    js.g[0].u1 = params->u1_mask;
+    js.g[0].N = N;
+    js.g[0].W = W;
+    js.g[0].n_jobs = n;
+    js.g[0].bits = bits;
+    js.g[0].out = lpsi;
+    js.g[0].carries_out = carries;
+    js.job_counter = counter;
+    js.status = ctx->status;
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        PSR_TRY(launch_lru_f32(js, pk, f, ctx->num_sms, st));
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_BWD);
+        float *out_rows = dout ? partial : g;
+        PSR_TRY(cudaMemsetAsync(out_rows, 0, rows * P * sizeof(float), st));
+        PSR_TRY(launch_bwd_lru(bits, n, N, W, params->u1_mask, theta, tl, pk, f, carries, dv, out_rows, grid,
+                               scratch, st));
+        if (dout) PSR_TRY(launch_reduce_rows(partial, grid, P, g, st));
+    }
+    if (!d_g)
+        PSR_TRY(cudaMemcpyAsync(dparams, g_ws, (dout ? P : (size_t)n * P) * sizeof(float),
+                                cudaMemcpyDeviceToHost, st));
+    if (!d_g || !d_s || !d_theta || !d_dout) return take_status(ctx);
+    return PSR_OK;
+}
+
 }  // extern "C"

@@ -376,4 +376,55 @@ int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *ham, const f
     return PSR_OK;
 }
 
+int psr_lru_vmc_step(const psr_params *params, const psr_hamiltonian *ham, const float *uniforms, int64_t n,
+                     const psr_adam *adam, float *theta_out, uint8_t *spins_out, float *eloc_out,
+                     double *stats_out, float *grad_out) {
+    int rc = check_ham(ham);
+    if (rc != PSR_OK) return rc;
+    const int N = ham->Lx * ham->Ly;
+    int64_t P = 0;
+    if (!params || !params->ctx || !params->theta) return PSR_EINVAL;
+    if ((rc = psr_lru_param_count(params->n_layers, params->hidden, &P)) != PSR_OK) return rc;
+    if (!uniforms || !adam || !adam->m || !adam->v || !theta_out || adam->step < 1 || n < 1)
+        return PSR_EINVAL;
+    if (!(adam->lr >= 0.0f) || !(adam->beta1 >= 0.0f && adam->beta1 < 1.0f) ||
+        !(adam->beta2 >= 0.0f && adam->beta2 < 1.0f) || !(adam->eps > 0.0f))
+        return PSR_EINVAL;
+    const void *dev_args[] = {params->theta, uniforms, adam->m, adam->v, theta_out};
+    for (const void *p : dev_args)
+        if (!is_device_ptr(p)) return PSR_EINVAL;
+    if ((spins_out && !is_device_ptr(spins_out)) || (eloc_out && !is_device_ptr(eloc_out)) ||
+        (stats_out && !is_device_ptr(stats_out)) || (grad_out && !is_device_ptr(grad_out)))
+        return PSR_EINVAL;
+    psr_context *ctx = params->ctx;
+    uint8_t *spins = nullptr;
+    float *eloc = nullptr, *dout = nullptr, *grad = nullptr;
+    double *stats = nullptr;
+    auto carve = [&](Carver &c) {
+        spins = c.get<uint8_t>(spins_out ? 0 : (size_t)n * N);
+        eloc = c.get<float>(eloc_out ? 0 : n);
+        stats = c.get<double>(stats_out ? 0 : 3);
+        dout = c.get<float>(n);
+        grad = c.get<float>(grad_out ? 0 : P);
+    };
+    Carver sz;
+    carve(sz);
+    if ((rc = ensure_ws2(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws2);
+    carve(cv);
+    if (spins_out) spins = spins_out;
+    if (eloc_out) eloc = eloc_out;
+    if (stats_out) stats = stats_out;
+    if (grad_out) grad = grad_out;
+    cudaStream_t st = ctx->stream;
+    if ((rc = psr_lru_sample(params, uniforms, n, N, spins, nullptr)) != PSR_OK) return rc;
+    if ((rc = psr_lru_local_energy(params, spins, n, ham, eloc, stats)) != PSR_OK) return rc;
+    PSR_TRY(launch_vmc_dout(eloc, stats, nullptr, n, 1, dout, st));
+    if ((rc = psr_lru_grad(params, spins, n, N, dout, grad)) != PSR_OK) return rc;
+    PSR_TRY(launch_adam(params->theta, grad, P, adam->lr, adam->beta1, adam->beta2, adam->eps,
+                        adam->step, adam->m, adam->v, theta_out, st));
+    return PSR_OK;
+}
+
 }  // extern "C"

@@ -239,6 +239,31 @@ cudaError_t launch_pack_theta_lru(const float *theta, const LruLayout &f, float 
 cudaError_t launch_lru_f32(const FwdJobs &jobs, const float *packed, const LruLayout &f, int num_sms,
                            cudaStream_t stream);
 
+// Offsets of the LRU's tensors in the flat theta (psr_bwd_lru.cu).
+struct TLruLayout {
+    int nL, H;
+    int64_t nu[kMaxLayers], th[kMaxLayers], ga[kMaxLayers], Bre[kMaxLayers], Bim[kMaxLayers];
+    int64_t Cre[kMaxLayers], Cim[kMaxLayers], D[kMaxLayers], Wa[kMaxLayers], ba[kMaxLayers];
+    int64_t Wg[kMaxLayers], bg[kMaxLayers];
+    int64_t Wo, bo;
+    int64_t total;
+};
+TLruLayout tlru_layout(int nL, int H);
+// Reverse-mode gradient of the LRU over n samples from the forward's complex
+// chunk carries [n][nch][nL][2][H]; grad_rows: [n][P] (dout == NULL) or
+// [grid][P] partial sums of dout_i O_k(s_i), zeroed by the caller.
+// scratch: grid * bwd_lru_scratch_floats_per_cta.
+size_t bwd_lru_scratch_floats_per_cta(int nL, int H);
+size_t bwd_lru_smem_bytes(int H);
+cudaError_t launch_bwd_lru(const uint64_t *bits, int64_t n, int N, int W, int u1, const float *theta,
+                           const TLruLayout &tl, const float *packed, const LruLayout &f,
+                           const float *carries, const float *dout, float *grad_rows, int grid,
+                           float *scratch, cudaStream_t stream);
+// Exact sampler of the LRU (psr_sample_lru.cu); per_cta 4, 8 or 16.
+size_t sample_lru_smem_bytes(int per_cta, int nL, int H);
+cudaError_t launch_sample_lru(int per_cta, const float *packed, const LruLayout &f, const float *unif,
+                              int64_t n, int N, int u1, uint8_t *out, float *logpsi, cudaStream_t stream);
+
 // c4v symmetrisation and VMC-step kernels (psr_vmc.cu).
 cudaError_t launch_c4v_images(const uint8_t *s, int64_t n, int L, uint8_t *out, cudaStream_t st);
 cudaError_t launch_c4v_pick(const uint8_t *s, const float *u, int64_t n, int L, uint8_t *out,

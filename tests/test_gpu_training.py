@@ -1,6 +1,7 @@
-"""Physics check of the whole on-device VMC loop (psr_vmc_step: exact
-sampling, E_loc, energy gradient, Adam): a short training run of the chain
-model must approach the exact ground-state energy from above.
+"""Physics check of the whole on-device VMC loop (psr_vmc_step and
+psr_lru_vmc_step: exact sampling, E_loc, energy gradient, Adam): a short
+training run of the chain minGRU or of the deep LRU must approach the exact
+ground-state energy from above.
 
 References: the 16-site open TFIM at h = 1 has E0/N = -1.2510242 (Table I;
 the oracle's exact diagonalisation is pinned to that table), the 4 x 4 open
@@ -72,3 +73,30 @@ def test_heisenberg_4x4_with_c4v_symmetry(oracle_mod):
     e, se = _train(0, 4, 4, 32, 3, True, 0.0, steps=400, n=1024, lr=5e-3, sym=True)
     assert e >= e0 - 4 * se
     assert (e - e0) / abs(e0) < 4e-2, (e, e0)
+
+
+def _train_lru(kind, N, H, nL, u1, hf, steps, n, lr):
+    ham = B.make_hamiltonian(kind, N, 1, False, True, 1.0, hf)
+    cfg = api.ModelConfig(nL, H, u1, "fp32")
+    th = torch.from_numpy(inputs.lru_params(nL, H, seed=0)).cuda()
+    adam = api.Adam(th.numel(), "cuda", lr=lr)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    for _ in range(steps):
+        u = torch.rand((n, N), generator=gen, device="cuda")
+        api.vmc_step_lru(th, cfg, ham, u, adam, theta_out=th)
+    u = torch.rand((8192, N), generator=gen, device="cuda")
+    frozen = api.Adam(th.numel(), "cuda", lr=0.0)
+    out = api.vmc_step_lru(th, cfg, ham, u, frozen)
+    api.sync()
+    assert torch.equal(out["theta"], th)
+    mean, var, se = out["stats"].cpu().numpy()
+    return mean / N, se / N
+
+
+@pytest.mark.parametrize("kind,u1,hf", [(1, False, 1.0), (0, True, 0.0)])
+def test_lru_chain_reaches_the_exact_energy(oracle_mod, kind, u1, hf):
+    e0 = _exact(oracle_mod, kind, 16, 1, hf)
+    e, se = _train_lru(kind, 16, 32, 2, u1, hf, steps=400, n=1024, lr=1e-2 if kind == 1 else 5e-3)
+    assert e >= e0 - 4 * se
+    assert (e - e0) / abs(e0) < 2e-3, (e, e0)
