@@ -424,7 +424,9 @@ def lru_flops_per_site(H):
 def lru_leg(dev, N=256, H=64, n=1024, reps=3):
     """The paper's deep 1D LRU on the 1D TFIM (Table IV configuration: 3
     layers, d = d_h = 64, N = 256 OBC, 1024 samples, h = 1): log psi + E_loc
-    over every site flip, FP32 CUDA cores."""
+    over every site flip, FP32 CUDA cores; then the gradient's reverse pass
+    and one full VMC step (sampling, E_loc, gradient, Adam) on the same
+    configuration."""
     import torch
 
     from paper_2605_13807_gb300 import api, binding as B, inputs
@@ -459,7 +461,27 @@ def lru_leg(dev, N=256, H=64, n=1024, reps=3):
     p = torch.arange(N, device=dev)
     conn_sites = n * int((N - (p // 32) * 32).sum().item())
     achieved = conn_sites * lru_flops_per_site(H) / (conn_ms / 1e3) / 1e12
+    # reverse-mode gradient (dout-weighted sum) and one full VMC step
+    w = torch.full((n,), 1.0 / n, dtype=torch.float32, device=dev)
+    api.grad_lru(theta, spins, cfg, dout=w)
+    bwd_ms = B.psr_context_stage_ms(ctx)["bwd"]
+    B.psr_context_set_profiling(ctx, False)
+    g = torch.Generator(device=dev)
+    g.manual_seed(6)
+    u = torch.rand((n, N), generator=g, device=dev)
+    adam = api.Adam(theta.numel(), dev, lr=1e-3)
+    th = theta.clone()  # updated in place by every step
+    api.vmc_step_lru(th, cfg, ham, u, adam, theta_out=th)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        out = api.vmc_step_lru(th, cfg, ham, u, adam, theta_out=th)
+    e1.record()
+    e1.synchronize()
+    vmc_ms = e0.elapsed_time(e1) / reps
     return {"model": "deep 1D LRU (complex diagonal recurrence + GLU), FP32 CUDA cores",
+            "grad_bwd_ms": bwd_ms, "vmc_step_ms": vmc_ms,
+            "vmc_energy_per_site": float(out["stats"][0].item()) / N,
             "workload": f"tfim_chain_{N}_obc_{n}_samples", "hidden": H, "connected": E,
             "value": (n + E) * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "roofline": {"kernel": "lru_f32_kernel (connected configurations)", "bound": "alu",
