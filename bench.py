@@ -33,7 +33,7 @@ METRIC = "configs·sites/s for log psi fwd+bwd+E_loc at 52x52, BF16 vs FP32; % H
 UNIT = "configs·sites/s"
 N_LAYERS, HIDDEN = 3, 128
 MMA_FLOPS_PER_SITE = 2 * HIDDEN * HIDDEN * 9  # nine HxH products per site (BF16 path)
-CHUNK_BF16 = 64
+CHUNK_BF16 = 32
 
 WORKLOADS = {
     # name: (Lx, Ly, samples)

@@ -3,12 +3,12 @@
 //
 // Layout: "feature-major" tiles.  Every MMA computes D[out unit][site] =
 // sum_k A[out unit][k] B[site][k] with M = 128 output units (one per TMEM
-// lane), N = 64 sites (one scan chunk) and K = 128 input units, so after
-// tcgen05.ld thread j of a warpgroup holds hidden unit j for all 64 sites of
+// lane), N = 32 sites (one scan chunk) and K = 128 input units, so after
+// tcgen05.ld thread j of a warpgroup holds hidden unit j for all 32 sites of
 // the chunk and the recurrence h_t = a_t h_{t-1} + b_t (Sec. II.C) is a plain
 // sequential FP32 loop in registers, with the carry kept across chunks.  The
 // activations of the chunk (h and x, BF16) are written straight into the
-// next MMA's B operand in shared memory (MN-major, 128-byte swizzle); they
+// next MMA's B operand in shared memory (MN-major, 64-byte swizzle); they
 // never touch HBM.  All weights stay on chip for the whole kernel:
 //   TMEM (A operand):  W_z^(1), W_h^(1), W_z^(2), W_h^(2)
 //   SMEM (A operand):  C^(0), C^(1), D^(1), C^(2), D^(2)   (K-major, SW128)
@@ -16,10 +16,11 @@
 // tables and only its output map C^(0) h is a contraction.  The readout
 // (logit difference, two-way softmax) and log-psi sums are FP32 on CUDA cores.
 //
-// A CTA (one per SM) runs two independent sequence streams, each on two
-// warpgroups that split the 64 sites of a chunk, with its own TMEM
-// accumulators, B tiles and mbarrier: while one stream runs its epilogue
-// (gates, scan, GELU) the tensor core works on the other stream's MMAs.  Jobs (full sequences or connected
+// A CTA (one per SM) runs four independent sequence streams, one warpgroup
+// each, with its own 64 TMEM accumulator columns, B tiles, mbarrier and named
+// barrier: while one stream waits for its MMAs or its TMEM loads, the other
+// three issue their epilogues (gates, scan, GELU), and the tensor core works
+// through the MMAs of all four.  Jobs (full sequences or connected
 // configurations resumed from a stored chunk carry) come from an atomic
 // counter.  Every mbarrier wait is bounded; on expiry the CTA records
 // PSR_ETIMEOUT, stops issuing work, frees its TMEM and returns.
@@ -35,10 +36,11 @@ namespace psr {
 namespace {
 
 constexpr int H = 128;
-constexpr int CH = kChunkBF16;  // 64 sites = MMA N
+constexpr int CH = kChunkBF16;  // 32 sites = MMA N
 constexpr int NL = 3;
-constexpr int kThreads = 512;   // two streams x two warpgroups
-constexpr uint32_t kTileBytes = 16384;     // [K=128 rows][64 sites] bf16
+constexpr int kStreams = 4;
+constexpr int kThreads = 128 * kStreams;  // one warpgroup per stream
+constexpr uint32_t kTileBytes = 8192;     // [K=128 rows][32 sites] bf16
 constexpr uint32_t kMatBytes = 32768;      // 128 x 128 bf16
 constexpr int kSmemMats = 5;               // C0, C1, D1, C2, D2
 constexpr int kTmemMats = 4;               // Wz1, Wh1, Wz2, Wh2
@@ -50,7 +52,7 @@ constexpr uint32_t kTmemWeightCol = 256;   // weights at columns 256..511
 // shared memory map (offsets from a 1024-aligned base)
 constexpr uint32_t OFF_W = 0;
 constexpr uint32_t OFF_TILES = OFF_W + kSmemMats * kMatBytes;   // per stream: X, H
-constexpr uint32_t OFF_MISC = OFF_TILES + 4 * kTileBytes;
+constexpr uint32_t OFF_MISC = OFF_TILES + 2 * kStreams * kTileBytes;
 constexpr uint32_t MISC_BYTES = 256;
 constexpr uint32_t kSmemBytes = OFF_MISC + MISC_BYTES + 1024;   // + alignment slack
 
@@ -60,7 +62,7 @@ constexpr size_t PK_TMEM = PK_SMEM + (size_t)kSmemMats * kMatBytes;
 constexpr size_t PK_TOTAL = PK_TMEM + (size_t)kTmemMats * kMatBytes;
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, A K-major,
-// B MN-major, N = 64, M = 128.
+// B MN-major, N = 32, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (1u << 16) |
                             ((uint32_t)(CH >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
@@ -118,10 +120,20 @@ __device__ __forceinline__ void tc_after() {
 }
 
 // Smem matrix descriptor (tcgen05): start >> 4, LBO >> 4 at bit 16,
-// SBO >> 4 at bit 32, version 1 at bit 46, 128-byte swizzle (2) at bit 61.
+// SBO >> 4 at bit 32, version 1 at bit 46, layout type at bit 61
+// (2: 128-byte swizzle, 4: 64-byte swizzle).
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// B operand: an activation tile, MN-major (32 sites = 64 bytes per K row),
+// 64-byte swizzle; 8-row groups of 512 bytes along K.  The 32 sites are one
+// swizzle atom wide, so only the K-direction stride is ever used; both
+// offsets are given that value.
+__device__ __forceinline__ uint64_t bdesc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(512u >> 4) << 16) |
+           ((uint64_t)(512u >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
 __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
@@ -176,11 +188,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 struct Misc {
-    uint64_t mbar[2];
-    long long job[2];
+    uint64_t mbar[kStreams];
+    long long job[kStreams];
     long long base[kMaxGroups + 1];  // first job of each group
     uint32_t tmem_base;
-    int abort_flag[2];
+    int abort_flag[kStreams];
+    float red2[kStreams];            // per-stream chunk sum of log P
 };
 static_assert(sizeof(Misc) <= MISC_BYTES, "misc block too large");
 static_assert(offsetof(Misc, mbar) == 0, "mbarriers open the misc block");
@@ -284,28 +297,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-        : "memory");
-}
-
-// Writes 8 sites (one 16-byte chunk, logical index c) of row k of an
-// MN-major SW128 B tile.
+// Writes 8 sites (one 16-byte chunk, logical index c = 0..3) of row k of an
+// MN-major SW64 B tile: the chunk sits at position c ^ ((k >> 1) & 3).
 __device__ __forceinline__ void tile_store8(uint8_t *tile, int k, int c, const float *v) {
     uint4 w;
     w.x = pack_bf16(v[0], v[1]);
     w.y = pack_bf16(v[2], v[3]);
     w.z = pack_bf16(v[4], v[5]);
     w.w = pack_bf16(v[6], v[7]);
-    *reinterpret_cast<uint4 *>(tile + k * 128 + ((c ^ (k & 7)) << 4)) = w;
-}
-
-// Address of logical 16-byte chunk c of row k (used as a mailbox before the
-// chunk receives its tile data).
-__device__ __forceinline__ float *tile_slot(uint8_t *tile, int k, int c) {
-    return reinterpret_cast<float *>(tile + k * 128 + ((c ^ (k & 7)) << 4));
+    *reinterpret_cast<uint4 *>(tile + k * 64 + ((c ^ ((k >> 1) & 3)) << 4)) = w;
 }
 
 }  // namespace
@@ -352,14 +352,15 @@ cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, vo
 // warp-uniform bases -- the CTA's shared-memory window (sbase) and TMEM
 // column 0 (the kernel owns all 512 columns, so its allocation starts
 // there) -- so the tensor-core descriptors stay in uniform registers.
+// Stream S accumulates in TMEM columns 64 S .. 64 S + 63 (Z, then h~).
 template <int S>
 __device__ __forceinline__ void issue_l0(uint32_t sbase) {
     const uint32_t tH = sbase + OFF_TILES + (2 * S + 1) * kTileBytes;
     const uint32_t wC = sbase + OFF_W + SM_C0 * kMatBytes;
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk)
-        mma_ss(128 * S, sdesc(wC + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-               sdesc(tH + kk * 2048, 1024, 1024), kk > 0);
+        mma_ss(64 * S, sdesc(wC + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), bdesc(tH + kk * 1024),
+               kk > 0);
     mma_commit(sbase + OFF_MISC + 8 * S);
 }
 
@@ -369,10 +370,9 @@ __device__ __forceinline__ void issue_proj(uint32_t sbase) {
     const uint32_t wz = kTmemWeightCol + (L == 1 ? TM_WZ1 : TM_WZ2) * 64;
     const uint32_t wh = kTmemWeightCol + (L == 1 ? TM_WH1 : TM_WH2) * 64;
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) mma_ts(128 * S, wz + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
+    for (int kk = 0; kk < 8; ++kk) mma_ts(64 * S, wz + kk * 8, bdesc(tX + kk * 1024), kk > 0);
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk)
-        mma_ts(128 * S + 64, wh + kk * 8, sdesc(tX + kk * 2048, 1024, 1024), kk > 0);
+    for (int kk = 0; kk < 8; ++kk) mma_ts(64 * S + 32, wh + kk * 8, bdesc(tX + kk * 1024), kk > 0);
     mma_commit(sbase + OFF_MISC + 8 * S);
 }
 
@@ -384,130 +384,76 @@ __device__ __forceinline__ void issue_out(uint32_t sbase) {
     const uint32_t wD = sbase + OFF_W + (L == 1 ? SM_D1 : SM_D2) * kMatBytes;
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk)
-        mma_ss(128 * S, sdesc(wC + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-               sdesc(tH + kk * 2048, 1024, 1024), kk > 0);
+        mma_ss(64 * S, sdesc(wC + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), bdesc(tH + kk * 1024),
+               kk > 0);
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk)
-        mma_ss(128 * S, sdesc(wD + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-               sdesc(tX + kk * 2048, 1024, 1024), 1);
+        mma_ss(64 * S, sdesc(wD + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), bdesc(tX + kk * 1024), 1);
     mma_commit(sbase + OFF_MISC + 8 * S);
 }
 
-// One dense layer (l = 1 or 2) of one stream half, from the proj MMA to the
-// output epilogue.  h1: layer 1 writes its FP32 h there (the residual of
-// layer 2); layer 2 adds it and overwrites it with the layer output x3.
-template <int L, class WaitF, class PubF, class BarF>
-__device__ __forceinline__ bool dense_layer(float hbz, float bh,
-                                            uint8_t *tileX, uint8_t *tileH, uint32_t sbase, int s,
-                                            uint32_t accZ, uint32_t accC, bool issuer, int hf, int j,
-                                            float &carry, float (&h1)[32], WaitF &sync_wait,
-                                            PubF &publish, BarF &sbar) {
-    if (issuer) {
-        if (s == 0) issue_proj<0, L>(sbase);
-        else issue_proj<1, L>(sbase);
+template <int S>
+__device__ __forceinline__ void issue_any(int what, uint32_t sbase) {
+    switch (what) {
+        case 0: issue_l0<S>(sbase); break;
+        case 1: issue_proj<S, 1>(sbase); break;
+        case 2: issue_out<S, 1>(sbase); break;
+        case 3: issue_proj<S, 2>(sbase); break;
+        default: issue_out<S, 2>(sbase); break;
     }
-    if (!sync_wait()) return false;
+}
+
+// MMA group `what` (0: layer-0 output map, 1/3: projections of layer 1/2,
+// 2/4: output maps of layer 1/2) of stream s.
+__device__ __forceinline__ void issue(int s, int what, uint32_t sbase) {
+    switch (s) {
+        case 0: issue_any<0>(what, sbase); break;
+        case 1: issue_any<1>(what, sbase); break;
+        case 2: issue_any<2>(what, sbase); break;
+        default: issue_any<3>(what, sbase); break;
+    }
+}
+
+// One dense layer (l = 1 or 2) of one stream's chunk, from the projection
+// MMAs to the output epilogue.  h1: layer 1 writes its FP32 h there (the
+// residual of layer 2); layer 2 adds it and overwrites it with the layer
+// output x3.
+template <int L, class WaitF, class PubF>
+__device__ __forceinline__ void dense_layer(float hbz, float bh, uint8_t *tileX, uint8_t *tileH,
+                                            uint32_t sbase, int s, uint32_t accZ, uint32_t accC,
+                                            bool issuer, int j, float &carry, float (&h1)[32],
+                                            WaitF &sync_wait, PubF &publish) {
+    if (issuer) issue(s, L == 1 ? 1 : 3, sbase);
+    sync_wait();
     const float2 hbz2 = make_float2(hbz, hbz), bh2 = make_float2(bh, bh);
-    // gates + scan; half 0 from the carry, half 1 as prefix pairs (P, S)
-    float keep[8];
-    float h31 = 0.0f;
-    if (hf == 0) {
-        float h = carry;
+    float h = carry;
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            uint32_t rz[8], rc[8];
-            tmem_ld8(accZ + 8 * g, rz);
-            tmem_ld8(accC + 8 * g, rc);
-            tmem_wait_ld();
-            float hv[8];
+    for (int g = 0; g < 4; ++g) {
+        uint32_t rz[8], rc[8];
+        tmem_ld8(accZ + 8 * g, rz);
+        tmem_ld8(accC + 8 * g, rc);
+        tmem_wait_ld();
+        float hv[8];
 #pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-                float2 a, b;
-                gates2(make_float2(__uint_as_float(rz[i]), __uint_as_float(rz[i + 1])),
-                       make_float2(__uint_as_float(rc[i]), __uint_as_float(rc[i + 1])), hbz2, bh2, a, b);
-                h = fmaf(a.x, h, b.x);  // h_t = a_t h_{t-1} + (1 - a_t) h~_t
-                hv[i] = h;
-                h = fmaf(a.y, h, b.y);
-                hv[i + 1] = h;
-            }
-            if (L == 1) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) h1[8 * g + i] = hv[i];
-            }
-            if (g == 0) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) keep[i] = hv[i];
-            } else {
-                tile_store8(tileH, j, g, hv);
-            }
+        for (int i = 0; i < 8; i += 2) {
+            float2 a, b;
+            gates2(make_float2(__uint_as_float(rz[i]), __uint_as_float(rz[i + 1])),
+                   make_float2(__uint_as_float(rc[i]), __uint_as_float(rc[i + 1])), hbz2, bh2, a, b);
+            h = fmaf(a.x, h, b.x);  // h_t = a_t h_{t-1} + (1 - a_t) h~_t
+            hv[i] = h;
+            h = fmaf(a.y, h, b.y);
+            hv[i + 1] = h;
         }
-        h31 = h;
-        *tile_slot(tileH, j, 4) = h31;
-    } else {
-        float P = 1.0f, S = 0.0f;
+        if (L == 1) {
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            uint32_t rz[8], rc[8];
-            tmem_ld8(accZ + 8 * g, rz);
-            tmem_ld8(accC + 8 * g, rc);
-            tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-                float2 a, b;
-                gates2(make_float2(__uint_as_float(rz[i]), __uint_as_float(rz[i + 1])),
-                       make_float2(__uint_as_float(rc[i]), __uint_as_float(rc[i + 1])), hbz2, bh2, a, b);
-                S = fmaf(a.x, S, b.x);
-                P *= a.x;
-                rz[i] = __float_as_uint(S);
-                rc[i] = __float_as_uint(P);
-                S = fmaf(a.y, S, b.y);
-                P *= a.y;
-                rz[i + 1] = __float_as_uint(S);
-                rc[i + 1] = __float_as_uint(P);
-            }
-            tmem_st8(accZ + 8 * g, rz);
-            tmem_st8(accC + 8 * g, rc);
+            for (int i = 0; i < 8; ++i) h1[8 * g + i] = hv[i];
         }
-        float *mb = tile_slot(tileH, j, 0);
-        mb[0] = P;
-        mb[1] = S;
-        tmem_wait_st();
+        tile_store8(tileH, j, g, hv);
     }
-    sbar();
-    if (hf == 0) {
-        const float *mb = tile_slot(tileH, j, 0);
-        carry = fmaf(mb[0], h31, mb[1]);
-        tile_store8(tileH, j, 0, keep);
-    } else {
-        const float hin = *tile_slot(tileH, j, 4);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            uint32_t rs[8], rp[8];
-            tmem_ld8(accZ + 8 * g, rs);
-            tmem_ld8(accC + 8 * g, rp);
-            tmem_wait_ld();
-            float hv[8];
-#pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-                const float2 v = __ffma2_rn(make_float2(__uint_as_float(rp[i]), __uint_as_float(rp[i + 1])),
-                                            make_float2(hin, hin),
-                                            make_float2(__uint_as_float(rs[i]), __uint_as_float(rs[i + 1])));
-                hv[i] = v.x;
-                hv[i + 1] = v.y;
-            }
-            if (L == 1) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) h1[8 * g + i] = hv[i];
-            }
-            tile_store8(tileH, j, 4 + g, hv);
-        }
-    }
+    carry = h;
     publish();
-    if (issuer) {
-        if (s == 0) issue_out<0, L>(sbase);
-        else issue_out<1, L>(sbase);
-    }
-    if (!sync_wait()) return false;
+    if (issuer) issue(s, L == 1 ? 2 : 4, sbase);
+    sync_wait();
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         uint32_t r[8];
@@ -526,19 +472,14 @@ __device__ __forceinline__ bool dense_layer(float hbz, float bh,
                 h1[8 * g + i + 1] = x.y;
             }
         }
-        if (L == 1) tile_store8(tileX, j, 4 * hf + g, xv);
+        if (L == 1) tile_store8(tileX, j, g, xv);
     }
     if (L == 1) publish();
-    return true;
 }
 
-// Two streams (independent sequences) per CTA; each stream has two
-// warpgroups that split the 64 sites of a chunk into halves of 32.  The scan
-// across the halves: the first half runs h_t = a_t h_{t-1} + b_t from the
-// carry; the second half composes its 32 affine maps into prefix pairs
-// (P_t, S_t) (h_t = P_t h_31 + S_t), parked in its own TMEM columns.  The
-// halves swap h_31 and (P_63, S_63) through mailboxes inside the B tile, then
-// each writes its part of the tile.
+// Four streams (independent sequences) per CTA, one warpgroup each; thread
+// j of a stream's warpgroup owns hidden unit j (TMEM lane j) for the 32
+// sites of the chunk.
 __global__ void __launch_bounds__(kThreads, 1)
 fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ pkb,
                 const float *__restrict__ pk, F32Layout fl) {
@@ -548,16 +489,14 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
     Misc &M = *reinterpret_cast<Misc *>(smem + OFF_MISC);
 
     const int tid = threadIdx.x;
-    const int wg = tid >> 7;         // warpgroup
-    const int s = wg >> 1;           // stream
-    const int hf = wg & 1;           // half of the chunk (sites 32*hf .. 32*hf+31)
+    const int s = tid >> 7;          // stream = warpgroup
     const int j = tid & 127;         // hidden unit = TMEM lane
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int lane_base = (warp & 3) * 32;
-    // one MMA-issuing thread per stream, on different SM sub-partitions
-    // (warp 0 and warp 10)
-    const bool issuer = (hf == 0 && j == (s == 0 ? 0 : 64));
+    // one MMA-issuing thread per stream, each on its own SM sub-partition
+    // (lane 0 of warp s of the stream's warpgroup)
+    const bool issuer = (j == 32 * s);
 
     uint8_t *tileX = smem + OFF_TILES + (2 * s) * kTileBytes;
     uint8_t *tileH = tileX + kTileBytes;
@@ -573,10 +512,10 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&M.mbar[0]), 1);
-        mbar_init(smem_u32(&M.mbar[1]), 1);
-        M.abort_flag[0] = 0;
-        M.abort_flag[1] = 0;
+        for (int i = 0; i < kStreams; ++i) {
+            mbar_init(smem_u32(&M.mbar[i]), 1);
+            M.abort_flag[i] = 0;
+        }
         long long b = 0;
         M.base[0] = 0;
         for (int i = 0; i < jb.n_groups; ++i) {
@@ -595,7 +534,7 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
     __syncthreads();
     tc_after();
     const uint32_t tmem = M.tmem_base;  // 0: the kernel owns all 512 columns
-    if (wg == 0) {
+    if (s == 0) {
 #pragma unroll 1
         for (int m = 0; m < kTmemMats; ++m) {
             const uint32_t *row =
@@ -625,8 +564,8 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
     const float bd = pk[fl.bd];
 
     const uint32_t lane_off = (uint32_t)lane_base << 16;
-    const uint32_t accZ = lane_off + 128 * s + 32 * hf;  // this half's Z columns
-    const uint32_t accC = accZ + 64;                     // this half's C columns
+    const uint32_t accZ = lane_off + 64 * s;  // this stream's Z (and output) columns
+    const uint32_t accC = accZ + 32;          // this stream's h~ columns
 
     // all 512 columns belong to this CTA, so the allocation starts at column 0;
     // anything else is reported and no work is done
@@ -635,15 +574,14 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
     const int bar_id = 1 + s;
     uint32_t phase = 0;
     bool aborted = false;
-    float *red = reinterpret_cast<float *>(tileX);        // readout scratch [2][4][32]
-    float *red2 = red + 2 * 4 * 32;                       // per-half site sums [2]
+    float *red = reinterpret_cast<float *>(tileX);  // readout scratch [4][32]
 
-    auto sbar = [&]() { asm volatile("bar.sync %0, 256;" ::"r"(bar_id) : "memory"); };
+    auto sbar = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory"); };
     // Waits for this stream's MMAs.  A wait that expires records
     // PSR_ETIMEOUT and the stream's abort flag but keeps the control flow
     // of every thread identical (all later waits are bounded too); the flag
     // is acted on at the end of the chunk, after a stream-wide barrier.
-    auto sync_wait = [&]() -> bool {
+    auto sync_wait = [&]() {
         const bool ok = mbar_wait(bar, phase);
         phase ^= 1u;
         if (!ok) {
@@ -651,7 +589,6 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
             set_status(jb.status, PSR_ETIMEOUT);
         }
         tc_after();
-        return true;
     };
     auto publish = [&]() {
         fence_proxy_async();
@@ -684,8 +621,8 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
             c0 = p / CH;
         }
         const uint64_t *row = G.bits + (int64_t)sample * G.W;
-        float cr[NL] = {0.0f, 0.0f, 0.0f};  // scan carries (used by half 0)
-        if (hf == 0 && c0 > 0) {
+        float cr[NL] = {0.0f, 0.0f, 0.0f};  // scan carries
+        if (c0 > 0) {
             const float *cin = G.carries_in + (((int64_t)sample * nch + c0) * NL) * H + j;
             cr[0] = cin[0];
             cr[1] = cin[H];
@@ -693,115 +630,64 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
         }
         int n_up = G.u1 ? count_up_before(row, c0 * CH) : 0;
         float acc = 0.0f;
-        uint64_t next_word = row[c0];
-        uint32_t next_prev = (c0 > 0) ? (uint32_t)(row[c0 - 1] >> 63) : 0u;
+        // the 64-bit word holding the current chunk's 32 spins; the spin
+        // before the chunk (s_{t0-1}) of the unflipped sample
+        uint64_t word = row[c0 >> 1];
+        uint32_t next_prev =
+            (c0 == 0) ? 0u : (uint32_t)(((c0 & 1) ? (word >> 31) : (row[(c0 >> 1) - 1] >> 63)) & 1ull);
 
         for (int c = c0; c < nch && !aborted; ++c) {
             const int t0 = c * CH;
-            if (hf == 0 && G.carries_out) {
+            if (G.carries_out) {
                 float *co = G.carries_out + (((int64_t)sample * nch + c) * NL) * H + j;
                 co[0] = cr[0];
                 co[H] = cr[1];
                 co[2 * H] = cr[2];
             }
-            uint64_t cur = next_word;
+            uint32_t cur = (uint32_t)(word >> (32 * (c & 1)));
             uint32_t prev = next_prev;
-            // next chunk's spins and this chunk's reference log P are fetched now,
-            // long before they are needed
-            next_prev = (uint32_t)(cur >> 63);
-            if (c + 1 < nch) next_word = row[c + 1];
+            next_prev = cur >> 31;
+            // the next word of spins and this chunk's reference log P are
+            // fetched now, long before they are needed
+            if ((c & 1) && c + 1 < nch) word = row[(c + 1) >> 1];
             float lp_ref = 0.0f;
-            if (jb.mode == 1 && (warp & 3) == 0 && t0 + 32 * hf + lane < N)
-                lp_ref = G.logp_ref[(int64_t)sample * N + t0 + 32 * hf + lane];
+            if (jb.mode == 1 && (warp & 3) == 0 && t0 + lane < N)
+                lp_ref = G.logp_ref[(int64_t)sample * N + t0 + lane];
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const int x = f ? q : p;
-                if (x >= t0 && x < t0 + CH) cur ^= 1ull << (x - t0);
+                if (x >= t0 && x < t0 + CH) cur ^= 1u << (x - t0);
                 else if (x >= 0 && x == t0 - 1) prev ^= 1u;
             }
             const int nvalid = min(CH, N - t0);
-            if (nvalid < 64) cur &= (1ull << nvalid) - 1ull;
-            // bit i = s_{t-1} for site t = t0 + 32 hf + i
-            const uint32_t inbits = (uint32_t)(((cur << 1) | prev) >> (32 * hf));
-            const bool seq_start = (t0 == 0 && hf == 0);  // site 0 has no predecessor
+            if (nvalid < 32) cur &= (1u << nvalid) - 1u;
+            // bit i = s_{t-1} for site t = t0 + i
+            const uint32_t inbits = (cur << 1) | prev;
+            const bool seq_start = (t0 == 0);  // site 0 has no predecessor
 
             float h1[32];  // FP32 h of layer 1 (residual of layer 2); becomes x3
 
             // ---------------- layer 0: lookup gates, scan -> tile H
             {
-                float keep[8];  // half 0: sites 0..7, written after the mailbox swap
-                float h31 = 0.0f;
-                if (hf == 0) {
-                    float h = cr[0];
+                float h = cr[0];
 #pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        float hv[8];
+                for (int g = 0; g < 4; ++g) {
+                    float hv[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const bool sb = (inbits >> (8 * g + i)) & 1u;
-                            float a = sb ? a0_2 : a0_1, b = sb ? b0_2 : b0_1;
-                            if (g == 0 && i == 0 && seq_start) { a = a0_0; b = b0_0; }
-                            h = fmaf(a, h, b);
-                            hv[i] = h;
-                        }
-                        if (g == 0) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) keep[i] = hv[i];
-                        } else {
-                            tile_store8(tileH, j, g, hv);
-                        }
+                    for (int i = 0; i < 8; ++i) {
+                        const bool sb = (inbits >> (8 * g + i)) & 1u;
+                        float a = sb ? a0_2 : a0_1, b = sb ? b0_2 : b0_1;
+                        if (g == 0 && i == 0 && seq_start) { a = a0_0; b = b0_0; }
+                        h = fmaf(a, h, b);
+                        hv[i] = h;
                     }
-                    h31 = h;
-                    *tile_slot(tileH, j, 4) = h31;
-                } else {
-                    float P = 1.0f, S = 0.0f;
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        uint32_t rs[8], rp[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const bool sb = (inbits >> (8 * g + i)) & 1u;
-                            const float a = sb ? a0_2 : a0_1, b = sb ? b0_2 : b0_1;
-                            S = fmaf(a, S, b);
-                            P *= a;
-                            rs[i] = __float_as_uint(S);
-                            rp[i] = __float_as_uint(P);
-                        }
-                        tmem_st8(accZ + 8 * g, rs);
-                        tmem_st8(accC + 8 * g, rp);
-                    }
-                    float *mb = tile_slot(tileH, j, 0);
-                    mb[0] = P;
-                    mb[1] = S;
-                    tmem_wait_st();
+                    tile_store8(tileH, j, g, hv);
                 }
-                sbar();
-                if (hf == 0) {
-                    const float *mb = tile_slot(tileH, j, 0);
-                    cr[0] = fmaf(mb[0], h31, mb[1]);
-                    tile_store8(tileH, j, 0, keep);
-                } else {
-                    const float hin = *tile_slot(tileH, j, 4);
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        uint32_t rs[8], rp[8];
-                        tmem_ld8(accZ + 8 * g, rs);
-                        tmem_ld8(accC + 8 * g, rp);
-                        tmem_wait_ld();
-                        float hv[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            hv[i] = fmaf(__uint_as_float(rp[i]), hin, __uint_as_float(rs[i]));
-                        tile_store8(tileH, j, 4 + g, hv);
-                    }
-                }
+                cr[0] = h;
             }
             publish();
-            if (issuer) {
-                if (s == 0) issue_l0<0>(sbase);
-                else issue_l0<1>(sbase);
-            }
-            if (!sync_wait()) { aborted = true; break; }
+            if (issuer) issue(s, 0, sbase);
+            sync_wait();
             // epilogue: x1 = GELU(C0 h0 + D0 u) -> tile X
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
@@ -819,18 +705,16 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
                     xv[i] = x.x;
                     xv[i + 1] = x.y;
                 }
-                tile_store8(tileX, j, 4 * hf + g, xv);
+                tile_store8(tileX, j, g, xv);
             }
             publish();
 
             // ---------------- layers 1 and 2
-            if (!dense_layer<1>(hbz1, bh1, tileX, tileH, sbase, s, accZ, accC, issuer, hf, j, cr[1], h1,
-                                sync_wait, publish, sbar))
-                { aborted = true; break; }
-            if (!dense_layer<2>(hbz2, bh2, tileX, tileH, sbase, s, accZ, accC, issuer, hf, j, cr[2], h1,
-                                sync_wait, publish, sbar))
-                { aborted = true; break; }
-            float (&xo)[32] = h1;  // layer-2 output (x3) of this half
+            dense_layer<1>(hbz1, bh1, tileX, tileH, sbase, s, accZ, accC, issuer, j, cr[1], h1, sync_wait,
+                           publish);
+            dense_layer<2>(hbz2, bh2, tileX, tileH, sbase, s, accZ, accC, issuer, j, cr[2], h1, sync_wait,
+                           publish);
+            float (&xo)[32] = h1;  // layer-2 output (x3) of the chunk
 
             // ---------------- readout: d_t = wd . x3_t + bd over the 128 units
             {
@@ -853,29 +737,27 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
                         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
                     }
                 }
-                // lane L holds site L of this half, summed over its warp's units
-                red[(hf * 4 + (warp & 3)) * 32 + lane] = v[0];
+                // lane L holds site L, summed over its warp's units
+                red[(warp & 3) * 32 + lane] = v[0];
                 sbar();
                 if ((warp & 3) == 0) {
-                    const int t = 32 * hf + lane;
-                    const float d = bd + red[(hf * 4 + 0) * 32 + lane] + red[(hf * 4 + 1) * 32 + lane] +
-                                    red[(hf * 4 + 2) * 32 + lane] + red[(hf * 4 + 3) * 32 + lane];
-                    const int tt = t0 + t;
+                    const float d = bd + red[lane] + red[32 + lane] + red[64 + lane] + red[96 + lane];
+                    const int tt = t0 + lane;
                     float sv = 0.0f;
                     if (tt < N) {
-                        const int sbit = (int)((cur >> t) & 1ull);
-                        const int nu = n_up + __popcll(cur & ((1ull << t) - 1ull));
+                        const int sbit = (int)((cur >> lane) & 1u);
+                        const int nu = n_up + __popc(cur & ((1u << lane) - 1u));
                         const float lp = site_logp_fast(d, sbit, u1_forced(G.u1, N, tt, nu));
                         if (G.logp_out) G.logp_out[(int64_t)sample * N + tt] = lp;
                         sv = (jb.mode == 1) ? lp - lp_ref : lp;
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-                    if (lane == 0) red2[hf] = sv;
+                    if (lane == 0) M.red2[s] = sv;
                 }
                 sbar();
-                if (issuer) acc += red2[0] + red2[1];
-                n_up += __popcll(cur);
+                if (issuer) acc += M.red2[s];
+                n_up += __popc(cur);
                 if (M.abort_flag[s]) aborted = true;  // uniform: read after the barrier
             }
         }
@@ -912,7 +794,7 @@ cudaError_t launch_fwd_bf16(const FwdJobs &jobs, const void *packed_bf16, const 
     cudaError_t e = prepare_fwd_bf16();
     if (e != cudaSuccess) return e;
     int64_t grid = num_sms;
-    const int64_t max_jobs_streams = (max_jobs(jobs) + 1) / 2;
+    const int64_t max_jobs_streams = (max_jobs(jobs) + kStreams - 1) / kStreams;
     if (grid > max_jobs_streams) grid = max_jobs_streams;
     if (grid < 1) grid = 1;
     fwd_bf16_kernel<<<(int)grid, kThreads, kSmemBytes, stream>>>(

@@ -11,7 +11,7 @@ namespace psr {
 constexpr int kMaxLayers = 8;
 constexpr int kChunkF32 = 32;   // scan chunk of the FP32 SIMT path (sites)
 constexpr int kChunkGrad = 16;  // chunk of the gradient path (carries, recompute)
-constexpr int kChunkBF16 = 64;  // scan chunk of the tcgen05 path (sites = MMA N)
+constexpr int kChunkBF16 = 32;  // scan chunk of the tcgen05 path (sites = MMA N)
 
 // Device status word values (first error wins).
 constexpr int kStatusOk = 0;
