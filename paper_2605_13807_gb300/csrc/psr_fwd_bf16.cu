@@ -175,9 +175,6 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -288,13 +285,42 @@ __device__ __forceinline__ void gates2(float2 z, float2 c, float2 hbz2, float2 b
     b = __ffma2_rn(make_float2(-a.x, -a.y), cv, cv);
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+#define PSR_R16(x, o)                                                                              \
+    "=r"(x[o + 0]), "=r"(x[o + 1]), "=r"(x[o + 2]), "=r"(x[o + 3]), "=r"(x[o + 4]), "=r"(x[o + 5]),    \
+    "=r"(x[o + 6]), "=r"(x[o + 7]), "=r"(x[o + 8]), "=r"(x[o + 9]), "=r"(x[o + 10]), "=r"(x[o + 11]), \
+    "=r"(x[o + 12]), "=r"(x[o + 13]), "=r"(x[o + 14]), "=r"(x[o + 15])
+#define PSR_P16(x, o)                                                                              \
+    "+r"(x[o + 0]), "+r"(x[o + 1]), "+r"(x[o + 2]), "+r"(x[o + 3]), "+r"(x[o + 4]), "+r"(x[o + 5]),    \
+    "+r"(x[o + 6]), "+r"(x[o + 7]), "+r"(x[o + 8]), "+r"(x[o + 9]), "+r"(x[o + 10]), "+r"(x[o + 11]), \
+    "+r"(x[o + 12]), "+r"(x[o + 13]), "+r"(x[o + 14]), "+r"(x[o + 15])
+
+// 16 consecutive columns (sites) of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7])
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%16];"
+        : PSR_R16(r, 0)
         : "r"(taddr)
         : "memory");
+}
+
+// 32 consecutive columns (sites) of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : PSR_R16(r, 0), PSR_R16(r, 16)
+        : "r"(taddr)
+        : "memory");
+}
+
+// tcgen05.wait::ld with the registers of the awaited loads as operands, so
+// that no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld16x2(uint32_t (&a)[16], uint32_t (&b)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(a, 0), PSR_P16(b, 0)::"memory");
+}
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(a, 0), PSR_P16(a, 16)::"memory");
 }
 
 // Writes 8 sites (one 16-byte chunk, logical index c = 0..3) of row k of an
@@ -348,69 +374,67 @@ cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, vo
     return cudaGetLastError();
 }
 
-// MMA issue for stream S.  Every operand is a compile-time offset from two
-// warp-uniform bases -- the CTA's shared-memory window (sbase) and TMEM
-// column 0 (the kernel owns all 512 columns, so its allocation starts
-// there) -- so the tensor-core descriptors stay in uniform registers.
-// Stream S accumulates in TMEM columns 64 S .. 64 S + 63 (Z, then h~).
-template <int S>
-__device__ __forceinline__ void issue_l0(uint32_t sbase) {
-    const uint32_t tH = sbase + OFF_TILES + (2 * S + 1) * kTileBytes;
-    const uint32_t wC = sbase + OFF_W + SM_C0 * kMatBytes;
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk)
-        mma_ss(64 * S, sdesc(wC + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), bdesc(tH + kk * 1024),
-               kk > 0);
-    mma_commit(sbase + OFF_MISC + 8 * S);
+// MMA issue for stream s: group WHAT = 0 (layer-0 output map C0 h), 1 / 3
+// (projections W_z x, W_h x of layer 1 / 2), 2 / 4 (output map C h + D x of
+// layer 1 / 2).  Stream s accumulates in TMEM columns 64 s .. 64 s + 63 (Z or
+// the output, then h~); the kernel owns all 512 columns, so its allocation
+// starts at column 0.
+__device__ __forceinline__ uint64_t adesc(uint32_t w, int kk) {
+    return sdesc(w + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
 }
 
-template <int S, int L>
-__device__ __forceinline__ void issue_proj(uint32_t sbase) {
-    const uint32_t tX = sbase + OFF_TILES + (2 * S) * kTileBytes;
-    const uint32_t wz = kTmemWeightCol + (L == 1 ? TM_WZ1 : TM_WZ2) * 64;
-    const uint32_t wh = kTmemWeightCol + (L == 1 ? TM_WH1 : TM_WH2) * 64;
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) mma_ts(64 * S, wz + kk * 8, bdesc(tX + kk * 1024), kk > 0);
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) mma_ts(64 * S + 32, wh + kk * 8, bdesc(tX + kk * 1024), kk > 0);
-    mma_commit(sbase + OFF_MISC + 8 * S);
-}
-
-template <int S, int L>
-__device__ __forceinline__ void issue_out(uint32_t sbase) {
-    const uint32_t tX = sbase + OFF_TILES + (2 * S) * kTileBytes;
+template <int WHAT>
+__device__ __forceinline__ void issue(int s, uint32_t sbase) {
+    const uint32_t tX = sbase + OFF_TILES + (uint32_t)(2 * s) * kTileBytes;
     const uint32_t tH = tX + kTileBytes;
-    const uint32_t wC = sbase + OFF_W + (L == 1 ? SM_C1 : SM_C2) * kMatBytes;
-    const uint32_t wD = sbase + OFF_W + (L == 1 ? SM_D1 : SM_D2) * kMatBytes;
+    const uint32_t d = 64u * (uint32_t)s;
+    if (WHAT == 0) {
+        const uint32_t wC = sbase + OFF_W + SM_C0 * kMatBytes;
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk)
-        mma_ss(64 * S, sdesc(wC + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), bdesc(tH + kk * 1024),
-               kk > 0);
+        for (int kk = 0; kk < 8; ++kk) mma_ss(d, adesc(wC, kk), bdesc(tH + kk * 1024), kk > 0);
+    } else if (WHAT == 1 || WHAT == 3) {
+        const uint32_t wz = kTmemWeightCol + (WHAT == 1 ? TM_WZ1 : TM_WZ2) * 64;
+        const uint32_t wh = kTmemWeightCol + (WHAT == 1 ? TM_WH1 : TM_WH2) * 64;
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk)
-        mma_ss(64 * S, sdesc(wD + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), bdesc(tX + kk * 1024), 1);
-    mma_commit(sbase + OFF_MISC + 8 * S);
-}
-
-template <int S>
-__device__ __forceinline__ void issue_any(int what, uint32_t sbase) {
-    switch (what) {
-        case 0: issue_l0<S>(sbase); break;
-        case 1: issue_proj<S, 1>(sbase); break;
-        case 2: issue_out<S, 1>(sbase); break;
-        case 3: issue_proj<S, 2>(sbase); break;
-        default: issue_out<S, 2>(sbase); break;
+        for (int kk = 0; kk < 8; ++kk) mma_ts(d, wz + kk * 8, bdesc(tX + kk * 1024), kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) mma_ts(d + 32, wh + kk * 8, bdesc(tX + kk * 1024), kk > 0);
+    } else {
+        const uint32_t wC = sbase + OFF_W + (WHAT == 2 ? SM_C1 : SM_C2) * kMatBytes;
+        const uint32_t wD = sbase + OFF_W + (WHAT == 2 ? SM_D1 : SM_D2) * kMatBytes;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) mma_ss(d, adesc(wC, kk), bdesc(tH + kk * 1024), kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) mma_ss(d, adesc(wD, kk), bdesc(tX + kk * 1024), 1);
     }
+    mma_commit(sbase + OFF_MISC + 8 * (uint32_t)s);
 }
 
-// MMA group `what` (0: layer-0 output map, 1/3: projections of layer 1/2,
-// 2/4: output maps of layer 1/2) of stream s.
-__device__ __forceinline__ void issue(int s, int what, uint32_t sbase) {
-    switch (s) {
-        case 0: issue_any<0>(what, sbase); break;
-        case 1: issue_any<1>(what, sbase); break;
-        case 2: issue_any<2>(what, sbase); break;
-        default: issue_any<3>(what, sbase); break;
+// Gates and scan of 16 sites (half hh of the chunk) from their Z and h~
+// accumulators: a = sigmoid(z + b_z), h_t = a_t h_{t-1} + (1 - a_t)(h~_t + b_h).
+template <int L>
+__device__ __forceinline__ void gates_scan16(const uint32_t (&rz)[16], const uint32_t (&rc)[16], int hh,
+                                             float2 hbz2, float2 bh2, float &h, float (&h1)[32],
+                                             uint8_t *tileH, int j) {
+#pragma unroll
+    for (int gg = 0; gg < 2; ++gg) {
+        float hv[8];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            const int k = 8 * gg + i;
+            float2 a, b;
+            gates2(make_float2(__uint_as_float(rz[k]), __uint_as_float(rz[k + 1])),
+                   make_float2(__uint_as_float(rc[k]), __uint_as_float(rc[k + 1])), hbz2, bh2, a, b);
+            h = fmaf(a.x, h, b.x);
+            hv[i] = h;
+            h = fmaf(a.y, h, b.y);
+            hv[i + 1] = h;
+        }
+        if (L == 1) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) h1[16 * hh + 8 * gg + i] = hv[i];
+        }
+        tile_store8(tileH, j, 2 * hh + gg, hv);
     }
 }
 
@@ -423,53 +447,43 @@ __device__ __forceinline__ void dense_layer(float hbz, float bh, uint8_t *tileX,
                                             uint32_t sbase, int s, uint32_t accZ, uint32_t accC,
                                             bool issuer, int j, float &carry, float (&h1)[32],
                                             WaitF &sync_wait, PubF &publish) {
-    if (issuer) issue(s, L == 1 ? 1 : 3, sbase);
+    if (issuer) issue<L == 1 ? 1 : 3>(s, sbase);
     sync_wait();
     const float2 hbz2 = make_float2(hbz, hbz), bh2 = make_float2(bh, bh);
     float h = carry;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        uint32_t rz[8], rc[8];
-        tmem_ld8(accZ + 8 * g, rz);
-        tmem_ld8(accC + 8 * g, rc);
-        tmem_wait_ld();
-        float hv[8];
-#pragma unroll
-        for (int i = 0; i < 8; i += 2) {
-            float2 a, b;
-            gates2(make_float2(__uint_as_float(rz[i]), __uint_as_float(rz[i + 1])),
-                   make_float2(__uint_as_float(rc[i]), __uint_as_float(rc[i + 1])), hbz2, bh2, a, b);
-            h = fmaf(a.x, h, b.x);  // h_t = a_t h_{t-1} + (1 - a_t) h~_t
-            hv[i] = h;
-            h = fmaf(a.y, h, b.y);
-            hv[i + 1] = h;
-        }
-        if (L == 1) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) h1[8 * g + i] = hv[i];
-        }
-        tile_store8(tileH, j, g, hv);
+    {
+        // sites 0..15, with the loads of sites 16..31 in flight meanwhile
+        uint32_t z0[16], c0[16], z1[16], c1[16];
+        tmem_ld16(accZ, z0);
+        tmem_ld16(accC, c0);
+        tmem_wait_ld16x2(z0, c0);
+        tmem_ld16(accZ + 16, z1);
+        tmem_ld16(accC + 16, c1);
+        gates_scan16<L>(z0, c0, 0, hbz2, bh2, h, h1, tileH, j);
+        tmem_wait_ld16x2(z1, c1);
+        gates_scan16<L>(z1, c1, 1, hbz2, bh2, h, h1, tileH, j);
     }
     carry = h;
     publish();
-    if (issuer) issue(s, L == 1 ? 2 : 4, sbase);
+    if (issuer) issue<L == 1 ? 2 : 4>(s, sbase);
     sync_wait();
+    uint32_t r[32];
+    tmem_ld32(accZ, r);
+    tmem_wait_ld32(r);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        uint32_t r[8];
-        tmem_ld8(accZ + 8 * g, r);
-        tmem_wait_ld();
         float xv[8];
 #pragma unroll
         for (int i = 0; i < 8; i += 2) {
-            float2 y = make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1]));
-            if (L == 2) y = __fadd2_rn(y, make_float2(h1[8 * g + i], h1[8 * g + i + 1]));
+            const int k = 8 * g + i;
+            float2 y = make_float2(__uint_as_float(r[k]), __uint_as_float(r[k + 1]));
+            if (L == 2) y = __fadd2_rn(y, make_float2(h1[k], h1[k + 1]));
             const float2 x = (L == 1) ? gelu_bf16out2(y) : gelu_fast2(y);
             xv[i] = x.x;
             xv[i + 1] = x.y;
             if (L == 2) {
-                h1[8 * g + i] = x.x;
-                h1[8 * g + i + 1] = x.y;
+                h1[k] = x.x;
+                h1[k + 1] = x.y;
             }
         }
         if (L == 1) tile_store8(tileX, j, g, xv);
@@ -686,26 +700,29 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
                 cr[0] = h;
             }
             publish();
-            if (issuer) issue(s, 0, sbase);
+            if (issuer) issue<0>(s, sbase);
             sync_wait();
             // epilogue: x1 = GELU(C0 h0 + D0 u) -> tile X
+            {
+                uint32_t r[32];
+                tmem_ld32(accZ, r);
+                tmem_wait_ld32(r);
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                uint32_t r[8];
-                tmem_ld8(accZ + 8 * g, r);
-                tmem_wait_ld();
-                float xv[8];
+                for (int g = 0; g < 4; ++g) {
+                    float xv[8];
 #pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    float du0 = ((inbits >> (8 * g + i)) & 1u) ? d0_2 : d0_1;
-                    const float du1 = ((inbits >> (8 * g + i + 1)) & 1u) ? d0_2 : d0_1;
-                    if (g == 0 && i == 0 && seq_start) du0 = d0_0;
-                    const float2 x = gelu_bf16out2(__fadd2_rn(
-                        make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1])), make_float2(du0, du1)));
-                    xv[i] = x.x;
-                    xv[i + 1] = x.y;
+                    for (int i = 0; i < 8; i += 2) {
+                        const int k = 8 * g + i;
+                        float du0 = ((inbits >> k) & 1u) ? d0_2 : d0_1;
+                        const float du1 = ((inbits >> (k + 1)) & 1u) ? d0_2 : d0_1;
+                        if (k == 0 && seq_start) du0 = d0_0;
+                        const float2 x = gelu_bf16out2(__fadd2_rn(
+                            make_float2(__uint_as_float(r[k]), __uint_as_float(r[k + 1])), make_float2(du0, du1)));
+                        xv[i] = x.x;
+                        xv[i + 1] = x.y;
+                    }
+                    tile_store8(tileX, j, g, xv);
                 }
-                tile_store8(tileX, j, g, xv);
             }
             publish();
 
