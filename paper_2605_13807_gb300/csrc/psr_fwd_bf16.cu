@@ -451,7 +451,7 @@ __device__ __forceinline__ void dense_layer(float hbz, float bh, uint8_t *tileX,
     sync_wait();
     const float2 hbz2 = make_float2(hbz, hbz), bh2 = make_float2(bh, bh);
     float h = carry;
-    {
+    if (L == 1) {
         // sites 0..15, with the loads of sites 16..31 in flight meanwhile
         uint32_t z0[16], c0[16], z1[16], c1[16];
         tmem_ld16(accZ, z0);
@@ -462,6 +462,16 @@ __device__ __forceinline__ void dense_layer(float hbz, float bh, uint8_t *tileX,
         gates_scan16<L>(z0, c0, 0, hbz2, bh2, h, h1, tileH, j);
         tmem_wait_ld16x2(z1, c1);
         gates_scan16<L>(z1, c1, 1, hbz2, bh2, h, h1, tileH, j);
+    } else {
+        // layer 2 keeps the residual h1 live: one half at a time
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            uint32_t z[16], cc[16];
+            tmem_ld16(accZ + 16 * hh, z);
+            tmem_ld16(accC + 16 * hh, cc);
+            tmem_wait_ld16x2(z, cc);
+            gates_scan16<L>(z, cc, hh, hbz2, bh2, h, h1, tileH, j);
+        }
     }
     carry = h;
     publish();
@@ -646,6 +656,56 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
         float acc = 0.0f;
         // the 64-bit word holding the current chunk's 32 spins; the spin
         // before the chunk (s_{t0-1}) of the unflipped sample
+        float h1[32];  // FP32 h of layer 1 (residual of layer 2), then the layer-2 output x3
+        uint32_t rd_cur = 0u;  // spins, first site and reference log P of the chunk read out next
+        int rd_t0 = 0;
+        float rd_lpref = 0.0f;
+        // readout of the last finished chunk: d_t = wd . x3_t + bd over the
+        // 128 units, log P, and the chunk's sum into acc
+        auto readout = [&]() {
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+                const float2 w = __fmul2_rn(make_float2(wdj, wdj), make_float2(h1[i], h1[i + 1]));
+                v[i] = w.x;
+                v[i + 1] = w.y;
+            }
+#pragma unroll
+            for (int st = 0; st < 5; ++st) {
+                const int m = 16 >> st;
+                const int half = 16 >> st;
+                const bool upper = (lane & m) != 0;
+#pragma unroll
+                for (int i = 0; i < half; ++i) {
+                    const float send = upper ? v[i] : v[i + half];
+                    const float keep = upper ? v[i + half] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+                }
+            }
+            // lane L holds site L, summed over its warp's units; the X tile is
+            // free while the layer-0 MMAs (which read only the H tile) run
+            red[(warp & 3) * 32 + lane] = v[0];
+            sbar();
+            if ((warp & 3) == 0) {
+                const float d = bd + red[lane] + red[32 + lane] + red[64 + lane] + red[96 + lane];
+                const int tt = rd_t0 + lane;
+                float sv = 0.0f;
+                if (tt < N) {
+                    const int sbit = (int)((rd_cur >> lane) & 1u);
+                    const int nu = n_up + __popc(rd_cur & ((1u << lane) - 1u));
+                    const float lp = site_logp_fast(d, sbit, u1_forced(G.u1, N, tt, nu));
+                    if (G.logp_out) G.logp_out[(int64_t)sample * N + tt] = lp;
+                    sv = (jb.mode == 1) ? lp - rd_lpref : lp;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                if (lane == 0) M.red2[s] = sv;
+            }
+            sbar();
+            if (issuer) acc += M.red2[s];
+            n_up += __popc(rd_cur);
+            if (M.abort_flag[s]) aborted = true;  // uniform: read after the barrier
+        };
         uint64_t word = row[c0 >> 1];
         uint32_t next_prev =
             (c0 == 0) ? 0u : (uint32_t)(((c0 & 1) ? (word >> 31) : (row[(c0 >> 1) - 1] >> 63)) & 1ull);
@@ -679,8 +739,6 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
             const uint32_t inbits = (cur << 1) | prev;
             const bool seq_start = (t0 == 0);  // site 0 has no predecessor
 
-            float h1[32];  // FP32 h of layer 1 (residual of layer 2); becomes x3
-
             // ---------------- layer 0: lookup gates, scan -> tile H
             {
                 float h = cr[0];
@@ -701,6 +759,7 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
             }
             publish();
             if (issuer) issue<0>(s, sbase);
+            if (c > c0) readout();  // the previous chunk, while the MMAs run
             sync_wait();
             // epilogue: x1 = GELU(C0 h0 + D0 u) -> tile X
             {
@@ -731,53 +790,12 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
                            publish);
             dense_layer<2>(hbz2, bh2, tileX, tileH, sbase, s, accZ, accC, issuer, j, cr[2], h1, sync_wait,
                            publish);
-            float (&xo)[32] = h1;  // layer-2 output (x3) of the chunk
-
-            // ---------------- readout: d_t = wd . x3_t + bd over the 128 units
-            {
-                float v[32];
-#pragma unroll
-                for (int i = 0; i < 32; i += 2) {
-                    const float2 w = __fmul2_rn(make_float2(wdj, wdj), make_float2(xo[i], xo[i + 1]));
-                    v[i] = w.x;
-                    v[i + 1] = w.y;
-                }
-#pragma unroll
-                for (int st = 0; st < 5; ++st) {
-                    const int m = 16 >> st;
-                    const int half = 16 >> st;
-                    const bool upper = (lane & m) != 0;
-#pragma unroll
-                    for (int i = 0; i < half; ++i) {
-                        const float send = upper ? v[i] : v[i + half];
-                        const float keep = upper ? v[i + half] : v[i];
-                        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-                    }
-                }
-                // lane L holds site L, summed over its warp's units
-                red[(warp & 3) * 32 + lane] = v[0];
-                sbar();
-                if ((warp & 3) == 0) {
-                    const float d = bd + red[lane] + red[32 + lane] + red[64 + lane] + red[96 + lane];
-                    const int tt = t0 + lane;
-                    float sv = 0.0f;
-                    if (tt < N) {
-                        const int sbit = (int)((cur >> lane) & 1u);
-                        const int nu = n_up + __popc(cur & ((1u << lane) - 1u));
-                        const float lp = site_logp_fast(d, sbit, u1_forced(G.u1, N, tt, nu));
-                        if (G.logp_out) G.logp_out[(int64_t)sample * N + tt] = lp;
-                        sv = (jb.mode == 1) ? lp - lp_ref : lp;
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-                    if (lane == 0) M.red2[s] = sv;
-                }
-                sbar();
-                if (issuer) acc += M.red2[s];
-                n_up += __popc(cur);
-                if (M.abort_flag[s]) aborted = true;  // uniform: read after the barrier
-            }
+            // x3 (in h1) is read out while the next chunk's layer-0 MMAs run
+            rd_cur = cur;
+            rd_t0 = t0;
+            rd_lpref = lp_ref;
         }
+        if (!aborted) readout();
         if (aborted) break;
         if (issuer) G.out[lj] = 0.5f * acc;
     }
