@@ -175,6 +175,12 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -374,7 +380,7 @@ cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, vo
     return cudaGetLastError();
 }
 
-// MMA issue for stream s: group WHAT = 0 (layer-0 output map C0 h), 1 / 3
+// MMA issue for stream s: group WHAT = 0 (layer-0 output map D0 u + C0 h), 1 / 3
 // (projections W_z x, W_h x of layer 1 / 2), 2 / 4 (output map C h + D x of
 // layer 1 / 2).  Stream s accumulates in TMEM columns 64 s .. 64 s + 63 (Z or
 // the output, then h~); the kernel owns all 512 columns, so its allocation
@@ -389,9 +395,10 @@ __device__ __forceinline__ void issue(int s, uint32_t sbase) {
     const uint32_t tH = tX + kTileBytes;
     const uint32_t d = 64u * (uint32_t)s;
     if (WHAT == 0) {
+        // accumulates onto D0 u, which the layer-0 scan stored in the columns
         const uint32_t wC = sbase + OFF_W + SM_C0 * kMatBytes;
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_ss(d, adesc(wC, kk), bdesc(tH + kk * 1024), kk > 0);
+        for (int kk = 0; kk < 8; ++kk) mma_ss(d, adesc(wC, kk), bdesc(tH + kk * 1024), 1);
     } else if (WHAT == 1 || WHAT == 3) {
         const uint32_t wz = kTmemWeightCol + (WHAT == 1 ? TM_WZ1 : TM_WZ2) * 64;
         const uint32_t wh = kTmemWeightCol + (WHAT == 1 ? TM_WH1 : TM_WH2) * 64;
@@ -739,23 +746,29 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
             const uint32_t inbits = (cur << 1) | prev;
             const bool seq_start = (t0 == 0);  // site 0 has no predecessor
 
-            // ---------------- layer 0: lookup gates, scan -> tile H
+            // ---------------- layer 0: lookup gates, scan -> tile H; the
+            // one-hot input's output term D0 u -> this stream's accumulator
+            // columns, which the layer-0 MMAs then add C0 h to
             {
                 float h = cr[0];
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     float hv[8];
+                    uint32_t du[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const bool sb = (inbits >> (8 * g + i)) & 1u;
-                        float a = sb ? a0_2 : a0_1, b = sb ? b0_2 : b0_1;
-                        if (g == 0 && i == 0 && seq_start) { a = a0_0; b = b0_0; }
+                        float a = sb ? a0_2 : a0_1, b = sb ? b0_2 : b0_1, dd = sb ? d0_2 : d0_1;
+                        if (g == 0 && i == 0 && seq_start) { a = a0_0; b = b0_0; dd = d0_0; }
                         h = fmaf(a, h, b);
                         hv[i] = h;
+                        du[i] = __float_as_uint(dd);
                     }
                     tile_store8(tileH, j, g, hv);
+                    tmem_st8(accZ + 8 * g, du);
                 }
                 cr[0] = h;
+                tmem_wait_st();
             }
             publish();
             if (issuer) issue<0>(s, sbase);
@@ -772,11 +785,7 @@ fwd_bf16_kernel(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__ 
 #pragma unroll
                     for (int i = 0; i < 8; i += 2) {
                         const int k = 8 * g + i;
-                        float du0 = ((inbits >> k) & 1u) ? d0_2 : d0_1;
-                        const float du1 = ((inbits >> (k + 1)) & 1u) ? d0_2 : d0_1;
-                        if (k == 0 && seq_start) du0 = d0_0;
-                        const float2 x = gelu_bf16out2(__fadd2_rn(
-                            make_float2(__uint_as_float(r[k]), __uint_as_float(r[k + 1])), make_float2(du0, du1)));
+                        const float2 x = gelu_bf16out2(make_float2(__uint_as_float(r[k]), __uint_as_float(r[k + 1])));
                         xv[i] = x.x;
                         xv[i + 1] = x.y;
                     }
