@@ -385,34 +385,37 @@ cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, vo
 // layer 1 / 2).  Stream s accumulates in TMEM columns 64 s .. 64 s + 63 (Z or
 // the output, then h~); the kernel owns all 512 columns, so its allocation
 // starts at column 0.
-__device__ __forceinline__ uint64_t adesc(uint32_t w, int kk) {
-    return sdesc(w + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
-}
+// Descriptors of the k-th K = 16 slice are the slice-0 descriptor plus the
+// slice's byte offset >> 4 in the start-address field (no carry: shared
+// addresses stay below 2^18 bytes).
+__device__ __forceinline__ uint64_t adesc0(uint32_t w) { return sdesc(w, 16, 1024); }
+__device__ __forceinline__ uint64_t aoff(int kk) { return (uint64_t)(((kk >> 2) * 16384 + (kk & 3) * 32) >> 4); }
+__device__ __forceinline__ uint64_t boff(int kk) { return (uint64_t)((kk * 1024) >> 4); }
 
 template <int WHAT>
 __device__ __forceinline__ void issue(int s, uint32_t sbase) {
     const uint32_t tX = sbase + OFF_TILES + (uint32_t)(2 * s) * kTileBytes;
-    const uint32_t tH = tX + kTileBytes;
+    const uint64_t bX = bdesc(tX), bH = bdesc(tX + kTileBytes);
     const uint32_t d = 64u * (uint32_t)s;
     if (WHAT == 0) {
         // accumulates onto D0 u, which the layer-0 scan stored in the columns
-        const uint32_t wC = sbase + OFF_W + SM_C0 * kMatBytes;
+        const uint64_t aC = adesc0(sbase + OFF_W + SM_C0 * kMatBytes);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_ss(d, adesc(wC, kk), bdesc(tH + kk * 1024), 1);
+        for (int kk = 0; kk < 8; ++kk) mma_ss(d, aC + aoff(kk), bH + boff(kk), 1);
     } else if (WHAT == 1 || WHAT == 3) {
         const uint32_t wz = kTmemWeightCol + (WHAT == 1 ? TM_WZ1 : TM_WZ2) * 64;
         const uint32_t wh = kTmemWeightCol + (WHAT == 1 ? TM_WH1 : TM_WH2) * 64;
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_ts(d, wz + kk * 8, bdesc(tX + kk * 1024), kk > 0);
+        for (int kk = 0; kk < 8; ++kk) mma_ts(d, wz + kk * 8, bX + boff(kk), kk > 0);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_ts(d + 32, wh + kk * 8, bdesc(tX + kk * 1024), kk > 0);
+        for (int kk = 0; kk < 8; ++kk) mma_ts(d + 32, wh + kk * 8, bX + boff(kk), kk > 0);
     } else {
-        const uint32_t wC = sbase + OFF_W + (WHAT == 2 ? SM_C1 : SM_C2) * kMatBytes;
-        const uint32_t wD = sbase + OFF_W + (WHAT == 2 ? SM_D1 : SM_D2) * kMatBytes;
+        const uint64_t aC = adesc0(sbase + OFF_W + (WHAT == 2 ? SM_C1 : SM_C2) * kMatBytes);
+        const uint64_t aD = adesc0(sbase + OFF_W + (WHAT == 2 ? SM_D1 : SM_D2) * kMatBytes);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_ss(d, adesc(wC, kk), bdesc(tH + kk * 1024), kk > 0);
+        for (int kk = 0; kk < 8; ++kk) mma_ss(d, aC + aoff(kk), bH + boff(kk), kk > 0);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_ss(d, adesc(wD, kk), bdesc(tX + kk * 1024), 1);
+        for (int kk = 0; kk < 8; ++kk) mma_ss(d, aD + aoff(kk), bX + boff(kk), 1);
     }
     mma_commit(sbase + OFF_MISC + 8 * (uint32_t)s);
 }
