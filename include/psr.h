@@ -343,8 +343,7 @@ int psr2d_sample(const psr_params *params, const float *uniforms, int64_t n, int
  * sum [P].  Rows of patches are recomputed from the forward's row
  * checkpoints and differentiated from the last row to the first, the
  * adjoint of each row's states reaching the row above through
- * W_h^T (the h_V columns).  FP32; hidden up to 128 (PSR_EUNSUPPORTED
- * above). */
+ * W_h^T (the h_V columns).  FP32; every hidden size psr2d_logpsi takes. */
 int psr2d_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
                const float *dout, float *dparams);
 
@@ -354,6 +353,19 @@ int psr2d_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_
  * the sample's stored row states. */
 int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
                        const psr_hamiltonian *hamiltonian, float *out, double *stats);
+
+/* c4v-symmetrised 2D model on an L x L lattice (Lx == Ly, else
+ * PSR_EINVAL): psi_sym(s) = sqrt(1/8 sum_g psi(g s)^2) over the 8
+ * operations of c4v (as psr_sym_logpsi, with the 2D model's psi), and its
+ * local energy E_loc(s) = diag(s) + sum_e c_e psi_sym(s'_e) / psi_sym(s).
+ * Every image of a connected configuration is a connected configuration
+ * of the sample's image and resumes from that image's stored row states.
+ * Requirements, arrays and errors as psr2d_logpsi / psr2d_local_energy;
+ * 8x the work of the unsymmetrised calls. */
+int psr2d_sym_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
+                     float *out);
+int psr2d_sym_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                           const psr_hamiltonian *hamiltonian, float *out, double *stats);
 
 /* ---------------------------------------------------------------------
  * The paper's deep 1D LRU ansatz (Sec. II.B Eq. lru; Sec. II.G 1D residual;
@@ -450,13 +462,18 @@ int psr_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, i
                  float *theta_out, uint8_t *spins_out, float *eloc_out, double *stats_out,
                  float *grad_out);
 
-/* One VMC step of the 2D patched minGRU on the device, as psr_vmc_step
- * without symmetrisation: exact samples from uniforms [n][Np] (Np patches
- * in path order, psr2d_sample), E_loc (psr2d_local_energy), the energy
- * gradient by psr2d_grad, Adam.  Same array rules as psr_vmc_step. */
-int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, const float *uniforms,
-                   int64_t n, const psr_adam *adam, float *theta_out, uint8_t *spins_out,
-                   float *eloc_out, double *stats_out, float *grad_out);
+/* One VMC step of the 2D patched minGRU on the device, as psr_vmc_step:
+ * exact samples from uniforms [n][Np] (Np patches in path order,
+ * psr2d_sample); with symmetrize = 1 each sample is replaced by its c4v
+ * image floor(8 sym_uniforms[i]) and E_loc and the gradient are those of
+ * psi_sym (psr2d_sym_local_energy; the gradient by psr2d_grad over the 8
+ * images with the images' weights); otherwise E_loc by psr2d_local_energy
+ * and the gradient by psr2d_grad; then Adam.  Same array rules as
+ * psr_vmc_step; symmetrize needs a square lattice. */
+int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, int32_t symmetrize,
+                   const float *uniforms, const float *sym_uniforms, int64_t n, const psr_adam *adam,
+                   float *theta_out, uint8_t *spins_out, float *eloc_out, double *stats_out,
+                   float *grad_out);
 
 /* One VMC step of the LRU ansatz on the device, as psr_vmc_step without
  * symmetrisation: exact samples from uniforms [n][N] (psr_lru_sample),

@@ -225,6 +225,26 @@ def grad_lru(theta, spins, cfg: ModelConfig, dout=None, out=None):
     return B.psr_lru_grad(p, spins, dout, out)
 
 
+def sym_logpsi2d(theta, spins, cfg: ModelConfig, L: int, out=None):
+    """c4v-symmetrised log psi of the 2D patched model on an L x L lattice."""
+    dev = _device_of(spins, theta)
+    if out is None:
+        out = torch.empty(spins.shape[0], dtype=torch.float32, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    return B.psr2d_sym_logpsi(p, spins, L, L, out)
+
+
+def sym_local_energy2d(theta, samples, cfg: ModelConfig, ham: B.psr_hamiltonian, out=None, stats=None):
+    dev = _device_of(samples, theta)
+    if out is None:
+        out = torch.empty(samples.shape[0], dtype=torch.float32, device=dev)
+    if stats is None:
+        stats = torch.empty(3, dtype=torch.float64, device=dev)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr2d_sym_local_energy(p, samples, ham, out, stats)
+    return out, stats
+
+
 def sym_logpsi(theta, spins, cfg: ModelConfig, L: int, out=None):
     """c4v-symmetrised log psi on an L x L lattice."""
     dev = _device_of(spins, theta)
@@ -280,8 +300,10 @@ def vmc_step(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: Ad
     return out
 
 
-def vmc_step2d(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: Adam, theta_out=None):
-    """One on-device VMC step of the 2D patched minGRU (uniforms [n, Np])."""
+def vmc_step2d(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: Adam, theta_out=None,
+               symmetrize=False, sym_uniforms=None):
+    """One on-device VMC step of the 2D patched minGRU (uniforms [n, Np]);
+    with symmetrize, of its c4v-symmetrised amplitude (sym_uniforms [n])."""
     n = uniforms.shape[0]
     dev = uniforms.device
     N = ham.Lx * ham.Ly
@@ -294,8 +316,8 @@ def vmc_step2d(theta, cfg: ModelConfig, ham: B.psr_hamiltonian, uniforms, adam: 
            "grad": torch.empty_like(theta)}
     adam.step += 1
     p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
-    B.psr2d_vmc_step(p, ham, uniforms, adam.state(), theta_out, out["spins"], out["eloc"], out["stats"],
-                     out["grad"])
+    B.psr2d_vmc_step(p, ham, symmetrize, uniforms, sym_uniforms, adam.state(), theta_out, out["spins"],
+                     out["eloc"], out["stats"], out["grad"])
     return out
 
 

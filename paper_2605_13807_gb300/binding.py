@@ -62,7 +62,8 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr2d_param_count", "psr2d_logpsi", "psr2d_local_energy", "psr_selftest_wait_timeout",
             "psr_lru_param_count", "psr_lru_logpsi", "psr_lru_local_energy", "psr_sym_logpsi",
             "psr_sym_local_energy", "psr_vmc_step", "psr2d_sample", "psr2d_grad", "psr2d_vmc_step",
-            "psr_lru_sample", "psr_lru_grad", "psr_lru_vmc_step")
+            "psr_lru_sample", "psr_lru_grad", "psr_lru_vmc_step", "psr2d_sym_logpsi",
+            "psr2d_sym_local_energy")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -118,8 +119,11 @@ def lib():
                                            i64, C.POINTER(psr_adam), vp, vp, vp, vp, vp]
                 L.psr2d_sample.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp, vp]
                 L.psr2d_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp, vp]
-                L.psr2d_vmc_step.argtypes = [C.POINTER(psr_params), C.POINTER(psr_hamiltonian), vp, i64,
-                                             C.POINTER(psr_adam), vp, vp, vp, vp, vp]
+                L.psr2d_vmc_step.argtypes = [C.POINTER(psr_params), C.POINTER(psr_hamiltonian), i32, vp, vp,
+                                             i64, C.POINTER(psr_adam), vp, vp, vp, vp, vp]
+                L.psr2d_sym_logpsi.argtypes = [C.POINTER(psr_params), vp, i64, i32, i32, vp]
+                L.psr2d_sym_local_energy.argtypes = [C.POINTER(psr_params), vp, i64,
+                                                     C.POINTER(psr_hamiltonian), vp, vp]
                 L.psr_lru_sample.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
                 L.psr_lru_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
                 L.psr_lru_vmc_step.argtypes = [C.POINTER(psr_params), C.POINTER(psr_hamiltonian), vp, i64,
@@ -403,13 +407,28 @@ def psr2d_grad(params, spins, Lx, Ly, dout, dparams):
     return dparams
 
 
-def psr2d_vmc_step(params, ham, uniforms, adam, theta_out, spins_out=None, eloc_out=None,
-                   stats_out=None, grad_out=None):
+def psr2d_vmc_step(params, ham, symmetrize, uniforms, sym_uniforms, adam, theta_out, spins_out=None,
+                   eloc_out=None, stats_out=None, grad_out=None):
     n = uniforms.shape[0]
-    _check(lib().psr2d_vmc_step(C.byref(params), C.byref(ham), _ptr(uniforms), int(n), C.byref(adam),
-                                _ptr(theta_out), _ptr(spins_out), _ptr(eloc_out), _ptr(stats_out),
-                                _ptr(grad_out)), "psr2d_vmc_step")
+    _check(lib().psr2d_vmc_step(C.byref(params), C.byref(ham), int(bool(symmetrize)), _ptr(uniforms),
+                                _ptr(sym_uniforms), int(n), C.byref(adam), _ptr(theta_out),
+                                _ptr(spins_out), _ptr(eloc_out), _ptr(stats_out), _ptr(grad_out)),
+           "psr2d_vmc_step")
     return theta_out
+
+
+def psr2d_sym_logpsi(params, spins, Lx, Ly, out):
+    n = spins.shape[0]
+    _check(lib().psr2d_sym_logpsi(C.byref(params), _ptr(spins), int(n), int(Lx), int(Ly), _ptr(out)),
+           "psr2d_sym_logpsi")
+    return out
+
+
+def psr2d_sym_local_energy(params, samples, ham, out, stats=None):
+    n = samples.shape[0]
+    _check(lib().psr2d_sym_local_energy(C.byref(params), _ptr(samples), int(n), C.byref(ham), _ptr(out),
+                                        _ptr(stats)), "psr2d_sym_local_energy")
+    return out
 
 
 def psr_lru_sample(params, uniforms, spins, logpsi=None):

@@ -169,7 +169,6 @@ int psr2d_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_
     int rc = check_params2d(params, n, Lx, Ly);
     if (rc != PSR_OK) return rc;
     if (!spins || !dparams) return PSR_EINVAL;
-    if (params->hidden > 128) return PSR_EUNSUPPORTED;
     psr_context *ctx = params->ctx;
     const int nL = params->n_layers, H = params->hidden, N = Lx * Ly, Py = Ly / 2;
     const int64_t P = param_count2d(nL, H);
@@ -365,6 +364,162 @@ int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t
         PSR_TRY(cudaMemcpyAsync(stats, stats_ws, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (!d_out || !d_s || !d_theta || !d_stats) return take_status(ctx);
     return PSR_OK;
+}
+
+// ------------------------------------------ c4v-symmetrised 2D patched model
+
+}  // extern "C"
+
+namespace {
+
+// Shared body of psr2d_sym_logpsi (ham == nullptr) and psr2d_sym_local_energy:
+// the 8 c4v images of every configuration in one forward launch (with row
+// checkpoints and per-patch log P when E_loc follows), the images of every
+// connected entry (sites g(p), g(q) flipped) resumed from their image
+// sample's checkpoints, one launch per image, then the log-sum-exp
+// combinations of the 8 images.
+int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t L,
+              const psr_hamiltonian *ham, float *out, double *stats) {
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers, H = params->hidden, N = L * L, Py = L / 2, Np = (L / 2) * Py;
+    const int64_t P = param_count2d(nL, H);
+    const F2Layout f = f2_layout(nL, H);
+    const bool eloc = ham != nullptr;
+    const int W = (int)words_per_row(N);
+    const int nb = eloc ? bond_count(L, L, ham->pbc) : 0;
+    const int64_t cap = eloc ? n * max_entries_per_sample(ham) : 0;
+    const size_t ckpt = fwd2d_checkpoint_floats(nL, H);
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
+               d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
+    float *theta_ws = nullptr, *out_ws = nullptr, *pk = nullptr, *lp8 = nullptr, *logp8 = nullptr,
+          *carries8 = nullptr, *delta8 = nullptr, *dsym = nullptr;
+    double *stats_ws = nullptr;
+    uint8_t *s_ws = nullptr, *imgs = nullptr;
+    uint64_t *bits = nullptr;
+    int32_t *ent8 = nullptr;
+    unsigned long long *counters = nullptr;
+    ConnBufs b{};
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
+        out_ws = c.get<float>(d_out ? 0 : n);
+        stats_ws = c.get<double>(d_stats ? 0 : 3);
+        pk = c.get<float>(f.total);
+        bits = c.get<uint64_t>((size_t)n * W);
+        imgs = c.get<uint8_t>((size_t)8 * n * N);
+        lp8 = c.get<float>((size_t)8 * n);
+        counters = c.get<unsigned long long>(9);
+        if (eloc) {
+            b.bonds = c.get<int32_t>(2 * (size_t)nb + 2);
+            b.counts = c.get<int64_t>(n);
+            b.offsets = c.get<int64_t>(n + 1);
+            b.diag = c.get<float>(n);
+            b.entries = c.get<int32_t>(3 * (size_t)cap);
+            ent8 = c.get<int32_t>((size_t)8 * 3 * cap);
+            logp8 = c.get<float>((size_t)8 * n * Np);
+            carries8 = c.get<float>((size_t)8 * n * Py * ckpt);
+            delta8 = c.get<float>((size_t)8 * cap);
+            dsym = c.get<float>(cap);
+        }
+    };
+    Carver sz;
+    carve(sz);
+    int rc = ensure_ws(ctx, sz.off);
+    if (rc != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(samples, s_ws, (size_t)n * N, d_s, st, &sp)) != PSR_OK) return rc;
+    float *o = d_out ? out : out_ws;
+    double *so = stats ? (d_stats ? stats : stats_ws) : nullptr;
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
+        PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));  // spin-byte check
+        PSR_TRY(launch_c4v_images(sp, n, L, imgs, st));
+        PSR_TRY(cudaMemsetAsync(counters, 0, 9 * sizeof(unsigned long long), st));
+    }
+    HamDev hd{};
+    if (eloc) {
+        StageScope sc(ctx, PSR_STAGE_GENERATOR);
+        if ((rc = enqueue_connected(ctx, ham, sp, n, b, hd)) != PSR_OK) return rc;
+        if (cap > 0) PSR_TRY(launch_c4v_entries(b.entries, b.offsets + n, cap, L, ent8, st));
+    }
+    Fwd2Jobs js{};
+    js.mode = 0;
+    js.g.Lx = L;
+    js.g.Ly = L;
+    js.g.u1 = params->u1_mask;
+    js.g.n_jobs = 8 * n;
+    js.g.spins = imgs;
+    js.g.out = lp8;
+    js.g.logp_out = logp8;
+    js.g.carries_out = carries8;
+    js.job_counter = counters;
+    js.status = ctx->status;
+    {
+        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+        PSR_TRY(launch_fwd2d_f32(js, pk, f, ctx->num_sms, st));
+    }
+    if (eloc && cap > 0) {
+        StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
+        for (int g = 0; g < 8; ++g) {
+            Fwd2Jobs jc = js;
+            jc.mode = 1;
+            jc.g.n_jobs = cap;
+            jc.g.n_jobs_dev = b.offsets + n;
+            jc.g.spins = imgs + (size_t)g * n * N;
+            jc.g.entries = ent8 + (size_t)g * 3 * cap;
+            jc.g.carries_in = carries8 + (size_t)g * n * Py * ckpt;
+            jc.g.logp_ref = logp8 + (size_t)g * n * Np;
+            jc.g.out = delta8 + (size_t)g * cap;
+            jc.g.logp_out = nullptr;
+            jc.g.carries_out = nullptr;
+            jc.job_counter = counters + 1 + g;
+            PSR_TRY(launch_fwd2d_f32(jc, pk, f, ctx->num_sms, st));
+        }
+        PSR_TRY(launch_sym_delta(b.entries, b.offsets + n, cap, lp8, n, delta8, dsym, st));
+    }
+    if (eloc) {
+        StageScope sc(ctx, PSR_STAGE_GATHER);
+        PSR_TRY(launch_eloc_gather(b.offsets, dsym, b.diag, hd.coeff, n, o, st));
+        if (so) PSR_TRY(launch_stats(o, n, so, st));
+    } else {
+        PSR_TRY(launch_sym_logpsi(lp8, n, o, st));
+    }
+    if (!d_out) PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (stats && !d_stats)
+        PSR_TRY(cudaMemcpyAsync(stats, stats_ws, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!d_out || !d_s || !d_theta || !d_stats) return take_status(ctx);
+    return PSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psr2d_sym_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
+                     float *out) {
+    if (Lx != Ly) return PSR_EINVAL;
+    int rc = check_params2d(params, n, Lx, Ly);
+    if (rc != PSR_OK) return rc;
+    if (!spins || !out || n > ((int64_t)1 << 28)) return PSR_EINVAL;
+    return sym2d_run(params, spins, n, Lx, nullptr, out, nullptr);
+}
+
+int psr2d_sym_local_energy(const psr_params *params, const uint8_t *samples, int64_t n,
+                           const psr_hamiltonian *ham, float *out, double *stats) {
+    int rc = check_ham(ham);
+    if (rc != PSR_OK) return rc;
+    if (ham->Lx != ham->Ly) return PSR_EINVAL;
+    if ((rc = check_params2d(params, n, ham->Lx, ham->Ly)) != PSR_OK) return rc;
+    if (!samples || !out || n > ((int64_t)1 << 28)) return PSR_EINVAL;
+    return sym2d_run(params, samples, n, ham->Lx, ham, out, stats);
 }
 
 // ------------------------------------------------------ deep 1D LRU model

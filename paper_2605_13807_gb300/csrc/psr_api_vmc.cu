@@ -325,12 +325,15 @@ int psr_vmc_step(const psr_params *params, const psr_hamiltonian *ham, int32_t s
     return PSR_OK;
 }
 
-int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *ham, const float *uniforms,
-                   int64_t n, const psr_adam *adam, float *theta_out, uint8_t *spins_out,
-                   float *eloc_out, double *stats_out, float *grad_out) {
+int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *ham, int32_t symmetrize,
+                   const float *uniforms, const float *sym_uniforms, int64_t n, const psr_adam *adam,
+                   float *theta_out, uint8_t *spins_out, float *eloc_out, double *stats_out,
+                   float *grad_out) {
     int rc = check_ham(ham);
     if (rc != PSR_OK) return rc;
     if (!params || !params->ctx || !params->theta) return PSR_EINVAL;
+    if (symmetrize != 0 && symmetrize != 1) return PSR_EINVAL;
+    if (symmetrize && (ham->Lx != ham->Ly || !sym_uniforms || n > ((int64_t)1 << 28))) return PSR_EINVAL;
     if (!uniforms || !adam || !adam->m || !adam->v || !theta_out || adam->step < 1 || n < 1)
         return PSR_EINVAL;
     if (!(adam->lr >= 0.0f) || !(adam->beta1 >= 0.0f && adam->beta1 < 1.0f) ||
@@ -339,21 +342,26 @@ int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *ham, const f
     const void *dev_args[] = {params->theta, uniforms, adam->m, adam->v, theta_out};
     for (const void *p : dev_args)
         if (!is_device_ptr(p)) return PSR_EINVAL;
-    if ((spins_out && !is_device_ptr(spins_out)) || (eloc_out && !is_device_ptr(eloc_out)) ||
-        (stats_out && !is_device_ptr(stats_out)) || (grad_out && !is_device_ptr(grad_out)))
+    if ((symmetrize && !is_device_ptr(sym_uniforms)) || (spins_out && !is_device_ptr(spins_out)) ||
+        (eloc_out && !is_device_ptr(eloc_out)) || (stats_out && !is_device_ptr(stats_out)) ||
+        (grad_out && !is_device_ptr(grad_out)))
         return PSR_EINVAL;
     psr_context *ctx = params->ctx;
     const int Lx = ham->Lx, Ly = ham->Ly, N = Lx * Ly;
+    const int n_img = symmetrize ? 8 : 1;
     int64_t P = 0;
     if ((rc = psr2d_param_count(params->n_layers, params->hidden, &P)) != PSR_OK) return rc;
-    uint8_t *spins = nullptr;
-    float *eloc = nullptr, *dout = nullptr, *grad = nullptr;
+    uint8_t *spins = nullptr, *spins_sym = nullptr, *imgs = nullptr;
+    float *eloc = nullptr, *lp8 = nullptr, *dout = nullptr, *grad = nullptr;
     double *stats = nullptr;
     auto carve = [&](Carver &c) {
-        spins = c.get<uint8_t>(spins_out ? 0 : (size_t)n * N);
+        spins = c.get<uint8_t>(spins_out && !symmetrize ? 0 : (size_t)n * N);
+        spins_sym = c.get<uint8_t>(symmetrize && !spins_out ? (size_t)n * N : 0);
+        imgs = c.get<uint8_t>(symmetrize ? (size_t)8 * n * N : 0);
         eloc = c.get<float>(eloc_out ? 0 : n);
         stats = c.get<double>(stats_out ? 0 : 3);
-        dout = c.get<float>(n);
+        lp8 = c.get<float>(symmetrize ? (size_t)8 * n : 0);
+        dout = c.get<float>((size_t)n_img * n);
         grad = c.get<float>(grad_out ? 0 : P);
     };
     Carver sz;
@@ -362,15 +370,33 @@ int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *ham, const f
     Carver cv;
     cv.base = static_cast<char *>(ctx->ws2);
     carve(cv);
-    if (spins_out) spins = spins_out;
+    if (spins_out && !symmetrize) spins = spins_out;
+    if (symmetrize && spins_out) spins_sym = spins_out;
     if (eloc_out) eloc = eloc_out;
     if (stats_out) stats = stats_out;
     if (grad_out) grad = grad_out;
     cudaStream_t st = ctx->stream;
+    // 1. exact samples of |psi|^2 (then a uniformly drawn c4v image of each)
     if ((rc = psr2d_sample(params, uniforms, n, Lx, Ly, spins, nullptr)) != PSR_OK) return rc;
-    if ((rc = psr2d_local_energy(params, spins, n, ham, eloc, stats)) != PSR_OK) return rc;
-    PSR_TRY(launch_vmc_dout(eloc, stats, nullptr, n, 1, dout, st));
-    if ((rc = psr2d_grad(params, spins, n, Lx, Ly, dout, grad)) != PSR_OK) return rc;
+    const uint8_t *used = spins;
+    if (symmetrize) {
+        PSR_TRY(launch_c4v_pick(spins, sym_uniforms, n, Lx, spins_sym, st));
+        used = spins_sym;
+    }
+    // 2. local energies and their FP64 statistics
+    rc = symmetrize ? psr2d_sym_local_energy(params, used, n, ham, eloc, stats)
+                    : psr2d_local_energy(params, used, n, ham, eloc, stats);
+    if (rc != PSR_OK) return rc;
+    // 3. centred energy-gradient weights (per image when symmetrised)
+    if (symmetrize) {
+        PSR_TRY(launch_c4v_images(used, n, Lx, imgs, st));
+        if ((rc = psr2d_logpsi(params, imgs, 8 * n, Lx, Ly, lp8)) != PSR_OK) return rc;
+    }
+    PSR_TRY(launch_vmc_dout(eloc, stats, lp8, n, n_img, dout, st));
+    // 4. gradient sum_i dout_i d log psi(s_i) / d theta
+    if ((rc = psr2d_grad(params, symmetrize ? imgs : used, n_img * n, Lx, Ly, dout, grad)) != PSR_OK)
+        return rc;
+    // 5. Adam update
     PSR_TRY(launch_adam(params->theta, grad, P, adam->lr, adam->beta1, adam->beta2, adam->eps,
                         adam->step, adam->m, adam->v, theta_out, st));
     return PSR_OK;

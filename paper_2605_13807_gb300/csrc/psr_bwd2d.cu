@@ -46,6 +46,8 @@ T2Layout t2_layout(int nL, int H) {
     return t;
 }
 
+size_t bwd2d_smem_bytes(int nL, int H);
+
 namespace {
 
 constexpr int kR = 32;       // patches per row (max)
@@ -63,13 +65,16 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                                                   const float *__restrict__ dout,
                                                   float *__restrict__ grad_rows,
                                                   float *__restrict__ scratch) {
+    // Above hidden 128 the previous row's states are read in place from the
+    // forward's row checkpoint in HBM (through L1) instead of a shared copy.
+    constexpr bool kHvG = H > 128;
     extern __shared__ __align__(16) float smem[];
     const int nL = f.nL;
     const int Px = Lx >> 1, Py = Ly >> 1, N = Lx * Ly;
     float *xs = smem;                 // [H][kLD] layer input / output
     float *hs = xs + H * kLD;         // [H][kLD] states of the current layer
-    float *hv = hs + H * kLD;         // [nL][H][kLD] previous row's states (this row's order)
-    float *g1 = hv + nL * H * kLD;    // [H][kLD] adjoint tile (gy, then dz)
+    float *hv_s = hs + H * kLD;       // [nL][H][kLD] previous row's states (this row's order)
+    float *g1 = kHvG ? hv_s : hv_s + nL * H * kLD;  // [H][kLD] adjoint tile (gy, then dz)
     float *g2 = g1 + H * kLD;         // [H][kLD] adjoint tile (dh~)
     float *lg = g2 + H * kLD;         // [16][kLD] logits, then their adjoints
     __shared__ int s_v[kR], s_vprev[kR];
@@ -97,9 +102,10 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
 
         for (int pj = Py - 1; pj >= 0; --pj) {
             // ------------------------------------------------ recompute the row
-            {
-                const float *src = carries + ((size_t)smp * Py + pj) * ckpt;
-                for (size_t i = j; i < ckpt; i += H) hv[i] = src[i];
+            const float *hv = carries + ((size_t)smp * Py + pj) * ckpt;
+            if (!kHvG) {
+                for (size_t i = j; i < ckpt; i += H) hv_s[i] = hv[i];
+                hv = hv_s;
             }
             if (j < Px) {
                 const int pi = (pj & 1) ? Px - 1 - j : j;
@@ -470,7 +476,7 @@ cudaError_t launch_bwd2d_h(const uint8_t *spins, int64_t n, int Lx, int Ly, int 
                            const T2Layout &tl, const float *packed, const F2Layout &f,
                            const float *carries, const float *dout, float *grad_rows, int grid,
                            float *scratch, cudaStream_t st) {
-    const size_t smem = ((size_t)(4 + f.nL) * H * kLD + 16 * kLD) * sizeof(float);
+    const size_t smem = bwd2d_smem_bytes(f.nL, H);
     cudaError_t e = cudaFuncSetAttribute(bwd2d_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -485,7 +491,9 @@ size_t bwd2d_scratch_floats_per_cta(int nL, int H) {
     return (size_t)nL * TQ_N * kR * H + 2 * (size_t)nL * H * kLD;
 }
 
-size_t bwd2d_smem_bytes(int nL, int H) { return ((size_t)(4 + nL) * H * kLD + 16 * kLD) * sizeof(float); }
+size_t bwd2d_smem_bytes(int nL, int H) {
+    return ((size_t)(4 + (H > 128 ? 0 : nL)) * H * kLD + 16 * kLD) * sizeof(float);
+}
 
 cudaError_t launch_bwd2d(const uint8_t *spins, int64_t n, int Lx, int Ly, int u1, const float *theta,
                          const T2Layout &tl, const float *packed, const F2Layout &f, const float *carries,
@@ -495,6 +503,7 @@ cudaError_t launch_bwd2d(const uint8_t *spins, int64_t n, int Lx, int Ly, int u1
         case 32: return launch_bwd2d_h<32>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, stream);
         case 64: return launch_bwd2d_h<64>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, stream);
         case 128: return launch_bwd2d_h<128>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, stream);
+        case 256: return launch_bwd2d_h<256>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -68,6 +68,10 @@ def test_null_arguments_are_rejected_without_touching_the_device(libpsr):
     assert libpsr.psr_lru_sample(None, None, 1, 4, None, None) == binding.PSR_EINVAL
     assert libpsr.psr_lru_grad(None, None, 1, 4, None, None) == binding.PSR_EINVAL
     assert libpsr.psr_lru_vmc_step(None, None, None, 1, None, None, None, None, None, None) == binding.PSR_EINVAL
+    assert libpsr.psr2d_sym_logpsi(None, None, 1, 4, 4, None) == binding.PSR_EINVAL
+    assert libpsr.psr2d_sym_local_energy(None, None, 1, None, None, None) == binding.PSR_EINVAL
+    assert libpsr.psr2d_vmc_step(None, None, 0, None, None, 1, None, None, None, None, None,
+                                 None) == binding.PSR_EINVAL
     assert libpsr.psr_sample(None, None, 1, 4, None, None) == binding.PSR_EINVAL
     assert libpsr.psr_scan(None, None, None, None, 1, 4, 4, None) == binding.PSR_EINVAL
     assert libpsr.psr_selftest_wait_timeout(None, None) == binding.PSR_EINVAL
