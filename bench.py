@@ -546,6 +546,48 @@ def vmc_leg(dev, L=10, n=1024, reps=3):
     return res
 
 
+# per-step wall times of the paper's 2D runs (Table VI, 1x A100 80GB, 3
+# layers, d_h = 256, 2x2 patches, c4v, 200 samples): context, not a target
+PAPER_2D_STEP_S = {10: 0.5, 20: 8.2}
+
+
+def paper2d_leg(dev, sizes=(10, 20), n=200, reps=2):
+    """One on-device VMC step of the 2D patched minGRU at the paper's 2D
+    configuration (3 layers, d_h = 256, 2x2 patches, c4v symmetrisation,
+    200 samples, Heisenberg OBC with zero magnetisation): exact sampling,
+    symmetrised E_loc (8 images), the gradient over the 8 images, Adam;
+    FP32 CUDA cores."""
+    import torch
+
+    from paper_2605_13807_gb300 import api, binding as B, inputs
+    H = 256
+    cfg = api.ModelConfig(N_LAYERS, H, True, "fp32")
+    res = {"model": "2D patched minGRU, c4v-symmetrised VMC step", "hidden": H, "layers": N_LAYERS,
+           "samples": n, "precision": "FP32", "paper_step_s_A100": {}}
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    for L in sizes:
+        ham = B.make_hamiltonian("heisenberg", L, L, False, True, 1.0, 0.0)
+        th = torch.from_numpy(inputs.glorot_params2d(N_LAYERS, H, seed=0)).to(dev)
+        u = torch.rand((n, (L // 2) ** 2), generator=g, device=dev)
+        us = torch.rand(n, generator=g, device=dev)
+        adam = api.Adam(th.numel(), dev, lr=1e-3)
+        out = api.vmc_step2d(th, cfg, ham, u, adam, theta_out=th, symmetrize=True, sym_uniforms=us)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = api.vmc_step2d(th, cfg, ham, u, adam, theta_out=th, symmetrize=True, sym_uniforms=us)
+        e1.record()
+        e1.synchronize()
+        res[f"{L}x{L}"] = {"ms_per_step": e0.elapsed_time(e1) / reps,
+                           "energy_per_site": float(out["stats"][0].item()) / (L * L)}
+        if L in PAPER_2D_STEP_S:
+            res["paper_step_s_A100"][f"{L}x{L}"] = PAPER_2D_STEP_S[L]
+    return res
+
+
 def run_scan_only(args):
     import torch
 
@@ -718,6 +760,7 @@ def run_mine(args):
         line["lru"] = lru_leg(dev)
     if not args.no_vmc and rank == 0:
         line["vmc_step"] = vmc_leg(dev)
+        line["paper2d_vmc_step"] = paper2d_leg(dev)
 
     # end to end through the C ABI with host buffers
     if not args.no_e2e:

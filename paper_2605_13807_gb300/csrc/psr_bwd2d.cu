@@ -56,7 +56,9 @@ enum { TQ_U = 0, TQ_Z = 1, TQ_C = 2, TQ_H = 3, TQ_Y = 4, TQ_N = 5 };
 
 __device__ __forceinline__ int sp2(int Lx, int i, int j) { return j * Lx + ((j & 1) ? Lx - 1 - i : i); }
 
-template <int H>
+// R: patches per row held in registers (8, 16 or 32 >= Lx / 2); the tape and
+// the shared rows keep the kR-wide layout.
+template <int H, int R>
 __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ spins, int64_t n,
                                                   int Lx, int Ly, int u1,
                                                   const float *__restrict__ theta, T2Layout tl,
@@ -124,13 +126,13 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 s_up = up;
             }
             __syncthreads();
-            float hl[kR];
+            float hl[R];
             {   // layer 0
                 const float *WzT = pk + f.WzT[0], *WhxT = pk + f.WhxT[0], *DT = pk + f.DT[0];
                 const float bz = pk[f.bz[0] + j], bh = pk[f.bh[0] + j];
-                float z[kR], c[kR], y[kR];
+                float z[R], c[R], y[R];
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     const int kk = k < Px ? k : Px - 1;
                     const int pi = (pj & 1) ? Px - 1 - kk : kk;
                     const int vh = kk > 0 ? s_v[kk - 1] : -1;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                         const float w = Wv[m * H + j];
                         const float4 *sv = reinterpret_cast<const float4 *>(hv + m * kLD);
 #pragma unroll
-                        for (int k4 = 0; k4 < kR / 4; ++k4) {
+                        for (int k4 = 0; k4 < R / 4; ++k4) {
                             const float4 v = sv[k4];
                             c[4 * k4] += w * v.x; c[4 * k4 + 1] += w * v.y;
                             c[4 * k4 + 2] += w * v.z; c[4 * k4 + 3] += w * v.w;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 }
                 float h = 0.0f;
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     const float a = sigmoid_f(z[k]);
                     h = a * h + (1.0f - a) * c[k];
                     hl[k] = h;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 }
                 float4 *dh = reinterpret_cast<float4 *>(hs + j * kLD);
 #pragma unroll
-                for (int k4 = 0; k4 < kR / 4; ++k4)
+                for (int k4 = 0; k4 < R / 4; ++k4)
                     dh[k4] = make_float4(hl[4 * k4], hl[4 * k4 + 1], hl[4 * k4 + 2], hl[4 * k4 + 3]);
                 __syncthreads();
                 const float *Ct = pk + f.CT[0];
@@ -174,14 +176,14 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     const float w = Ct[m * H + j];
                     const float4 *sh = reinterpret_cast<const float4 *>(hs + m * kLD);
 #pragma unroll
-                    for (int k4 = 0; k4 < kR / 4; ++k4) {
+                    for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 v = sh[k4];
                         y[4 * k4] += w * v.x; y[4 * k4 + 1] += w * v.y;
                         y[4 * k4 + 2] += w * v.z; y[4 * k4 + 3] += w * v.w;
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     T(0, TQ_Y, k)[j] = y[k];
                     xs[j * kLD + k] = gelu_f(y[k]);
                 }
@@ -190,10 +192,10 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
             for (int l = 1; l < nL; ++l) {
                 const float *WzT = pk + f.WzT[l], *WhxT = pk + f.WhxT[l], *Wv = pk + f.WhvT[l];
                 const float *hvl = hv + (size_t)l * H * kLD;
-                float z[kR], c[kR];
+                float z[R], c[R];
                 const float bz = pk[f.bz[l] + j], bh = pk[f.bh[l] + j];
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     z[k] = bz;
                     c[k] = bh;
                     T(l, TQ_U, k)[j] = xs[j * kLD + k];
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     const float4 *sx = reinterpret_cast<const float4 *>(xs + m * kLD);
                     const float4 *sv = reinterpret_cast<const float4 *>(hvl + m * kLD);
 #pragma unroll
-                    for (int k4 = 0; k4 < kR / 4; ++k4) {
+                    for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 x = sx[k4], v = sv[k4];
                         z[4 * k4] += wz * x.x; z[4 * k4 + 1] += wz * x.y;
                         z[4 * k4 + 2] += wz * x.z; z[4 * k4 + 3] += wz * x.w;
@@ -212,10 +214,10 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                         c[4 * k4 + 2] += wh * x.z + wv * v.z; c[4 * k4 + 3] += wh * x.w + wv * v.w;
                     }
                 }
-                float hn[kR];
+                float hn[R];
                 float h = 0.0f;
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     const float a = sigmoid_f(z[k]);
                     h = a * h + (1.0f - a) * c[k];
                     hn[k] = h;
@@ -226,12 +228,12 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 __syncthreads();
                 float4 *dh = reinterpret_cast<float4 *>(hs + j * kLD);
 #pragma unroll
-                for (int k4 = 0; k4 < kR / 4; ++k4)
+                for (int k4 = 0; k4 < R / 4; ++k4)
                     dh[k4] = make_float4(hn[4 * k4], hn[4 * k4 + 1], hn[4 * k4 + 2], hn[4 * k4 + 3]);
                 __syncthreads();
-                float y[kR];
+                float y[R];
 #pragma unroll
-                for (int k = 0; k < kR; ++k) y[k] = (l >= 2) ? hl[k] : 0.0f;
+                for (int k = 0; k < R; ++k) y[k] = (l >= 2) ? hl[k] : 0.0f;
                 const float *Ct = pk + f.CT[l], *DT = pk + f.DT[l];
 #pragma unroll 2
                 for (int m = 0; m < H; ++m) {
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     const float4 *sh = reinterpret_cast<const float4 *>(hs + m * kLD);
                     const float4 *sx = reinterpret_cast<const float4 *>(xs + m * kLD);
 #pragma unroll
-                    for (int k4 = 0; k4 < kR / 4; ++k4) {
+                    for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 a = sh[k4], b = sx[k4];
                         y[4 * k4] += wc * a.x + wd * b.x; y[4 * k4 + 1] += wc * a.y + wd * b.y;
                         y[4 * k4 + 2] += wc * a.z + wd * b.z; y[4 * k4 + 3] += wc * a.w + wd * b.w;
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 }
                 __syncthreads();
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     T(l, TQ_Y, k)[j] = y[k];
                     xs[j * kLD + k] = gelu_f(y[k]);
                     hl[k] = hn[k];
@@ -294,15 +296,15 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
             for (int i = j; i < 16 * kLD; i += H)
                 if ((i % kLD) >= Px) lg[i] = 0.0f;
             __syncthreads();
-            float gx[kR];
+            float gx[R];
             {
 #pragma unroll
-                for (int k = 0; k < kR; ++k) gx[k] = 0.0f;
+                for (int k = 0; k < R; ++k) gx[k] = 0.0f;
                 for (int o = 0; o < 16; ++o) {
                     const float w = theta[tl.Wo + o * H + j];
                     float gw = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < kR; ++k) {
+                    for (int k = 0; k < R; ++k) {
                         const float g = lg[o * kLD + k];
                         gx[k] += w * g;
                         gw += g * xs[j * kLD + k];
@@ -317,23 +319,23 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
             }
 
             // ------------------------------------------------ layers, top down
-            float gy_up[kR];
+            float gy_up[R];
 #pragma unroll
-            for (int k = 0; k < kR; ++k) gy_up[k] = 0.0f;
+            for (int k = 0; k < R; ++k) gy_up[k] = 0.0f;
             float *gv_in = gvb[cur], *gv_out = gvb[cur ^ 1];
             for (int l = nL - 1; l >= 0; --l) {
                 const int din = l == 0 ? 32 : H;
-                float gy[kR];
+                float gy[R];
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     gy[k] = k < Px ? gx[k] * gelu_grad_f(T(l, TQ_Y, k)[j]) : 0.0f;
                     g1[j * kLD + k] = gy[k];
                 }
                 __syncthreads();
                 // unit j as the input unit m: C^T gy, D^T gy, dC, dD
-                float ghd[kR], gud[kR], hk[kR], uk[kR];
+                float ghd[R], gud[R], hk[R], uk[R];
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     hk[k] = T(l, TQ_H, k)[j];
                     uk[k] = (l >= 1) ? T(l, TQ_U, k)[j] : 0.0f;
                     ghd[k] = (l + 1 < nL && l + 1 >= 2 ? gy_up[k] : 0.0f) +
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                         const float dij = (l >= 1) ? Dw[(int64_t)i * H + j] : 0.0f;
                         float ac = 0.0f, ad = 0.0f;
 #pragma unroll
-                        for (int k = 0; k < kR; ++k) {
+                        for (int k = 0; k < R; ++k) {
                             const float g = g1[i * kLD + k];
                             ghd[k] += cij * g;
                             gud[k] += dij * g;
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 {
                     float lam = 0.0f, an = 0.0f, sz = 0.0f, sc = 0.0f;
 #pragma unroll
-                    for (int k = kR - 1; k >= 0; --k) {
+                    for (int k = R - 1; k >= 0; --k) {
                         float dz = 0.0f, dc = 0.0f;
                         if (k < Px) {
                             lam = ghd[k] + an * lam;
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 }
                 __syncthreads();  // every read of g1 (gy) is done
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
+                for (int k = 0; k < R; ++k) {
                     g1[j * kLD + k] = ghd[k];  // dz
                     g2[j * kLD + k] = hk[k];   // dh~
                 }
@@ -402,9 +404,9 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     const float *Wzw = theta + tl.Wz[l];
                     const float *Whw = theta + tl.Wh[l];
                     const float *hvl = hv + (size_t)l * H * kLD;
-                    float gn[kR], gvo[kR];
+                    float gn[R], gvo[R];
 #pragma unroll
-                    for (int k = 0; k < kR; ++k) {
+                    for (int k = 0; k < R; ++k) {
                         gn[k] = gud[k];
                         gvo[k] = 0.0f;
                     }
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                         const float wv = Whw[(int64_t)i * (din + H) + din + j];
                         float az = 0.0f, ah = 0.0f, avv = 0.0f;
 #pragma unroll
-                        for (int k = 0; k < kR; ++k) {
+                        for (int k = 0; k < R; ++k) {
                             const float dz = g1[i * kLD + k], dc = g2[i * kLD + k];
                             gn[k] += wz * dz + wh * dc;
                             gvo[k] += wv * dc;
@@ -444,10 +446,10 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     }
                     // adjoint into the row above (path order of that row: reversed)
 #pragma unroll
-                    for (int k = 0; k < kR; ++k)
+                    for (int k = 0; k < R; ++k)
                         if (k < Px) gv_out[((size_t)l * H + j) * kLD + (Px - 1 - k)] = gvo[k];
 #pragma unroll
-                    for (int k = 0; k < kR; ++k) {
+                    for (int k = 0; k < R; ++k) {
                         gx[k] = gn[k];
                         gy_up[k] = gy[k];
                     }
@@ -471,18 +473,34 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
     }
 }
 
+template <int H, int R>
+cudaError_t launch_bwd2d_hr(const uint8_t *spins, int64_t n, int Lx, int Ly, int u1, const float *theta,
+                           const T2Layout &tl, const float *packed, const F2Layout &f,
+                           const float *carries, const float *dout, float *grad_rows, int grid,
+                           float *scratch, cudaStream_t st) {
+    const size_t smem = bwd2d_smem_bytes(f.nL, H);
+    cudaError_t e = cudaFuncSetAttribute(bwd2d_kernel<H, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    bwd2d_kernel<H, R><<<grid, H, smem, st>>>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout,
+                                            grad_rows, scratch);
+    return cudaGetLastError();
+}
+
 template <int H>
 cudaError_t launch_bwd2d_h(const uint8_t *spins, int64_t n, int Lx, int Ly, int u1, const float *theta,
                            const T2Layout &tl, const float *packed, const F2Layout &f,
                            const float *carries, const float *dout, float *grad_rows, int grid,
                            float *scratch, cudaStream_t st) {
-    const size_t smem = bwd2d_smem_bytes(f.nL, H);
-    cudaError_t e = cudaFuncSetAttribute(bwd2d_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    bwd2d_kernel<H><<<grid, H, smem, st>>>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout,
-                                            grad_rows, scratch);
-    return cudaGetLastError();
+    const int Px = Lx / 2;
+    if (Px <= 8)
+        return launch_bwd2d_hr<H, 8>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid,
+                                     scratch, st);
+    if (Px <= 16)
+        return launch_bwd2d_hr<H, 16>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows,
+                                      grid, scratch, st);
+    return launch_bwd2d_hr<H, 32>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid,
+                                  scratch, st);
 }
 
 }  // namespace

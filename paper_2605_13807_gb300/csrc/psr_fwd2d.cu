@@ -113,7 +113,9 @@ __device__ __forceinline__ int spin_at(const uint8_t *s, int Lx, int i, int j, i
     return (int)(s[pos] & 1u) ^ (pos == p) ^ (pos == q);
 }
 
-template <int H>
+// R: patches per row held in registers (8, 16 or 32 >= Lx / 2); shared rows
+// and checkpoints keep the kRow-wide layout.
+template <int H, int R>
 __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fwd2Jobs jb,
                                                       const float *__restrict__ pk, F2Layout f) {
     extern __shared__ __align__(16) float smem[];
@@ -191,14 +193,14 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
             }
             __syncthreads();
 
-            float hl[kRow];  // this unit's states of the layer below (residual source)
+            float hl[R];  // this unit's states of the layer below (residual source)
             // ---------------- layer 0: inputs onehot(v_H), onehot(v_V)
             {
                 const float *WzT = pk + f.WzT[0], *WhxT = pk + f.WhxT[0], *DT = pk + f.DT[0];
                 const float bz = pk[f.bz[0] + j], bh = pk[f.bh[0] + j];
-                float z[kRow], c[kRow], y[kRow];
+                float z[R], c[R], y[R];
 #pragma unroll
-                for (int k = 0; k < kRow; ++k) {
+                for (int k = 0; k < R; ++k) {
                     const int kk = k < Px ? k : Px - 1;
                     const int pi = (pj & 1) ? Px - 1 - kk : kk;
                     const int vh = kk > 0 ? s_v[kk - 1] : -1;
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                         const float w = Wv[m * H + j];
                         const float4 *src = reinterpret_cast<const float4 *>(hv0 + m * kLD);
 #pragma unroll
-                        for (int k4 = 0; k4 < kRow / 4; ++k4) {
+                        for (int k4 = 0; k4 < R / 4; ++k4) {
                             const float4 v = src[k4];
                             c[4 * k4] += w * v.x; c[4 * k4 + 1] += w * v.y;
                             c[4 * k4 + 2] += w * v.z; c[4 * k4 + 3] += w * v.w;
@@ -224,14 +226,14 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                 }
                 float h = 0.0f;  // the row starts from h_H = 0
 #pragma unroll
-                for (int k = 0; k < kRow; ++k) {
+                for (int k = 0; k < R; ++k) {
                     const float a = sigmoid_f(z[k]);
                     h = a * h + (1.0f - a) * c[k];
                     hl[k] = h;
                 }
                 float4 *dst = reinterpret_cast<float4 *>(hs + j * kLD);
 #pragma unroll
-                for (int k4 = 0; k4 < kRow / 4; ++k4)
+                for (int k4 = 0; k4 < R / 4; ++k4)
                     dst[k4] = make_float4(hl[4 * k4], hl[4 * k4 + 1], hl[4 * k4 + 2], hl[4 * k4 + 3]);
                 __syncthreads();  // all reads of hv[0] and writes of hs done
                 const float *Ct = pk + f.CT[0];
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                     const float w = Ct[m * H + j];
                     const float4 *src = reinterpret_cast<const float4 *>(hs + m * kLD);
 #pragma unroll
-                    for (int k4 = 0; k4 < kRow / 4; ++k4) {
+                    for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 v = src[k4];
                         y[4 * k4] += w * v.x; y[4 * k4 + 1] += w * v.y;
                         y[4 * k4 + 2] += w * v.z; y[4 * k4 + 3] += w * v.w;
@@ -248,11 +250,11 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                 }
                 float4 *xd = reinterpret_cast<float4 *>(xs + j * kLD);
 #pragma unroll
-                for (int k4 = 0; k4 < kRow / 4; ++k4)
+                for (int k4 = 0; k4 < R / 4; ++k4)
                     xd[k4] = make_float4(gelu_f(y[4 * k4]), gelu_f(y[4 * k4 + 1]), gelu_f(y[4 * k4 + 2]),
                                          gelu_f(y[4 * k4 + 3]));
 #pragma unroll
-                for (int k = 0; k < kRow; ++k)
+                for (int k = 0; k < R; ++k)
                     if (k < Px) hv[j * kLD + (Px - 1 - k)] = hl[k];
                 __syncthreads();
             }
@@ -260,10 +262,10 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
             for (int l = 1; l < nL; ++l) {
                 const float *WzT = pk + f.WzT[l], *WhxT = pk + f.WhxT[l], *Wv = pk + f.WhvT[l];
                 float *hvl = hv + (size_t)l * H * kLD;
-                float z[kRow], c[kRow];
+                float z[R], c[R];
                 const float bz = pk[f.bz[l] + j], bh = pk[f.bh[l] + j];
 #pragma unroll
-                for (int k = 0; k < kRow; ++k) {
+                for (int k = 0; k < R; ++k) {
                     z[k] = bz;
                     c[k] = bh;
                 }
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                     const float4 *sx = reinterpret_cast<const float4 *>(xs + m * kLD);
                     const float4 *sv = reinterpret_cast<const float4 *>(hvl + m * kLD);
 #pragma unroll
-                    for (int k4 = 0; k4 < kRow / 4; ++k4) {
+                    for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 x = sx[k4], v = sv[k4];
                         z[4 * k4] += wz * x.x; z[4 * k4 + 1] += wz * x.y;
                         z[4 * k4 + 2] += wz * x.z; z[4 * k4 + 3] += wz * x.w;
@@ -281,11 +283,11 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                         c[4 * k4 + 2] += wh * x.z + wv * v.z; c[4 * k4 + 3] += wh * x.w + wv * v.w;
                     }
                 }
-                float hn[kRow];
+                float hn[R];
                 {
                     float h = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < kRow; ++k) {
+                    for (int k = 0; k < R; ++k) {
                         const float a = sigmoid_f(z[k]);
                         h = a * h + (1.0f - a) * c[k];
                         hn[k] = h;
@@ -294,15 +296,15 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                 __syncthreads();  // every read of hs (previous layer) and hv[l] is done
                 float4 *dst = reinterpret_cast<float4 *>(hs + j * kLD);
 #pragma unroll
-                for (int k4 = 0; k4 < kRow / 4; ++k4)
+                for (int k4 = 0; k4 < R / 4; ++k4)
                     dst[k4] = make_float4(hn[4 * k4], hn[4 * k4 + 1], hn[4 * k4 + 2], hn[4 * k4 + 3]);
 #pragma unroll
-                for (int k = 0; k < kRow; ++k)
+                for (int k = 0; k < R; ++k)
                     if (k < Px) hvl[j * kLD + (Px - 1 - k)] = hn[k];
                 __syncthreads();
-                float y[kRow];
+                float y[R];
 #pragma unroll
-                for (int k = 0; k < kRow; ++k) y[k] = (l >= 2) ? hl[k] : 0.0f;
+                for (int k = 0; k < R; ++k) y[k] = (l >= 2) ? hl[k] : 0.0f;
                 const float *Ct = pk + f.CT[l], *DT = pk + f.DT[l];
 #pragma unroll 2
                 for (int m = 0; m < H; ++m) {
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                     const float4 *sh = reinterpret_cast<const float4 *>(hs + m * kLD);
                     const float4 *sx = reinterpret_cast<const float4 *>(xs + m * kLD);
 #pragma unroll
-                    for (int k4 = 0; k4 < kRow / 4; ++k4) {
+                    for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 a = sh[k4], b = sx[k4];
                         y[4 * k4] += wc * a.x + wd * b.x; y[4 * k4 + 1] += wc * a.y + wd * b.y;
                         y[4 * k4 + 2] += wc * a.z + wd * b.z; y[4 * k4 + 3] += wc * a.w + wd * b.w;
@@ -319,11 +321,11 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                 __syncthreads();  // every read of xs done
                 float4 *xd = reinterpret_cast<float4 *>(xs + j * kLD);
 #pragma unroll
-                for (int k4 = 0; k4 < kRow / 4; ++k4)
+                for (int k4 = 0; k4 < R / 4; ++k4)
                     xd[k4] = make_float4(gelu_f(y[4 * k4]), gelu_f(y[4 * k4 + 1]), gelu_f(y[4 * k4 + 2]),
                                          gelu_f(y[4 * k4 + 3]));
 #pragma unroll
-                for (int k = 0; k < kRow; ++k) hl[k] = hn[k];
+                for (int k = 0; k < R; ++k) hl[k] = hn[k];
                 __syncthreads();
             }
             // ---------------- readout: 16 logits per patch, masked softmax
@@ -387,22 +389,31 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
     }
 }
 
-template <int H>
-cudaError_t launch_fwd2d_h(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f, int num_sms,
-                           cudaStream_t stream) {
+template <int H, int R>
+cudaError_t launch_fwd2d_hr(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f, int num_sms,
+                            cudaStream_t stream) {
     const size_t smem = ((size_t)(2 + f.nL) * H * kLD + 16 * kLD) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fwd2d_f32_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fwd2d_f32_kernel<H, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd2d_f32_kernel<H>, H, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd2d_f32_kernel<H, R>, H, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (jobs.g.n_jobs < grid) grid = jobs.g.n_jobs;
     if (grid < 1) grid = 1;
-    fwd2d_f32_kernel<H><<<(int)grid, H, smem, stream>>>(jobs, packed, f);
+    fwd2d_f32_kernel<H, R><<<(int)grid, H, smem, stream>>>(jobs, packed, f);
     return cudaGetLastError();
+}
+
+template <int H>
+cudaError_t launch_fwd2d_h(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f, int num_sms,
+                           cudaStream_t stream) {
+    const int Px = jobs.g.Lx / 2;
+    if (Px <= 8) return launch_fwd2d_hr<H, 8>(jobs, packed, f, num_sms, stream);
+    if (Px <= 16) return launch_fwd2d_hr<H, 16>(jobs, packed, f, num_sms, stream);
+    return launch_fwd2d_hr<H, 32>(jobs, packed, f, num_sms, stream);
 }
 
 }  // namespace

@@ -38,7 +38,8 @@ def _spins(seed, n, Lx, Ly, u1):
 @pytest.mark.parametrize("Lx,Ly,H,nL,u1", [(4, 4, 32, 3, False), (6, 4, 64, 2, True),
                                            (10, 10, 128, 3, True), (8, 6, 32, 1, False),
                                            (64, 4, 32, 2, False), (2, 8, 64, 3, True),
-                                           (8, 6, 256, 3, True)])
+                                           (8, 6, 256, 3, True), (20, 4, 64, 2, True),
+                                           (32, 2, 32, 3, False), (34, 2, 128, 2, True)])
 def test_logpsi_matches_oracle(oracle_mod, Lx, Ly, H, nL, u1):
     theta = _theta(oracle_mod, nL, H, seed=400 + Lx + Ly + H, scale=2.0)
     s = _spins(401 + Lx, 40, Lx, Ly, u1)
@@ -55,7 +56,7 @@ def test_logpsi_matches_oracle(oracle_mod, Lx, Ly, H, nL, u1):
 @pytest.mark.parametrize("kind,Lx,Ly,H,u1,hf", [(0, 4, 4, 32, True, 0.0), (0, 6, 6, 64, True, 0.0),
                                                 (1, 4, 6, 32, False, 3.044),
                                                 (0, 10, 10, 128, True, 0.0),
-                                                (0, 6, 4, 256, True, 0.0)])
+                                                (0, 6, 4, 256, True, 0.0), (0, 18, 4, 64, True, 0.0)])
 def test_local_energy_matches_oracle(oracle_mod, kind, Lx, Ly, H, u1, hf):
     nL = 3
     theta = _theta(oracle_mod, nL, H, seed=410 + Lx * Ly + kind, scale=2.0)
@@ -203,7 +204,8 @@ def test_sampler_tuned_tile_draws_identical_samples(oracle_mod):
 
 
 @pytest.mark.parametrize("Lx,Ly,H,nL,u1", [(6, 6, 32, 3, True), (8, 4, 64, 2, False),
-                                           (4, 8, 32, 1, False), (6, 4, 128, 3, True)])
+                                           (4, 8, 32, 1, False), (6, 4, 128, 3, True),
+                                           (18, 4, 32, 2, True), (34, 2, 32, 1, False)])
 def test_gradient_matches_oracle_finite_differences(oracle_mod, Lx, Ly, H, nL, u1):
     """Per-sample O_k against central differences of the FP64 oracle's
     log psi: 80 sampled components (|dO_k| <= 1e-3 max|O|) and 3 random
