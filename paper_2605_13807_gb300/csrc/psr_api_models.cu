@@ -175,10 +175,10 @@ int psr2d_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_
     const F2Layout f = f2_layout(nL, H);
     const T2Layout tl = t2_layout(nL, H);
     const int W = (int)words_per_row(N);
-    const size_t ckpt = fwd2d_checkpoint_floats(nL, H);
+    const size_t ckpt = fwd2d_checkpoint_floats(nL, H, Lx);
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
-    int per_sm = (int)(dev_smem / (bwd2d_smem_bytes(nL, H) + 1024));
+    int per_sm = (int)(dev_smem / (bwd2d_smem_bytes(nL, H, Lx) + 1024));
     per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
     int64_t grid64 = (int64_t)ctx->num_sms * per_sm;
     if (grid64 > n) grid64 = n;
@@ -268,7 +268,7 @@ int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t
     const int W = (int)words_per_row(N);
     const int nb = bond_count(Lx, Ly, ham->pbc);
     const int64_t cap = n * max_entries_per_sample(ham);
-    const size_t ckpt = fwd2d_checkpoint_floats(nL, H);
+    const size_t ckpt = fwd2d_checkpoint_floats(nL, H, Lx);
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
                d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
 
@@ -388,7 +388,7 @@ int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32
     const int W = (int)words_per_row(N);
     const int nb = eloc ? bond_count(L, L, ham->pbc) : 0;
     const int64_t cap = eloc ? n * max_entries_per_sample(ham) : 0;
-    const size_t ckpt = fwd2d_checkpoint_floats(nL, H);
+    const size_t ckpt = fwd2d_checkpoint_floats(nL, H, L);
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
                d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
     float *theta_ws = nullptr, *out_ws = nullptr, *pk = nullptr, *lp8 = nullptr, *logp8 = nullptr,

@@ -46,7 +46,7 @@ T2Layout t2_layout(int nL, int H) {
     return t;
 }
 
-size_t bwd2d_smem_bytes(int nL, int H);
+size_t bwd2d_smem_bytes(int nL, int H, int Lx);
 
 namespace {
 
@@ -56,8 +56,8 @@ enum { TQ_U = 0, TQ_Z = 1, TQ_C = 2, TQ_H = 3, TQ_Y = 4, TQ_N = 5 };
 
 __device__ __forceinline__ int sp2(int Lx, int i, int j) { return j * Lx + ((j & 1) ? Lx - 1 - i : i); }
 
-// R: patches per row held in registers (8, 16 or 32 >= Lx / 2); the tape and
-// the shared rows keep the kR-wide layout.
+// R: patches per row (8, 16 or 32 >= Lx / 2), held in registers; shared rows
+// and row checkpoints are R + 4 floats wide, the tape keeps kR-wide rows.
 template <int H, int R>
 __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ spins, int64_t n,
                                                   int Lx, int Ly, int u1,
@@ -70,21 +70,22 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
     // Above hidden 128 the previous row's states are read in place from the
     // forward's row checkpoint in HBM (through L1) instead of a shared copy.
     constexpr bool kHvG = H > 128;
+    constexpr int LD = R + 4;
     extern __shared__ __align__(16) float smem[];
     const int nL = f.nL;
     const int Px = Lx >> 1, Py = Ly >> 1, N = Lx * Ly;
-    float *xs = smem;                 // [H][kLD] layer input / output
-    float *hs = xs + H * kLD;         // [H][kLD] states of the current layer
-    float *hv_s = hs + H * kLD;       // [nL][H][kLD] previous row's states (this row's order)
-    float *g1 = kHvG ? hv_s : hv_s + nL * H * kLD;  // [H][kLD] adjoint tile (gy, then dz)
-    float *g2 = g1 + H * kLD;         // [H][kLD] adjoint tile (dh~)
-    float *lg = g2 + H * kLD;         // [16][kLD] logits, then their adjoints
+    float *xs = smem;                 // [H][LD] layer input / output
+    float *hs = xs + H * LD;         // [H][LD] states of the current layer
+    float *hv_s = hs + H * LD;       // [nL][H][LD] previous row's states (this row's order)
+    float *g1 = kHvG ? hv_s : hv_s + nL * H * LD;  // [H][LD] adjoint tile (gy, then dz)
+    float *g2 = g1 + H * LD;         // [H][LD] adjoint tile (dh~)
+    float *lg = g2 + H * LD;         // [16][LD] logits, then their adjoints
     __shared__ int s_v[kR], s_vprev[kR];
     __shared__ int s_up;
 
     const int j = threadIdx.x;
     const int64_t P = tl.total;
-    const size_t ckpt = (size_t)nL * H * kLD;
+    const size_t ckpt = (size_t)nL * H * LD;
     float *tape = scratch + (size_t)blockIdx.x * ((size_t)nL * TQ_N * kR * H + 2 * ckpt);
     float *gvb[2] = {tape + (size_t)nL * TQ_N * kR * H, tape + (size_t)nL * TQ_N * kR * H + ckpt};
     auto T = [&](int l, int q, int k) -> float * { return tape + (((size_t)l * TQ_N + q) * kR + k) * H; };
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
 #pragma unroll 2
                     for (int m = 0; m < H; ++m) {
                         const float w = Wv[m * H + j];
-                        const float4 *sv = reinterpret_cast<const float4 *>(hv + m * kLD);
+                        const float4 *sv = reinterpret_cast<const float4 *>(hv + m * LD);
 #pragma unroll
                         for (int k4 = 0; k4 < R / 4; ++k4) {
                             const float4 v = sv[k4];
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     T(0, TQ_C, k)[j] = c[k];
                     T(0, TQ_H, k)[j] = h;
                 }
-                float4 *dh = reinterpret_cast<float4 *>(hs + j * kLD);
+                float4 *dh = reinterpret_cast<float4 *>(hs + j * LD);
 #pragma unroll
                 for (int k4 = 0; k4 < R / 4; ++k4)
                     dh[k4] = make_float4(hl[4 * k4], hl[4 * k4 + 1], hl[4 * k4 + 2], hl[4 * k4 + 3]);
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
 #pragma unroll 2
                 for (int m = 0; m < H; ++m) {
                     const float w = Ct[m * H + j];
-                    const float4 *sh = reinterpret_cast<const float4 *>(hs + m * kLD);
+                    const float4 *sh = reinterpret_cast<const float4 *>(hs + m * LD);
 #pragma unroll
                     for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 v = sh[k4];
@@ -185,26 +186,26 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
                     T(0, TQ_Y, k)[j] = y[k];
-                    xs[j * kLD + k] = gelu_f(y[k]);
+                    xs[j * LD + k] = gelu_f(y[k]);
                 }
                 __syncthreads();
             }
             for (int l = 1; l < nL; ++l) {
                 const float *WzT = pk + f.WzT[l], *WhxT = pk + f.WhxT[l], *Wv = pk + f.WhvT[l];
-                const float *hvl = hv + (size_t)l * H * kLD;
+                const float *hvl = hv + (size_t)l * H * LD;
                 float z[R], c[R];
                 const float bz = pk[f.bz[l] + j], bh = pk[f.bh[l] + j];
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
                     z[k] = bz;
                     c[k] = bh;
-                    T(l, TQ_U, k)[j] = xs[j * kLD + k];
+                    T(l, TQ_U, k)[j] = xs[j * LD + k];
                 }
 #pragma unroll 2
                 for (int m = 0; m < H; ++m) {
                     const float wz = WzT[m * H + j], wh = WhxT[m * H + j], wv = Wv[m * H + j];
-                    const float4 *sx = reinterpret_cast<const float4 *>(xs + m * kLD);
-                    const float4 *sv = reinterpret_cast<const float4 *>(hvl + m * kLD);
+                    const float4 *sx = reinterpret_cast<const float4 *>(xs + m * LD);
+                    const float4 *sv = reinterpret_cast<const float4 *>(hvl + m * LD);
 #pragma unroll
                     for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 x = sx[k4], v = sv[k4];
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     T(l, TQ_H, k)[j] = h;
                 }
                 __syncthreads();
-                float4 *dh = reinterpret_cast<float4 *>(hs + j * kLD);
+                float4 *dh = reinterpret_cast<float4 *>(hs + j * LD);
 #pragma unroll
                 for (int k4 = 0; k4 < R / 4; ++k4)
                     dh[k4] = make_float4(hn[4 * k4], hn[4 * k4 + 1], hn[4 * k4 + 2], hn[4 * k4 + 3]);
@@ -238,8 +239,8 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
 #pragma unroll 2
                 for (int m = 0; m < H; ++m) {
                     const float wc = Ct[m * H + j], wd = DT[m * H + j];
-                    const float4 *sh = reinterpret_cast<const float4 *>(hs + m * kLD);
-                    const float4 *sx = reinterpret_cast<const float4 *>(xs + m * kLD);
+                    const float4 *sh = reinterpret_cast<const float4 *>(hs + m * LD);
+                    const float4 *sx = reinterpret_cast<const float4 *>(xs + m * LD);
 #pragma unroll
                     for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 a = sh[k4], b = sx[k4];
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
                     T(l, TQ_Y, k)[j] = y[k];
-                    xs[j * kLD + k] = gelu_f(y[k]);
+                    xs[j * LD + k] = gelu_f(y[k]);
                     hl[k] = hn[k];
                 }
                 __syncthreads();
@@ -262,8 +263,8 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 const int o = j & 15;
                 for (int k = j >> 4; k < Px; k += H / 16) {
                     float v = theta[tl.bo + o];
-                    for (int m = 0; m < H; ++m) v += theta[tl.Wo + o * H + m] * xs[m * kLD + k];
-                    lg[o * kLD + k] = v;
+                    for (int m = 0; m < H; ++m) v += theta[tl.Wo + o * H + m] * xs[m * LD + k];
+                    lg[o * LD + k] = v;
                 }
             }
             __syncthreads();
@@ -281,20 +282,20 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 };
                 float mx = -INFINITY;
                 for (int v = 0; v < 16; ++v)
-                    if (allowed(v)) mx = fmaxf(mx, lg[v * kLD + k]);
+                    if (allowed(v)) mx = fmaxf(mx, lg[v * LD + k]);
                 float ssum = 0.0f;
                 for (int v = 0; v < 16; ++v)
-                    if (allowed(v)) ssum += expf(lg[v * kLD + k] - mx);
+                    if (allowed(v)) ssum += expf(lg[v * LD + k] - mx);
                 const int vk = s_v[k];
                 for (int v = 0; v < 16; ++v) {
-                    const float p = allowed(v) ? expf(lg[v * kLD + k] - mx) / ssum : 0.0f;
-                    lg[v * kLD + k] = 0.5f * scale * ((v == vk ? 1.0f : 0.0f) - p);
+                    const float p = allowed(v) ? expf(lg[v * LD + k] - mx) / ssum : 0.0f;
+                    lg[v * LD + k] = 0.5f * scale * ((v == vk ? 1.0f : 0.0f) - p);
                 }
             }
             __syncthreads();
             // zero the padding sites' adjoints
-            for (int i = j; i < 16 * kLD; i += H)
-                if ((i % kLD) >= Px) lg[i] = 0.0f;
+            for (int i = j; i < 16 * LD; i += H)
+                if ((i % LD) >= Px) lg[i] = 0.0f;
             __syncthreads();
             float gx[R];
             {
@@ -305,15 +306,15 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     float gw = 0.0f;
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
-                        const float g = lg[o * kLD + k];
+                        const float g = lg[o * LD + k];
                         gx[k] += w * g;
-                        gw += g * xs[j * kLD + k];
+                        gw += g * xs[j * LD + k];
                     }
                     atomicAdd(&G[tl.Wo + o * H + j], gw);
                 }
                 if (j < 16) {
                     float gb = 0.0f;
-                    for (int k = 0; k < Px; ++k) gb += lg[j * kLD + k];
+                    for (int k = 0; k < Px; ++k) gb += lg[j * LD + k];
                     atomicAdd(&G[tl.bo + j], gb);
                 }
             }
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
                     gy[k] = k < Px ? gx[k] * gelu_grad_f(T(l, TQ_Y, k)[j]) : 0.0f;
-                    g1[j * kLD + k] = gy[k];
+                    g1[j * LD + k] = gy[k];
                 }
                 __syncthreads();
                 // unit j as the input unit m: C^T gy, D^T gy, dC, dD
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     hk[k] = T(l, TQ_H, k)[j];
                     uk[k] = (l >= 1) ? T(l, TQ_U, k)[j] : 0.0f;
                     ghd[k] = (l + 1 < nL && l + 1 >= 2 ? gy_up[k] : 0.0f) +
-                             gv_in[((size_t)l * H + j) * kLD + k];
+                             gv_in[((size_t)l * H + j) * LD + k];
                     gud[k] = 0.0f;
                 }
                 {
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                         float ac = 0.0f, ad = 0.0f;
 #pragma unroll
                         for (int k = 0; k < R; ++k) {
-                            const float g = g1[i * kLD + k];
+                            const float g = g1[i * LD + k];
                             ghd[k] += cij * g;
                             gud[k] += dij * g;
                             ac += g * hk[k];
@@ -395,15 +396,15 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                 __syncthreads();  // every read of g1 (gy) is done
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    g1[j * kLD + k] = ghd[k];  // dz
-                    g2[j * kLD + k] = hk[k];   // dh~
+                    g1[j * LD + k] = ghd[k];  // dz
+                    g2[j * LD + k] = hk[k];   // dh~
                 }
                 __syncthreads();
                 // unit j as the input unit m: weight gradients, g_V, gx of the layer below
                 {
                     const float *Wzw = theta + tl.Wz[l];
                     const float *Whw = theta + tl.Wh[l];
-                    const float *hvl = hv + (size_t)l * H * kLD;
+                    const float *hvl = hv + (size_t)l * H * LD;
                     float gn[R], gvo[R];
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
@@ -417,12 +418,12 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                         float az = 0.0f, ah = 0.0f, avv = 0.0f;
 #pragma unroll
                         for (int k = 0; k < R; ++k) {
-                            const float dz = g1[i * kLD + k], dc = g2[i * kLD + k];
+                            const float dz = g1[i * LD + k], dc = g2[i * LD + k];
                             gn[k] += wz * dz + wh * dc;
                             gvo[k] += wv * dc;
                             az += dz * uk[k];
                             ah += dc * uk[k];
-                            avv += dc * hvl[j * kLD + k];
+                            avv += dc * hvl[j * LD + k];
                         }
                         if (l >= 1) {
                             atomicAdd(&G[tl.Wz[l] + (int64_t)i * din + j], az);
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     if (l == 0) {  // W_z^(0), W_hx^(0) act on the one-hot inputs
                         for (int k = 0; k < Px; ++k) {
                             const int pi = (pj & 1) ? Px - 1 - k : k;
-                            const float dz = g1[j * kLD + k], dc = g2[j * kLD + k];
+                            const float dz = g1[j * LD + k], dc = g2[j * LD + k];
                             if (k > 0) {
                                 atomicAdd(&G[tl.Wz[0] + (int64_t)j * 32 + s_v[k - 1]], dz);
                                 atomicAdd(&G[tl.Wh[0] + (int64_t)j * (32 + H) + s_v[k - 1]], dc);
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ sp
                     // adjoint into the row above (path order of that row: reversed)
 #pragma unroll
                     for (int k = 0; k < R; ++k)
-                        if (k < Px) gv_out[((size_t)l * H + j) * kLD + (Px - 1 - k)] = gvo[k];
+                        if (k < Px) gv_out[((size_t)l * H + j) * LD + (Px - 1 - k)] = gvo[k];
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
                         gx[k] = gn[k];
@@ -478,7 +479,7 @@ cudaError_t launch_bwd2d_hr(const uint8_t *spins, int64_t n, int Lx, int Ly, int
                            const T2Layout &tl, const float *packed, const F2Layout &f,
                            const float *carries, const float *dout, float *grad_rows, int grid,
                            float *scratch, cudaStream_t st) {
-    const size_t smem = bwd2d_smem_bytes(f.nL, H);
+    const size_t smem = bwd2d_smem_bytes(f.nL, H, Lx);
     cudaError_t e = cudaFuncSetAttribute(bwd2d_kernel<H, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -492,11 +493,11 @@ cudaError_t launch_bwd2d_h(const uint8_t *spins, int64_t n, int Lx, int Ly, int 
                            const T2Layout &tl, const float *packed, const F2Layout &f,
                            const float *carries, const float *dout, float *grad_rows, int grid,
                            float *scratch, cudaStream_t st) {
-    const int Px = Lx / 2;
-    if (Px <= 8)
+    const int Px = row2d_width(Lx);
+    if (Px == 8)
         return launch_bwd2d_hr<H, 8>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid,
                                      scratch, st);
-    if (Px <= 16)
+    if (Px == 16)
         return launch_bwd2d_hr<H, 16>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows,
                                       grid, scratch, st);
     return launch_bwd2d_hr<H, 32>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid,
@@ -509,8 +510,9 @@ size_t bwd2d_scratch_floats_per_cta(int nL, int H) {
     return (size_t)nL * TQ_N * kR * H + 2 * (size_t)nL * H * kLD;
 }
 
-size_t bwd2d_smem_bytes(int nL, int H) {
-    return ((size_t)(4 + (H > 128 ? 0 : nL)) * H * kLD + 16 * kLD) * sizeof(float);
+size_t bwd2d_smem_bytes(int nL, int H, int Lx) {
+    const size_t ld = (size_t)row2d_width(Lx) + 4;
+    return ((size_t)(4 + (H > 128 ? 0 : nL)) * H * ld + 16 * ld) * sizeof(float);
 }
 
 cudaError_t launch_bwd2d(const uint8_t *spins, int64_t n, int Lx, int Ly, int u1, const float *theta,

@@ -101,7 +101,6 @@ __global__ void pack_f2_kernel(const float *__restrict__ theta, F2Layout f, floa
 }
 
 constexpr int kRow = 32;       // patches per row handled by one CTA (max)
-constexpr int kLD = kRow + 4;  // padded row of site values (float4 rows)
 
 __device__ __forceinline__ int seq_pos2d(int Lx, int i, int j) {
     return j * Lx + ((j & 1) ? (Lx - 1 - i) : i);
@@ -113,17 +112,18 @@ __device__ __forceinline__ int spin_at(const uint8_t *s, int Lx, int i, int j, i
     return (int)(s[pos] & 1u) ^ (pos == p) ^ (pos == q);
 }
 
-// R: patches per row held in registers (8, 16 or 32 >= Lx / 2); shared rows
-// and checkpoints keep the kRow-wide layout.
+// R: patches per row (8, 16 or 32 >= Lx / 2), held in registers; shared rows
+// and row checkpoints are R + 4 floats wide (float4 rows).
 template <int H, int R>
 __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fwd2Jobs jb,
                                                       const float *__restrict__ pk, F2Layout f) {
+    constexpr int LD = R + 4;
     extern __shared__ __align__(16) float smem[];
     const int nL = f.nL;
-    float *xs = smem;                    // [H][kLD] layer input / output of the row
-    float *hs = xs + H * kLD;            // [H][kLD] states of the current layer
-    float *hv = hs + H * kLD;            // [nL][H][kLD] previous row's states (path order)
-    float *lg = hv + nL * H * kLD;       // [16][kLD] logits of the row
+    float *xs = smem;                    // [H][LD] layer input / output of the row
+    float *hs = xs + H * LD;            // [H][LD] states of the current layer
+    float *hv = hs + H * LD;            // [nL][H][LD] previous row's states (path order)
+    float *lg = hv + nL * H * LD;       // [16][LD] logits of the row
     __shared__ int s_v[kRow];            // patch values of the row (path order)
     __shared__ int s_vprev[kRow];        // previous row's values by column
     __shared__ float s_part[1];
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
     const int Lx = G.Lx, Ly = G.Ly, Px = Lx >> 1, Py = Ly >> 1, N = Lx * Ly, Np = Px * Py;
     const long long njobs = jb.mode == 1 ? (long long)*G.n_jobs_dev : (long long)G.n_jobs;
     const float *Wo = pk + f.Wo;
-    const size_t ckpt_row = (size_t)nL * H * kLD;  // floats of one row checkpoint
+    const size_t ckpt_row = (size_t)nL * H * LD;  // floats of one row checkpoint
 
     for (;;) {
         if (j == 0) s_job = (long long)atomicAdd(jb.job_counter, 1ull);
@@ -158,10 +158,10 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
         // state before row r0: the previous row's states and values, the
         // up / down counts of every earlier patch (the flips come later)
         if (r0 == 0) {
-            for (int i = j; i < nL * H * kLD; i += H) hv[i] = 0.0f;
+            for (int i = j; i < nL * H * LD; i += H) hv[i] = 0.0f;
         } else {
             const float *src = G.carries_in + ((size_t)sample * Py + r0) * ckpt_row;
-            for (int i = j; i < nL * H * kLD; i += H) hv[i] = src[i];
+            for (int i = j; i < nL * H * LD; i += H) hv[i] = src[i];
         }
         if (j < Px && r0 > 0) {
             const int pj = r0 - 1;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
         for (int pj = r0; pj < Py; ++pj) {
             if (jb.mode == 0 && G.carries_out) {
                 float *dst = G.carries_out + ((size_t)sample * Py + pj) * ckpt_row;
-                for (int i = j; i < nL * H * kLD; i += H) dst[i] = hv[i];
+                for (int i = j; i < nL * H * LD; i += H) dst[i] = hv[i];
             }
             if (j < Px) {
                 const int pi = (pj & 1) ? Px - 1 - j : j;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
 #pragma unroll 4
                     for (int m = 0; m < H; ++m) {
                         const float w = Wv[m * H + j];
-                        const float4 *src = reinterpret_cast<const float4 *>(hv0 + m * kLD);
+                        const float4 *src = reinterpret_cast<const float4 *>(hv0 + m * LD);
 #pragma unroll
                         for (int k4 = 0; k4 < R / 4; ++k4) {
                             const float4 v = src[k4];
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                     h = a * h + (1.0f - a) * c[k];
                     hl[k] = h;
                 }
-                float4 *dst = reinterpret_cast<float4 *>(hs + j * kLD);
+                float4 *dst = reinterpret_cast<float4 *>(hs + j * LD);
 #pragma unroll
                 for (int k4 = 0; k4 < R / 4; ++k4)
                     dst[k4] = make_float4(hl[4 * k4], hl[4 * k4 + 1], hl[4 * k4 + 2], hl[4 * k4 + 3]);
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
 #pragma unroll 4
                 for (int m = 0; m < H; ++m) {
                     const float w = Ct[m * H + j];
-                    const float4 *src = reinterpret_cast<const float4 *>(hs + m * kLD);
+                    const float4 *src = reinterpret_cast<const float4 *>(hs + m * LD);
 #pragma unroll
                     for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 v = src[k4];
@@ -248,20 +248,20 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                         y[4 * k4 + 2] += w * v.z; y[4 * k4 + 3] += w * v.w;
                     }
                 }
-                float4 *xd = reinterpret_cast<float4 *>(xs + j * kLD);
+                float4 *xd = reinterpret_cast<float4 *>(xs + j * LD);
 #pragma unroll
                 for (int k4 = 0; k4 < R / 4; ++k4)
                     xd[k4] = make_float4(gelu_f(y[4 * k4]), gelu_f(y[4 * k4 + 1]), gelu_f(y[4 * k4 + 2]),
                                          gelu_f(y[4 * k4 + 3]));
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    if (k < Px) hv[j * kLD + (Px - 1 - k)] = hl[k];
+                    if (k < Px) hv[j * LD + (Px - 1 - k)] = hl[k];
                 __syncthreads();
             }
             // ---------------- layers l >= 1
             for (int l = 1; l < nL; ++l) {
                 const float *WzT = pk + f.WzT[l], *WhxT = pk + f.WhxT[l], *Wv = pk + f.WhvT[l];
-                float *hvl = hv + (size_t)l * H * kLD;
+                float *hvl = hv + (size_t)l * H * LD;
                 float z[R], c[R];
                 const float bz = pk[f.bz[l] + j], bh = pk[f.bh[l] + j];
 #pragma unroll
@@ -272,8 +272,8 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
 #pragma unroll 2
                 for (int m = 0; m < H; ++m) {
                     const float wz = WzT[m * H + j], wh = WhxT[m * H + j], wv = Wv[m * H + j];
-                    const float4 *sx = reinterpret_cast<const float4 *>(xs + m * kLD);
-                    const float4 *sv = reinterpret_cast<const float4 *>(hvl + m * kLD);
+                    const float4 *sx = reinterpret_cast<const float4 *>(xs + m * LD);
+                    const float4 *sv = reinterpret_cast<const float4 *>(hvl + m * LD);
 #pragma unroll
                     for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 x = sx[k4], v = sv[k4];
@@ -294,13 +294,13 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                     }
                 }
                 __syncthreads();  // every read of hs (previous layer) and hv[l] is done
-                float4 *dst = reinterpret_cast<float4 *>(hs + j * kLD);
+                float4 *dst = reinterpret_cast<float4 *>(hs + j * LD);
 #pragma unroll
                 for (int k4 = 0; k4 < R / 4; ++k4)
                     dst[k4] = make_float4(hn[4 * k4], hn[4 * k4 + 1], hn[4 * k4 + 2], hn[4 * k4 + 3]);
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    if (k < Px) hvl[j * kLD + (Px - 1 - k)] = hn[k];
+                    if (k < Px) hvl[j * LD + (Px - 1 - k)] = hn[k];
                 __syncthreads();
                 float y[R];
 #pragma unroll
@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
 #pragma unroll 2
                 for (int m = 0; m < H; ++m) {
                     const float wc = Ct[m * H + j], wd = DT[m * H + j];
-                    const float4 *sh = reinterpret_cast<const float4 *>(hs + m * kLD);
-                    const float4 *sx = reinterpret_cast<const float4 *>(xs + m * kLD);
+                    const float4 *sh = reinterpret_cast<const float4 *>(hs + m * LD);
+                    const float4 *sx = reinterpret_cast<const float4 *>(xs + m * LD);
 #pragma unroll
                     for (int k4 = 0; k4 < R / 4; ++k4) {
                         const float4 a = sh[k4], b = sx[k4];
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                     }
                 }
                 __syncthreads();  // every read of xs done
-                float4 *xd = reinterpret_cast<float4 *>(xs + j * kLD);
+                float4 *xd = reinterpret_cast<float4 *>(xs + j * LD);
 #pragma unroll
                 for (int k4 = 0; k4 < R / 4; ++k4)
                     xd[k4] = make_float4(gelu_f(y[4 * k4]), gelu_f(y[4 * k4 + 1]), gelu_f(y[4 * k4 + 2]),
@@ -335,8 +335,8 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                 const float bo = Wo[16 * H + o];
                 for (int k = g; k < Px; k += G16) {
                     float v = bo;
-                    for (int m = 0; m < H; ++m) v += Wo[o * H + m] * xs[m * kLD + k];
-                    lg[o * kLD + k] = v;
+                    for (int m = 0; m < H; ++m) v += Wo[o * H + m] * xs[m * LD + k];
+                    lg[o * LD + k] = v;
                 }
             }
             __syncthreads();
@@ -359,13 +359,13 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
                     float mx = -INFINITY;
 #pragma unroll
                     for (int u = 0; u < 16; ++u)
-                        if (allowed(u)) mx = fmaxf(mx, lg[u * kLD + k]);
+                        if (allowed(u)) mx = fmaxf(mx, lg[u * LD + k]);
                     float ssum = 0.0f;
 #pragma unroll
                     for (int u = 0; u < 16; ++u)
-                        if (allowed(u)) ssum += expf(lg[u * kLD + k] - mx);
+                        if (allowed(u)) ssum += expf(lg[u * LD + k] - mx);
                     const int v = s_v[k];
-                    const float lp = allowed(v) ? lg[v * kLD + k] - mx - logf(ssum) : -INFINITY;
+                    const float lp = allowed(v) ? lg[v * LD + k] - mx - logf(ssum) : -INFINITY;
                     const int t = pj * Px + k;
                     if (G.logp_out) G.logp_out[(size_t)sample * Np + t] = lp;
                     d = (jb.mode == 1) ? lp - G.logp_ref[(size_t)sample * Np + t] : lp;
@@ -392,7 +392,8 @@ __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fw
 template <int H, int R>
 cudaError_t launch_fwd2d_hr(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f, int num_sms,
                             cudaStream_t stream) {
-    const size_t smem = ((size_t)(2 + f.nL) * H * kLD + 16 * kLD) * sizeof(float);
+    constexpr int LD = R + 4;
+    const size_t smem = ((size_t)(2 + f.nL) * H * LD + 16 * LD) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(fwd2d_f32_kernel<H, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -410,10 +411,11 @@ cudaError_t launch_fwd2d_hr(const Fwd2Jobs &jobs, const float *packed, const F2L
 template <int H>
 cudaError_t launch_fwd2d_h(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f, int num_sms,
                            cudaStream_t stream) {
-    const int Px = jobs.g.Lx / 2;
-    if (Px <= 8) return launch_fwd2d_hr<H, 8>(jobs, packed, f, num_sms, stream);
-    if (Px <= 16) return launch_fwd2d_hr<H, 16>(jobs, packed, f, num_sms, stream);
-    return launch_fwd2d_hr<H, 32>(jobs, packed, f, num_sms, stream);
+    switch (row2d_width(jobs.g.Lx)) {
+        case 8: return launch_fwd2d_hr<H, 8>(jobs, packed, f, num_sms, stream);
+        case 16: return launch_fwd2d_hr<H, 16>(jobs, packed, f, num_sms, stream);
+        default: return launch_fwd2d_hr<H, 32>(jobs, packed, f, num_sms, stream);
+    }
 }
 
 }  // namespace
@@ -424,7 +426,12 @@ cudaError_t launch_pack_theta_f2(const float *theta, const F2Layout &f, float *p
     return cudaGetLastError();
 }
 
-size_t fwd2d_checkpoint_floats(int nL, int H) { return (size_t)nL * H * kLD; }
+int row2d_width(int Lx) {
+    const int Px = Lx / 2;
+    return Px <= 8 ? 8 : (Px <= 16 ? 16 : 32);
+}
+
+size_t fwd2d_checkpoint_floats(int nL, int H, int Lx) { return (size_t)nL * H * (row2d_width(Lx) + 4); }
 
 cudaError_t launch_fwd2d_f32(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f,
                              int num_sms, cudaStream_t stream) {

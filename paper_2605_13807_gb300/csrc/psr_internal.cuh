@@ -187,7 +187,10 @@ struct Fwd2Jobs {
     unsigned long long *job_counter;
     int *status;
 };
-size_t fwd2d_checkpoint_floats(int nL, int H);
+// Patches per row held in registers by the 2D kernels (8, 16 or 32 >= Lx / 2);
+// shared rows and row checkpoints are row2d_width + 4 floats wide.
+int row2d_width(int Lx);
+size_t fwd2d_checkpoint_floats(int nL, int H, int Lx);
 cudaError_t launch_pack_theta_f2(const float *theta, const F2Layout &f, float *packed,
                                  cudaStream_t stream);
 cudaError_t launch_fwd2d_f32(const Fwd2Jobs &jobs, const float *packed, const F2Layout &f,
@@ -206,7 +209,7 @@ T2Layout t2_layout(int nL, int H);
 // row checkpoints; grad_rows: [n][P] (dout == NULL) or [grid][P] partial
 // sums of dout_i O_k(s_i).  scratch: grid * bwd2d_scratch_floats_per_cta.
 size_t bwd2d_scratch_floats_per_cta(int nL, int H);
-size_t bwd2d_smem_bytes(int nL, int H);
+size_t bwd2d_smem_bytes(int nL, int H, int Lx);
 cudaError_t launch_bwd2d(const uint8_t *spins, int64_t n, int Lx, int Ly, int u1, const float *theta,
                          const T2Layout &tl, const float *packed, const F2Layout &f, const float *carries,
                          const float *dout, float *grad_rows, int grid, float *scratch,
