@@ -1,7 +1,7 @@
 """Physics check of the whole on-device VMC loop (psr_vmc_step and
-psr_lru_vmc_step: exact sampling, E_loc, energy gradient, Adam): a short
-training run of the chain minGRU or of the deep LRU must approach the exact
-ground-state energy from above.
+psr_lru_vmc_step, psr2d_vmc_step: exact sampling, E_loc, energy gradient,
+Adam): a short training run of the chain minGRU, of the deep LRU or of the
+2D patched minGRU must approach the exact ground-state energy from above.
 
 References: the 16-site open TFIM at h = 1 has E0/N = -1.2510242 (Table I;
 the oracle's exact diagonalisation is pinned to that table), the 4 x 4 open
@@ -100,3 +100,34 @@ def test_lru_chain_reaches_the_exact_energy(oracle_mod, kind, u1, hf):
     e, se = _train_lru(kind, 16, 32, 2, u1, hf, steps=400, n=1024, lr=1e-2 if kind == 1 else 5e-3)
     assert e >= e0 - 4 * se
     assert (e - e0) / abs(e0) < 2e-3, (e, e0)
+
+
+def _train2d(L, H, nL, sym, steps, n, lr):
+    ham = B.make_hamiltonian("heisenberg", L, L, False, True, 1.0, 0.0)
+    cfg = api.ModelConfig(nL, H, True, "fp32")
+    th = torch.from_numpy(inputs.glorot_params2d(nL, H, seed=0)).cuda()
+    adam = api.Adam(th.numel(), "cuda", lr=lr)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    Np = (L // 2) ** 2
+    for _ in range(steps):
+        u = torch.rand((n, Np), generator=gen, device="cuda")
+        us = torch.rand(n, generator=gen, device="cuda") if sym else None
+        api.vmc_step2d(th, cfg, ham, u, adam, theta_out=th, symmetrize=sym, sym_uniforms=us)
+    m = 8192
+    u = torch.rand((m, Np), generator=gen, device="cuda")
+    us = torch.rand(m, generator=gen, device="cuda") if sym else None
+    frozen = api.Adam(th.numel(), "cuda", lr=0.0)
+    out = api.vmc_step2d(th, cfg, ham, u, frozen, symmetrize=sym, sym_uniforms=us)
+    api.sync()
+    assert torch.equal(out["theta"], th)
+    mean, var, se = out["stats"].cpu().numpy()
+    return mean / (L * L), se / (L * L)
+
+
+@pytest.mark.parametrize("sym,tol", [(False, 1e-2), (True, 5e-3)])
+def test_2d_model_on_the_4x4_heisenberg_lattice(oracle_mod, sym, tol):
+    e0 = _exact(oracle_mod, 0, 4, 4, 0.0)
+    e, se = _train2d(4, 32, 3, sym, steps=300, n=1024, lr=5e-3)
+    assert e >= e0 - 4 * se
+    assert (e - e0) / abs(e0) < tol, (e, e0)
