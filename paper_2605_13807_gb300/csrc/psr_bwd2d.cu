@@ -56,7 +56,7 @@ enum { TQ_U = 0, TQ_Z = 1, TQ_C = 2, TQ_H = 3, TQ_Y = 4, TQ_N = 5 };
 
 __device__ __forceinline__ int sp2(int Lx, int i, int j) { return j * Lx + ((j & 1) ? Lx - 1 - i : i); }
 
-// R: patches per row (8, 16 or 32 >= Lx / 2), held in registers; shared rows
+// R: patches per row (row2d_width(Lx) >= Lx / 2), held in registers; shared rows
 // and row checkpoints are R + 4 floats wide, the tape keeps kR-wide rows.
 template <int H, int R>
 __global__ void __launch_bounds__(H) bwd2d_kernel(const uint8_t *__restrict__ spins, int64_t n,
@@ -493,15 +493,14 @@ cudaError_t launch_bwd2d_h(const uint8_t *spins, int64_t n, int Lx, int Ly, int 
                            const T2Layout &tl, const float *packed, const F2Layout &f,
                            const float *carries, const float *dout, float *grad_rows, int grid,
                            float *scratch, cudaStream_t st) {
-    const int Px = row2d_width(Lx);
-    if (Px == 8)
-        return launch_bwd2d_hr<H, 8>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid,
-                                     scratch, st);
-    if (Px == 16)
-        return launch_bwd2d_hr<H, 16>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows,
-                                      grid, scratch, st);
-    return launch_bwd2d_hr<H, 32>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid,
-                                  scratch, st);
+    switch (row2d_width(Lx)) {
+        case 8: return launch_bwd2d_hr<H, 8>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, st);
+        case 12: return launch_bwd2d_hr<H, 12>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, st);
+        case 16: return launch_bwd2d_hr<H, 16>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, st);
+        case 24: return launch_bwd2d_hr<H, 24>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, st);
+        case 28: return launch_bwd2d_hr<H, 28>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, st);
+        default: return launch_bwd2d_hr<H, 32>(spins, n, Lx, Ly, u1, theta, tl, packed, f, carries, dout, grad_rows, grid, scratch, st);
+    }
 }
 
 }  // namespace

@@ -112,7 +112,7 @@ __device__ __forceinline__ int spin_at(const uint8_t *s, int Lx, int i, int j, i
     return (int)(s[pos] & 1u) ^ (pos == p) ^ (pos == q);
 }
 
-// R: patches per row (8, 16 or 32 >= Lx / 2), held in registers; shared rows
+// R: patches per row (row2d_width(Lx) >= Lx / 2), held in registers; shared rows
 // and row checkpoints are R + 4 floats wide (float4 rows).
 template <int H, int R>
 __global__ void __launch_bounds__(H) fwd2d_f32_kernel(const __grid_constant__ Fwd2Jobs jb,
@@ -413,7 +413,10 @@ cudaError_t launch_fwd2d_h(const Fwd2Jobs &jobs, const float *packed, const F2La
                            cudaStream_t stream) {
     switch (row2d_width(jobs.g.Lx)) {
         case 8: return launch_fwd2d_hr<H, 8>(jobs, packed, f, num_sms, stream);
+        case 12: return launch_fwd2d_hr<H, 12>(jobs, packed, f, num_sms, stream);
         case 16: return launch_fwd2d_hr<H, 16>(jobs, packed, f, num_sms, stream);
+        case 24: return launch_fwd2d_hr<H, 24>(jobs, packed, f, num_sms, stream);
+        case 28: return launch_fwd2d_hr<H, 28>(jobs, packed, f, num_sms, stream);
         default: return launch_fwd2d_hr<H, 32>(jobs, packed, f, num_sms, stream);
     }
 }
@@ -428,7 +431,9 @@ cudaError_t launch_pack_theta_f2(const float *theta, const F2Layout &f, float *p
 
 int row2d_width(int Lx) {
     const int Px = Lx / 2;
-    return Px <= 8 ? 8 : (Px <= 16 ? 16 : 32);
+    for (int r : {8, 12, 16, 24, 28})
+        if (Px <= r) return r;
+    return 32;
 }
 
 size_t fwd2d_checkpoint_floats(int nL, int H, int Lx) { return (size_t)nL * H * (row2d_width(Lx) + 4); }

@@ -187,7 +187,8 @@ struct Fwd2Jobs {
     unsigned long long *job_counter;
     int *status;
 };
-// Patches per row held in registers by the 2D kernels (8, 16 or 32 >= Lx / 2);
+// Patches per row held in registers by the 2D kernels (8, 12, 16, 24, 28 or
+// 32, the first >= Lx / 2);
 // shared rows and row checkpoints are row2d_width + 4 floats wide.
 int row2d_width(int Lx);
 size_t fwd2d_checkpoint_floats(int nL, int H, int Lx);

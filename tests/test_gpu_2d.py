@@ -205,7 +205,8 @@ def test_sampler_tuned_tile_draws_identical_samples(oracle_mod):
 
 @pytest.mark.parametrize("Lx,Ly,H,nL,u1", [(6, 6, 32, 3, True), (8, 4, 64, 2, False),
                                            (4, 8, 32, 1, False), (6, 4, 128, 3, True),
-                                           (18, 4, 32, 2, True), (34, 2, 32, 1, False)])
+                                           (18, 4, 32, 2, True), (34, 2, 32, 1, False),
+                                           (32, 4, 32, 1, True), (56, 2, 32, 1, False)])
 def test_gradient_matches_oracle_finite_differences(oracle_mod, Lx, Ly, H, nL, u1):
     """Per-sample O_k against central differences of the FP64 oracle's
     log psi: 80 sampled components (|dO_k| <= 1e-3 max|O|) and 3 random
