@@ -70,6 +70,13 @@ def parse():
                     help="sequences of the scan-only run (default: the workload's samples)")
     ap.add_argument("--scan-tile", default="",
                     help="units,chunk: fixed tile shape of the scan-only run (default: autotuned)")
+    ap.add_argument("--paper2d-only", action="store_true",
+                    help="only the 2D VMC step at the paper's 2D configuration")
+    ap.add_argument("--paper2d-sizes", default="10,20",
+                    help="lattice sides L of the paper-configuration 2D leg")
+    ap.add_argument("--paper2d-reps", type=int, default=2)
+    ap.add_argument("--paper2d-warmup", type=int, default=1,
+                    help="untimed steps before the timed ones (the sampler is tuned in any case)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -548,10 +555,10 @@ def vmc_leg(dev, L=10, n=1024, reps=3):
 
 # per-step wall times of the paper's 2D runs (Table VI, 1x A100 80GB, 3
 # layers, d_h = 256, 2x2 patches, c4v, 200 samples): context, not a target
-PAPER_2D_STEP_S = {10: 0.5, 20: 8.2}
+PAPER_2D_STEP_S = {10: 0.5, 20: 8.2, 52: 405.6}
 
 
-def paper2d_leg(dev, sizes=(10, 20), n=200, reps=2):
+def paper2d_leg(dev, sizes=(10, 20), n=200, reps=2, warmup=1):
     """One on-device VMC step of the 2D patched minGRU at the paper's 2D
     configuration (3 layers, d_h = 256, 2x2 patches, c4v symmetrisation,
     200 samples, Heisenberg OBC with zero magnetisation): exact sampling,
@@ -572,7 +579,9 @@ def paper2d_leg(dev, sizes=(10, 20), n=200, reps=2):
         u = torch.rand((n, (L // 2) ** 2), generator=g, device=dev)
         us = torch.rand(n, generator=g, device=dev)
         adam = api.Adam(th.numel(), dev, lr=1e-3)
-        out = api.vmc_step2d(th, cfg, ham, u, adam, theta_out=th, symmetrize=True, sym_uniforms=us)
+        api.sample2d(th, u, cfg, L, L)  # the sampler's tile is tuned here, outside the timing
+        for _ in range(warmup):
+            api.vmc_step2d(th, cfg, ham, u, adam, theta_out=th, symmetrize=True, sym_uniforms=us)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -586,6 +595,22 @@ def paper2d_leg(dev, sizes=(10, 20), n=200, reps=2):
         if L in PAPER_2D_STEP_S:
             res["paper_step_s_A100"][f"{L}x{L}"] = PAPER_2D_STEP_S[L]
     return res
+
+
+def paper2d_sizes(args):
+    return tuple(int(x) for x in args.paper2d_sizes.split(",") if x)
+
+
+def run_paper2d_only(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    res = paper2d_leg(torch.device("cuda", 0), sizes=paper2d_sizes(args), reps=args.paper2d_reps,
+                      warmup=args.paper2d_warmup)
+    print(json.dumps({"paper2d_vmc_step": res}), flush=True)
+    return 0
 
 
 def run_scan_only(args):
@@ -760,7 +785,8 @@ def run_mine(args):
         line["lru"] = lru_leg(dev)
     if not args.no_vmc and rank == 0:
         line["vmc_step"] = vmc_leg(dev)
-        line["paper2d_vmc_step"] = paper2d_leg(dev)
+        line["paper2d_vmc_step"] = paper2d_leg(dev, sizes=paper2d_sizes(args), reps=args.paper2d_reps,
+                                               warmup=args.paper2d_warmup)
 
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
@@ -808,6 +834,8 @@ def main():
         return run_reference(args)
     if args.scan_only:
         return run_scan_only(args)
+    if args.paper2d_only:
+        return run_paper2d_only(args)
     return run_mine(args)
 
 
