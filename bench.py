@@ -486,8 +486,26 @@ def lru_leg(dev, N=256, H=64, n=1024, reps=3):
     e1.record()
     e1.synchronize()
     vmc_ms = e0.elapsed_time(e1) / reps
+    # the same step at shorter chains, beside the paper's Table I step times
+    # (1x H100, same model and sample count; context, not a target)
+    by_n = {}
+    for Nc in (32, 64, 128):
+        ham_c = B.make_hamiltonian("tfim", Nc, 1, False, True, 1.0, 1.0)
+        u_c = torch.rand((n, Nc), generator=g, device=dev)
+        th_c = theta.clone()
+        adam_c = api.Adam(theta.numel(), dev, lr=1e-3)
+        api.vmc_step_lru(th_c, cfg, ham_c, u_c, adam_c, theta_out=th_c)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            api.vmc_step_lru(th_c, cfg, ham_c, u_c, adam_c, theta_out=th_c)
+        e1.record()
+        e1.synchronize()
+        by_n[str(Nc)] = e0.elapsed_time(e1) / reps
+    by_n[str(N)] = vmc_ms
     return {"model": "deep 1D LRU (complex diagonal recurrence + GLU), FP32 CUDA cores",
-            "grad_bwd_ms": bwd_ms, "vmc_step_ms": vmc_ms,
+            "grad_bwd_ms": bwd_ms, "vmc_step_ms": vmc_ms, "vmc_step_ms_by_N": by_n,
+            "paper_step_ms_H100_by_N": {"32": 28, "64": 71, "128": 260, "256": 900},
             "vmc_energy_per_site": float(out["stats"][0].item()) / N,
             "workload": f"tfim_chain_{N}_obc_{n}_samples", "hidden": H, "connected": E,
             "value": (n + E) * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
