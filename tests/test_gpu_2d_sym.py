@@ -174,3 +174,41 @@ def test_symmetrised_vmc_step_of_the_2d_model(oracle_mod):
     assert np.linalg.norm(grad - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
     t1, _, _ = vmc.adam(theta, grad, np.zeros(theta.size), np.zeros(theta.size), 1, 1e-2)
     assert np.max(np.abs(out["theta"].cpu().numpy() - t1)) <= 1e-6 + 1e-6 * np.max(np.abs(t1))
+
+
+def test_sym_local_energy2d_host_arrays_equal_device_result(oracle_mod):
+    L, nL, H = 4, 2, 32
+    theta = _theta(oracle_mod, nL, H, 960)
+    s = inputs.neel_like_spins(961, 5, L, L)
+    ham = B.make_hamiltonian("heisenberg", L, L, False, True, 1.0, 0.0)
+    p_host = B.make_params(theta, nL, H, True, "fp32", api._ctx())
+    e_host = np.empty(5, dtype=np.float32)
+    st_host = np.empty(3, dtype=np.float64)
+    B.psr2d_sym_local_energy(p_host, s, ham, e_host, st_host)
+    e_dev, st_dev = api.sym_local_energy2d(torch.from_numpy(theta).cuda(), torch.from_numpy(s).cuda(),
+                                           api.ModelConfig(nL, H, True, "fp32"), ham)
+    api.sync()
+    assert np.array_equal(e_host, e_dev.cpu().numpy())
+    assert np.array_equal(st_host, st_dev.cpu().numpy())
+
+
+def test_vmc_step2d_rejections(oracle_mod):
+    L, nL, H = 4, 2, 32
+    theta = torch.from_numpy(_theta(oracle_mod, nL, H, 970)).cuda()
+    p = B.make_params(theta, nL, H, True, "fp32")
+    adam = api.Adam(theta.numel(), "cuda")
+    adam.step = 1
+    out = torch.empty_like(theta)
+    u = torch.zeros((8, 4), device="cuda")
+    us = torch.zeros(8, device="cuda")
+    rect = B.make_hamiltonian("heisenberg", 4, 8, False, True, 1.0, 0.0)
+    with pytest.raises(B.PsrError) as ei:  # c4v needs a square lattice
+        B.psr2d_vmc_step(p, rect, True, torch.zeros((8, 8), device="cuda"), us, adam.state(), out)
+    assert ei.value.code == B.PSR_EINVAL
+    sq = B.make_hamiltonian("heisenberg", L, L, False, True, 1.0, 0.0)
+    with pytest.raises(B.PsrError) as ei:  # symmetrize without its uniforms
+        B.psr2d_vmc_step(p, sq, True, u, None, adam.state(), out)
+    assert ei.value.code == B.PSR_EINVAL
+    with pytest.raises(B.PsrError) as ei:  # host uniforms
+        B.psr2d_vmc_step(p, sq, False, u.cpu().numpy(), None, adam.state(), out)
+    assert ei.value.code == B.PSR_EINVAL
