@@ -50,7 +50,7 @@ def _lp(theta, spins, u1, prec="bf16"):
 
 @pytest.mark.parametrize("N,u1,seed", [(64, False, 1), (1, False, 2), (2, True, 3), (36, True, 4),
                                        (63, False, 5), (65, False, 6), (100, True, 7), (128, True, 8),
-                                       (200, False, 9)])
+                                       (200, False, 9), (31, False, 10), (32, True, 11), (33, False, 12)])
 def test_logpsi_bf16_matches_oracle(oracle_mod, N, u1, seed):
     theta = inputs.glorot_params(NL, H, seed=seed)
     n = 40
