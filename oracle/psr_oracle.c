@@ -30,7 +30,7 @@
  *   W_z[H][d_in], b_z[H], W_h[H][d_in], b_h[H], C[H][H], D[H][d_in]
  * then the readout W_o[2][H], b_o[2].
  *
- * Readings of points the paper leaves open (listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - layer-0 input at site t is onehot(s_{t-1}) (2-dim), zero at t = 0;
  *   - the readout is a linear map to 2 logits followed by a softmax;
  *   - GELU is the exact erf form;

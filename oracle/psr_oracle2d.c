@@ -24,7 +24,7 @@
  *   - the conditional of patch t is softmax(W_o x_{nL} + b_o) over its 16
  *     values, log psi = 1/2 sum_t log P(v_t | v_<t).
  *
- * Readings of points the paper leaves open (listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - the bit order of a patch value (above) and the readout (a linear map
  *     to 16 logits and a softmax);
  *   - zero magnetisation (u1): a patch value is allowed while neither the

@@ -19,7 +19,7 @@
  *   GLU(y) = (W_a y + b_a) * sigmoid(W_g y + b_g)
  * then softmax(W_o x^(nL) + b_o) over s_t and log psi = 1/2 sum log P.
  *
- * Readings of points the paper leaves open (listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - D is elementwise (D in R^d) for l >= 1 as written; at l = 0 the input
  *     is the 2-entry one-hot, so D^(0) is a d x 2 matrix;
  *   - the single-layer GLU is (W_a y + b_a) * sigmoid(W_g y + b_g);
