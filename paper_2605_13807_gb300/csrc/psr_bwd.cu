@@ -40,15 +40,17 @@ size_t bwd_tape_floats_per_cta(int nL, int H) { return tape_floats(nL, H); }
 // (hc0, hcar, lam, anext: [nL][H] each) are sized by the layer count.
 template <int H>
 struct BwdSmem {
-    float xs[H * LD];        // forward recompute: layer input tile [k][t]
+    union {
+        float xs[H * LD];    // forward recompute: layer input tile [k][t]
+        float gy[H * LD];    // layer loop: gy, one padded row per unit [j][t]
+    };
     float hs[H * LD];        // forward recompute: hidden tile [k][t]
-    float gy[CH * H];        // [t][j]
-    float gzc[2 * CH * H];   // gz, gc [t][j] in the layer loop; before it the
-                             // last-layer output xl [t][k] (padded rows)
+    float gzc[2 * H * LD];   // gz, gc [j][t] (padded unit rows) in the layer
+                             // loop; before it the last-layer output xl [t][k]
     float g1[CH];
     int code[CH];
 };
-static_assert(CH * (128 + 1) <= 2 * CH * 128, "xl fits in the gz / gc storage");
+static_assert(CH * (128 + 1) <= 2 * 128 * LD, "xl fits in the gz / gc storage");
 
 template <int H>
 __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
         V.lam = tail + 2 * nL * H;  // adjoint carry lambda_{t0+CH}
         V.anext = tail + 3 * nL * H;  // a_{t0+CH} of the later chunk
         V.gz = S.gzc;
-        V.gc = S.gzc + CH * H;
+        V.gc = S.gzc + H * LD;
         V.xl = S.gzc;
     }
     const int nch = (N + CH - 1) / CH;
@@ -273,9 +275,12 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
                 const int din = (l == 0) ? 2 : H;
                 float gy[CH];
 #pragma unroll
-                for (int t = 0; t < CH; ++t) {
-                    gy[t] = gx[t] * gelu_grad_f(T(l, TQ_Y, t)[j]);
-                    S.gy[t * H + j] = gy[t];
+                for (int t = 0; t < CH; ++t) gy[t] = gx[t] * gelu_grad_f(T(l, TQ_Y, t)[j]);
+                {
+                    float4 *gyr = reinterpret_cast<float4 *>(S.gy + j * LD);
+#pragma unroll
+                    for (int t4 = 0; t4 < CH / 4; ++t4)
+                        gyr[t4] = make_float4(gy[4 * t4], gy[4 * t4 + 1], gy[4 * t4 + 2], gy[4 * t4 + 3]);
                 }
                 __syncthreads();
                 // k-role: direct dL/dh, D^T gy, dC, dD
@@ -300,13 +305,20 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
                         djk_n = (l >= 1) ? Dw[(int64_t)(jj + 1) * H + j] : 0.0f;
                     }
                     float ac = 0.0f, ad = 0.0f;
+                    const float4 *gr = reinterpret_cast<const float4 *>(S.gy + jj * LD);
 #pragma unroll
-                    for (int t = 0; t < CH; ++t) {
-                        const float g = S.gy[t * H + jj];
-                        ghd[t] += cjk * g;
-                        gud[t] += djk * g;
-                        ac += g * hk[t];
-                        ad += g * uk[t];
+                    for (int t4 = 0; t4 < CH / 4; ++t4) {
+                        const float4 g4 = gr[t4];
+                        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int t = 4 * t4 + e;
+                            const float g = gv[e];
+                            ghd[t] += cjk * g;
+                            gud[t] += djk * g;
+                            ac += g * hk[t];
+                            ad += g * uk[t];
+                        }
                     }
                     atomicAdd(&G[tl.C[l] + (int64_t)jj * H + j], ac);
                     if (l >= 1) atomicAdd(&G[tl.D[l] + (int64_t)jj * H + j], ad);
@@ -335,11 +347,18 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
                         const float ga = lam * (hp - cd);
                         const float gcv = lam * (1.0f - a);
                         const float gzv = ga * a * (1.0f - a);
-                        V.gz[t * H + j] = gzv;
-                        V.gc[t * H + j] = gcv;
+                        ghd[t] = gzv;  // ghd[t] and hk[t] are not read again
+                        hk[t] = gcv;
                         sz += gzv;
                         sc += gcv;
                         an = a;
+                    }
+                    float4 *gzr = reinterpret_cast<float4 *>(V.gz + j * LD);
+                    float4 *gcr = reinterpret_cast<float4 *>(V.gc + j * LD);
+#pragma unroll
+                    for (int t4 = 0; t4 < CH / 4; ++t4) {
+                        gzr[t4] = make_float4(ghd[4 * t4], ghd[4 * t4 + 1], ghd[4 * t4 + 2], ghd[4 * t4 + 3]);
+                        gcr[t4] = make_float4(hk[4 * t4], hk[4 * t4 + 1], hk[4 * t4 + 2], hk[4 * t4 + 3]);
                     }
                     V.lam[l * H + j] = lam;
                     V.anext[l * H + j] = an;
@@ -362,12 +381,19 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
                             wh_n = Whw[(int64_t)(jj + 1) * H + j];
                         }
                         float az = 0.0f, ah = 0.0f;
+                        const float4 *zr = reinterpret_cast<const float4 *>(V.gz + jj * LD);
+                        const float4 *cr = reinterpret_cast<const float4 *>(V.gc + jj * LD);
 #pragma unroll
-                        for (int t = 0; t < CH; ++t) {
-                            const float gzv = V.gz[t * H + jj], gcv = V.gc[t * H + jj];
-                            gn[t] += wz * gzv + wh * gcv;
-                            az += gzv * uk[t];
-                            ah += gcv * uk[t];
+                        for (int t4 = 0; t4 < CH / 4; ++t4) {
+                            const float4 z4 = zr[t4], c4 = cr[t4];
+                            const float zv[4] = {z4.x, z4.y, z4.z, z4.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int t = 4 * t4 + e;
+                                gn[t] += wz * zv[e] + wh * cv[e];
+                                az += zv[e] * uk[t];
+                                ah += cv[e] * uk[t];
+                            }
                         }
                         atomicAdd(&G[tl.Wz[l] + (int64_t)jj * H + j], az);
                         atomicAdd(&G[tl.Wh[l] + (int64_t)jj * H + j], ah);
@@ -381,7 +407,7 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
                     float z0 = 0.0f, z1 = 0.0f, c0v = 0.0f, c1v = 0.0f;
                     for (int t = 0; t < CH; ++t) {
                         const int cd = S.code[t];
-                        const float gzv = V.gz[t * H + j], gcv = V.gc[t * H + j];
+                        const float gzv = V.gz[j * LD + t], gcv = V.gc[j * LD + t];
                         if (cd == 1) { z0 += gzv; c0v += gcv; }
                         if (cd == 2) { z1 += gzv; c1v += gcv; }
                     }
