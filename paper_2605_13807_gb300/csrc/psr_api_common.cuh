@@ -211,7 +211,7 @@ inline int64_t max_entries_per_sample(const psr_hamiltonian *ham) {
 
 // ---------------------------------------------------------------- autotuner
 
-enum { kTuneScan = 1, kTuneSample = 2, kTuneSample2d = 3 };
+enum { kTuneScan = 1, kTuneSample = 2, kTuneSample2d = 3, kTuneSampleLru = 4 };
 
 // Times run(i) for every candidate i on the context's stream with CUDA
 // events (two runs each when a run is short, the second counted) and

@@ -709,18 +709,37 @@ int psr_lru_sample(const psr_params *params, const float *uniforms, int64_t n, i
     if ((rc = stage_in(uniforms, u_ws, (size_t)n * N, d_u, st, &uu)) != PSR_OK) return rc;
     uint8_t *so = d_s ? spins : s_ws;
     float *lo = logpsi ? (d_lp ? logpsi : lp_ws) : nullptr;
-    // samples per CTA: the most that still gives every SM a CTA (weights are
-    // read once per CTA and site, so more samples per CTA read less)
+    // samples per CTA: measured by the autotuner when it is on; otherwise
+    // the most that still gives every SM a CTA (weights are read once per
+    // CTA and site, so more samples per CTA read less)
+    std::vector<int> cands;
+    for (int b : {4, 8, 16})
+        if (sample_lru_smem_bytes(b, nL, H) <= 220 * 1024) cands.push_back(b);
     int per_cta = 4;
     for (int b : {16, 8})
         if ((n + b - 1) / b >= ctx->num_sms && sample_lru_smem_bytes(b, nL, H) <= 220 * 1024) {
             per_cta = b;
             break;
         }
+    const int64_t key2 = (int64_t)nL * 1024 + H;
+    bool tune_now = false;
+    if (const psr_context::Tuned *t = find_tuned(ctx, kTuneSampleLru, n, N, key2))
+        per_cta = t->v0;
+    else if (ctx->autotune && !ctx->capturing) tune_now = true;
     reset_stages(ctx);
     {
         StageScope sc(ctx, PSR_STAGE_PACK);
         PSR_TRY(launch_pack_theta_lru(theta, f, pk, st));
+    }
+    if (tune_now) {
+        int bi = 0;
+        float best = 0.0f;
+        rc = measure_candidates(ctx, (int)cands.size(), [&](int i) {
+            return from_cuda(launch_sample_lru(cands[i], pk, f, uu, n, N, params->u1_mask, so, lo, st));
+        }, &bi, &best);
+        if (rc != PSR_OK) return rc;
+        per_cta = cands[bi];
+        ctx->tuned.push_back(psr_context::Tuned{kTuneSampleLru, n, N, key2, per_cta, 0, best});
     }
     {
         StageScope sc(ctx, PSR_STAGE_SAMPLE);

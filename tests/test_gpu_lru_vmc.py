@@ -83,6 +83,15 @@ def test_samples_do_not_depend_on_the_cta_grouping():
     for s, lp in outs[1:]:
         assert torch.equal(s[:64], outs[0][0]) and torch.equal(lp[:64], outs[0][1])
     assert torch.equal(outs[1][0], outs[2][0][:1280])
+    # the autotuner's measured choice draws the same samples
+    api.set_autotune(True)
+    try:
+        s_t, lp_t = api.sample_lru(theta, u[:1280].contiguous(), cfg)
+        s_t2, _ = api.sample_lru(theta, u[:1280].contiguous(), cfg)  # cached choice
+    finally:
+        api.set_autotune(False)
+    api.sync()
+    assert torch.equal(s_t, outs[1][0]) and torch.equal(lp_t, outs[1][1]) and torch.equal(s_t2, s_t)
 
 
 def test_sampler_frequencies_chi2(oracle_mod):
