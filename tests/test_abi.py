@@ -15,7 +15,7 @@ def _declared():
         if h.endswith(".h"):
             src = open(os.path.join(ROOT, "include", h)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"\b(psr_\w+)\s*\(", src)
+            names += re.findall(r"\b(psr[a-z0-9]*_\w+)\s*\(", src)
     return sorted(set(names))
 
 
