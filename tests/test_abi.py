@@ -92,3 +92,21 @@ def test_library_has_no_oracle_dependency():
     for f in os.listdir(csrc):
         assert "psr_oracle" not in open(os.path.join(csrc, f)).read()
     assert binding.LIB_PATH.endswith("libpsr.so")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libpsr.so every entry point raises: there is no CPU path."""
+    import numpy as np
+
+    from paper_2605_13807_gb300 import api, binding, inputs
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libpsr.so"))
+    with pytest.raises(ImportError):
+        binding.lib()
+    theta = inputs.glorot_params(3, 32, seed=0)
+    spins = np.zeros((2, 8), dtype=np.uint8)
+    with pytest.raises(ImportError):
+        # (a placeholder context handle: the call must fail before using it)
+        binding.psr_logpsi(binding.make_params(theta, 3, 32, ctx=1), spins, np.empty(2, np.float32))
+    with pytest.raises(ImportError):
+        api.param_count(3, 32)
