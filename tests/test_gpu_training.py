@@ -131,3 +131,28 @@ def test_2d_model_on_the_4x4_heisenberg_lattice(oracle_mod, sym, tol):
     e, se = _train2d(4, 32, 3, sym, steps=300, n=1024, lr=5e-3)
     assert e >= e0 - 4 * se
     assert (e - e0) / abs(e0) < tol, (e, e0)
+
+
+def _table1_exact(n_sites):
+    """e_exact(N) of the open TFIM chain at h = 1, read from the Table I
+    fixture (the oracle pins check the fixture against its closed form)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "tfim_obc_h1_exact.txt")
+    for line in open(path):
+        f = line.split()
+        if f and not f[0].startswith("#") and int(f[0]) == n_sites:
+            return float(f[1])
+    raise KeyError(n_sites)
+
+
+@pytest.mark.parametrize("model,tol", [("mingru", 2e-3), ("lru", 5e-4)])
+def test_tfim_chain_of_32_sites_against_table1(model, tol):
+    """Beyond exact diagonalisation: the 32-site open TFIM at h = 1 against
+    the paper's tabulated exact energy (Table I, e_exact = -1.2620098)."""
+    e0 = _table1_exact(32)
+    if model == "mingru":
+        e, se = _train(1, 32, 1, 32, 2, False, 1.0, steps=600, n=1024, lr=1e-2, sym=False)
+    else:
+        e, se = _train_lru(1, 32, 32, 2, False, 1.0, steps=600, n=1024, lr=1e-2)
+    assert e >= e0 - 4 * se
+    assert (e - e0) / abs(e0) < tol, (e, e0)
