@@ -145,14 +145,16 @@ def _table1_exact(n_sites):
     raise KeyError(n_sites)
 
 
-@pytest.mark.parametrize("model,tol", [("mingru", 2e-3), ("lru", 5e-4)])
-def test_tfim_chain_of_32_sites_against_table1(model, tol):
-    """Beyond exact diagonalisation: the 32-site open TFIM at h = 1 against
-    the paper's tabulated exact energy (Table I, e_exact = -1.2620098)."""
-    e0 = _table1_exact(32)
+@pytest.mark.parametrize("model,N,tol", [("mingru", 32, 2e-3), ("lru", 32, 5e-4),
+                                         ("mingru", 64, 2e-3), ("lru", 64, 5e-4)])
+def test_tfim_chain_against_table1(model, N, tol):
+    """Beyond exact diagonalisation: the 32- and 64-site open TFIM at h = 1
+    against the paper's tabulated exact energies (Table I: e_exact =
+    -1.2620098 and -1.2675934)."""
+    e0 = _table1_exact(N)
     if model == "mingru":
-        e, se = _train(1, 32, 1, 32, 2, False, 1.0, steps=600, n=1024, lr=1e-2, sym=False)
+        e, se = _train(1, N, 1, 32, 2, False, 1.0, steps=600, n=1024, lr=1e-2, sym=False)
     else:
-        e, se = _train_lru(1, 32, 32, 2, False, 1.0, steps=600, n=1024, lr=1e-2)
+        e, se = _train_lru(1, N, 32, 2, False, 1.0, steps=600, n=1024, lr=1e-2)
     assert e >= e0 - 4 * se
     assert (e - e0) / abs(e0) < tol, (e, e0)
