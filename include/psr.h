@@ -222,9 +222,22 @@ int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t 
  * set-up (it looks up the array's device address); make that first call
  * before any stream capture begins.  Every call shares the array and leaves
  * its contents behind; calls whose work overlaps on one device race on it.
- * Device-side checks (a spin byte other than 0/1) are not reported. */
+ * The call returns before its kernels run, so device-side failures (a spin
+ * byte other than 0/1: PSR_EDEVICE; an expired bounded wait: PSR_ETIMEOUT; a
+ * tensor-memory allocation not at column 0: PSR_EDEVICE) are not in its
+ * return code: they are recorded in a status word inside the array, and
+ * `out` may then be partly or wholly unwritten.  Read that word with
+ * psr_noalloc_status before the next call on the device clears it. */
 int psr_logpsi_noalloc(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
                        float *out, void *stream);
+
+/* Device-side status of the most recent psr_logpsi_noalloc call on the
+ * current device (service of the library; the paper has no counterpart).
+ * Synchronises `stream` (the stream that call used), then returns the
+ * status word: PSR_OK, PSR_EDEVICE or PSR_ETIMEOUT as described above, or
+ * PSR_ECUDA if the stream or the read failed.  Allocates nothing; the word
+ * is left as it is (the next psr_logpsi_noalloc call clears it). */
+int psr_noalloc_status(void *stream);
 
 /* Standalone scan of the diagonal linear recurrence at the heart of the
  * minGRU layer (Eq. minGRU with a_t = 1 - z_t, b_t = z_t h~_t), evaluated as

@@ -63,7 +63,7 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_lru_param_count", "psr_lru_logpsi", "psr_lru_local_energy", "psr_sym_logpsi",
             "psr_sym_local_energy", "psr_vmc_step", "psr2d_sample", "psr2d_grad", "psr2d_vmc_step",
             "psr_lru_sample", "psr_lru_grad", "psr_lru_vmc_step", "psr2d_sym_logpsi",
-            "psr2d_sym_local_energy")
+            "psr2d_sym_local_energy", "psr_noalloc_status")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -92,6 +92,7 @@ def lib():
                                             C.POINTER(i64)]
                 L.psr_grad.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
                 L.psr_logpsi_noalloc.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
+                L.psr_noalloc_status.argtypes = [vp]
                 L.psr_local_energy_batch.argtypes = [C.POINTER(psr_params), C.POINTER(psr_batch_item), i32]
                 L.psr_context_set_graphs.argtypes = [vp, C.c_int]
                 L.psr_context_set_profiling.argtypes = [vp, C.c_int]
@@ -257,6 +258,16 @@ def psr_logpsi_noalloc(params, spins, out, stream=None):
     _check(lib().psr_logpsi_noalloc(C.byref(params), _ptr(spins), int(n), int(L), _ptr(out),
                                     C.c_void_p(handle)), "psr_logpsi_noalloc")
     return out
+
+
+def psr_noalloc_status(stream=None):
+    """Device-side status code of the last psr_logpsi_noalloc call on the
+    current device (waits for `stream`; allocates nothing)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream or 0)
+    return int(lib().psr_noalloc_status(C.c_void_p(handle)))
 
 
 def psr_context_set_graphs(ctx, enable=True):

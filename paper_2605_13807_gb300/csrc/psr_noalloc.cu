@@ -20,6 +20,13 @@
 // keeps whatever the last call left in it; each call clears the job counter
 // and the status word itself before use.  Two calls whose work overlaps on a
 // device (different streams, or different host threads) race on the array.
+//
+// Status: the kernels record device-side failures (a spin byte other than
+// 0/1, an expired bounded wait, a tensor-memory allocation that does not
+// start at column 0) in a status word at a fixed place in the array; such a
+// call still returns PSR_OK, since it does not wait for its kernels, and may
+// leave `out` partly or wholly unwritten.  psr_noalloc_status reads that word
+// after the call's work has finished, without allocating.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,6 +37,8 @@ namespace {
 
 constexpr size_t kScratchBytes = size_t(8) << 20;  // stated maximum: 8 MiB per device
 constexpr size_t kBitsBytes = size_t(4) << 20;     // bit-packed spins of one batch of samples
+constexpr size_t kOffCounter = kScratchBytes - 512; // job counter (fixed place)
+constexpr size_t kOffStatus = kScratchBytes - 256;  // status word (fixed place, read by psr_noalloc_status)
 constexpr int kMaxDevices = 64;
 
 }  // namespace
@@ -108,16 +117,15 @@ extern "C" int psr_logpsi_noalloc(const psr_params *params, const uint8_t *spins
     const bool bf16 = params->precision == PSR_BF16;
     if (bf16 && (H != 128 || nL != 3)) return PSR_EUNSUPPORTED;
 
-    // Fixed carve-up of the array: packed FP32 weights, BF16 images,
-    // bit-packed spins of one batch, job counter, status word.
+    // Carve-up of the array: packed FP32 weights, BF16 images, bit-packed
+    // spins of one batch; the job counter and the status word sit at fixed
+    // places at its end.
     const ThetaLayout tl = theta_layout(nL, H);
     const F32Layout fl = f32_layout(nL, H);
     const size_t off_pk = 0;
     const size_t off_pkb = align256(off_pk + (size_t)fl.total * sizeof(float));
     const size_t off_bits = align256(off_pkb + (bf16 ? bf16_packed_bytes() : 0));
-    const size_t off_counter = off_bits + kBitsBytes;
-    const size_t off_status = off_counter + 256;
-    if (off_status + 256 > kScratchBytes) return PSR_EINVAL;
+    if (off_bits + kBitsBytes > kOffCounter) return PSR_EINVAL;
     const int64_t W = (L + 63) / 64 + 1;
     const int64_t rows_per_batch = (int64_t)(kBitsBytes / ((size_t)W * sizeof(uint64_t)));
     if (rows_per_batch < 1) return PSR_EINVAL;  // one configuration longer than the array allows
@@ -132,8 +140,8 @@ extern "C" int psr_logpsi_noalloc(const psr_params *params, const uint8_t *spins
     float *pk = reinterpret_cast<float *>(dev->base + off_pk);
     void *pkb = dev->base + off_pkb;
     uint64_t *bits = reinterpret_cast<uint64_t *>(dev->base + off_bits);
-    unsigned long long *counter = reinterpret_cast<unsigned long long *>(dev->base + off_counter);
-    int *status = reinterpret_cast<int *>(dev->base + off_status);
+    unsigned long long *counter = reinterpret_cast<unsigned long long *>(dev->base + kOffCounter);
+    int *status = reinterpret_cast<int *>(dev->base + kOffStatus);
 
     if ((rc = to_rc(cudaMemsetAsync(status, 0, sizeof(int), st))) != PSR_OK) return rc;
     if ((rc = to_rc(launch_pack_theta_f32(params->theta, tl, fl, pk, st))) != PSR_OK) return rc;
@@ -160,4 +168,21 @@ extern "C" int psr_logpsi_noalloc(const psr_params *params, const uint8_t *spins
         if (rc != PSR_OK) return rc;
     }
     return PSR_OK;
+}
+
+extern "C" int psr_noalloc_status(void *stream) {
+    // Waits for the stream, then copies the status word out of the fixed
+    // array by its symbol (no address set-up and no allocation needed).
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return PSR_ECUDA;
+    }
+    int word = 0;
+    if (cudaMemcpyFromSymbol(&word, g_psr_noalloc_scratch, sizeof(int), kOffStatus,
+                             cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return PSR_ECUDA;
+    }
+    return word;
 }

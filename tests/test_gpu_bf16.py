@@ -7,8 +7,9 @@ sums stay FP32.  Tolerances:
   log psi : |d| <= 2e-2 + 2e-5 |log psi|   (spec 2e-2 for N <= 100; the
             relative term covers the growth of independent per-site rounding
             errors with N)
-  E_loc   : |d| <= 1e-2 (|diag| + sum_e |c_e ratio_e|)  (a BF16 ratio error of
-            a few 1e-3 per connected configuration)
+  E_loc   : |d| <= 1e-3 (|diag| + sum_e |c_e ratio_e|)  (the stated relative
+            bound; a connected configuration shares its prefix with the
+            sample, so most of the BF16 rounding cancels in the ratio)
 With BF16-representable parameters the weight rounding vanishes and only
 activation rounding remains; those runs use tolerances 5x tighter.
 """
@@ -105,7 +106,7 @@ def test_local_energy_bf16_matches_oracle(oracle_mod, kind, Lx, Ly, pbc, u1, hf,
                                   h=hf, u1=u1)
     _, _, diag = oracle_mod.connected(kind, Lx, Ly, pbc, spins)
     scale = np.abs(diag) + np.abs(ref - diag)
-    assert np.all(np.abs(e - ref) <= 1e-2 * scale), (np.abs(e - ref) / scale).max()
+    assert np.all(np.abs(e - ref) <= 1e-3 * scale), (np.abs(e - ref) / scale).max()
     assert abs(st[0] - np.mean(e)) <= 1e-6 * max(1.0, abs(st[0]))
 
 

@@ -160,3 +160,31 @@ def test_energy_gradient_ignores_a_constant_energy_shift(oracle_mod):
     g1, m1 = vmc.energy_gradient(e + 5.0, ok)
     assert abs(m1 - m0 - 5.0) < 1e-12
     assert np.max(np.abs(g1 - g0)) < 1e-12 * max(1.0, np.max(np.abs(g0)))
+
+
+def test_finite_difference_gradient_helper_matches_reverse_mode(oracle_mod):
+    """The GPU tests' oracle-only energy-gradient reference (tests/fdcheck.py)
+    agrees with the energy-gradient estimator over the oracle's analytic
+    reverse-mode O_k (chain model, plain and c4v-symmetrised), and rejects a
+    gradient with the centring dropped or the image weights replaced by 1/8."""
+    import fdcheck
+
+    nL, H, L = 2, 4, 4
+    theta = _theta(nL, H, seed=720)
+    s = inputs.zero_magnetisation_spins(721, 24, L * L)
+    e = inputs.uniform(722, (24,)) * 3.0 - 1.0   # any energies: the helper only weights them
+    _, ok = oracle_mod.grad(theta, nL, H, s, u1=True)
+    g, _ = vmc.energy_gradient(e, ok)
+    lp = lambda t: oracle_mod.logpsi(t, nL, H, s, u1=True)  # noqa: E731
+    fdcheck.check_energy_gradient(g, lp, theta, e, seed=723, n_top=8, n_rand=8)
+    with pytest.raises(AssertionError):  # centring dropped
+        fdcheck.check_energy_gradient(2.0 * (e @ ok) / e.size, lp, theta, e, seed=723, n_top=8, n_rand=8)
+    ok_sym = vmc.grad_logpsi_sym(theta, nL, H, s, L, u1=True)
+    g_sym, _ = vmc.energy_gradient(e, ok_sym)
+    lps = lambda t: vmc.logpsi_sym(lambda x: oracle_mod.logpsi(t, nL, H, x, u1=True), s, L)  # noqa: E731
+    fdcheck.check_energy_gradient(g_sym, lps, theta, e, seed=724, n_top=8, n_rand=8)
+    imgs = vmc.c4v_images(s, L)
+    ok_avg = np.mean([oracle_mod.grad(theta, nL, H, x, u1=True)[1] for x in imgs], axis=0)
+    with pytest.raises(AssertionError):  # equal image weights instead of psi(g s)^2
+        fdcheck.check_energy_gradient(vmc.energy_gradient(e, ok_avg)[0], lps, theta, e, seed=724,
+                                      n_top=8, n_rand=8)

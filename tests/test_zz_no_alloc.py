@@ -65,7 +65,8 @@ def _close(got, ref, precision):
 
 def test_two_calls_in_a_row_match_psr_logpsi():
     first = _case(3, 64, 100, 300, True, "fp32", 1)
-    # 12000 samples of 2704 sites need three batches through the fixed array
+    # 12000 samples of 2704 sites need two batches through the fixed array
+    # (11,915 rows of 44 words each fit its 4 MiB spin region)
     second = _case(3, 128, 2704, 12000, True, "bf16", 2)
     ref1 = _reference(*first)
     ref2 = _reference(*second)
@@ -73,6 +74,7 @@ def test_two_calls_in_a_row_match_psr_logpsi():
     got2 = _noalloc(*second)
     _close(got1, ref1, "fp32")
     _close(got2, ref2, "bf16")
+    assert B.psr_noalloc_status() == B.PSR_OK
     # the array keeps the last call's contents; a later call must not depend on them
     _close(_noalloc(*first), ref1, "fp32")
 
@@ -101,3 +103,18 @@ def test_rejects_host_arrays_and_oversized_configurations():
     rc = B.lib().psr_logpsi_noalloc(C.byref(p), C.c_void_p(spins.data_ptr()), 1, 33554369,
                                     C.c_void_p(out.data_ptr()), None)
     assert rc == B.PSR_EINVAL
+
+
+def test_device_side_failure_is_visible_through_the_status_query():
+    """A spin byte other than 0/1 is found by a kernel, after the call has
+    returned PSR_OK; the status query reports it, and the next clean call
+    clears it."""
+    theta, spins, cfg = _case(3, 32, 16, 4, False, "fp32", 5)
+    out = torch.empty(4, dtype=torch.float32, device="cuda")
+    bad = spins.clone()
+    bad[2, 7] = 2
+    B.psr_logpsi_noalloc(_params(theta, cfg), bad, out)
+    assert B.psr_noalloc_status() == B.PSR_EDEVICE
+    got = _noalloc(theta, spins, cfg)
+    assert B.psr_noalloc_status() == B.PSR_OK
+    _close(got, _reference(theta, spins, cfg), "fp32")
