@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--no-lru", action="store_true")
     ap.add_argument("--no-vmc", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="only the mixed-lattice batch leg")
     ap.add_argument("--samples-2d", type=int, default=32,
                     help="samples of the 2D patched-model leg (52x52, FP32)")
     ap.add_argument("--scan-only", action="store_true",
@@ -78,6 +81,8 @@ def parse():
     ap.add_argument("--paper2d-warmup", type=int, default=1,
                     help="untimed steps before the timed ones (the sampler is tuned in any case)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--fwd-shape", type=int, default=0,
+                    help="BF16 forward shape: sequences per MMA stream (1 or 2); 0 = the library's choice")
     return ap.parse_args()
 
 
@@ -517,6 +522,99 @@ def lru_leg(dev, N=256, H=64, n=1024, reps=3):
                          "launch_ms": conn_ms}}
 
 
+# The mixed persistent batch: 2D Heisenberg 16x16, 24x24, 32x32 (open, zero
+# magnetisation, Neel-like samples) and the 2D TFIM 20x20 at h/J = 3.044
+# (open, uniform random spins), 2048 samples each, hidden 128, BF16.
+MIXED_SPEC = (("heisenberg", 16, True, 0.0), ("heisenberg", 24, True, 0.0),
+              ("heisenberg", 32, True, 0.0), ("tfim", 20, False, 3.044))
+
+
+def mixed_leg(dev, n=2048, reps=3, warmup=2):
+    """One hot-path step (log psi, per-sample O_k and E_loc over every
+    connected configuration) of four sample sets on different lattices and
+    Hamiltonians in one psr_step_batch call: one launch per kernel of the
+    step over all lattices, the forward shape picked by the autotuner on the
+    first call, the launch sequence captured in a CUDA graph on the next and
+    replayed in the timed steps."""
+    import torch
+
+    from paper_2605_13807_gb300 import api, binding as B, inputs
+    theta = torch.from_numpy(inputs.glorot_params(N_LAYERS, HIDDEN, seed=0)).to(dev)
+    P = theta.numel()
+    items, logical, evaluated_conn, evaluated = [], 0, 0, 0
+    for k, (kind, L, u1, hf) in enumerate(MIXED_SPEC):
+        N = L * L
+        s = (inputs.neel_like_spins(3000 + k, n, L, L) if kind == "heisenberg"
+             else inputs.random_spins(3000 + k, n, N))
+        sp = torch.from_numpy(s).to(dev)
+        ham = B.make_hamiltonian(kind, L, L, False, True, 1.0, hf)
+        _, ent, _ = api.connected(sp, ham)
+        E = int(ent.shape[0])
+        p = ent[:, 1].to(torch.int64)
+        conn = int((N - (p // CHUNK_BF16) * CHUNK_BF16).sum().item())
+        logical += (n + E) * N
+        evaluated_conn += conn
+        evaluated += n * N + conn
+        out = {"logpsi": torch.empty(n, dtype=torch.float32, device=dev),
+               "eloc": torch.empty(n, dtype=torch.float32, device=dev),
+               "stats": torch.empty(3, dtype=torch.float64, device=dev),
+               "grad": torch.empty((n, P), dtype=torch.float32, device=dev)}
+        items.append((sp, ham, u1, out, E, f"{kind}_{L}x{L}"))
+        del ent, p
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.context(stream)
+    p_ = B.make_params(theta, N_LAYERS, HIDDEN, False, "bf16", ctx)
+    args = [(sp, ham, u1, o["logpsi"], o["eloc"], o["stats"], o["grad"]) for sp, ham, u1, o, _, _ in items]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        # uncaptured call with the tuner on (picks the forward shape of this
+        # batch) and per-stage events (connected-forward time for the roofline)
+        B.psr_context_set_autotune(ctx, True)
+        B.psr_step_batch(p_, args)
+        B.psr_context_set_autotune(ctx, False)
+        B.psr_context_set_profiling(ctx, True)
+        B.psr_step_batch(p_, args)
+        stages = B.psr_context_stage_ms(ctx)
+        B.psr_context_set_profiling(ctx, False)
+        B.psr_context_set_graphs(ctx, True)
+        for _ in range(warmup):           # capture, then replays
+            B.psr_step_batch(p_, args)
+        B.psr_context_sync(ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            B.psr_step_batch(p_, args)
+        e1.record(stream)
+        e1.synchronize()
+        B.psr_context_sync(ctx)
+        B.psr_context_set_graphs(ctx, False)
+    ms = e0.elapsed_time(e1) / reps
+    conn_ms = stages["fwd_connected"]
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    achieved = evaluated_conn * MMA_FLOPS_PER_SITE / (conn_ms / 1e3) / 1e12
+    res = {"workload": "mixed batch: heisenberg 16x16, 24x24, 32x32 OBC + tfim 20x20 OBC h/J=3.044, "
+                       f"{n} samples each, hidden 128, BF16",
+           "call": "psr_step_batch (log psi + O_k + E_loc), CUDA-graph replay",
+           "value": logical / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "logical_units_per_step": logical, "evaluated_units_per_step": evaluated,
+           "stages_ms_uncaptured": stages,
+           "items": {name: {"connected": E, "mean_energy_per_site": float(o["stats"][0].item()) / (h.Lx * h.Ly)}
+                     for _, h, _, o, E, name in items},
+           "roofline": {"kernel": "fwd_bf16_kernel (connected configurations of all four lattices, one launch)",
+                        "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                        "traffic": None, "launch_ms": conn_ms, "units_per_launch": evaluated_conn,
+                        "flops_per_unit": MMA_FLOPS_PER_SITE}}
+    shape, tuned = B.psr_fwd_shape_for(ctx, "bf16", 2, [n] * len(MIXED_SPEC),
+                                       [L * L for _, L, _, _ in MIXED_SPEC])
+    res["bf16_seqs_per_mma_stream"] = {"shape": shape, "tuned": tuned}
+    del items, args
+    torch.cuda.empty_cache()
+    return res
+
+
 def vmc_leg(dev, L=10, n=1024, reps=3):
     """One full on-device VMC step (exact sampling, E_loc, energy gradient,
     Adam; the paper's definition of a training step, Sec. III.A) for the
@@ -631,6 +729,16 @@ def run_paper2d_only(args):
     return 0
 
 
+def run_mixed_only(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"mixed_batch": mixed_leg(torch.device("cuda", 0))}), flush=True)
+    return 0
+
+
 def run_scan_only(args):
     import torch
 
@@ -683,6 +791,9 @@ def run_mine(args):
 
     ctx = B.context()
     B.psr_context_set_profiling(ctx, True)
+    if args.fwd_shape:
+        api.set_fwd_shape("bf16", args.fwd_shape)
+    fwd_shape = api.fwd_shape_for("bf16", 1, n, N)[0]
 
     def step():
         api.logpsi(theta, spins, cfg, out=lp)
@@ -753,6 +864,7 @@ def run_mine(args):
         "config": {"workload": f"heisenberg_{Lx}x{Ly}_obc_{n}_samples", "lattice": f"{Lx}x{Ly} OBC",
                    "samples_per_gpu": n, "hidden": HIDDEN, "layers": N_LAYERS,
                    "precision": "BF16 tcgen05 projections, FP32 scan/softmax, FP32 backward",
+                   "bf16_seqs_per_mma_stream": fwd_shape,
                    "connected_per_step": E, "logical_units_per_step": logical,
                    "evaluated_units_per_step": evaluated,
                    "l2": "256 MB buffer written between timed steps",
@@ -801,6 +913,8 @@ def run_mine(args):
         line["model2d"] = model2d_leg(Lx, Ly, min(args.samples_2d, n), dev)
     if not args.no_lru and rank == 0:
         line["lru"] = lru_leg(dev)
+    if not args.no_mixed and rank == 0:
+        line["mixed_batch"] = mixed_leg(dev)
     if not args.no_vmc and rank == 0:
         line["vmc_step"] = vmc_leg(dev)
         line["paper2d_vmc_step"] = paper2d_leg(dev, sizes=paper2d_sizes(args), reps=args.paper2d_reps,
@@ -854,6 +968,8 @@ def main():
         return run_scan_only(args)
     if args.paper2d_only:
         return run_paper2d_only(args)
+    if args.mixed_only:
+        return run_mixed_only(args)
     return run_mine(args)
 
 

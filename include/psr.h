@@ -191,8 +191,41 @@ typedef struct {
 int psr_local_energy_batch(const psr_params *params, const psr_batch_item *items,
                            int32_t n_items);
 
+/* One sample set of a full mixed-batch step: its own lattice, size and
+ * Hamiltonian, the model shared with the other items.  Each output may be
+ * NULL (not computed); at least one must be given. */
+typedef struct {
+    const uint8_t *samples; /* uint8 [n][Lx*Ly] in sequence order, host or device */
+    int64_t n;              /* >= 1 */
+    psr_hamiltonian ham;    /* lattice (and, for eloc, the Hamiltonian) */
+    int32_t u1_mask;        /* zero-magnetisation masking for this item (params->u1_mask is ignored) */
+    float *logpsi;          /* float [n]: log psi, as psr_logpsi gives it, or NULL */
+    float *eloc;            /* float [n]: E_loc, as psr_local_energy gives it, or NULL */
+    double *stats;          /* double [3] {mean, variance, standard error} of E_loc, or NULL (needs eloc) */
+    float *grad;            /* float [n][P]: O_k rows, as psr_grad with dout = NULL gives them, or NULL */
+} psr_step_item;
+
+/* The hot path of one VMC step (log psi, per-sample O_k = d log psi / d theta
+ * and E_loc over every connected configuration; Sec. II.A local-energy
+ * paragraph, Sec. III.B) for up to 8 sample sets that share one model, e.g.
+ * several lattice sizes and both Hamiltonians.  Each item gets what
+ * psr_logpsi, psr_local_energy and psr_grad (dout = NULL) would give it with
+ * the same forward shape (psr_context_set_fwd_shape): bit for bit.  One
+ * launch covers the sample forwards of all items, one persistent launch the
+ * connected configurations of all items (ragged over samples and lattices),
+ * one launch the gradient forwards and one the reverse-scan gradients; the
+ * generator, packing and gather kernels run per item.  The forward shape is
+ * tuned per batch (sizes of all items) when the autotuner is on.  With
+ * graphs enabled (psr_context_set_graphs), a non-default stream and device
+ * arrays only, the launch sequence is captured into a CUDA graph on the
+ * first call (after the autotuner, if on, has tuned the batch on an earlier
+ * uncaptured call) and replayed by later calls with the same arguments.
+ * PSR_EINVAL for n_items outside 1..8, an item with no output, stats without
+ * eloc, or any item the single calls would reject. */
+int psr_step_batch(const psr_params *params, const psr_step_item *items, int32_t n_items);
+
 /* Enables (1) or disables (0) CUDA-graph capture and replay of
- * psr_local_energy_batch on this context. */
+ * psr_local_energy_batch and psr_step_batch on this context. */
 int psr_context_set_graphs(psr_context *ctx, int enable);
 
 /* Gradient of log psi (Sec. III.B: stochastic energy-gradient estimates).
@@ -300,15 +333,39 @@ int psr_sample_tile_for(psr_context *ctx, int64_t n, int32_t L, int32_t n_layers
 int psr_selftest_wait_timeout(psr_context *ctx, float *elapsed_ms);
 
 /* Enables (1) or disables (0) the autotuner of this context.  While enabled,
- * the first call of psr_scan or psr_sample for a shape it has not seen
- * (scan: n, N, H; sample: n, L, layers, hidden), when not being captured
- * into a graph, times every candidate tile shape (scan: unit-block width x
- * chunk length; sample: samples per CTA) on its own inputs with CUDA events,
- * keeps the fastest for the context's lifetime and then computes its result
- * with it; that first call synchronises the stream.  Every scan tile
- * computes the same recurrence (results differ only by FP32 rounding of the
- * composed maps); every sampler tile gives identical samples. */
+ * the first call of psr_scan, psr_sample, psr_logpsi, psr_local_energy,
+ * psr_local_energy_batch or psr_step_batch for a shape it has not seen
+ * (scan: n, N, H; sample: n, L, layers, hidden; the forwards: precision,
+ * kind of call and the sizes of every sample set), when not being captured
+ * into a graph, times every candidate (scan: unit-block width x chunk
+ * length; sample: samples per CTA; the fused forwards: their shape, see
+ * psr_context_set_fwd_shape) on its own inputs with CUDA events, keeps the
+ * fastest for the context's lifetime and then computes its result with it;
+ * that first call synchronises the stream.  Every scan tile computes the
+ * same recurrence (results differ only by FP32 rounding of the composed
+ * maps); every sampler tile gives identical samples; the BF16 forward shapes
+ * give identical results, the FP32 chunk lengths results that differ by FP32
+ * summation order. */
 int psr_context_set_autotune(psr_context *ctx, int enable);
+
+/* Shape of the fused forward kernels (log psi, and the sample and connected
+ * forwards of E_loc).  precision PSR_BF16: sequences per MMA stream of the
+ * tcgen05 kernel, 1 (four streams per SM, MMA N = 32 sites) or 2 (two
+ * streams, N = 64: each shared-memory weight slice serves twice the sites);
+ * PSR_FP32: scan chunk of the SIMT kernel, 32 or 16 sites.  shape 0 returns
+ * the choice to the context (the autotuned shape, else the built-in
+ * default); any other value fixes it for every later call.  PSR_EINVAL for
+ * another shape.  The paper has no counterpart (a tuning choice). */
+int psr_context_set_fwd_shape(psr_context *ctx, int32_t precision, int32_t shape);
+
+/* The forward shape a call would use on this context: what = 0 for
+ * psr_logpsi of n[0] configurations of L[0] sites, 1 for psr_local_energy
+ * of n[0] samples of L[0] sites (n_sets = 1 for both), 2 for
+ * psr_local_energy_batch or a psr_step_batch whose n_sets items all ask
+ * for E_loc (n[i] samples of L[i] sites each, in item order).  *tuned = 1
+ * when it comes from the autotuner.  tuned may be NULL. */
+int psr_fwd_shape_for(psr_context *ctx, int32_t precision, int32_t what, int32_t n_sets,
+                      const int64_t *n, const int32_t *L, int32_t *shape, int32_t *tuned);
 
 /* ---------------------------------------------------------------------
  * The paper's two-dimensional patched minGRU (Sec. II.F, two-dimensional

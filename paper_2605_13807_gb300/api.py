@@ -78,6 +78,40 @@ def local_energy_batch(theta, batch, cfg: ModelConfig, outs=None, stats=None):
     return outs, stats
 
 
+def step_batch(theta, batch, cfg: ModelConfig, want=("logpsi", "eloc", "grad"), outs=None):
+    """One hot-path step (log psi, E_loc with stats, per-sample O_k) for several
+    sample sets in one call: batch is a list of (samples, hamiltonian,
+    u1_mask).  Returns a list of dicts with the requested outputs."""
+    dev = _device_of(theta, *[b[0] for b in batch])
+    P = theta.numel()
+    if outs is None:
+        outs = []
+        for s, _, _ in batch:
+            n = s.shape[0]
+            o = {}
+            if "logpsi" in want:
+                o["logpsi"] = torch.empty(n, dtype=torch.float32, device=dev)
+            if "eloc" in want:
+                o["eloc"] = torch.empty(n, dtype=torch.float32, device=dev)
+                o["stats"] = torch.empty(3, dtype=torch.float64, device=dev)
+            if "grad" in want:
+                o["grad"] = torch.empty((n, P), dtype=torch.float32, device=dev)
+            outs.append(o)
+    p = B.make_params(theta, cfg.n_layers, cfg.hidden, cfg.u1, cfg.precision, _ctx())
+    B.psr_step_batch(p, [(s, h, u1, o.get("logpsi"), o.get("eloc"), o.get("stats"), o.get("grad"))
+                         for (s, h, u1), o in zip(batch, outs)])
+    return outs
+
+
+def set_fwd_shape(precision, shape):
+    """Fixes the fused forward's shape on the context (0: autotuned / default)."""
+    B.psr_context_set_fwd_shape(_ctx(), precision, shape)
+
+
+def fwd_shape_for(precision, what, n, L):
+    return B.psr_fwd_shape_for(_ctx(), precision, what, n, L)
+
+
 def max_entries(ham: B.psr_hamiltonian, n: int) -> int:
     N = ham.Lx * ham.Ly
     if ham.kind == B.PSR_TFIM:

@@ -54,6 +54,12 @@ class psr_batch_item(C.Structure):
                 ("u1_mask", C.c_int32), ("out", C.c_void_p), ("stats", C.c_void_p)]
 
 
+class psr_step_item(C.Structure):
+    _fields_ = [("samples", C.c_void_p), ("n", C.c_int64), ("ham", psr_hamiltonian),
+                ("u1_mask", C.c_int32), ("logpsi", C.c_void_p), ("eloc", C.c_void_p),
+                ("stats", C.c_void_p), ("grad", C.c_void_p)]
+
+
 EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "psr_param_count",
             "psr_logpsi", "psr_local_energy", "psr_connected", "psr_grad", "psr_strerror",
             "psr_context_set_profiling", "psr_context_stage_ms", "psr_logpsi_noalloc",
@@ -63,7 +69,8 @@ EXPORTED = ("psr_context_create", "psr_context_destroy", "psr_context_sync", "ps
             "psr_lru_param_count", "psr_lru_logpsi", "psr_lru_local_energy", "psr_sym_logpsi",
             "psr_sym_local_energy", "psr_vmc_step", "psr2d_sample", "psr2d_grad", "psr2d_vmc_step",
             "psr_lru_sample", "psr_lru_grad", "psr_lru_vmc_step", "psr2d_sym_logpsi",
-            "psr2d_sym_local_energy", "psr_noalloc_status")
+            "psr2d_sym_local_energy", "psr_noalloc_status", "psr_step_batch",
+            "psr_context_set_fwd_shape", "psr_fwd_shape_for")
 STAGES = ("pack", "generator", "fwd_samples", "fwd_connected", "gather", "bwd", "scan", "sample")
 
 _lib = None
@@ -94,6 +101,10 @@ def lib():
                 L.psr_logpsi_noalloc.argtypes = [C.POINTER(psr_params), vp, i64, i32, vp, vp]
                 L.psr_noalloc_status.argtypes = [vp]
                 L.psr_local_energy_batch.argtypes = [C.POINTER(psr_params), C.POINTER(psr_batch_item), i32]
+                L.psr_step_batch.argtypes = [C.POINTER(psr_params), C.POINTER(psr_step_item), i32]
+                L.psr_context_set_fwd_shape.argtypes = [vp, i32, i32]
+                L.psr_fwd_shape_for.argtypes = [vp, i32, i32, i32, C.POINTER(i64), C.POINTER(i32),
+                                                C.POINTER(i32), C.POINTER(i32)]
                 L.psr_context_set_graphs.argtypes = [vp, C.c_int]
                 L.psr_context_set_profiling.argtypes = [vp, C.c_int]
                 L.psr_context_stage_ms.argtypes = [vp, C.c_int, C.POINTER(C.c_float)]
@@ -285,6 +296,43 @@ def psr_local_energy_batch(params, items):
         arr[k].out = _ptr(out)
         arr[k].stats = _ptr(stats)
     _check(lib().psr_local_energy_batch(C.byref(params), arr, len(items)), "psr_local_energy_batch")
+
+
+def psr_step_batch(params, items):
+    """items: sequence of (samples, hamiltonian, u1_mask, logpsi, eloc, stats, grad),
+    each output an array or None."""
+    arr = (psr_step_item * len(items))()
+    for k, (samples, ham, u1, logpsi, eloc, stats, grad) in enumerate(items):
+        arr[k].samples = _ptr(samples)
+        arr[k].n = int(samples.shape[0])
+        arr[k].ham = ham
+        arr[k].u1_mask = int(u1)
+        arr[k].logpsi = _ptr(logpsi)
+        arr[k].eloc = _ptr(eloc)
+        arr[k].stats = _ptr(stats)
+        arr[k].grad = _ptr(grad)
+    _check(lib().psr_step_batch(C.byref(params), arr, len(items)), "psr_step_batch")
+
+
+def psr_context_set_fwd_shape(ctx, precision, shape):
+    """Fixes the fused forward's shape (BF16: 1 or 2 sequences per MMA stream;
+    FP32: 32- or 16-site chunks); 0 returns the choice to the context."""
+    _check(lib().psr_context_set_fwd_shape(C.c_void_p(ctx), _PRECISION[precision], int(shape)),
+           "psr_context_set_fwd_shape")
+
+
+def psr_fwd_shape_for(ctx, precision, what, n, L):
+    """(shape, tuned) a call would use: what 0 = log psi, 1 = E_loc (n, L
+    integers), 2 = a batch whose items all ask for E_loc (n, L sequences)."""
+    ns = [int(x) for x in (n if what == 2 else [n])]
+    Ls = [int(x) for x in (L if what == 2 else [L])]
+    na = (C.c_int64 * len(ns))(*ns)
+    la = (C.c_int32 * len(Ls))(*Ls)
+    shape = C.c_int32()
+    tuned = C.c_int32()
+    _check(lib().psr_fwd_shape_for(C.c_void_p(ctx), _PRECISION[precision], int(what), len(ns), na, la,
+                                   C.byref(shape), C.byref(tuned)), "psr_fwd_shape_for")
+    return shape.value, bool(tuned.value)
 
 
 def psr_scan(ctx, a, b, h, h0=None, tile=None):

@@ -1,6 +1,6 @@
 // C ABI of libpsr, chain minGRU model: errors, contexts, log psi, the
-// connected-configuration generator, local energy (single and batched) and
-// the gradient.  The argument checks, workspace carving and staging are in
+// connected-configuration generator, local energy and the gradient (the
+// batched forms are in psr_api_batch.cu).  The argument checks, workspace carving and staging are in
 // psr_api_common.cuh; all compute happens in the kernels.
 #include "psr_api_common.cuh"
 
@@ -145,7 +145,6 @@ int psr_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_
         PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
         if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
         PSR_TRY(launch_bitpack(sp, n, L, W, bits, ctx->status, st));
-        PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
     }
     FwdJobs jb{};
     jb.mode = 0;
@@ -158,11 +157,19 @@ int psr_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_
     jb.g[0].out = o;
     jb.job_counter = counter;
     jb.status = ctx->status;
-    {
+    const int32_t Ns[1] = {L};
+    const int64_t ns[1] = {n};
+    const FwdKey key = fwd_key(bf16, 0, 1, Ns, ns);
+    auto run_fwd = [&](int shape) -> int {
         StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
-        if (bf16) PSR_TRY(launch_fwd_bf16(jb, pkb, pk, fl, ctx->num_sms, st));
-        else PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st));
-    }
+        PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+        if (bf16) PSR_TRY(launch_fwd_bf16(jb, pkb, pk, fl, ctx->num_sms, st, shape));
+        else PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st, shape));
+        return PSR_OK;
+    };
+    int shape = 0;
+    if ((rc = tune_fwd_shape(ctx, bf16, key, run_fwd, &shape)) != PSR_OK) return rc;
+    if ((rc = run_fwd(shape)) != PSR_OK) return rc;
     if (!d_out) {
         PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
     }
@@ -234,8 +241,9 @@ int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n
     psr_context *ctx = params->ctx;
     const int nL = params->n_layers, H = params->hidden;
     const bool bf16 = params->precision == PSR_BF16;
-    const int CH = bf16 ? kChunkBF16 : kChunkF32;
-    const int nch = (N + CH - 1) / CH;
+    // carries sized for the shortest chunk any forward shape uses
+    const int CHmin = bf16 ? kChunkBF16 : kChunkGrad;
+    const int nch = (N + CHmin - 1) / CHmin;
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
                d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
     const ThetaLayout tl = theta_layout(nL, H);
@@ -292,7 +300,6 @@ int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n
         PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
         if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
         PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));
-        PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
     }
     HamDev hd{};
     {
@@ -328,16 +335,26 @@ int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n
     jc.g[0].out = delta;
     jc.job_counter = counters + 1;
     jc.status = ctx->status;
-    {
-        StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
-        if (bf16) PSR_TRY(launch_fwd_bf16(js, pkb, pk, fl, ctx->num_sms, st));
-        else PSR_TRY(launch_fwd_f32(js, pk, fl, ctx->num_sms, st));
-    }
-    if (cap > 0) {
-        StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
-        if (bf16) PSR_TRY(launch_fwd_bf16(jc, pkb, pk, fl, ctx->num_sms, st));
-        else PSR_TRY(launch_fwd_f32(jc, pk, fl, ctx->num_sms, st));
-    }
+    const int32_t Ns[1] = {N};
+    const int64_t ns[1] = {n};
+    const FwdKey key = fwd_key(bf16, 1, 1, Ns, ns);
+    auto run_fwd = [&](int shape) -> int {
+        PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
+        {
+            StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
+            if (bf16) PSR_TRY(launch_fwd_bf16(js, pkb, pk, fl, ctx->num_sms, st, shape));
+            else PSR_TRY(launch_fwd_f32(js, pk, fl, ctx->num_sms, st, shape));
+        }
+        if (cap > 0) {
+            StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
+            if (bf16) PSR_TRY(launch_fwd_bf16(jc, pkb, pk, fl, ctx->num_sms, st, shape));
+            else PSR_TRY(launch_fwd_f32(jc, pk, fl, ctx->num_sms, st, shape));
+        }
+        return PSR_OK;
+    };
+    int shape = 0;
+    if ((rc = tune_fwd_shape(ctx, bf16, key, run_fwd, &shape)) != PSR_OK) return rc;
+    if ((rc = run_fwd(shape)) != PSR_OK) return rc;
     {
         StageScope sc(ctx, PSR_STAGE_GATHER);
         PSR_TRY(launch_eloc_gather(b.offsets, delta, b.diag, hd.coeff, n, o, st));
@@ -450,220 +467,5 @@ int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t 
     return PSR_OK;
 }
 
-
-int psr_local_energy_batch(const psr_params *params, const psr_batch_item *items, int32_t n_items) {
-    if (!params || !items || n_items < 1 || n_items > kMaxGroups) return PSR_EINVAL;
-    int rc;
-    for (int i = 0; i < n_items; ++i) {
-        const psr_batch_item &it = items[i];
-        if ((rc = check_ham(&it.ham)) != PSR_OK) return rc;
-        if (it.u1_mask != 0 && it.u1_mask != 1) return PSR_EINVAL;
-        psr_params pi = *params;
-        pi.u1_mask = it.u1_mask;
-        if ((rc = check_params(&pi, it.n, it.ham.Lx * it.ham.Ly)) != PSR_OK) return rc;
-        if (!it.samples || !it.out) return PSR_EINVAL;
-    }
-    psr_context *ctx = params->ctx;
-    const int nL = params->n_layers, H = params->hidden;
-    const bool bf16 = params->precision == PSR_BF16;
-    const int CH = bf16 ? kChunkBF16 : kChunkF32;
-    const ThetaLayout tl = theta_layout(nL, H);
-    const F32Layout fl = f32_layout(nL, H);
-    const bool d_theta = is_device_ptr(params->theta);
-    bool d_s[kMaxGroups], d_out[kMaxGroups], d_st[kMaxGroups];
-    bool all_device = d_theta;
-    for (int i = 0; i < n_items; ++i) {
-        d_s[i] = is_device_ptr(items[i].samples);
-        d_out[i] = is_device_ptr(items[i].out);
-        d_st[i] = items[i].stats ? is_device_ptr(items[i].stats) : true;
-        all_device = all_device && d_s[i] && d_out[i] && d_st[i];
-    }
-
-    struct ItemWs {
-        uint8_t *s_ws;
-        float *out_ws;
-        double *stats_ws;
-        uint64_t *bits;
-        ConnBufs b;
-        float *lpsi, *logp, *carries, *delta;
-        int N, W, nch, nb;
-        int64_t cap;
-    } w[kMaxGroups];
-    for (int i = 0; i < n_items; ++i) {
-        const psr_hamiltonian &hm = items[i].ham;
-        w[i].N = hm.Lx * hm.Ly;
-        w[i].W = (int)words_per_row(w[i].N);
-        w[i].nch = (w[i].N + CH - 1) / CH;
-        w[i].nb = bond_count(hm.Lx, hm.Ly, hm.pbc);
-        w[i].cap = items[i].n * max_entries_per_sample(&hm);
-    }
-    float *theta_ws = nullptr, *pk = nullptr;
-    void *pkb = nullptr;
-    unsigned long long *counters = nullptr;
-    auto carve = [&](Carver &c) {
-        theta_ws = c.get<float>(d_theta ? 0 : tl.total);
-        pk = c.get<float>(fl.total);
-        pkb = c.get<char>(bf16 ? bf16_packed_bytes() : 0);
-        counters = c.get<unsigned long long>(2);
-        for (int i = 0; i < n_items; ++i) {
-            const int64_t n = items[i].n;
-            ItemWs &x = w[i];
-            x.s_ws = c.get<uint8_t>(d_s[i] ? 0 : (size_t)n * x.N);
-            x.out_ws = c.get<float>(d_out[i] ? 0 : n);
-            x.stats_ws = c.get<double>(d_st[i] ? 0 : 3);
-            x.bits = c.get<uint64_t>((size_t)n * x.W);
-            x.b.bonds = c.get<int32_t>(2 * (size_t)x.nb + 2);
-            x.b.counts = c.get<int64_t>(n);
-            x.b.offsets = c.get<int64_t>(n + 1);
-            x.b.diag = c.get<float>(n);
-            x.b.entries = c.get<int32_t>(3 * (size_t)x.cap);
-            x.lpsi = c.get<float>(n);
-            x.logp = c.get<float>((size_t)n * x.N);
-            x.carries = c.get<float>((size_t)n * x.nch * nL * H);
-            x.delta = c.get<float>(x.cap);
-        }
-    };
-    Carver sz;
-    carve(sz);
-    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
-    Carver cv;
-    cv.base = static_cast<char *>(ctx->ws);
-    carve(cv);
-    cudaStream_t st = ctx->stream;
-
-    // graph replay when the arguments are the ones the cached graph was built for
-    const bool use_graph = ctx->graphs && all_device && st != nullptr;
-    std::vector<unsigned char> key;
-    if (use_graph) {
-        const unsigned char *pp = reinterpret_cast<const unsigned char *>(params);
-        key.assign(pp, pp + sizeof(psr_params));
-        const unsigned char *ip = reinterpret_cast<const unsigned char *>(items);
-        key.insert(key.end(), ip, ip + sizeof(psr_batch_item) * n_items);
-        if (ctx->graph_exec && key == ctx->graph_key && ctx->graph_ws_generation == ctx->ws_generation) {
-            reset_stages(ctx);
-            PSR_TRY(cudaGraphLaunch(ctx->graph_exec, st));
-            return PSR_OK;
-        }
-        // kernel attributes are set outside the capture
-        if (bf16) PSR_TRY(prepare_fwd_bf16());
-        PSR_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        ctx->capturing = true;
-    }
-
-    auto enqueue = [&]() -> int {
-        int r;
-        const float *theta = nullptr;
-        if ((r = stage_in(params->theta, theta_ws, tl.total, d_theta, st, &theta)) != PSR_OK) return r;
-        const uint8_t *sp[kMaxGroups];
-        for (int i = 0; i < n_items; ++i)
-            if ((r = stage_in(items[i].samples, w[i].s_ws, (size_t)items[i].n * w[i].N, d_s[i], st,
-                              &sp[i])) != PSR_OK)
-                return r;
-        reset_stages(ctx);
-        HamDev hd[kMaxGroups];
-        {
-            StageScope sc(ctx, PSR_STAGE_PACK);
-            PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
-            if (bf16) PSR_TRY(launch_pack_theta_bf16(theta, tl, pkb, st));
-            for (int i = 0; i < n_items; ++i)
-                PSR_TRY(launch_bitpack(sp[i], items[i].n, w[i].N, w[i].W, w[i].bits, ctx->status, st));
-            PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
-        }
-        {
-            StageScope sc(ctx, PSR_STAGE_GENERATOR);
-            for (int i = 0; i < n_items; ++i) {
-                hd[i] = HamDev{};
-                if ((r = enqueue_connected(ctx, &items[i].ham, sp[i], items[i].n, w[i].b, hd[i])) != PSR_OK)
-                    return r;
-            }
-        }
-        FwdJobs js{}, jc{};
-        js.mode = 0;
-        jc.mode = 1;
-        js.n_groups = jc.n_groups = n_items;
-        js.job_counter = counters;
-        jc.job_counter = counters + 1;
-        js.status = jc.status = ctx->status;
-        for (int i = 0; i < n_items; ++i) {
-            FwdGroup &a = js.g[i];
-            a.u1 = items[i].u1_mask;
-            a.N = w[i].N;
-            a.W = w[i].W;
-            a.n_jobs = items[i].n;
-            a.bits = w[i].bits;
-            a.out = w[i].lpsi;
-            a.logp_out = w[i].logp;
-            a.carries_out = w[i].carries;
-            FwdGroup &b = jc.g[i];
-            b.u1 = items[i].u1_mask;
-            b.N = w[i].N;
-            b.W = w[i].W;
-            b.n_jobs = w[i].cap;
-            b.n_jobs_dev = w[i].b.offsets + items[i].n;
-            b.bits = w[i].bits;
-            b.entries = w[i].b.entries;
-            b.carries_in = w[i].carries;
-            b.logp_ref = w[i].logp;
-            b.out = w[i].delta;
-        }
-        {
-            StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
-            if (bf16) PSR_TRY(launch_fwd_bf16(js, pkb, pk, fl, ctx->num_sms, st));
-            else PSR_TRY(launch_fwd_f32(js, pk, fl, ctx->num_sms, st));
-        }
-        {
-            StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
-            if (bf16) PSR_TRY(launch_fwd_bf16(jc, pkb, pk, fl, ctx->num_sms, st));
-            else PSR_TRY(launch_fwd_f32(jc, pk, fl, ctx->num_sms, st));
-        }
-        {
-            StageScope sc(ctx, PSR_STAGE_GATHER);
-            for (int i = 0; i < n_items; ++i) {
-                float *o = d_out[i] ? items[i].out : w[i].out_ws;
-                double *so = items[i].stats ? (d_st[i] ? items[i].stats : w[i].stats_ws) : nullptr;
-                PSR_TRY(launch_eloc_gather(w[i].b.offsets, w[i].delta, w[i].b.diag, hd[i].coeff,
-                                           items[i].n, o, st));
-                if (so) PSR_TRY(launch_stats(o, items[i].n, so, st));
-            }
-        }
-        for (int i = 0; i < n_items; ++i) {
-            if (!d_out[i])
-                PSR_TRY(cudaMemcpyAsync(items[i].out, w[i].out_ws, items[i].n * sizeof(float),
-                                        cudaMemcpyDeviceToHost, st));
-            if (items[i].stats && !d_st[i])
-                PSR_TRY(cudaMemcpyAsync(items[i].stats, w[i].stats_ws, 3 * sizeof(double),
-                                        cudaMemcpyDeviceToHost, st));
-        }
-        return PSR_OK;
-    };
-    rc = enqueue();
-    if (use_graph) {
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(st, &graph);
-        ctx->capturing = false;
-        if (rc != PSR_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (e != cudaSuccess) return from_cuda(e);
-        if (ctx->graph_exec) {
-            cudaGraphExecDestroy(ctx->graph_exec);
-            ctx->graph_exec = nullptr;
-        }
-        e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            ctx->graph_exec = nullptr;
-            return from_cuda(e);
-        }
-        ctx->graph_key = key;
-        ctx->graph_ws_generation = ctx->ws_generation;
-        PSR_TRY(cudaGraphLaunch(ctx->graph_exec, st));
-        return PSR_OK;
-    }
-    if (rc != PSR_OK) return rc;
-    if (!all_device) return take_status(ctx);
-    return PSR_OK;
-}
 
 }  // extern "C"

@@ -42,6 +42,9 @@ struct psr_context {
     };
     std::vector<Tuned> tuned;
     cudaEvent_t tune_ev[2] = {};
+    // shape of the fused forward kernels fixed by psr_context_set_fwd_shape
+    // ([0] FP32, [1] BF16; 0 = chosen per call: tuned, else the default)
+    int fwd_shape_fixed[2] = {0, 0};
     // second workspace: arrays psr_vmc_step keeps across the calls it makes
     void *ws2 = nullptr;
     size_t ws2_size = 0;
@@ -211,7 +214,7 @@ inline int64_t max_entries_per_sample(const psr_hamiltonian *ham) {
 
 // ---------------------------------------------------------------- autotuner
 
-enum { kTuneScan = 1, kTuneSample = 2, kTuneSample2d = 3, kTuneSampleLru = 4 };
+enum { kTuneScan = 1, kTuneSample = 2, kTuneSample2d = 3, kTuneSampleLru = 4, kTuneFwd = 5 };
 
 // Times run(i) for every candidate i on the context's stream with CUDA
 // events (two runs each when a run is short, the second counted) and
@@ -249,6 +252,64 @@ inline const psr_context::Tuned *find_tuned(const psr_context *ctx, int op, int6
     for (const auto &t : ctx->tuned)
         if (t.op == op && t.k0 == k0 && t.k1 == k1 && t.k2 == k2) return &t;
     return nullptr;
+}
+
+// ------------------------------------------- shapes of the fused forwards
+// BF16 (tcgen05) forward: sequences per MMA stream, 1 (four streams, N = 32)
+// or 2 (two streams, N = 64).  FP32 forward: scan chunk, 32 or 16 sites.
+// Every shape computes the same function; the FP32 chunk changes only the
+// summation order of a configuration's log P (the resume points are chunk
+// starts), the BF16 shapes give identical results.
+constexpr int kFwdShapeDefault[2] = {kChunkF32, 1};
+constexpr int kFwdShapes[2][2] = {{kChunkF32, kChunkGrad}, {1, 2}};
+
+inline bool fwd_shape_valid(bool bf16, int shape) {
+    return shape == kFwdShapes[bf16][0] || shape == kFwdShapes[bf16][1];
+}
+
+// Key of the forward launches of one call: precision, kind of call (0: log
+// psi of the samples, 1: samples + connected configurations) and the
+// (sites, samples) of every sample set.
+struct FwdKey {
+    int64_t k0, k1, k2;
+};
+inline FwdKey fwd_key(bool bf16, int what, int groups, const int *N, const int64_t *n) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the sizes
+    for (int g = 0; g < groups; ++g) {
+        h = (h ^ (uint64_t)N[g]) * 1099511628211ull;
+        h = (h ^ (uint64_t)n[g]) * 1099511628211ull;
+    }
+    return FwdKey{bf16 ? 1 : 0, what, (int64_t)(h >> 1)};
+}
+
+// The shape a call uses: the fixed one, else the tuned one, else the default.
+inline int fwd_shape(const psr_context *ctx, bool bf16, const FwdKey &k, bool *tuned) {
+    *tuned = false;
+    if (ctx->fwd_shape_fixed[bf16]) return ctx->fwd_shape_fixed[bf16];
+    if (const psr_context::Tuned *t = find_tuned(ctx, kTuneFwd, k.k0, k.k1, k.k2)) {
+        *tuned = true;
+        return t->v0;
+    }
+    return kFwdShapeDefault[bf16];
+}
+
+// With the autotuner on and the shape neither fixed nor tuned (and no graph
+// being captured), times run(shape) for both shapes and records the faster;
+// *shape receives the shape to use.  run must enqueue the call's complete
+// forward launches (idempotent).  Synchronises the stream when it tunes.
+template <class Run>
+inline int tune_fwd_shape(psr_context *ctx, bool bf16, const FwdKey &k, Run run, int *shape) {
+    bool tuned = false;
+    *shape = fwd_shape(ctx, bf16, k, &tuned);
+    if (!ctx->autotune || tuned || ctx->capturing || ctx->fwd_shape_fixed[bf16]) return PSR_OK;
+    int best = 0;
+    float ms = 0.0f;
+    int rc = measure_candidates(ctx, 2, [&](int i) { return run(kFwdShapes[bf16][i]); }, &best, &ms);
+    if (rc != PSR_OK) return rc;
+    psr_context::Tuned t{kTuneFwd, k.k0, k.k1, k.k2, kFwdShapes[bf16][best], 0, ms};
+    ctx->tuned.push_back(t);
+    *shape = t.v0;
+    return PSR_OK;
 }
 
 }  // namespace apiutil

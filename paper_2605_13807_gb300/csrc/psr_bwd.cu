@@ -54,10 +54,8 @@ static_assert(CH * (128 + 1) <= 2 * 128 * LD, "xl fits in the gz / gc storage");
 
 template <int H>
 __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
-    const uint64_t *__restrict__ bits, int64_t n, int N, int W, int u1,
-    const float *__restrict__ theta, ThetaLayout tl, const float *__restrict__ pk, F32Layout fl,
-    const float *__restrict__ carries, const float *__restrict__ dout, float *__restrict__ grad_rows,
-    float *__restrict__ tape_all, int *status) {
+    const __grid_constant__ BwdJobs bj, const float *__restrict__ theta, ThetaLayout tl,
+    const float *__restrict__ pk, F32Layout fl, float *__restrict__ tape_all, int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdSmem<H> &S = *reinterpret_cast<BwdSmem<H> *>(smem_raw);
     const int j = threadIdx.x;
@@ -75,7 +73,6 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
         V.gc = S.gzc + H * LD;
         V.xl = S.gzc;
     }
-    const int nch = (N + CH - 1) / CH;
     const int64_t P = tl.total;
     float *tape = tape_all + (size_t)blockIdx.x * tape_floats(nL, H);
     auto T = [&](int l, int q, int t) -> float * {
@@ -89,10 +86,18 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
     const float bd = pk[fl.bd];
     const float wdj = pk[fl.wd + j];
 
-    for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
-        const uint64_t *row = bits + s * W;
-        const float scale = dout ? dout[s] : 1.0f;
-        float *G = dout ? grad_rows + (size_t)blockIdx.x * P : grad_rows + (size_t)s * P;
+    // samples of all groups in order; sample s of group gi is sample s - first[gi] there
+    for (int64_t sg = blockIdx.x; sg < bj.first[bj.n_groups]; sg += gridDim.x) {
+        int gi = 0;
+        while (gi + 1 < bj.n_groups && sg >= bj.first[gi + 1]) ++gi;
+        const BwdGroup &BG = bj.g[gi];
+        const int64_t s = sg - bj.first[gi];
+        const int N = BG.N, u1 = BG.u1;
+        const int nch = (N + CH - 1) / CH;
+        const float *carries = BG.carries;
+        const uint64_t *row = BG.bits + s * BG.W;
+        const float scale = BG.dout ? BG.dout[s] : 1.0f;
+        float *G = BG.dout ? BG.rows + (size_t)blockIdx.x * P : BG.rows + (size_t)s * P;
         for (int l = 0; l < nL; ++l) {
             V.lam[l * H + j] = 0.0f;
             V.anext[l * H + j] = 0.0f;
@@ -430,18 +435,41 @@ __global__ void __launch_bounds__(H, 4) bwd_f32_kernel(
 }
 
 template <int H>
-static cudaError_t launch_bwd_h(const uint64_t *bits, int64_t n, int N, int W, int u1,
-                                const float *theta, const ThetaLayout &tl, const float *packed,
-                                const F32Layout &fl, const float *carries, const float *dout,
-                                float *grad_rows, int grid, float *tape, int *status,
-                                cudaStream_t stream) {
+static cudaError_t prepare_bwd_h(int nL) {
+    const size_t smem = sizeof(BwdSmem<H>) + 4 * (size_t)nL * H * sizeof(float);
+    return cudaFuncSetAttribute(bwd_f32_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prepare_bwd_f32(int H, int nL) {
+    switch (H) {
+        case 32: return prepare_bwd_h<32>(nL);
+        case 64: return prepare_bwd_h<64>(nL);
+        case 128: return prepare_bwd_h<128>(nL);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int H>
+static cudaError_t launch_bwd_h(const BwdJobs &bj, const float *theta, const ThetaLayout &tl,
+                                const float *packed, const F32Layout &fl, int grid, float *tape,
+                                int *status, cudaStream_t stream) {
     const size_t smem = sizeof(BwdSmem<H>) + 4 * (size_t)tl.nL * H * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(bwd_f32_kernel<H>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prepare_bwd_h<H>(tl.nL);
     if (e != cudaSuccess) return e;
-    bwd_f32_kernel<H><<<grid, H, smem, stream>>>(bits, n, N, W, u1, theta, tl, packed, fl, carries,
-                                                  dout, grad_rows, tape, status);
+    bwd_f32_kernel<H><<<grid, H, smem, stream>>>(bj, theta, tl, packed, fl, tape, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_f32_groups(const BwdJobs &bj, const float *theta, const ThetaLayout &tl,
+                                  const float *packed, const F32Layout &fl, int grid, float *tape,
+                                  int *status, cudaStream_t stream) {
+    if (bj.n_groups < 1 || bj.n_groups > kMaxGroups) return cudaErrorInvalidValue;
+    switch (tl.H) {
+        case 32: return launch_bwd_h<32>(bj, theta, tl, packed, fl, grid, tape, status, stream);
+        case 64: return launch_bwd_h<64>(bj, theta, tl, packed, fl, grid, tape, status, stream);
+        case 128: return launch_bwd_h<128>(bj, theta, tl, packed, fl, grid, tape, status, stream);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1,
@@ -449,12 +477,12 @@ cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1
                            const F32Layout &fl, const float *carries, const float *dout,
                            float *grad_rows, int grid, float *tape, int *status,
                            cudaStream_t stream) {
-    switch (tl.H) {
-        case 32: return launch_bwd_h<32>(bits, n, N, W, u1, theta, tl, packed, fl, carries, dout, grad_rows, grid, tape, status, stream);
-        case 64: return launch_bwd_h<64>(bits, n, N, W, u1, theta, tl, packed, fl, carries, dout, grad_rows, grid, tape, status, stream);
-        case 128: return launch_bwd_h<128>(bits, n, N, W, u1, theta, tl, packed, fl, carries, dout, grad_rows, grid, tape, status, stream);
-        default: return cudaErrorInvalidValue;
-    }
+    BwdJobs bj{};
+    bj.n_groups = 1;
+    bj.first[0] = 0;
+    bj.first[1] = n;
+    bj.g[0] = BwdGroup{bits, N, W, u1, carries, dout, grad_rows};
+    return launch_bwd_f32_groups(bj, theta, tl, packed, fl, grid, tape, status, stream);
 }
 
 size_t bwd_smem_bytes(int H, int nL) {

@@ -99,8 +99,11 @@ cudaError_t launch_fwd_f32(const FwdJobs &jobs, const float *packed, const F32La
 size_t bf16_packed_bytes();
 cudaError_t launch_pack_theta_bf16(const float *theta, const ThetaLayout &tl, void *packed,
                                    cudaStream_t stream);
+// seqs_per_stream: 1 (four MMA streams of one sequence, N = 32) or 2 (two
+// streams of two sequences side by side, N = 64); same results bit for bit.
 cudaError_t launch_fwd_bf16(const FwdJobs &jobs, const void *packed_bf16, const float *packed_f32,
-                            const F32Layout &fl, int num_sms, cudaStream_t stream);
+                            const F32Layout &fl, int num_sms, cudaStream_t stream,
+                            int seqs_per_stream = 1);
 // Sets the kernel's shared-memory attribute on the current device (once).
 cudaError_t prepare_fwd_bf16();
 
@@ -283,7 +286,29 @@ cudaError_t launch_vmc_dout(const float *eloc, const double *stats, const float 
 cudaError_t launch_adam(const float *theta, const float *grad, int64_t P, float lr, float b1, float b2,
                         float eps, int step, float *m, float *v, float *out, cudaStream_t st);
 
-// Backward (FP32).
+// Backward (FP32).  Samples of up to kMaxGroups sample sets (one lattice
+// each) in one launch: group g holds samples first[g] .. first[g+1]-1 of the
+// launch; its chunk carries come from a forward on kChunkGrad-site chunks;
+// rows: [n][P] O_k rows (dout == NULL) or per-CTA partial sums of
+// dout_i O_k(s_i) ([grid][P], zeroed by the caller).
+struct BwdGroup {
+    const uint64_t *bits;  // [n][W] bit-packed spins
+    int N, W, u1;
+    const float *carries;  // [n][nch][nL][H]
+    const float *dout;     // [n] or NULL
+    float *rows;
+};
+struct BwdJobs {
+    int n_groups;
+    int64_t first[kMaxGroups + 1];
+    BwdGroup g[kMaxGroups];
+};
+// Sets the backward kernel's shared-memory attribute (done by every launch;
+// call it before a stream capture that will contain a launch).
+cudaError_t prepare_bwd_f32(int H, int nL);
+cudaError_t launch_bwd_f32_groups(const BwdJobs &bj, const float *theta, const ThetaLayout &tl,
+                                  const float *packed, const F32Layout &fl, int grid, float *tape,
+                                  int *status, cudaStream_t stream);
 size_t bwd_tape_floats_per_cta(int nL, int H);
 cudaError_t launch_bwd_f32(const uint64_t *bits, int64_t n, int N, int W, int u1,
                            const float *theta, const ThetaLayout &tl, const float *packed,
