@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--no-lru", action="store_true")
     ap.add_argument("--no-vmc", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--depth-only", action="store_true",
+                    help="only the fused-forward latency versus sample count, beside the parallel scan")
+    ap.add_argument("--sample-only", action="store_true",
+                    help="only the sampler leg (profiling runs)")
+    ap.add_argument("--sample-n", type=int, default=0,
+                    help="samples of the sample-only run (default: the workload's samples)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="only the mixed-lattice batch leg")
     ap.add_argument("--samples-2d", type=int, default=32,
@@ -215,9 +221,13 @@ def profiled_traffic_per_unit(profile="fwd_bf16_connected_52x52.md", src_name="p
 # ------------------------------------------------------------- reference arm
 
 def oracle_rate(Lx, Ly, seconds, threads=None):
-    """The FP64 oracle (sequential recurrence) timed on the host cores: log psi
-    of connected configurations of one sample, the dominant work of E_loc.
-    Returns (config-sites/s, cores, sample description)."""
+    """The FP64 oracle (sequential recurrence) timed on the host cores over
+    the step's three stages for one sample: its log psi and O_k (the
+    oracle's reverse mode), and E_loc over k of its connected
+    configurations (each a full sequential forward), k chosen so the run
+    takes about `seconds`.  Units as in the GPU metric: (1 + k) logical
+    configuration x site pairs.  Returns (config-sites/s, cores, sample
+    description)."""
     import numpy as np
 
     from oracle import oracle as orc
@@ -227,7 +237,7 @@ def oracle_rate(Lx, Ly, seconds, threads=None):
     N = Lx * Ly
     theta = inputs.glorot_params(N_LAYERS, HIDDEN, seed=0)
     s = inputs.neel_like_spins(1000, 1, Lx, Ly)
-    offs, ent, _ = orc.connected(orc.HEISENBERG, Lx, Ly, False, s)
+    offs, ent, diag = orc.connected(orc.HEISENBERG, Lx, Ly, False, s)
     sp = np.repeat(s, len(ent), axis=0)
     r = np.arange(len(ent))
     sp[r, ent[:, 1]] ^= 1
@@ -235,14 +245,20 @@ def oracle_rate(Lx, Ly, seconds, threads=None):
     t0 = time.perf_counter()
     orc.logpsi(theta, N_LAYERS, HIDDEN, sp[:1], u1=True, threads=1)
     t1 = time.perf_counter() - t0
-    per_core = max(1, int(round(seconds / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    lp_s, _ok = orc.grad(theta, N_LAYERS, HIDDEN, s, u1=True, threads=1)
+    t_grad = time.perf_counter() - t0
+    per_core = max(1, int(round(max(seconds - t_grad, t1) / max(t1, 1e-6))))
     k = min(len(sp), per_core * cores)
     t0 = time.perf_counter()
-    orc.logpsi(theta, N_LAYERS, HIDDEN, sp[:k], u1=True, threads=cores)
+    lp_s, _ok = orc.grad(theta, N_LAYERS, HIDDEN, s, u1=True, threads=1)
+    lp_c = orc.logpsi(theta, N_LAYERS, HIDDEN, sp[:k], u1=True, threads=cores)
+    orc.eloc_combine(diag[0], orc.offdiag_coeff(orc.HEISENBERG), lp_s[0], lp_c)
     dt = time.perf_counter() - t0
-    desc = (f"FP64 oracle log psi of {k} connected configurations of one {Lx}x{Ly} sample "
-            f"(full sequential forward, {N} sites each), {cores} threads, {dt:.1f} s")
-    return k * N / dt, cores, desc
+    desc = (f"FP64 oracle on one {Lx}x{Ly} sample: log psi and O_k (reverse mode, 1 thread), then E_loc "
+            f"over {k} of its {len(ent)} connected configurations (full sequential forwards, {cores} "
+            f"threads); units (1 + {k}) x {N} sites in {dt:.1f} s")
+    return (1 + k) * N / dt, cores, desc
 
 
 def run_reference(args):
@@ -739,6 +755,75 @@ def run_mixed_only(args):
     return 0
 
 
+def depth_leg(dev, L=52, ns=(1, 16, 200, 4096), reps=5):
+    """Where the fused forward's sequential-in-chunk recurrence stops being
+    the right choice: log psi of n samples at L x L (BF16, one launch, no
+    connected configurations) for small and large n, beside one standalone
+    parallel scan (psr_scan: warp-shuffle step scans with a decoupled
+    look-back carry between chunks) of one layer of the same n sequences of
+    L^2 sites x 128 units, the kernel a scan-based evaluation of the
+    recurrence would run three times per forward."""
+    import torch
+
+    from paper_2605_13807_gb300 import api, binding as B, inputs
+    ctx = B.context()
+    B.psr_context_set_profiling(ctx, True)
+    N = L * L
+    theta = torch.from_numpy(inputs.glorot_params(N_LAYERS, HIDDEN, seed=0)).to(dev)
+    cfg = api.ModelConfig(N_LAYERS, HIDDEN, True, "bf16")
+    out = {}
+    for n in ns:
+        sp = torch.from_numpy(inputs.neel_like_spins(4000 + n, n, L, L)).to(dev)
+        lp = torch.empty(n, dtype=torch.float32, device=dev)
+        api.logpsi(theta, sp, cfg, out=lp)
+        fwd = []
+        for _ in range(reps):
+            api.logpsi(theta, sp, cfg, out=lp)
+            fwd.append(B.psr_context_stage_ms(ctx)["fwd_samples"])
+        a, b, h0 = inputs.scan_inputs_device(7, n, N, HIDDEN, dev)
+        h = torch.empty_like(a)
+        B.psr_context_set_autotune(ctx, True)
+        api.scan(a, b, h0, out=h)
+        B.psr_context_set_autotune(ctx, False)
+        sc = []
+        for _ in range(reps):
+            api.scan(a, b, h0, out=h)
+            sc.append(B.psr_context_stage_ms(ctx)["scan"])
+        tile, _ = B.psr_scan_tile_for(ctx, n, N, HIDDEN)
+        out[str(n)] = {"fused_forward_ms": min(fwd), "scan_one_layer_ms": min(sc),
+                       "scan_tile": {"units": tile[0], "chunk": tile[1]},
+                       "fused_sites_per_us": n * N / (min(fwd) * 1e3)}
+        del a, b, h0, h, sp, lp
+        torch.cuda.empty_cache()
+    B.psr_context_set_profiling(ctx, False)
+    return {"lattice": f"{L}x{L}", "hidden": HIDDEN, "by_samples": out}
+
+
+def run_depth_only(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"depth": depth_leg(torch.device("cuda", 0))}), flush=True)
+    return 0
+
+
+def run_sample_only(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_13807_gb300 import inputs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    Lx, Ly, n = WORKLOADS[args.workload]
+    n = args.sample_n or n
+    theta = torch.from_numpy(inputs.glorot_params(N_LAYERS, HIDDEN, seed=0)).to(dev)
+    print(json.dumps({"sample": sample_leg(theta, n, Lx * Ly, dev)}), flush=True)
+    return 0
+
+
 def run_scan_only(args):
     import torch
 
@@ -895,14 +980,17 @@ def run_mine(args):
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
+        reps32 = 3
         a0.record()
-        step32()
+        for _ in range(reps32):
+            step32()
         a1.record()
         a1.synchronize()
-        ms32 = a0.elapsed_time(a1)
+        ms32 = a0.elapsed_time(a1) / reps32
         line["fp32_path"] = {"value": (m * N + E2 * N) / (ms32 / 1e3), "unit": UNIT,
-                             "samples": m, "ms": ms32,
-                             "note": "plain FP32 SIMT path, same workload on a sample subset"}
+                             "samples": m, "ms": ms32, "repeats": reps32,
+                             "note": "plain FP32 SIMT path, same workload on a sample subset; "
+                                     "mean of 3 steps after one warm-up step"}
         del ok32
 
     if not args.no_scan and rank == 0:
@@ -970,6 +1058,10 @@ def main():
         return run_paper2d_only(args)
     if args.mixed_only:
         return run_mixed_only(args)
+    if args.depth_only:
+        return run_depth_only(args)
+    if args.sample_only:
+        return run_sample_only(args)
     return run_mine(args)
 
 

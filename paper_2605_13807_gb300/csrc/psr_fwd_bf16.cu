@@ -760,10 +760,8 @@ fwd_bf16_kernel1(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-                if (lane == 0) M.red2[s] = sv;
+                acc += sv;  // kept by thread j == 0 of the stream
             }
-            sbar();
-            if (issuer) acc += M.red2[s];
             n_up += __popc(rd_cur);
             if (M.abort_flag[s]) aborted = true;  // uniform: read after the barrier
         };
@@ -860,7 +858,7 @@ fwd_bf16_kernel1(const __grid_constant__ FwdJobs jb, const uint8_t *__restrict__
         }
         if (!aborted) readout();
         if (aborted) break;
-        if (issuer) G.out[lj] = 0.5f * acc;
+        if (j == 0) G.out[lj] = 0.5f * acc;
     }
 
     // ------------------------------------------------------------ teardown
