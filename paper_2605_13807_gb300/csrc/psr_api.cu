@@ -367,11 +367,62 @@ int psr_local_energy(const psr_params *params, const uint8_t *samples, int64_t n
     return PSR_OK;
 }
 
+// psr_grad on the tensor cores (BF16 precision, per-sample rows, hidden 128).
+static int grad_tc_call(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, float *dparams) {
+    psr_context *ctx = params->ctx;
+    const int nL = params->n_layers;
+    const ThetaLayout tl = theta_layout(nL, 128);
+    const F32Layout fl = f32_layout(nL, 128);
+    const int64_t P = tl.total;
+    const int W = (int)words_per_row(L);
+    const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(spins), d_g = is_device_ptr(dparams);
+    const int64_t B = grad_tc_batch(nL, L, n);
+    float *theta_ws = nullptr, *g_ws = nullptr, *pk = nullptr;
+    uint8_t *s_ws = nullptr;
+    uint64_t *bits = nullptr;
+    GradTcWs tw{};
+    auto carve = [&](Carver &c) {
+        theta_ws = c.get<float>(d_theta ? 0 : P);
+        s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * L);
+        g_ws = c.get<float>(d_g ? 0 : (size_t)n * P);
+        pk = c.get<float>(fl.total);
+        bits = c.get<uint64_t>((size_t)n * W);
+        grad_tc_carve(c, nL, L, B, tw);
+    };
+    Carver sz;
+    carve(sz);
+    int rc;
+    if ((rc = ensure_ws(ctx, sz.off)) != PSR_OK) return rc;
+    Carver cv;
+    cv.base = static_cast<char *>(ctx->ws);
+    carve(cv);
+    cudaStream_t st = ctx->stream;
+    const float *theta = nullptr;
+    const uint8_t *sp = nullptr;
+    if ((rc = stage_in(params->theta, theta_ws, P, d_theta, st, &theta)) != PSR_OK) return rc;
+    if ((rc = stage_in(spins, s_ws, (size_t)n * L, d_s, st, &sp)) != PSR_OK) return rc;
+    float *g = d_g ? dparams : g_ws;
+    reset_stages(ctx);
+    {
+        StageScope sc(ctx, PSR_STAGE_PACK);
+        PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+        PSR_TRY(launch_bitpack(sp, n, L, W, bits, ctx->status, st));
+    }
+    {
+        StageScope sc(ctx, PSR_STAGE_BWD);  // the stash forward and the reverse pass
+        if ((rc = enqueue_grad_tc(ctx, nL, params->u1_mask, theta, pk, bits, n, L, W, g, tw)) != PSR_OK) return rc;
+    }
+    if (!d_g) PSR_TRY(cudaMemcpyAsync(dparams, g_ws, (size_t)n * P * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (!d_g || !d_s || !d_theta) return take_status(ctx);
+    return PSR_OK;
+}
+
 int psr_grad(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L,
              const float *dout, float *dparams) {
     int rc = check_params(params, n, L);
     if (rc != PSR_OK && rc != PSR_EUNSUPPORTED) return rc;
     if (!spins || !dparams) return PSR_EINVAL;
+    if (rc == PSR_OK && grad_tc_applies(params, dout)) return grad_tc_call(params, spins, n, L, dparams);
     psr_context *ctx = params->ctx;
     const int nL = params->n_layers, H = params->hidden;
     const ThetaLayout tl = theta_layout(nL, H);

@@ -91,6 +91,22 @@ int step_batch_impl(const psr_params *params, const StepItem *items, int n_items
         grad_grid = (int)(g > n_grad ? n_grad : g);
     }
 
+    // BF16 gradients run on the tensor cores one item after another (as
+    // psr_grad does), through one set of batch buffers sized for the largest
+    const bool use_tc = bf16 && H == 128;
+    size_t tc_stash = 0, tc_arr = 0;
+    if (use_tc) {
+        for (int i = 0; i < n_items; ++i) {
+            if (!items[i].grad) continue;
+            const int64_t B = grad_tc_batch(nL, w[i].N, items[i].n);
+            const size_t st_i = (size_t)B * stash_floats_per_sample(nL, 128, w[i].N);
+            const size_t ar_i = (size_t)B * 128 * stash_npad(w[i].N);
+            tc_stash = st_i > tc_stash ? st_i : tc_stash;
+            tc_arr = ar_i > tc_arr ? ar_i : tc_arr;
+        }
+        grad_grid = 0;
+    }
+    GradTcWs tw{};
     float *theta_ws = nullptr, *pk = nullptr, *tape = nullptr;
     void *pkb = nullptr;
     unsigned long long *counters = nullptr;
@@ -100,6 +116,21 @@ int step_batch_impl(const psr_params *params, const StepItem *items, int n_items
         pkb = c.get<char>(bf16 ? bf16_packed_bytes() : 0);
         counters = c.get<unsigned long long>(3);
         tape = c.get<float>((size_t)grad_grid * bwd_tape_floats_per_cta(nL, H));
+        if (use_tc && n_grad > 0) {
+            tw.images = c.get<char>(bwd_tc_image_bytes(nL));
+            tw.counter = c.get<unsigned long long>(1);
+            tw.stash = c.get<float>(tc_stash);
+            for (int k = 0; k < 2; ++k) {
+                tw.gx[k] = c.get<float>(tc_arr);
+                tw.gy[k] = c.get<float>(tc_arr);
+            }
+            tw.gh = c.get<float>(tc_arr);
+            tw.dz = c.get<float>(tc_arr);
+            tw.dc = c.get<float>(tc_arr);
+            size_t maxn = 0;
+            for (int i = 0; i < n_items; ++i) maxn = (size_t)items[i].n > maxn ? (size_t)items[i].n : maxn;
+            tw.lpsi = c.get<float>(maxn);
+        }
         for (int i = 0; i < n_items; ++i) {
             const StepItem &it = items[i];
             const int64_t n = it.n;
@@ -122,8 +153,8 @@ int step_batch_impl(const psr_params *params, const StepItem *items, int n_items
             x.logp = c.get<float>(it.eloc ? (size_t)n * x.N : 0);
             x.carries = c.get<float>(it.eloc ? (size_t)n * nch * nL * H : 0);
             x.delta = c.get<float>(x.cap);
-            x.carries_g = c.get<float>(it.grad ? (size_t)n * nchg * nL * H : 0);
-            x.lpsi_g = c.get<float>(it.grad ? n : 0);
+            x.carries_g = c.get<float>(it.grad && !use_tc ? (size_t)n * nchg * nL * H : 0);
+            x.lpsi_g = c.get<float>(it.grad && !use_tc ? n : 0);
         }
     };
     Carver sz;
@@ -163,7 +194,8 @@ int step_batch_impl(const psr_params *params, const StepItem *items, int n_items
         }
         // kernel attributes are set outside the capture
         if (bf16) PSR_TRY(prepare_fwd_bf16());
-        if (n_grad > 0) PSR_TRY(prepare_bwd_f32(H, nL));
+        if (n_grad > 0 && !use_tc) PSR_TRY(prepare_bwd_f32(H, nL));
+        if (n_grad > 0 && use_tc) PSR_TRY(prepare_bwd_tc());
         PSR_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         ctx->capturing = true;
     }
@@ -255,8 +287,21 @@ int step_batch_impl(const psr_params *params, const StepItem *items, int n_items
                 if (so) PSR_TRY(launch_stats(o, it.n, so, st));
             }
         }
+        // ---- gradient on the tensor cores (BF16), one item after another
+        if (n_grad > 0 && use_tc) {
+            StageScope sc(ctx, PSR_STAGE_BWD);
+            for (int i = 0; i < n_items; ++i) {
+                const StepItem &it = items[i];
+                if (!it.grad) continue;
+                tw.B = grad_tc_batch(nL, w[i].N, it.n);
+                float *rows = w[i].d_g ? it.grad : w[i].g_ws;
+                if ((r = enqueue_grad_tc(ctx, nL, it.u1, theta, pk, w[i].bits, it.n, w[i].N, w[i].W, rows, tw)) !=
+                    PSR_OK)
+                    return r;
+            }
+        }
         // ---- gradient: FP32 forward on gradient chunks, then the reverse scan
-        if (n_grad > 0) {
+        if (n_grad > 0 && !use_tc) {
             FwdJobs jg{};
             jg.mode = 0;
             jg.job_counter = counters + 2;

@@ -68,7 +68,24 @@ struct FwdGroup {
     float *out;                  // mode 0: [n] log psi; mode 1: [E] delta
     float *logp_out;             // mode 0, optional: [n][N]
     float *carries_out;          // mode 0, optional: [n][nch][nL][H]
+    float *stash;                // mode 0, optional (FP32 kernel): per sample the
+                                 // layer values the tensor-core backward needs,
+                                 // see stash_floats_per_sample
 };
+
+// Stash of one sample for the tensor-core backward, written by the FP32
+// forward (mode 0): for layer l and quantity q (kStashA: gate a, kStashC:
+// candidate c = W_h u + b_h, kStashH: state h, kStashY: output-map
+// pre-activation y, residual included) a [H][Npad] block at
+// ((l * kStashQ + q) * H) * Npad, then the readout adjoint g [Npad] at
+// nL * kStashQ * H * Npad, g_t = 1/2 (s_t - P(1 | s_<t)) (0 where the
+// zero-magnetisation mask forces s_t).  Npad = N rounded up to 64; every
+// value at t >= N is 0.
+enum { kStashA = 0, kStashC = 1, kStashH = 2, kStashY = 3, kStashQ = 4 };
+__host__ __device__ inline int stash_npad(int N) { return (N + 63) & ~63; }
+__host__ __device__ inline size_t stash_floats_per_sample(int nL, int H, int N) {
+    return ((size_t)nL * kStashQ * H + 1) * (size_t)stash_npad(N);
+}
 struct FwdJobs {
     int mode;
     int n_groups;
@@ -303,6 +320,34 @@ struct BwdJobs {
     int64_t first[kMaxGroups + 1];
     BwdGroup g[kMaxGroups];
 };
+// Tensor-core backward (hidden 128; psr_bwd_tc.cu): one layer at a time over
+// the samples of a batch, from the FP32 forward's stash.  Arrays [n][H][Np]
+// FP32 (unit-major, Np = stash_npad(N)).
+struct BwdTcArgs {
+    int n, N, Np, W, nL, l;
+    int64_t P;
+    ThetaLayout tl;
+    const float *stash;      // batch stash, stash_stride floats per sample
+    int64_t stash_stride;
+    const float *wd;         // readout logit-difference weights [H]
+    const uint8_t *images;   // launch_pack_bwd_tc output
+    const uint64_t *bits;    // [n][W] bit-packed spins of the batch
+    const float *gx_in;      // gradient w.r.t. this layer's output x^{l+1} (l < nL - 1)
+    float *gx_out;           // gradient w.r.t. its input x^l (l >= 1)
+    float *gy;               // gx_in (.) GELU'(y) of this layer
+    const float *gy_up;      // gy of layer l + 1 (its residual input is h^l)
+    float *gh;               // C^T gy
+    float *dz, *dc;          // gate and candidate adjoints
+    float *rows;             // [n][P] O_k rows of the batch
+    int *status;
+};
+size_t bwd_tc_image_bytes(int nL);
+cudaError_t launch_pack_bwd_tc(const float *theta, const ThetaLayout &tl, void *images, cudaStream_t stream);
+cudaError_t launch_bwd_tc_layer(const BwdTcArgs &A, int num_sms, cudaStream_t stream);
+// Sets the tensor-core backward kernels' shared-memory attributes (once per
+// device; call before a stream capture that will contain their launches).
+cudaError_t prepare_bwd_tc();
+
 // Sets the backward kernel's shared-memory attribute (done by every launch;
 // call it before a stream capture that will contain a launch).
 cudaError_t prepare_bwd_f32(int H, int nL);
