@@ -118,7 +118,6 @@ int step_batch_impl(const psr_params *params, const StepItem *items, int n_items
         tape = c.get<float>((size_t)grad_grid * bwd_tape_floats_per_cta(nL, H));
         if (use_tc && n_grad > 0) {
             tw.images = c.get<char>(bwd_tc_image_bytes(nL));
-            tw.counter = c.get<unsigned long long>(1);
             tw.stash = c.get<float>(tc_stash);
             for (int k = 0; k < 2; ++k) {
                 tw.gx[k] = c.get<float>(tc_arr);
@@ -127,9 +126,6 @@ int step_batch_impl(const psr_params *params, const StepItem *items, int n_items
             tw.gh = c.get<float>(tc_arr);
             tw.dz = c.get<float>(tc_arr);
             tw.dc = c.get<float>(tc_arr);
-            size_t maxn = 0;
-            for (int i = 0; i < n_items; ++i) maxn = (size_t)items[i].n > maxn ? (size_t)items[i].n : maxn;
-            tw.lpsi = c.get<float>(maxn);
         }
         for (int i = 0; i < n_items; ++i) {
             const StepItem &it = items[i];

@@ -316,7 +316,7 @@ inline int tune_fwd_shape(psr_context *ctx, bool bf16, const FwdKey &k, Run run,
 // Per-sample O_k rows on the tensor cores: used by psr_grad (BF16 precision,
 // dout == NULL) and by psr_step_batch for its BF16 gradient items.  Samples
 // go through in batches whose stash and layer arrays fit kTcBudget bytes.
-constexpr size_t kTcBudget = size_t(8) << 30;
+constexpr size_t kTcBudget = size_t(16) << 30;
 
 inline bool grad_tc_applies(const psr_params *p, const float *dout) {
     return p->precision == PSR_BF16 && p->hidden == 128 && dout == nullptr;
@@ -324,9 +324,8 @@ inline bool grad_tc_applies(const psr_params *p, const float *dout) {
 
 struct GradTcWs {
     int64_t B;          // samples per batch
-    float *stash, *gx[2], *gy[2], *gh, *dz, *dc, *lpsi;
+    float *stash, *gx[2], *gy[2], *gh, *dz, *dc;
     void *images;
-    unsigned long long *counter;
 };
 
 inline int64_t grad_tc_batch(int nL, int L, int64_t n) {
@@ -342,7 +341,6 @@ inline void grad_tc_carve(Carver &c, int nL, int L, int64_t B, GradTcWs &w) {
     const size_t arr = (size_t)B * 128 * stash_npad(L);
     w.B = B;
     w.images = c.get<char>(bwd_tc_image_bytes(nL));
-    w.counter = c.get<unsigned long long>(1);
     w.stash = c.get<float>((size_t)B * stash_floats_per_sample(nL, 128, L));
     w.gx[0] = c.get<float>(arr);
     w.gx[1] = c.get<float>(arr);
@@ -351,7 +349,6 @@ inline void grad_tc_carve(Carver &c, int nL, int L, int64_t B, GradTcWs &w) {
     w.gh = c.get<float>(arr);
     w.dz = c.get<float>(arr);
     w.dc = c.get<float>(arr);
-    w.lpsi = c.get<float>((size_t)B);
 }
 
 // Enqueues the O_k rows of n samples of L sites (bit-packed `bits`, W words
@@ -365,20 +362,6 @@ inline int enqueue_grad_tc(psr_context *ctx, int nL, int u1, const float *theta,
     PSR_TRY(launch_pack_bwd_tc(theta, tl, w.images, st));
     for (int64_t s0 = 0; s0 < n; s0 += w.B) {
         const int64_t b = (n - s0 < w.B) ? n - s0 : w.B;
-        FwdJobs jb{};
-        jb.mode = 0;
-        jb.n_groups = 1;
-        jb.g[0].u1 = u1;
-        jb.g[0].N = L;
-        jb.g[0].W = W;
-        jb.g[0].n_jobs = b;
-        jb.g[0].bits = bits + s0 * W;
-        jb.g[0].out = w.lpsi;
-        jb.g[0].stash = w.stash;
-        jb.job_counter = w.counter;
-        jb.status = ctx->status;
-        PSR_TRY(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), st));
-        PSR_TRY(launch_fwd_f32(jb, pk, fl, ctx->num_sms, st, kChunkGrad));
         BwdTcArgs A{};
         A.n = (int)b;
         A.N = L;
@@ -396,7 +379,11 @@ inline int enqueue_grad_tc(psr_context *ctx, int nL, int u1, const float *theta,
         A.gh = w.gh;
         A.dz = w.dz;
         A.dc = w.dc;
+        A.pk = pk;
+        A.fl = fl;
+        A.u1 = u1;
         A.status = ctx->status;
+        PSR_TRY(launch_fwd_tc(A, ctx->num_sms, st));  // fills the stash of the batch
         for (int l = nL - 1; l >= 0; --l) {
             A.l = l;
             A.gx_in = w.gx[(l + 1) & 1];

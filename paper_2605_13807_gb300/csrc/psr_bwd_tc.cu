@@ -54,7 +54,9 @@ constexpr int H = 128;
 constexpr int TS = 64;                      // sites per tile (one 128-byte swizzle row)
 constexpr uint32_t kTile = 128 * TS * 2;    // [128 rows][64 sites] bf16 = 16 KB
 constexpr uint32_t kImg = 32768;            // 128 x 128 bf16 image
-constexpr int kImgPerLayer = 8;             // C^T, W_z^T, W_h^T, D^T, each hi and lo
+constexpr int kImgPerLayer = 16;            // C, W_z, W_h, D transposed (backward), then as
+                                            // stored (forward), each hi and lo
+constexpr int kImgPlain = 8;                // first plain image of a layer
 enum { IM_C = 0, IM_WZ = 1, IM_WH = 2, IM_D = 3 };
 
 // kind::f16, D = F32, A = B = BF16, M = 128.
@@ -196,9 +198,11 @@ struct TcMisc {
 
 size_t bwd_tc_image_bytes(int nL) { return (size_t)nL * kImgPerLayer * kImg; }
 
-// Transposed images of C, W_z, W_h, D of every layer (layer 0: C only; its
-// other matrices act on the one-hot input), high and low BF16 parts, in the
-// TMEM row layout: image row m, element k at m * 256 + 2 k, value M[k][m].
+// Images of C, W_z, W_h, D of every layer (layer 0: C only; its other
+// matrices act on the one-hot input), high and low BF16 parts, in the TMEM
+// row layout (image row m, element k at m * 256 + 2 k): transposed (value
+// M[k][m], the backward's products) and as stored (value M[m][k], the
+// forward's products).
 __global__ void pack_bwd_tc_kernel(const float *__restrict__ theta, ThetaLayout tl, uint8_t *__restrict__ out) {
     const int64_t total = (int64_t)tl.nL * 4 * H * H;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -209,12 +213,16 @@ __global__ void pack_bwd_tc_kernel(const float *__restrict__ theta, ThetaLayout 
         const int m = e / H, k = e % H;
         if (l == 0 && mat != IM_C) continue;
         const int64_t src = mat == IM_C ? tl.C[l] : mat == IM_WZ ? tl.Wz[l] : mat == IM_WH ? tl.Wh[l] : tl.D[l];
-        const float v = theta[src + (int64_t)k * H + m];
-        const __nv_bfloat16 hv = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lv = __float2bfloat16_rn(v - __bfloat162float(hv));
-        const size_t base = ((size_t)l * kImgPerLayer + 2 * mat) * kImg + (size_t)m * 256 + (size_t)k * 2;
-        *reinterpret_cast<__nv_bfloat16 *>(out + base) = hv;
-        *reinterpret_cast<__nv_bfloat16 *>(out + base + kImg) = lv;
+#pragma unroll
+        for (int plain = 0; plain < 2; ++plain) {
+            const float v = plain ? theta[src + (int64_t)m * H + k] : theta[src + (int64_t)k * H + m];
+            const __nv_bfloat16 hv = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lv = __float2bfloat16_rn(v - __bfloat162float(hv));
+            const size_t base = ((size_t)l * kImgPerLayer + plain * kImgPlain + 2 * mat) * kImg + (size_t)m * 256 +
+                                (size_t)k * 2;
+            *reinterpret_cast<__nv_bfloat16 *>(out + base) = hv;
+            *reinterpret_cast<__nv_bfloat16 *>(out + base + kImg) = lv;
+        }
     }
 }
 
@@ -471,8 +479,9 @@ __global__ void __launch_bounds__(H) scan_bwd_kernel(const __grid_constant__ Bwd
     float lam = 0.0f, an = 0.0f;
     float sz = 0.0f, sc = 0.0f, swo = 0.0f, sbo = 0.0f;
     float z1 = 0.0f, z2 = 0.0f, c1 = 0.0f, c2 = 0.0f, d1 = 0.0f, d2 = 0.0f;  // layer 0: codes 1, 2
-    for (int t = Np - 8; t >= 0; t -= 8) {
-        float g[8], a[8], c[8], h[8], r[8];
+    // the next (lower) step's inputs are fetched while this one is computed
+    float ng[8], na[8], nc[8], nh[8], nr[8], nhb = 0.0f;
+    auto fetch = [&](int t) {
         const float4 *g4 = reinterpret_cast<const float4 *>(gr + t);
         const float4 *a4 = reinterpret_cast<const float4 *>(ar + t);
         const float4 *c4 = reinterpret_cast<const float4 *>(cr + t);
@@ -480,18 +489,32 @@ __global__ void __launch_bounds__(H) scan_bwd_kernel(const __grid_constant__ Bwd
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const float4 gv = g4[q], av = a4[q], cv = c4[q], hv = h4[q];
-            g[4 * q] = gv.x; g[4 * q + 1] = gv.y; g[4 * q + 2] = gv.z; g[4 * q + 3] = gv.w;
-            a[4 * q] = av.x; a[4 * q + 1] = av.y; a[4 * q + 2] = av.z; a[4 * q + 3] = av.w;
-            c[4 * q] = cv.x; c[4 * q + 1] = cv.y; c[4 * q + 2] = cv.z; c[4 * q + 3] = cv.w;
-            h[4 * q] = hv.x; h[4 * q + 1] = hv.y; h[4 * q + 2] = hv.z; h[4 * q + 3] = hv.w;
+            ng[4 * q] = gv.x; ng[4 * q + 1] = gv.y; ng[4 * q + 2] = gv.z; ng[4 * q + 3] = gv.w;
+            na[4 * q] = av.x; na[4 * q + 1] = av.y; na[4 * q + 2] = av.z; na[4 * q + 3] = av.w;
+            nc[4 * q] = cv.x; nc[4 * q + 1] = cv.y; nc[4 * q + 2] = cv.z; nc[4 * q + 3] = cv.w;
+            nh[4 * q] = hv.x; nh[4 * q + 1] = hv.y; nh[4 * q + 2] = hv.z; nh[4 * q + 3] = hv.w;
             if (resid) {
                 const float4 rv = reinterpret_cast<const float4 *>(rr + t)[q];
-                r[4 * q] = rv.x; r[4 * q + 1] = rv.y; r[4 * q + 2] = rv.z; r[4 * q + 3] = rv.w;
+                nr[4 * q] = rv.x; nr[4 * q + 1] = rv.y; nr[4 * q + 2] = rv.z; nr[4 * q + 3] = rv.w;
             } else {
-                r[4 * q] = r[4 * q + 1] = r[4 * q + 2] = r[4 * q + 3] = 0.0f;
+                nr[4 * q] = nr[4 * q + 1] = nr[4 * q + 2] = nr[4 * q + 3] = 0.0f;
             }
         }
-        const float hbefore = (t > 0) ? hr[t - 1] : 0.0f;
+        nhb = (t > 0) ? hr[t - 1] : 0.0f;
+    };
+    fetch(Np - 8);
+    for (int t = Np - 8; t >= 0; t -= 8) {
+        float g[8], a[8], c[8], h[8], r[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            g[i] = ng[i];
+            a[i] = na[i];
+            c[i] = nc[i];
+            h[i] = nh[i];
+            r[i] = nr[i];
+        }
+        const float hbefore = nhb;
+        if (t >= 8) fetch(t - 8);
         float dz[8], dc[8];
 #pragma unroll
         for (int i = 7; i >= 0; --i) {
@@ -669,6 +692,367 @@ __global__ void __launch_bounds__(128, 1) wgrad_kernel(const __grid_constant__ B
     }
 }
 
+// --------------------------------------------------------------- stash forward
+// The forward the backward needs, layer by layer over whole samples on the
+// same tensor-core path: layer l >= 1 projections z = W_z u + b_z,
+// c = W_h u + b_h (u = GELU(y of layer l-1)), a = sigmoid(z); the scan
+// h_t = a_t h_{t-1} + (1 - a_t) c_t in FP32 (layer 0: a, c from the one-hot
+// lookup tables); the output map y = C h + D u (+ h of layer l-1 for l >= 2;
+// layer 0: C0 h + D0 onehot(s_{t-1})); then the readout adjoint g.  The
+// products use the split BF16 operands of the backward.
+constexpr int kFwStreams = 2;
+constexpr uint32_t kFwSmem = kFwStreams * 4 * kTile + 256 + 1024;
+
+// layer l >= 1: a and c of every site into the stash
+__global__ void __launch_bounds__(128 * kFwStreams, 1) proj_fwd_kernel(const __grid_constant__ BwdTcArgs A) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    TcMisc &M = *reinterpret_cast<TcMisc *>(smem + kFwStreams * 4 * kTile);
+    const int tid = threadIdx.x, s = tid >> 7, j = tid & 127, warp = tid >> 5;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    uint8_t *tiles = smem + (4 * s) * kTile;  // u hi, lo
+    if (warp == 0) tmem_alloc_all(smem_u32(&M.tmem_base), 512);
+    if (tid == 0) {
+        for (int i = 0; i < kFwStreams; ++i) mbar_init(smem_u32(&M.mbar[i]), 1);
+        M.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = M.tmem_base;
+    const int l = A.l;
+    const uint8_t *img = A.images + ((size_t)l * kImgPerLayer + kImgPlain) * kImg;
+    if (s == 0) {
+        image_to_tmem(img + (2 * IM_WZ) * kImg, tmem, lane_off, 256, j);
+        image_to_tmem(img + (2 * IM_WZ + 1) * kImg, tmem, lane_off, 320, j);
+    } else {
+        image_to_tmem(img + (2 * IM_WH) * kImg, tmem, lane_off, 384, j);
+        image_to_tmem(img + (2 * IM_WH + 1) * kImg, tmem, lane_off, 448, j);
+    }
+    tmem_wait_st();
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const bool ok_tmem = (tmem == 0);
+    if (!ok_tmem && tid == 0) set_status(A.status, PSR_EDEVICE);
+    const uint32_t accz = 128u * (uint32_t)s, accc = accz + 64u;
+    const uint32_t bar = smem_u32(&M.mbar[s]);
+    const int bar_id = 1 + s;
+    uint32_t phase = 0;
+    const int Np = A.Np, ntile = Np / TS;
+    const float bz = A.pk[A.fl.bz[l] + j], bh = A.pk[A.fl.bh[l] + j];
+    const int64_t items = ok_tmem ? (int64_t)A.n * ntile : 0;
+    for (int64_t it = (int64_t)blockIdx.x * kFwStreams + s; it < items; it += (int64_t)gridDim.x * kFwStreams) {
+        const int64_t sample = it / ntile;
+        const int t0 = (int)(it % ntile) * TS;
+        float *st = const_cast<float *>(A.stash) + sample * A.stash_stride;
+#pragma unroll 1
+        for (int hh = 0; hh < 2; ++hh) {
+            float v[32];
+            loadk<32>(st + ((int64_t)((l - 1) * kStashQ + kStashY) * H + j) * Np + t0 + 32 * hh, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = gelu_f(v[i]);
+            store_half_split(tiles, tiles + kTile, j, 4 * hh, v);
+        }
+        fence_proxy_async();
+        tc_before();
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+        tc_after();
+        if (j == 0) {
+            const uint64_t bh_ = tdesc(smem_u32(tiles)), bl_ = tdesc(smem_u32(tiles + kTile));
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const uint32_t d = w ? accc : accz, ahi = w ? 384u : 256u, alo = ahi + 64u;
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(d, ahi + kk * 8, bh_ + fm_boff(kk), kk > 0);
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(d, ahi + kk * 8, bl_ + fm_boff(kk), 1);
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(d, alo + kk * 8, bh_ + fm_boff(kk), 1);
+            }
+            mma_commit(bar);
+        }
+        if (!mbar_wait(bar, phase)) {
+            M.abort_flag = 1;
+            set_status(A.status, PSR_ETIMEOUT);
+        }
+        phase ^= 1u;
+        tc_after();
+#pragma unroll 1
+        for (int hh = 0; hh < 2; ++hh) {
+            uint32_t rz[32], rc[32];
+            tmem_ld32(tmem + lane_off + accz + 32 * hh, rz);
+            tmem_ld32(tmem + lane_off + accc + 32 * hh, rc);
+            tmem_wait_ld32(rz);
+            tmem_wait_ld32(rc);
+            float av[32], cv[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const bool in = (t0 + 32 * hh + i) < A.N;
+                av[i] = in ? sigmoid_f(__uint_as_float(rz[i]) + bz) : 0.0f;
+                cv[i] = in ? __uint_as_float(rc[i]) + bh : 0.0f;
+            }
+            storek<32>(st + ((int64_t)(l * kStashQ + kStashA) * H + j) * Np + t0 + 32 * hh, av);
+            storek<32>(st + ((int64_t)(l * kStashQ + kStashC) * H + j) * Np + t0 + 32 * hh, cv);
+        }
+        tc_before();
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+        tc_after();
+        if (M.abort_flag) break;
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        tmem_free_all(tmem, 512);
+    }
+}
+
+// forward scan of layer l: one CTA per sample, thread j = unit j
+__global__ void __launch_bounds__(H) scan_fwd_kernel(const __grid_constant__ BwdTcArgs A) {
+    const int j = threadIdx.x;
+    const int64_t sample = blockIdx.x;
+    const int l = A.l, Np = A.Np, N = A.N;
+    float *st = const_cast<float *>(A.stash) + sample * A.stash_stride;
+    float *ar = st + ((int64_t)(l * kStashQ + kStashA) * H + j) * Np;
+    float *cr = st + ((int64_t)(l * kStashQ + kStashC) * H + j) * Np;
+    float *hr = st + ((int64_t)(l * kStashQ + kStashH) * H + j) * Np;
+    const uint64_t *bits = A.bits + sample * A.W;
+    float ta[3] = {0, 0, 0}, tb[3] = {0, 0, 0}, tc_[3] = {0, 0, 0};
+    if (l == 0) {
+#pragma unroll
+        for (int code = 0; code < 3; ++code) {
+            ta[code] = A.pk[A.fl.A0 + code * H + j];
+            tb[code] = A.pk[A.fl.B0 + code * H + j];
+            tc_[code] = A.pk[A.fl.CD0 + code * H + j];
+        }
+    }
+    float h = 0.0f;
+    float na[8], nc[8];
+    auto fetch = [&](int t, float (&a)[8], float (&c)[8]) {
+        if (l == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int tt = t + i;
+                const int code = (tt == 0) ? 0 : 1 + (int)((bits[(tt - 1) >> 6] >> ((tt - 1) & 63)) & 1ull);
+                a[i] = ta[code];
+                c[i] = tc_[code];
+            }
+        } else {
+            const float4 *a4 = reinterpret_cast<const float4 *>(ar + t);
+            const float4 *c4 = reinterpret_cast<const float4 *>(cr + t);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float4 av = a4[q], cv = c4[q];
+                a[4 * q] = av.x; a[4 * q + 1] = av.y; a[4 * q + 2] = av.z; a[4 * q + 3] = av.w;
+                c[4 * q] = cv.x; c[4 * q + 1] = cv.y; c[4 * q + 2] = cv.z; c[4 * q + 3] = cv.w;
+            }
+        }
+    };
+    fetch(0, na, nc);
+    for (int t = 0; t < Np; t += 8) {
+        float a[8], c[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            a[i] = na[i];
+            c[i] = nc[i];
+        }
+        if (t + 8 < Np) fetch(t + 8, na, nc);  // the next step's inputs, in flight meanwhile
+        float hv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const bool in = (t + i) < N;
+            if (l == 0) {
+                const int tt = t + i;
+                const int code = (tt == 0) ? 0 : 1 + (int)((bits[(tt - 1) >> 6] >> ((tt - 1) & 63)) & 1ull);
+                h = a[i] * h + tb[code];
+            } else {
+                h = a[i] * h + (1.0f - a[i]) * c[i];
+            }
+            hv[i] = in ? h : 0.0f;
+            if (!in) { a[i] = 0.0f; c[i] = 0.0f; }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            reinterpret_cast<float4 *>(hr + t)[q] = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+            if (l == 0) {
+                reinterpret_cast<float4 *>(ar + t)[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+                reinterpret_cast<float4 *>(cr + t)[q] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+            }
+        }
+    }
+}
+
+// output map of layer l: y into the stash
+__global__ void __launch_bounds__(128 * kFwStreams, 1) outmap_fwd_kernel(const __grid_constant__ BwdTcArgs A) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    TcMisc &M = *reinterpret_cast<TcMisc *>(smem + kFwStreams * 4 * kTile);
+    const int tid = threadIdx.x, s = tid >> 7, j = tid & 127, warp = tid >> 5;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    uint8_t *tiles = smem + (4 * s) * kTile;  // h hi, lo, u hi, lo
+    if (warp == 0) tmem_alloc_all(smem_u32(&M.tmem_base), 512);
+    if (tid == 0) {
+        for (int i = 0; i < kFwStreams; ++i) mbar_init(smem_u32(&M.mbar[i]), 1);
+        M.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = M.tmem_base;
+    const int l = A.l;
+    const uint8_t *img = A.images + ((size_t)l * kImgPerLayer + kImgPlain) * kImg;
+    if (s == 0) {
+        image_to_tmem(img + (2 * IM_C) * kImg, tmem, lane_off, 256, j);
+        image_to_tmem(img + (2 * IM_C + 1) * kImg, tmem, lane_off, 320, j);
+    } else if (l >= 1) {
+        image_to_tmem(img + (2 * IM_D) * kImg, tmem, lane_off, 384, j);
+        image_to_tmem(img + (2 * IM_D + 1) * kImg, tmem, lane_off, 448, j);
+    }
+    tmem_wait_st();
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const bool ok_tmem = (tmem == 0);
+    if (!ok_tmem && tid == 0) set_status(A.status, PSR_EDEVICE);
+    const uint32_t acc = 64u * (uint32_t)s;
+    const uint32_t bar = smem_u32(&M.mbar[s]);
+    const int bar_id = 1 + s;
+    uint32_t phase = 0;
+    const int Np = A.Np, ntile = Np / TS;
+    float du[3] = {0, 0, 0};
+    if (l == 0) {
+#pragma unroll
+        for (int code = 0; code < 3; ++code) du[code] = A.pk[A.fl.DU0 + code * H + j];
+    }
+    const int64_t items = ok_tmem ? (int64_t)A.n * ntile : 0;
+    for (int64_t it = (int64_t)blockIdx.x * kFwStreams + s; it < items; it += (int64_t)gridDim.x * kFwStreams) {
+        const int64_t sample = it / ntile;
+        const int t0 = (int)(it % ntile) * TS;
+        float *st = const_cast<float *>(A.stash) + sample * A.stash_stride;
+#pragma unroll 1
+        for (int hh = 0; hh < 2; ++hh) {
+            float v[32];
+            loadk<32>(st + ((int64_t)(l * kStashQ + kStashH) * H + j) * Np + t0 + 32 * hh, v);
+            store_half_split(tiles, tiles + kTile, j, 4 * hh, v);
+            if (l >= 1) {
+                loadk<32>(st + ((int64_t)((l - 1) * kStashQ + kStashY) * H + j) * Np + t0 + 32 * hh, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = gelu_f(v[i]);
+                store_half_split(tiles + 2 * kTile, tiles + 3 * kTile, j, 4 * hh, v);
+            }
+        }
+        fence_proxy_async();
+        tc_before();
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+        tc_after();
+        if (j == 0) {
+            const uint64_t hh_ = tdesc(smem_u32(tiles)), hl_ = tdesc(smem_u32(tiles + kTile));
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(acc, 256 + kk * 8, hh_ + fm_boff(kk), kk > 0);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(acc, 256 + kk * 8, hl_ + fm_boff(kk), 1);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(acc, 320 + kk * 8, hh_ + fm_boff(kk), 1);
+            if (l >= 1) {
+                const uint64_t uh = tdesc(smem_u32(tiles + 2 * kTile)), ul = tdesc(smem_u32(tiles + 3 * kTile));
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(acc, 384 + kk * 8, uh + fm_boff(kk), 1);
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(acc, 384 + kk * 8, ul + fm_boff(kk), 1);
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) mma_ts<kIdescFM>(acc, 448 + kk * 8, uh + fm_boff(kk), 1);
+            }
+            mma_commit(bar);
+        }
+        if (!mbar_wait(bar, phase)) {
+            M.abort_flag = 1;
+            set_status(A.status, PSR_ETIMEOUT);
+        }
+        phase ^= 1u;
+        tc_after();
+        const uint64_t *bits = A.bits + sample * A.W;
+#pragma unroll 1
+        for (int hh = 0; hh < 2; ++hh) {
+            uint32_t r[32];
+            tmem_ld32(tmem + lane_off + acc + 32 * hh, r);
+            tmem_wait_ld32(r);
+            float y[32];
+            if (l >= 2) loadk<32>(st + ((int64_t)((l - 1) * kStashQ + kStashH) * H + j) * Np + t0 + 32 * hh, y);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int tt = t0 + 32 * hh + i;
+                float v = __uint_as_float(r[i]);
+                if (l >= 2) v += y[i];
+                if (l == 0) {
+                    const int code = (tt == 0) ? 0 : 1 + (int)((bits[(tt - 1) >> 6] >> ((tt - 1) & 63)) & 1ull);
+                    v += du[code];
+                }
+                y[i] = (tt < A.N) ? v : 0.0f;
+            }
+            storek<32>(st + ((int64_t)(l * kStashQ + kStashY) * H + j) * Np + t0 + 32 * hh, y);
+        }
+        tc_before();
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+        tc_after();
+        if (M.abort_flag) break;
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        tmem_free_all(tmem, 512);
+    }
+}
+
+// readout adjoint g_t = 1/2 (s_t - sigmoid(d_t)) with d = wd . GELU(y) + bd
+// of the top layer (0 at forced sites and at t >= N): one thread per site
+__global__ void readout_fwd_kernel(const __grid_constant__ BwdTcArgs A) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Np = A.Np, N = A.N;
+    if (i >= (int64_t)A.n * Np) return;
+    const int64_t sample = i / Np;
+    const int t = (int)(i % Np);
+    float *st = const_cast<float *>(A.stash) + sample * A.stash_stride;
+    float g = 0.0f;
+    if (t < N) {
+        const float *y = st + ((int64_t)((A.nL - 1) * kStashQ + kStashY) * H) * Np + t;
+        float d = A.pk[A.fl.bd];
+        for (int k = 0; k < H; ++k) d += A.wd[k] * gelu_f(y[(int64_t)k * Np]);
+        const uint64_t *row = A.bits + sample * A.W;
+        const int sv = (int)((row[t >> 6] >> (t & 63)) & 1ull);
+        const int forced = u1_forced(A.u1, N, t, A.u1 ? count_up_before(row, t) : 0);
+        g = (forced >= 0) ? 0.0f : 0.5f * ((float)sv - 1.0f / (1.0f + expf(-d)));
+    }
+    st[(int64_t)A.nL * kStashQ * H * Np + t] = g;
+}
+
+cudaError_t launch_fwd_tc(const BwdTcArgs &A0, int num_sms, cudaStream_t stream) {
+    cudaError_t e = prepare_bwd_tc();  // declared in psr_internal.cuh
+    if (e != cudaSuccess) return e;
+    BwdTcArgs A = A0;
+    const int64_t items = (int64_t)A.n * (A.Np / TS);
+    int g = num_sms;
+    if ((int64_t)g * kFwStreams > items) g = (int)((items + kFwStreams - 1) / kFwStreams);
+    if (g < 1) g = 1;
+    for (int l = 0; l < A.nL; ++l) {
+        A.l = l;
+        if (l >= 1) {
+            proj_fwd_kernel<<<g, 128 * kFwStreams, kFwSmem, stream>>>(A);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        scan_fwd_kernel<<<A.n, H, 0, stream>>>(A);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        outmap_fwd_kernel<<<g, 128 * kFwStreams, kFwSmem, stream>>>(A);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int64_t sites = (int64_t)A.n * A.Np;
+    readout_fwd_kernel<<<(unsigned)((sites + 255) / 256), 256, 0, stream>>>(A);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_bwd_tc() {
     static bool done[64] = {};
     int dev = 0;
@@ -680,6 +1064,10 @@ cudaError_t prepare_bwd_tc() {
         e = cudaFuncSetAttribute(gx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGxSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(proj_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(outmap_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwSmem);
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
 }

@@ -150,10 +150,7 @@ cudaError_t launch_bitpack(const uint8_t *spins, int64_t n, int N, int W, uint64
     return cudaGetLastError();
 }
 
-// STASH: also write the per-layer values the tensor-core backward needs
-// (groups whose stash pointer is set, mode 0); a separate instantiation so
-// that the plain forward keeps its register budget.
-template <int H, int CH, bool STASH>
+template <int H, int CH>
 __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJobs jb,
                                                    const float *__restrict__ pk, F32Layout fl) {
     static_assert(CH == 16 || CH == 32, "chunk of 16 or 32 sites");
@@ -182,7 +179,6 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
     const float b0_0 = pk[fl.B0 + j], b0_1 = pk[fl.B0 + H + j], b0_2 = pk[fl.B0 + 2 * H + j];
     const float d0_0 = pk[fl.DU0 + j], d0_1 = pk[fl.DU0 + H + j], d0_2 = pk[fl.DU0 + 2 * H + j];
     const float bd = pk[fl.bd];
-    __shared__ float s_gd[CH];
 
     for (;;) {
         if (j == 0) s_job = (long long)atomicAdd((unsigned long long *)jb.job_counter, 1ull);
@@ -213,24 +209,6 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                 : G.carries_in[(((int64_t)sample * nch + c0) * nL + l) * H + j];
         int n_up = G.u1 ? count_up_before(row, c0 * CH) : 0;
         float acc = 0.0f;
-        // stash of this sample (mode 0): [l][q][H][Npad] blocks, then g [Npad]
-        const int Np = stash_npad(N);
-        float *stash = (STASH && jb.mode == 0 && G.stash)
-                           ? G.stash + (int64_t)sample * stash_floats_per_sample(nL, H, N)
-                           : nullptr;
-        // one chunk of sites of row j of block (l, q); zero beyond N
-        auto stash_put = [&](int l, int q, int t0, const float *v) {
-            float *dst = stash + ((int64_t)(l * kStashQ + q) * H + j) * Np + t0;
-#pragma unroll
-            for (int t4 = 0; t4 < CH / 4; ++t4) {
-                float4 w;
-                w.x = (t0 + 4 * t4 + 0 < N) ? v[4 * t4 + 0] : 0.0f;
-                w.y = (t0 + 4 * t4 + 1 < N) ? v[4 * t4 + 1] : 0.0f;
-                w.z = (t0 + 4 * t4 + 2 < N) ? v[4 * t4 + 2] : 0.0f;
-                w.w = (t0 + 4 * t4 + 3 < N) ? v[4 * t4 + 3] : 0.0f;
-                if (t0 + 4 * t4 < Np) reinterpret_cast<float4 *>(dst)[t4] = w;
-            }
-        };
 
         for (int c = c0; c < nch; ++c) {
             const int t0 = c * CH;
@@ -259,19 +237,6 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                     y[t] = first ? d0_0 : (sb ? d0_2 : d0_1);
                 }
                 hcar[j] = hv;
-                if (stash) {
-                    float av[CH], cv[CH];
-#pragma unroll
-                    for (int t = 0; t < CH; ++t) {
-                        const bool first = (t0 + t == 0);
-                        const uint32_t sb = (prevbits >> t) & 1u;
-                        av[t] = first ? a0_0 : (sb ? a0_2 : a0_1);
-                        cv[t] = pk[fl.CD0 + (first ? 0 : (sb ? 2 : 1)) * H + j];
-                    }
-                    stash_put(0, kStashA, t0, av);
-                    stash_put(0, kStashC, t0, cv);
-                    stash_put(0, kStashH, t0, hl);
-                }
                 float4 *dst = reinterpret_cast<float4 *>(hs + j * LD);
 #pragma unroll
                 for (int t4 = 0; t4 < CH / 4; ++t4)
@@ -291,7 +256,6 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                         y[4 * t4 + 2] += w * v.z; y[4 * t4 + 3] += w * v.w;
                     }
                 }
-                if (stash) stash_put(0, kStashY, t0, y);
                 float4 *dst = reinterpret_cast<float4 *>(xs + j * LD);
 #pragma unroll
                 for (int t4 = 0; t4 < CH / 4; ++t4)
@@ -328,14 +292,8 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                         const float a = sigmoid_f(z[t]);
                         hv = a * hv + (1.0f - a) * y[t];
                         hn[t] = hv;
-                        if (stash) z[t] = a;  // z is not needed after the gate
                     }
                     hcar[l * H + j] = hv;
-                    if (stash) {
-                        stash_put(l, kStashA, t0, z);
-                        stash_put(l, kStashC, t0, y);
-                        stash_put(l, kStashH, t0, hn);
-                    }
                     float4 *dst = reinterpret_cast<float4 *>(hs + j * LD);
 #pragma unroll
                     for (int t4 = 0; t4 < CH / 4; ++t4)
@@ -361,7 +319,6 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                     }
                 }
                 __syncthreads();
-                if (stash) stash_put(l, kStashY, t0, y);
                 float4 *dst = reinterpret_cast<float4 *>(xs + j * LD);
 #pragma unroll
                 for (int t4 = 0; t4 < CH / 4; ++t4)
@@ -383,14 +340,9 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
                     for (int k = 0; k < H; ++k) d += wd[k] * xs[k * LD + t];
                     const int s = (cur >> t) & 1u;
                     const int nu = n_up + __popc(cur & ((1u << t) - 1u));
-                    const int forced = u1_forced(G.u1, N, tt, nu);
-                    const float lp = site_logp(d, s, forced);
+                    const float lp = site_logp(d, s, u1_forced(G.u1, N, tt, nu));
                     if (G.logp_out) G.logp_out[(int64_t)sample * N + tt] = lp;
-                    // d log P / d d = s - P(1 | s_<t) = s - sigma(d); 0 when forced
-                    if (stash) s_gd[t] = (forced >= 0) ? 0.0f : 0.5f * ((float)s - 1.0f / (1.0f + expf(-d)));
                     v = (jb.mode == 1) ? lp - G.logp_ref[(int64_t)sample * N + tt] : lp;
-                } else if (stash && t < CH) {
-                    s_gd[t] = 0.0f;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -398,62 +350,42 @@ __global__ void __launch_bounds__(H) fwd_f32_kernel(const __grid_constant__ FwdJ
             }
             n_up += __popc(cur);
             __syncthreads();
-            if (stash && j < CH && t0 + j < Np)
-                stash[(int64_t)nL * kStashQ * H * Np + t0 + j] = s_gd[j];
-        }
-        if (stash) {
-            // sites from the end of the last chunk to the padded length
-            for (int t = nch * CH; t < Np; ++t) {
-                for (int l = 0; l < nL; ++l)
-                    for (int q = 0; q < kStashQ; ++q) stash[((int64_t)(l * kStashQ + q) * H + j) * Np + t] = 0.0f;
-                if (j == 0) stash[(int64_t)nL * kStashQ * H * Np + t] = 0.0f;
-            }
         }
         if (j == 0) G.out[lj] = 0.5f * acc;
     }
 }
 
-template <int H, int CH, bool STASH>
+template <int H, int CH>
 static cudaError_t launch_fwd_f32_h(const FwdJobs &jobs, const float *packed, const F32Layout &fl,
                                     int num_sms, cudaStream_t stream) {
     const size_t smem = (size_t)(2 * H * (CH + 4) + kMaxLayers * H) * sizeof(float);
     int per_sm = 0;
-    cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_f32_kernel<H, CH, STASH>, H, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_f32_kernel<H, CH>, H, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
     const int64_t nj = max_jobs(jobs);
     if (nj < grid) grid = nj;
     if (grid < 1) grid = 1;
-    fwd_f32_kernel<H, CH, STASH><<<(int)grid, H, smem, stream>>>(jobs, packed, fl);
+    fwd_f32_kernel<H, CH><<<(int)grid, H, smem, stream>>>(jobs, packed, fl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_f32(const FwdJobs &jobs, const float *packed, const F32Layout &fl,
                            int num_sms, cudaStream_t stream, int chunk) {
-    bool stash = false;
-    for (int i = 0; i < jobs.n_groups; ++i) stash = stash || jobs.g[i].stash != nullptr;
-    if (stash) {
-        // the stash serves the tensor-core backward (hidden 128, log psi jobs)
-        if (fl.H != 128 || jobs.mode != 0) return cudaErrorInvalidValue;
-        if (chunk == kChunkGrad) return launch_fwd_f32_h<128, kChunkGrad, true>(jobs, packed, fl, num_sms, stream);
-        if (chunk == kChunkF32) return launch_fwd_f32_h<128, kChunkF32, true>(jobs, packed, fl, num_sms, stream);
-        return cudaErrorInvalidValue;
-    }
     if (chunk == kChunkGrad) {
         switch (fl.H) {
-            case 32: return launch_fwd_f32_h<32, kChunkGrad, false>(jobs, packed, fl, num_sms, stream);
-            case 64: return launch_fwd_f32_h<64, kChunkGrad, false>(jobs, packed, fl, num_sms, stream);
-            case 128: return launch_fwd_f32_h<128, kChunkGrad, false>(jobs, packed, fl, num_sms, stream);
+            case 32: return launch_fwd_f32_h<32, kChunkGrad>(jobs, packed, fl, num_sms, stream);
+            case 64: return launch_fwd_f32_h<64, kChunkGrad>(jobs, packed, fl, num_sms, stream);
+            case 128: return launch_fwd_f32_h<128, kChunkGrad>(jobs, packed, fl, num_sms, stream);
             default: return cudaErrorInvalidValue;
         }
     }
     if (chunk != kChunkF32) return cudaErrorInvalidValue;
     switch (fl.H) {
-        case 32: return launch_fwd_f32_h<32, kChunkF32, false>(jobs, packed, fl, num_sms, stream);
-        case 64: return launch_fwd_f32_h<64, kChunkF32, false>(jobs, packed, fl, num_sms, stream);
-        case 128: return launch_fwd_f32_h<128, kChunkF32, false>(jobs, packed, fl, num_sms, stream);
+        case 32: return launch_fwd_f32_h<32, kChunkF32>(jobs, packed, fl, num_sms, stream);
+        case 64: return launch_fwd_f32_h<64, kChunkF32>(jobs, packed, fl, num_sms, stream);
+        case 128: return launch_fwd_f32_h<128, kChunkF32>(jobs, packed, fl, num_sms, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -68,13 +68,10 @@ struct FwdGroup {
     float *out;                  // mode 0: [n] log psi; mode 1: [E] delta
     float *logp_out;             // mode 0, optional: [n][N]
     float *carries_out;          // mode 0, optional: [n][nch][nL][H]
-    float *stash;                // mode 0, optional (FP32 kernel): per sample the
-                                 // layer values the tensor-core backward needs,
-                                 // see stash_floats_per_sample
 };
 
-// Stash of one sample for the tensor-core backward, written by the FP32
-// forward (mode 0): for layer l and quantity q (kStashA: gate a, kStashC:
+// Stash of one sample for the tensor-core backward, written by its own
+// forward (launch_fwd_tc): for layer l and quantity q (kStashA: gate a, kStashC:
 // candidate c = W_h u + b_h, kStashH: state h, kStashY: output-map
 // pre-activation y, residual included) a [H][Npad] block at
 // ((l * kStashQ + q) * H) * Npad, then the readout adjoint g [Npad] at
@@ -339,8 +336,14 @@ struct BwdTcArgs {
     float *gh;               // C^T gy
     float *dz, *dc;          // gate and candidate adjoints
     float *rows;             // [n][P] O_k rows of the batch
+    const float *pk;         // packed FP32 weights (layer-0 tables, biases, readout)
+    F32Layout fl;
+    int u1;
     int *status;
 };
+// The forward that fills the stash of a batch (all layers and the readout
+// adjoint) with the same split-BF16 tensor-core products.
+cudaError_t launch_fwd_tc(const BwdTcArgs &A, int num_sms, cudaStream_t stream);
 size_t bwd_tc_image_bytes(int nL);
 cudaError_t launch_pack_bwd_tc(const float *theta, const ThetaLayout &tl, void *images, cudaStream_t stream);
 cudaError_t launch_bwd_tc_layer(const BwdTcArgs &A, int num_sms, cudaStream_t stream);
