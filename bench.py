@@ -43,7 +43,18 @@ WORKLOADS = {
 }
 
 # kernels launched per call of each entry point (BF16 precision)
-LAUNCHES = {"logpsi": 4, "grad": 4, "local_energy": 11}
+LAUNCHES = {"logpsi": 4, "local_energy": 11}
+TC_STASH_BUDGET = 16 << 30      # bytes of stash and layer arrays per gradient batch
+
+
+def grad_launches(n, L, nL=N_LAYERS, H=HIDDEN):
+    """Kernels of one tensor-core gradient call: three packing kernels, then per
+    batch 3 nL forward launches (scan and output map per layer, projections
+    above layer 0, the readout adjoint) and 4 nL - 1 backward launches."""
+    npad = (L + 63) & ~63
+    per = ((nL * 4 * H + 1) * npad + 7 * H * npad) * 4
+    B = max(1, min(n, TC_STASH_BUDGET // per))
+    return 3 + -(-n // B) * (7 * nL - 1)
 
 
 def parse():
@@ -956,7 +967,7 @@ def run_mine(args):
                    "parallelism": f"dp{world} (independent samples per GPU)"},
         "evaluated_value": evaluated_value,
         "roofline": roofline,
-        "gpu_launches": args.steps * sum(LAUNCHES.values()),
+        "gpu_launches": args.steps * (sum(LAUNCHES.values()) + grad_launches(n, N)),
         "clocks": clk,
         "wall_s_timed_region": wall,
         "stages_ms_last_local_energy": B.psr_context_stage_ms(ctx),
