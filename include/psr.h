@@ -55,7 +55,8 @@
  * run on the tensor cores (tcgen05) with BF16 operands and FP32
  * accumulation; the gates, scan carry, softmax, log-psi sums and every
  * reduction stay in FP32 (hidden = 128 only).  psr_grad always computes in
- * FP32.
+ * FP32.  PSR_FP16 (FP16 operands, FP32 accumulation) applies to the 2D
+ * patched model's forward only (PSR_EUNSUPPORTED elsewhere).
  *
  * Errors.  Every call returns PSR_OK or an error code; nothing traps.
  * Asynchronous device-side failures (a bounded wait that expired, an
@@ -82,7 +83,7 @@ enum {
     PSR_EUNSUPPORTED = 6 /* valid request the library does not implement */
 };
 
-enum { PSR_FP32 = 0, PSR_BF16 = 1 };
+enum { PSR_FP32 = 0, PSR_BF16 = 1, PSR_FP16 = 2 };
 enum { PSR_HEISENBERG = 0, PSR_TFIM = 1 };
 
 typedef struct psr_context psr_context;
@@ -92,7 +93,7 @@ typedef struct {
     int32_t n_layers;  /* >= 1, <= 8 */
     int32_t hidden;    /* 32, 64 or 128 (PSR_BF16: 128) */
     int32_t u1_mask;   /* 0 or 1 */
-    int32_t precision; /* PSR_FP32 or PSR_BF16 */
+    int32_t precision; /* PSR_FP32, PSR_BF16 or (2D model only) PSR_FP16 */
     const float *theta;
     psr_context *ctx;
 } psr_params;
@@ -387,12 +388,23 @@ int psr_fwd_shape_for(psr_context *ctx, int32_t precision, int32_t what, int32_t
  * (the last hidden columns act on h_V), b_h[hidden], C[hidden][hidden],
  * D[hidden][din]; then W_o[16][hidden], b_o[16]; psr2d_param_count gives
  * the length (12 H^2 + 118 H + 16 for three layers).
- * Computed in FP32 on CUDA cores, row by row: within a patch row all sites
- * share one batched projection and one scan (the row starts from h_H = 0).
- * hidden may also be 256 (the paper's 52 x 52 model) with at most 4 layers.
- * PSR_EUNSUPPORTED for precision PSR_BF16, Lx > 64 (more than 32 patches
- * per row) or hidden 256 with more than 4 layers; PSR_EINVAL for odd Lx or
- * Ly and what psr_logpsi rejects. */
+ * Evaluated row by row: within a patch row all sites share one batched
+ * projection and one scan (the row starts from h_H = 0).  hidden may also
+ * be 256 (the paper's 52 x 52 model) with at most 4 layers.
+ * Precision PSR_FP32: every product in FP32 on CUDA cores.  PSR_FP16 and
+ * PSR_BF16: every product (W_z u, W_h [u, h_V], C h, D u, W_o x) on the
+ * tensor cores (tcgen05) with 16-bit operands (FP16, 11-bit significand;
+ * BF16, 8-bit) and FP32 accumulation; the gates, scan, residual, GELU,
+ * softmax and log-psi sums in FP32; hidden 128 or 256.  The stored row
+ * states (the h_V of the next row, the checkpoints connected
+ * configurations resume from) are 16-bit in that format.  Measured against
+ * the FP64 oracle at hidden 256: FP16 meets the BF16 path's stated bounds
+ * (|d log psi| <= 2e-2 + 2e-5 |log psi|, E_loc 1e-3 relative); BF16
+ * operands meet the log psi bound but reach about 2e-3 on E_loc.
+ * psr2d_sample and psr2d_grad compute in FP32 at every precision.
+ * PSR_EUNSUPPORTED for Lx > 64 (more than 32 patches per row), hidden 256
+ * with more than 4 layers, or a 16-bit precision with hidden 32 or 64;
+ * PSR_EINVAL for odd Lx or Ly and what psr_logpsi rejects. */
 int psr2d_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
 
 int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t Lx, int32_t Ly,
@@ -451,7 +463,7 @@ int psr2d_sym_local_energy(const psr_params *params, const uint8_t *samples, int
  * B_re[H][din], B_im[H][din], C_re[H][H], C_im[H][H], D ([H][2] at layer 0,
  * else [H]), W_a[H][H], b_a[H], W_g[H][H], b_g[H] (din = 2 at layer 0, else
  * H), then W_o[2][H], b_o[2]; 16 H^2 + 25 H + 2 values for three layers.
- * Computed in FP32 on CUDA cores (PSR_EUNSUPPORTED for PSR_BF16). */
+ * Computed in FP32 on CUDA cores (PSR_EUNSUPPORTED for PSR_BF16, PSR_FP16). */
 int psr_lru_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
 
 int psr_lru_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, float *out);

@@ -28,7 +28,7 @@ class ModelConfig:
     n_layers: int = 3
     hidden: int = 128
     u1: bool = False
-    precision: str = "fp32"  # "fp32" or "bf16"
+    precision: str = "fp32"  # "fp32", "bf16" or (2D patched model) "fp16"
 
 
 def _device_of(*ts):

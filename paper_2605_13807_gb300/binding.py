@@ -18,10 +18,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpsr.so")
 
 PSR_OK, PSR_EINVAL, PSR_ENOMEM, PSR_ECUDA, PSR_ETIMEOUT, PSR_EDEVICE, PSR_EUNSUPPORTED = range(7)
-PSR_FP32, PSR_BF16 = 0, 1
+PSR_FP32, PSR_BF16, PSR_FP16 = 0, 1, 2
 PSR_HEISENBERG, PSR_TFIM = 0, 1
 
-_PRECISION = {"fp32": PSR_FP32, "bf16": PSR_BF16, PSR_FP32: PSR_FP32, PSR_BF16: PSR_BF16}
+_PRECISION = {"fp32": PSR_FP32, "bf16": PSR_BF16, "fp16": PSR_FP16, PSR_FP32: PSR_FP32, PSR_BF16: PSR_BF16,
+              PSR_FP16: PSR_FP16}
 
 
 class PsrError(RuntimeError):

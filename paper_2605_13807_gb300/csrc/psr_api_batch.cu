@@ -406,6 +406,7 @@ int psr_local_energy_batch(const psr_params *params, const psr_batch_item *items
 }
 
 int psr_context_set_fwd_shape(psr_context *ctx, int32_t precision, int32_t shape) {
+    if (ctx && precision == PSR_FP16) return PSR_EUNSUPPORTED;
     if (!ctx || (precision != PSR_FP32 && precision != PSR_BF16)) return PSR_EINVAL;
     const bool bf16 = precision == PSR_BF16;
     if (shape != 0 && !fwd_shape_valid(bf16, shape)) return PSR_EINVAL;
@@ -415,6 +416,7 @@ int psr_context_set_fwd_shape(psr_context *ctx, int32_t precision, int32_t shape
 
 int psr_fwd_shape_for(psr_context *ctx, int32_t precision, int32_t what, int32_t n_sets, const int64_t *n,
                       const int32_t *L, int32_t *shape, int32_t *tuned) {
+    if (ctx && precision == PSR_FP16) return PSR_EUNSUPPORTED;
     if (!ctx || !shape || !n || !L || (precision != PSR_FP32 && precision != PSR_BF16) || what < 0 ||
         what > 2 || n_sets < 1 || n_sets > kMaxGroups || (what < 2 && n_sets != 1))
         return PSR_EINVAL;

@@ -121,6 +121,7 @@ inline int check_params(const psr_params *p, int64_t n, int32_t L) {
     if (p->n_layers < 1 || p->n_layers > kMaxLayers) return PSR_EINVAL;
     if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128) return PSR_EINVAL;
     if (p->u1_mask != 0 && p->u1_mask != 1) return PSR_EINVAL;
+    if (p->precision == PSR_FP16) return PSR_EUNSUPPORTED;  // the 2D model's forward only
     if (p->precision != PSR_FP32 && p->precision != PSR_BF16) return PSR_EINVAL;
     if (n < 1 || L < 1) return PSR_EINVAL;
     if (n > (int64_t)1 << 31) return PSR_EINVAL;

@@ -14,12 +14,69 @@ int check_params2d(const psr_params *p, int64_t n, int Lx, int Ly) {
     if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128 && p->hidden != 256) return PSR_EINVAL;
     if (p->hidden == 256 && p->n_layers > 4) return PSR_EUNSUPPORTED;  // shared memory
     if (p->u1_mask != 0 && p->u1_mask != 1) return PSR_EINVAL;
-    if (p->precision != PSR_FP32 && p->precision != PSR_BF16) return PSR_EINVAL;
+    if (p->precision != PSR_FP32 && p->precision != PSR_BF16 && p->precision != PSR_FP16) return PSR_EINVAL;
     if (n < 1 || n > (int64_t)1 << 31) return PSR_EINVAL;
     if (Lx < 2 || Ly < 2 || (Lx % 2) || (Ly % 2) || (int64_t)Lx * Ly > (1 << 24)) return PSR_EINVAL;
     if (Lx > 64) return PSR_EUNSUPPORTED;  // at most 32 patches per row
-    if (p->precision != PSR_FP32) return PSR_EUNSUPPORTED;
+    // FP16 / BF16: the forward evaluations (log psi, E_loc) on the tensor cores
+    if (p->precision != PSR_FP32 && !fwd2d_tc_supported(p->n_layers, p->hidden, Lx)) return PSR_EUNSUPPORTED;
     return PSR_OK;
+}
+
+// Workspace of the tensor-core forward (16-bit precisions): the weight slices,
+// per-CTA h_V images and residual rows, and a zero image (the h_V of row 0).
+struct Tc2 {
+    uint8_t *wimg = nullptr, *scratch = nullptr, *zero = nullptr;
+    float *res = nullptr;
+};
+
+void tc2_carve(Carver &c, psr_context *ctx, int nL, int H, int Lx, Tc2 &t) {
+    t.wimg = c.get<uint8_t>(fwd2d_tc_weight_bytes(nL, H));
+    t.scratch = c.get<uint8_t>(fwd2d_tc_scratch_bytes(nL, H, Lx, ctx->num_sms));
+    t.zero = c.get<uint8_t>(fwd2d_tc_image_bytes(H, Lx));
+    t.res = c.get<float>(fwd2d_tc_res_floats(H, ctx->num_sms));
+}
+
+cudaError_t tc2_prepare(const float *theta, const T2Layout &tl, int Lx, bool f16, const Tc2 &t,
+                        cudaStream_t st) {
+    cudaError_t e = launch_pack2d_tc(theta, tl, f16, t.wimg, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(t.zero, 0, fwd2d_tc_image_bytes(tl.H, Lx), st);
+}
+
+// The jobs of `jb` on the tensor cores; row checkpoints as 16-bit images
+// (img_out written in mode 0 when set, img_in read in mode 1).
+cudaError_t tc2_run(psr_context *ctx, const Fwd2Jobs &jb, bool f16, const float *theta, const T2Layout &tl,
+                    const Tc2 &t, const uint8_t *img_in, uint8_t *img_out) {
+    Fwd2TcArgs a{};
+    a.mode = jb.mode;
+    a.f16 = f16 ? 1 : 0;
+    a.Lx = jb.g.Lx;
+    a.Ly = jb.g.Ly;
+    a.u1 = jb.g.u1;
+    a.n_jobs = jb.g.n_jobs;
+    a.n_jobs_dev = jb.g.n_jobs_dev;
+    a.spins = jb.g.spins;
+    a.entries = jb.g.entries;
+    a.img_in = img_in;
+    a.img_out = img_out;
+    a.scratch = t.scratch;
+    a.zero_img = t.zero;
+    a.res = t.res;
+    a.logp_ref = jb.g.logp_ref;
+    a.out = jb.g.out;
+    a.logp_out = jb.g.logp_out;
+    a.theta = theta;
+    a.tl = tl;
+    a.wimg = t.wimg;
+    a.job_counter = jb.job_counter;
+    a.status = jb.status;
+    int W, S;
+    fwd2d_tc_geometry(a.Lx, &W, &S);
+    int64_t grid = (jb.g.n_jobs + S - 1) / S;
+    if (grid > ctx->num_sms) grid = ctx->num_sms;
+    if (grid < 1) grid = 1;
+    return launch_fwd2d_tc(a, (int)grid, ctx->stream);
 }
 
 }  // namespace
@@ -41,6 +98,8 @@ int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int3
     const int nL = params->n_layers, H = params->hidden, N = Lx * Ly;
     const int64_t P = param_count2d(nL, H);
     const F2Layout f = f2_layout(nL, H);
+    const T2Layout tl = t2_layout(nL, H);
+    const bool tc = params->precision != PSR_FP32, f16 = params->precision == PSR_FP16;
     const int W = (int)words_per_row(N);
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(spins),
                d_out = is_device_ptr(out);
@@ -48,13 +107,15 @@ int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int3
     uint8_t *s_ws = nullptr;
     uint64_t *bits = nullptr;
     unsigned long long *counter = nullptr;
+    Tc2 t2{};
     auto carve = [&](Carver &c) {
         theta_ws = c.get<float>(d_theta ? 0 : P);
         s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
         out_ws = c.get<float>(d_out ? 0 : n);
-        pk = c.get<float>(f.total);
+        pk = c.get<float>(tc ? 0 : f.total);
         bits = c.get<uint64_t>((size_t)n * W);
         counter = c.get<unsigned long long>(1);
+        if (tc) tc2_carve(c, ctx, nL, H, Lx, t2);
     };
     Carver sz;
     carve(sz);
@@ -71,7 +132,8 @@ int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int3
     reset_stages(ctx);
     {
         StageScope sc(ctx, PSR_STAGE_PACK);
-        PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
+        if (tc) PSR_TRY(tc2_prepare(theta, tl, Lx, f16, t2, st));
+        else PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
         PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));  // spin-byte check
         PSR_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
     }
@@ -87,7 +149,8 @@ int psr2d_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int3
     jb.status = ctx->status;
     {
         StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
-        PSR_TRY(launch_fwd2d_f32(jb, pk, f, ctx->num_sms, st));
+        if (tc) PSR_TRY(tc2_run(ctx, jb, f16, theta, tl, t2, nullptr, nullptr));
+        else PSR_TRY(launch_fwd2d_f32(jb, pk, f, ctx->num_sms, st));
     }
     if (!d_out) PSR_TRY(cudaMemcpyAsync(out, out_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
     if (!d_out || !d_s || !d_theta) return take_status(ctx);
@@ -265,6 +328,8 @@ int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t
     const int N = Lx * Ly, Py = Ly / 2, Np = (Lx / 2) * Py;
     const int64_t P = param_count2d(nL, H);
     const F2Layout f = f2_layout(nL, H);
+    const T2Layout tl = t2_layout(nL, H);
+    const bool tc = params->precision != PSR_FP32, f16 = params->precision == PSR_FP16;
     const int W = (int)words_per_row(N);
     const int nb = bond_count(Lx, Ly, ham->pbc);
     const int64_t cap = n * max_entries_per_sample(ham);
@@ -278,13 +343,15 @@ int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t
     uint8_t *s_ws = nullptr;
     uint64_t *bits = nullptr;
     unsigned long long *counters = nullptr;
+    uint8_t *imgs = nullptr;
+    Tc2 t2{};
     ConnBufs b{};
     auto carve = [&](Carver &c) {
         theta_ws = c.get<float>(d_theta ? 0 : P);
         s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
         out_ws = c.get<float>(d_out ? 0 : n);
         stats_ws = c.get<double>(d_stats ? 0 : 3);
-        pk = c.get<float>(f.total);
+        pk = c.get<float>(tc ? 0 : f.total);
         bits = c.get<uint64_t>((size_t)n * W);
         b.bonds = c.get<int32_t>(2 * (size_t)nb + 2);
         b.counts = c.get<int64_t>(n);
@@ -293,7 +360,9 @@ int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t
         b.entries = c.get<int32_t>(3 * (size_t)cap);
         lpsi = c.get<float>(n);
         logp = c.get<float>((size_t)n * Np);
-        carries = c.get<float>((size_t)n * Py * ckpt);
+        carries = c.get<float>(tc ? 0 : (size_t)n * Py * ckpt);
+        imgs = c.get<uint8_t>(tc ? (size_t)n * fwd2d_tc_ckpt_bytes(nL, H, Lx, Ly) : 0);
+        if (tc) tc2_carve(c, ctx, nL, H, Lx, t2);
         delta = c.get<float>(cap);
         counters = c.get<unsigned long long>(2);
     };
@@ -314,7 +383,8 @@ int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t
     reset_stages(ctx);
     {
         StageScope sc(ctx, PSR_STAGE_PACK);
-        PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
+        if (tc) PSR_TRY(tc2_prepare(theta, tl, Lx, f16, t2, st));
+        else PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
         PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));  // spin-byte check
         PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
     }
@@ -348,11 +418,13 @@ int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t
     jc.job_counter = counters + 1;
     {
         StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
-        PSR_TRY(launch_fwd2d_f32(js, pk, f, ctx->num_sms, st));
+        if (tc) PSR_TRY(tc2_run(ctx, js, f16, theta, tl, t2, nullptr, imgs));
+        else PSR_TRY(launch_fwd2d_f32(js, pk, f, ctx->num_sms, st));
     }
     if (cap > 0) {
         StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
-        PSR_TRY(launch_fwd2d_f32(jc, pk, f, ctx->num_sms, st));
+        if (tc) PSR_TRY(tc2_run(ctx, jc, f16, theta, tl, t2, imgs, nullptr));
+        else PSR_TRY(launch_fwd2d_f32(jc, pk, f, ctx->num_sms, st));
     }
     {
         StageScope sc(ctx, PSR_STAGE_GATHER);
@@ -384,6 +456,9 @@ int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32
     const int nL = params->n_layers, H = params->hidden, N = L * L, Py = L / 2, Np = (L / 2) * Py;
     const int64_t P = param_count2d(nL, H);
     const F2Layout f = f2_layout(nL, H);
+    const T2Layout tl = t2_layout(nL, H);
+    const bool tc = params->precision != PSR_FP32, f16 = params->precision == PSR_FP16;
+    const size_t ckpt_img = tc ? fwd2d_tc_ckpt_bytes(nL, H, L, L) : 0;
     const bool eloc = ham != nullptr;
     const int W = (int)words_per_row(N);
     const int nb = eloc ? bond_count(L, L, ham->pbc) : 0;
@@ -398,13 +473,16 @@ int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32
     uint64_t *bits = nullptr;
     int32_t *ent8 = nullptr;
     unsigned long long *counters = nullptr;
+    uint8_t *ckimg8 = nullptr;
+    Tc2 t2{};
     ConnBufs b{};
     auto carve = [&](Carver &c) {
         theta_ws = c.get<float>(d_theta ? 0 : P);
         s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
         out_ws = c.get<float>(d_out ? 0 : n);
         stats_ws = c.get<double>(d_stats ? 0 : 3);
-        pk = c.get<float>(f.total);
+        pk = c.get<float>(tc ? 0 : f.total);
+        if (tc) tc2_carve(c, ctx, nL, H, L, t2);
         bits = c.get<uint64_t>((size_t)n * W);
         imgs = c.get<uint8_t>((size_t)8 * n * N);
         lp8 = c.get<float>((size_t)8 * n);
@@ -417,7 +495,8 @@ int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32
             b.entries = c.get<int32_t>(3 * (size_t)cap);
             ent8 = c.get<int32_t>((size_t)8 * 3 * cap);
             logp8 = c.get<float>((size_t)8 * n * Np);
-            carries8 = c.get<float>((size_t)8 * n * Py * ckpt);
+            carries8 = c.get<float>(tc ? 0 : (size_t)8 * n * Py * ckpt);
+            ckimg8 = c.get<uint8_t>(tc ? (size_t)8 * n * ckpt_img : 0);
             delta8 = c.get<float>((size_t)8 * cap);
             dsym = c.get<float>(cap);
         }
@@ -439,7 +518,8 @@ int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32
     reset_stages(ctx);
     {
         StageScope sc(ctx, PSR_STAGE_PACK);
-        PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
+        if (tc) PSR_TRY(tc2_prepare(theta, tl, L, f16, t2, st));
+        else PSR_TRY(launch_pack_theta_f2(theta, f, pk, st));
         PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));  // spin-byte check
         PSR_TRY(launch_c4v_images(sp, n, L, imgs, st));
         PSR_TRY(cudaMemsetAsync(counters, 0, 9 * sizeof(unsigned long long), st));
@@ -464,7 +544,8 @@ int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32
     js.status = ctx->status;
     {
         StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
-        PSR_TRY(launch_fwd2d_f32(js, pk, f, ctx->num_sms, st));
+        if (tc) PSR_TRY(tc2_run(ctx, js, f16, theta, tl, t2, nullptr, eloc ? ckimg8 : nullptr));
+        else PSR_TRY(launch_fwd2d_f32(js, pk, f, ctx->num_sms, st));
     }
     if (eloc && cap > 0) {
         StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
@@ -475,13 +556,14 @@ int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32
             jc.g.n_jobs_dev = b.offsets + n;
             jc.g.spins = imgs + (size_t)g * n * N;
             jc.g.entries = ent8 + (size_t)g * 3 * cap;
-            jc.g.carries_in = carries8 + (size_t)g * n * Py * ckpt;
+            jc.g.carries_in = tc ? nullptr : carries8 + (size_t)g * n * Py * ckpt;
             jc.g.logp_ref = logp8 + (size_t)g * n * Np;
             jc.g.out = delta8 + (size_t)g * cap;
             jc.g.logp_out = nullptr;
             jc.g.carries_out = nullptr;
             jc.job_counter = counters + 1 + g;
-            PSR_TRY(launch_fwd2d_f32(jc, pk, f, ctx->num_sms, st));
+            if (tc) PSR_TRY(tc2_run(ctx, jc, f16, theta, tl, t2, ckimg8 + (size_t)g * n * ckpt_img, nullptr));
+            else PSR_TRY(launch_fwd2d_f32(jc, pk, f, ctx->num_sms, st));
         }
         PSR_TRY(launch_sym_delta(b.entries, b.offsets + n, cap, lp8, n, delta8, dsym, st));
     }
@@ -533,7 +615,7 @@ int check_params_lru(const psr_params *p, int64_t n, int32_t L) {
     if (p->n_layers < 1 || p->n_layers > kMaxLayers) return PSR_EINVAL;
     if (p->hidden != 32 && p->hidden != 64 && p->hidden != 128) return PSR_EINVAL;
     if (p->u1_mask != 0 && p->u1_mask != 1) return PSR_EINVAL;
-    if (p->precision != PSR_FP32 && p->precision != PSR_BF16) return PSR_EINVAL;
+    if (p->precision != PSR_FP32 && p->precision != PSR_BF16 && p->precision != PSR_FP16) return PSR_EINVAL;
     if (n < 1 || L < 1 || n > (int64_t)1 << 31) return PSR_EINVAL;
     if (p->u1_mask && (L % 2)) return PSR_EINVAL;
     if (p->precision != PSR_FP32) return PSR_EUNSUPPORTED;

@@ -376,8 +376,12 @@ int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *ham, int32_t
     if (stats_out) stats = stats_out;
     if (grad_out) grad = grad_out;
     cudaStream_t st = ctx->stream;
+    // BF16 precision selects the tensor-core forward for the local energies
+    // only; sampling, the image weights and the gradient run in FP32.
+    psr_params p32 = *params;
+    p32.precision = PSR_FP32;
     // 1. exact samples of |psi|^2 (then a uniformly drawn c4v image of each)
-    if ((rc = psr2d_sample(params, uniforms, n, Lx, Ly, spins, nullptr)) != PSR_OK) return rc;
+    if ((rc = psr2d_sample(&p32, uniforms, n, Lx, Ly, spins, nullptr)) != PSR_OK) return rc;
     const uint8_t *used = spins;
     if (symmetrize) {
         PSR_TRY(launch_c4v_pick(spins, sym_uniforms, n, Lx, spins_sym, st));
@@ -390,11 +394,11 @@ int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *ham, int32_t
     // 3. centred energy-gradient weights (per image when symmetrised)
     if (symmetrize) {
         PSR_TRY(launch_c4v_images(used, n, Lx, imgs, st));
-        if ((rc = psr2d_logpsi(params, imgs, 8 * n, Lx, Ly, lp8)) != PSR_OK) return rc;
+        if ((rc = psr2d_logpsi(&p32, imgs, 8 * n, Lx, Ly, lp8)) != PSR_OK) return rc;
     }
     PSR_TRY(launch_vmc_dout(eloc, stats, lp8, n, n_img, dout, st));
     // 4. gradient sum_i dout_i d log psi(s_i) / d theta
-    if ((rc = psr2d_grad(params, symmetrize ? imgs : used, n_img * n, Lx, Ly, dout, grad)) != PSR_OK)
+    if ((rc = psr2d_grad(&p32, symmetrize ? imgs : used, n_img * n, Lx, Ly, dout, grad)) != PSR_OK)
         return rc;
     // 5. Adam update
     PSR_TRY(launch_adam(params->theta, grad, P, adam->lr, adam->beta1, adam->beta2, adam->eps,

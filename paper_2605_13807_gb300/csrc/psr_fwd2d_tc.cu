@@ -1,0 +1,792 @@
+// Forward of the paper's two-dimensional patched minGRU (Sec. II.F,
+// two-dimensional recurrences; Sec. II.G residual and GELU) on the tensor
+// cores: BF16 operands, FP32 accumulation in tensor memory, FP32 gates,
+// scan, GELU and softmax.
+//
+// The model is the one psr_fwd2d.cu evaluates in FP32 (2 x 2 patches along
+// the zigzag path of the patch lattice, row by row: within a patch row the
+// gates and candidates of all sites are one batched projection, the h_V part
+// acting on the previous row's states, followed by the scan
+// h = a h_H + (1 - a) h~ along the row).  Here every contraction of a row is
+// a tcgen05 MMA with the weights as the A operand (M = 128 hidden units, one
+// or two halves) and the row's sites as B (N = 128 columns):
+//   z = W_z x,  c = W_hx x + W_hv h_V,  y = D x + C h,  logits = W_o x.
+// Layer 0's input is the one-hot pair (v_H, v_V) of 32 entries, zero-padded
+// to one 64-wide K chunk.
+//
+// Work layout.  One persistent CTA per SM holds 128 site columns cut into S
+// slots of W = 8 ceil(P_x / 8) columns; each slot evaluates one job
+// (configuration) and advances one patch row per step, so all slots share
+// every weight fetch.  A slot whose job has finished takes the next job from
+// a counter.  The weights (about 1.7 MB per row step at d_h = 256) do not fit
+// in shared memory: they are stored once, in MMA order, as 16 KB slices
+// (128 rows x 64 BF16, 128-byte swizzle) and streamed through a ring of
+// slices by bulk copies, from L2, where every CTA's stream hits.
+//
+// Roles: H epilogue threads (thread j = hidden unit j: its tensor-memory lane
+// holds unit j's accumulators for all 128 columns), one producer thread (the
+// weight stream) and one MMA thread.  Per row step and layer:
+//   MMA  z, c (needs x, then h_V)  ->  epilogue: gates and scan, h -> smem
+//   MMA  y = D x + C h             ->  epilogue: GELU(y + residual) -> x
+// then the readout MMA and the masked 16-way softmax of every patch.
+// The next row's h_V is this row's h, path-reversed (consecutive rows run in
+// opposite directions); the scan writes it to global memory as a BF16 image
+// in the tile layout, and the next row bulk-copies it into the h tile.  In
+// mode 0 these images are the row checkpoints that mode 1 (connected
+// configurations, resumed at the patch row of the first flipped spin) reads.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "psr_bf16_math.cuh"
+#include "psr_device.cuh"
+#include "psr_internal.cuh"
+#include "psr_tc.cuh"
+
+namespace psr {
+
+namespace {
+
+using namespace tc;
+using namespace bf16m;
+
+constexpr int kCols = 128;          // site columns per CTA (MMA N)
+constexpr uint32_t kSlice = 16384;  // 128 rows x 64 BF16
+constexpr int kMaxSlots = 16;
+constexpr int kMaxRing = 10;
+
+// kind::f16, D = F32, A = B = FP16 (F16) or BF16, both K-major, M = 128,
+// N = 128.
+template <bool F16>
+constexpr uint32_t idesc2() {
+    return (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) | (0u << 15) | (0u << 16) |
+           ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// Descriptor of a K-major, 128-byte-swizzled operand: 8-row atoms of 1024
+// bytes stacked along M (or N); K = 16 step kk is 32 bytes along the row.
+__device__ __forceinline__ uint64_t kdesc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(1024u >> 4) << 16) |
+           ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+__device__ __forceinline__ uint64_t kstep(int kk) { return (uint64_t)((kk * 32) >> 4); }
+
+struct Slot2 {
+    long long job;        // -1: needs a job, -2: none left
+    int sample, p, q;     // configuration (p, q: flipped sites or -1)
+    int row, r0, n_up;    // current patch row, first row, up spins before it
+    float acc;            // sum of log P (mode 0) or of its differences (mode 1)
+    uint8_t v[32];        // patch values of the current row, path order
+    uint8_t vprev[32];    // previous row's values by column
+};
+
+struct Misc2 {
+    uint64_t full[kMaxRing], empty[kMaxRing];
+    uint64_t e2m, m2e, hv, go[2];
+    uint32_t tmem_base;
+    int abort_flag;
+    int go_flag[2];
+    int pad_;
+    Slot2 slot[kMaxSlots];
+};
+
+// Bounded wait that also gives up once another role has aborted.
+__device__ __forceinline__ bool wait_ab(uint32_t bar, uint32_t parity, const volatile int *ab) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u && (*ab || globaltimer() - t0 > kWaitNs)) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int seq_pos2d(int Lx, int i, int j) {
+    return j * Lx + ((j & 1) ? (Lx - 1 - i) : i);
+}
+
+// Value (0..15) of patch (pi, pj): spin (2 pi + dx, 2 pj + dy) is bit
+// 2 dy + dx, with sites p and q flipped.
+__device__ __forceinline__ int patch_value(const uint8_t *s, int Lx, int pi, int pj, int p, int q) {
+    int v = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int pos = seq_pos2d(Lx, 2 * pi + (b & 1), 2 * pj + (b >> 1));
+        v |= ((int)(s[pos] & 1u) ^ (pos == p) ^ (pos == q)) << b;
+    }
+    return v;
+}
+
+// Barrier of the epilogue threads that also ORs a flag over them, so that
+// every epilogue thread takes the same exit.
+__device__ __forceinline__ bool epi_bar_or(int nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+// Operand bits of an FP32 value, rounded to nearest: FP16 (values beyond the
+// largest finite FP16 saturate to it) or BF16.
+template <bool F16>
+__device__ __forceinline__ uint16_t op_bits(float x) {
+    if (F16) return __half_as_ushort(__float2half_rn(fminf(fmaxf(x, -65504.0f), 65504.0f)));
+    const __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<const uint16_t *>(&b);
+}
+template <bool F16>
+__device__ __forceinline__ uint32_t op_pack(float lo, float hi) {
+    return (uint32_t)op_bits<F16>(lo) | ((uint32_t)op_bits<F16>(hi) << 16);
+}
+
+template <int H, bool F16>
+__global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_constant__ Fwd2TcArgs A) {
+    constexpr int NH = H / 128;     // unit halves (M tiles)
+    constexpr int KC = H / 64;      // K chunks of a hidden-size input
+    constexpr int NW = H / 32;      // epilogue warps
+    constexpr uint32_t kTileBytes = KC * 16384u;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    Misc2 &M = *reinterpret_cast<Misc2 *>(smem_raw);
+    uint8_t *tiles = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + sizeof(Misc2) + 1023) & ~uintptr_t(1023));
+    uint8_t *xt = tiles;                    // layer input x (K-major rows = columns)
+    uint8_t *ht = tiles + kTileBytes;       // h_V, then the layer's states h
+    uint8_t *ring = tiles + 2 * kTileBytes; // weight slices
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = A.R, S = A.S, W = A.W, Lx = A.Lx, Ly = A.Ly, Px = Lx >> 1, Py = Ly >> 1;
+    const int nL = A.tl.nL, N = Lx * Ly, Np = Px * Py;
+    const uint32_t img_bytes = (uint32_t)KC * (uint32_t)W * 128u;  // one layer's h_V image of a slot
+    const volatile int *ab = &M.abort_flag;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&M.tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < R; ++i) {
+            mbar_init(smem_u32(&M.full[i]), 1);
+            mbar_init(smem_u32(&M.empty[i]), 1);
+        }
+        mbar_init(smem_u32(&M.e2m), H);
+        mbar_init(smem_u32(&M.m2e), 1);
+        mbar_init(smem_u32(&M.hv), 1);
+        mbar_init(smem_u32(&M.go[0]), 1);
+        mbar_init(smem_u32(&M.go[1]), 1);
+        M.abort_flag = 0;
+        M.go_flag[0] = 1;
+        M.go_flag[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int s = tid; s < kMaxSlots; s += blockDim.x) {
+        M.slot[s].job = -1;
+        M.slot[s].acc = 0.0f;
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = M.tmem_base;
+    if (tmem != 0) {  // all 512 columns are needed from column 0
+        if (tid == 0) set_status(A.status, PSR_EDEVICE);
+        M.abort_flag = 1;
+    }
+    if (tid == 0) mbar_arrive(smem_u32(&M.go[0]));  // row step 0 runs
+    __syncthreads();
+    const long long njobs = A.mode == 1 ? (long long)*A.n_jobs_dev : (long long)A.n_jobs;
+    const uint32_t e2m = smem_u32(&M.e2m), m2e = smem_u32(&M.m2e), hvb = smem_u32(&M.hv);
+
+    if (warp == NW) {
+        // ------------------------------------------------ producer: weight stream
+        if (lane == 0 && !M.abort_flag) {
+            uint32_t q = 0;
+            for (uint32_t row = 0;; ++row) {
+                if (!wait_ab(smem_u32(&M.go[row & 1]), (row >> 1) & 1, ab)) break;
+                if (!*(volatile int *)&M.go_flag[row & 1]) break;
+                bool ok = true;
+                for (int i = 0; i < A.n_slices; ++i, ++q) {
+                    const uint32_t slot = q % (uint32_t)R, use = q / (uint32_t)R;
+                    if (use > 0 && !wait_ab(smem_u32(&M.empty[slot]), (use - 1) & 1, ab)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_tx(smem_u32(&M.full[slot]), kSlice);
+                    bulk_g2s(smem_u32(ring + slot * kSlice), A.wimg + (size_t)i * kSlice, kSlice,
+                             smem_u32(&M.full[slot]));
+                }
+                if (!ok) break;
+            }
+            // copies still in flight land before the CTA may exit
+            const uint32_t last = q < (uint32_t)R ? q : (uint32_t)R;
+            for (uint32_t t = 0; t < last; ++t) {
+                const uint32_t qq = q - 1 - t;
+                if (!mbar_wait(smem_u32(&M.full[qq % R]), (qq / R) & 1)) set_status(A.status, PSR_ETIMEOUT);
+            }
+            if (*ab) set_status(A.status, PSR_ETIMEOUT);
+        }
+    } else if (warp == NW + 1) {
+        // ------------------------------------------------ MMA issue
+        if (lane == 0 && !M.abort_flag) {
+            uint32_t q = 0, pe = 0, ph = 0;
+            const uint32_t xa = smem_u32(xt), ha = smem_u32(ht), ra = smem_u32(ring);
+            bool ok = true;
+            for (uint32_t row = 0; ok; ++row) {
+                if (!wait_ab(smem_u32(&M.go[row & 1]), (row >> 1) & 1, ab)) {
+                    ok = false;
+                    break;
+                }
+                if (!*(volatile int *)&M.go_flag[row & 1]) break;
+                for (int i = 0; i < A.n_slices; ++i, ++q) {
+                    const uint8_t ty = A.sched.type[i], g = A.sched.g[i], kc = A.sched.kc[i],
+                                  fl = A.sched.flags[i];
+                    if (fl & kSchedCommit) mma_commit(m2e);
+                    if (fl & kSchedWaitX) {
+                        if (!wait_ab(e2m, pe, ab)) { ok = false; break; }
+                        pe ^= 1u;
+                        tc_after();
+                    }
+                    if (fl & kSchedWaitHv) {
+                        if (!wait_ab(hvb, ph, ab)) { ok = false; break; }
+                        ph ^= 1u;
+                    }
+                    const uint32_t slot = q % (uint32_t)R;
+                    if (!wait_ab(smem_u32(&M.full[slot]), (q / (uint32_t)R) & 1, ab)) { ok = false; break; }
+                    tc_after();
+                    uint32_t dcol, b;
+                    bool acc;
+                    switch (ty) {
+                        case kMtWz: dcol = 128u * g; b = xa; acc = kc > 0; break;
+                        case kMtWhx: dcol = 128u * (NH + g); b = xa; acc = kc > 0; break;
+                        case kMtWhv: dcol = 128u * (NH + g); b = ha; acc = true; break;
+                        case kMtD: dcol = 128u * g; b = xa; acc = kc > 0; break;
+                        case kMtC: dcol = 128u * g; b = ha; acc = true; break;
+                        default: dcol = 128u * NH; b = xa; acc = kc > 0; break;  // readout
+                    }
+                    const uint64_t ad = kdesc(ra + slot * kSlice), bd = kdesc(b + (uint32_t)kc * 16384u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_ss<idesc2<F16>()>(tmem + dcol, ad + kstep(kk), bd + kstep(kk), (acc || kk > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(&M.empty[slot]));
+                }
+                if (ok) mma_commit(m2e);  // logits of the row
+            }
+            // the MMAs of the last slices complete before the CTA may exit
+            const uint32_t last = q < (uint32_t)R ? q : (uint32_t)R;
+            for (uint32_t t = 0; t < last; ++t) {
+                const uint32_t qq = q - 1 - t;
+                if (!mbar_wait(smem_u32(&M.empty[qq % R]), (qq / R) & 1)) set_status(A.status, PSR_ETIMEOUT);
+            }
+            if (!ok) {
+                M.abort_flag = 1;
+                set_status(A.status, PSR_ETIMEOUT);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (thread j = unit j)
+        const int j = tid, g = j >> 7;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        const uint32_t tz = tmem + lane_off + 128u * g;          // z, then y
+        const uint32_t tcc = tmem + lane_off + 128u * (NH + g);  // c
+        const uint32_t tlg = tmem + lane_off + 128u * NH;        // logits (lanes 0..15)
+        // unit j's place in a K-major tile row and in a slot image row
+        const uint32_t kreg = (uint32_t)(j >> 6) * 16384u;
+        const int ch = (j & 63) >> 3;
+        const uint32_t eb = (uint32_t)(j & 7) * 2u;
+        auto tile_off = [&](int n) -> uint32_t {
+            return kreg + (uint32_t)n * 128u + ((uint32_t)(ch ^ (n & 7)) << 4) + eb;
+        };
+        const uint32_t ireg = (uint32_t)(j >> 6) * (uint32_t)W * 128u;
+        auto img_off = [&](int r) -> uint32_t {
+            return ireg + (uint32_t)r * 128u + ((uint32_t)(ch ^ (r & 7)) << 4) + eb;
+        };
+        const int nch = W >> 3;
+        uint8_t *scratch = A.scratch + (size_t)blockIdx.x * S * nL * img_bytes;
+        float *res = A.res + (size_t)blockIdx.x * 2 * kCols * H;
+        uint32_t pm = 0;       // m2e phase
+        uint32_t hv_armed = 0; // h_V loads issued (thread 0)
+        bool ok = !M.abort_flag;
+
+        // h_V image of layer l for slot s's current row (source) and for its
+        // next row (destination, null after the last row)
+        auto img_src = [&](const Slot2 &st, int s, int l) -> const uint8_t * {
+            if (st.row == st.r0) {
+                if (st.r0 == 0) return A.zero_img;
+                return A.img_in + (((size_t)st.sample * Py + st.r0) * nL + l) * img_bytes;
+            }
+            if (A.img_out) return A.img_out + (((size_t)st.sample * Py + st.row) * nL + l) * img_bytes;
+            return scratch + ((size_t)s * nL + l) * img_bytes;
+        };
+        auto img_dst = [&](const Slot2 &st, int s, int l) -> uint8_t * {
+            if (st.row + 1 >= Py) return nullptr;
+            if (A.img_out) return A.img_out + (((size_t)st.sample * Py + st.row + 1) * nL + l) * img_bytes;
+            return scratch + ((size_t)s * nL + l) * img_bytes;
+        };
+        // thread 0: bulk copies of every active slot's h_V image of layer l
+        auto issue_hv = [&](int l) {
+            uint32_t bytes = 0;
+            for (int s = 0; s < S; ++s)
+                if (M.slot[s].job >= 0) bytes += img_bytes;
+            mbar_arrive_tx(hvb, bytes);
+            for (int s = 0; s < S; ++s) {
+                const Slot2 &st = M.slot[s];
+                if (st.job < 0) continue;
+                const uint8_t *src = img_src(st, s, l);
+                for (int kc = 0; kc < KC; ++kc)
+                    bulk_g2s(smem_u32(ht + kc * 16384 + s * W * 128), src + (size_t)kc * W * 128, (uint32_t)W * 128u,
+                             hvb);
+            }
+            ++hv_armed;
+        };
+        auto wait_m2e = [&]() {
+            bool w = ok && wait_ab(m2e, pm, ab);
+            w = __all_sync(0xffffffffu, w);
+            if (!w && ok) {
+                M.abort_flag = 1;
+                set_status(A.status, PSR_ETIMEOUT);
+            }
+            ok = ok && w;
+            pm ^= 1u;
+            tc_after();
+        };
+
+        for (uint32_t row_it = 0; ok; ++row_it) {
+            // ---- slot update: finished or empty slots take the next job; the
+            // others advance one patch row
+            for (int s = warp; s < S; s += NW) {
+                Slot2 &st = M.slot[s];
+                const long long job = st.job;
+                if (job == -2) continue;
+                if (job == -1 || st.row + 1 >= Py) {
+                    unsigned long long nj = 0;
+                    if (lane == 0) nj = atomicAdd(A.job_counter, 1ull);
+                    nj = __shfl_sync(0xffffffffu, nj, 0);
+                    __syncwarp();
+                    if ((long long)nj >= njobs) {
+                        if (lane == 0) st.job = -2;
+                        __syncwarp();
+                        continue;
+                    }
+                    int sample = (int)nj, p = -1, q = -1, r0 = 0;
+                    if (A.mode == 1) {
+                        const int32_t *e = A.entries + 3 * nj;
+                        sample = e[0];
+                        p = e[1];
+                        q = e[2];
+                        r0 = (p / Lx) >> 1;
+                    }
+                    const uint8_t *sp = A.spins + (size_t)sample * N;
+                    int up = 0;
+                    for (int t = lane; t < 2 * r0 * Lx; t += 32) up += sp[t] & 1;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(0xffffffffu, up, o);
+                    if (lane < Px) {
+                        if (r0 > 0) st.vprev[lane] = (uint8_t)patch_value(sp, Lx, lane, r0 - 1, -1, -1);
+                        const int pi = (r0 & 1) ? Px - 1 - lane : lane;
+                        st.v[lane] = (uint8_t)patch_value(sp, Lx, pi, r0, p, q);
+                    }
+                    if (lane == 0) {
+                        st.job = (long long)nj;
+                        st.sample = sample;
+                        st.p = p;
+                        st.q = q;
+                        st.row = r0;
+                        st.r0 = r0;
+                        st.n_up = up;
+                        st.acc = 0.0f;
+                    }
+                    __syncwarp();
+                } else {
+                    const int r = st.row;
+                    int old = 0, pc = 0;
+                    if (lane < Px) {
+                        old = st.v[lane];
+                        pc = __popc(old);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, o);
+                    __syncwarp();
+                    const uint8_t *sp = A.spins + (size_t)st.sample * N;
+                    if (lane < Px) {
+                        st.vprev[(r & 1) ? Px - 1 - lane : lane] = (uint8_t)old;
+                        const int pi = ((r + 1) & 1) ? Px - 1 - lane : lane;
+                        st.v[lane] = (uint8_t)patch_value(sp, Lx, pi, r + 1, st.p, st.q);
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        st.n_up += pc;
+                        st.row = r + 1;
+                    }
+                    __syncwarp();
+                }
+            }
+            if (epi_bar_or(H, !ok || *ab)) {
+                ok = false;
+                break;
+            }
+            if (j == 0) {
+                // does a row step follow this one?
+                bool more = false;
+                for (int s = 0; s < S; ++s)
+                    if (M.slot[s].job >= 0 && M.slot[s].row + 1 < Py) more = true;
+                if (!more) more = (long long)atomicAdd(A.job_counter, 0ull) < njobs;
+                M.go_flag[(row_it + 1) & 1] = more ? 1 : 0;
+                mbar_arrive(smem_u32(&M.go[(row_it + 1) & 1]));
+                issue_hv(0);
+            }
+            // ---- layer-0 input: one-hot (v_H, v_V) of every column, K chunk 0
+            constexpr uint32_t kOne = F16 ? 0x3C00u : 0x3F80u;  // 1.0
+            for (int id = j; id < kCols * 8; id += H) {
+                const int n = id >> 3, c = id & 7, s = n / W, k = n - s * W;
+                int vh = -1, vv = -1;
+                if (s < S && k < Px) {
+                    const Slot2 &st = M.slot[s];
+                    if (st.job >= 0) {
+                        if (k > 0) vh = st.v[k - 1];
+                        if (st.row > 0) vv = 16 + st.vprev[(st.row & 1) ? Px - 1 - k : k];
+                    }
+                }
+                uint32_t w4[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int e0 = 8 * c + 2 * i, e1 = e0 + 1;
+                    const uint32_t lo = (e0 == vh || e0 == vv) ? kOne : 0u;
+                    const uint32_t hi = (e1 == vh || e1 == vv) ? kOne : 0u;
+                    w4[i] = lo | (hi << 16);
+                }
+                *reinterpret_cast<uint4 *>(xt + n * 128 + ((c ^ (n & 7)) << 4)) =
+                    make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+            fence_proxy_async();
+            mbar_arrive(e2m);
+
+            for (int l = 0; l < nL; ++l) {
+                // ---- gates and scan along each slot's row
+                wait_m2e();
+                {
+                    const float hbz = 0.5f * A.theta[A.tl.bz[l] + j], bh = A.theta[A.tl.bh[l] + j];
+                    const float2 hbz2 = make_float2(hbz, hbz), bh2 = make_float2(bh, bh);
+                    const bool keep_res = (l >= 1) && (l + 1 < nL);
+                    float *resw = res + (size_t)(l & 1) * kCols * H;
+                    for (int s = 0; s < S; ++s) {
+                        const Slot2 &st = M.slot[s];
+                        if (st.job < 0) continue;
+                        const int n0 = s * W;
+                        uint32_t zr[32], cr[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) zr[i] = cr[i] = 0u;
+#pragma unroll
+                        for (int c8 = 0; c8 < 4; ++c8)
+                            if (c8 < nch) {
+                                const int b = 8 * c8;
+                                tmem_ld8(tz + n0 + b, zr[b], zr[b + 1], zr[b + 2], zr[b + 3], zr[b + 4], zr[b + 5],
+                                         zr[b + 6], zr[b + 7]);
+                                tmem_ld8(tcc + n0 + b, cr[b], cr[b + 1], cr[b + 2], cr[b + 3], cr[b + 4], cr[b + 5],
+                                         cr[b + 6], cr[b + 7]);
+                            }
+                        tmem_wait_ld32x2(zr, cr);
+                        uint8_t *dst = img_dst(st, s, l);
+                        float h = 0.0f;  // the row starts from h_H = 0
+#pragma unroll
+                        for (int k = 0; k < 32; k += 2) {
+                            if (k < Px) {
+                                float2 a, bb;
+                                gates2(make_float2(__uint_as_float(zr[k]), __uint_as_float(zr[k + 1])),
+                                       make_float2(__uint_as_float(cr[k]), __uint_as_float(cr[k + 1])), hbz2, bh2, a,
+                                       bb);
+                                h = fmaf(a.x, h, bb.x);
+                                const float h0 = h;
+                                h = fmaf(a.y, h, bb.y);
+                                const float h1 = h;
+                                *reinterpret_cast<uint16_t *>(ht + tile_off(n0 + k)) = op_bits<F16>(h0);
+                                if (dst) *reinterpret_cast<uint16_t *>(dst + img_off(Px - 1 - k)) = op_bits<F16>(h0);
+                                if (keep_res) resw[(size_t)(n0 + k) * H + j] = h0;
+                                if (k + 1 < Px) {
+                                    *reinterpret_cast<uint16_t *>(ht + tile_off(n0 + k + 1)) = op_bits<F16>(h1);
+                                    if (dst)
+                                        *reinterpret_cast<uint16_t *>(dst + img_off(Px - 2 - k)) = op_bits<F16>(h1);
+                                    if (keep_res) resw[(size_t)(n0 + k + 1) * H + j] = h1;
+                                }
+                            }
+                        }
+                    }
+                }
+                fence_proxy_async();
+                fence_proxy_async_global();
+                tc_before();
+                mbar_arrive(e2m);
+
+                // ---- output map: x = GELU(y + residual)
+                wait_m2e();
+                if (j == 0 && l + 1 < nL && ok) issue_hv(l + 1);
+                {
+                    const bool use_res = (l >= 2);
+                    const float *resr = res + (size_t)((l - 1) & 1) * kCols * H;
+                    for (int s = 0; s < S; ++s) {
+                        const Slot2 &st = M.slot[s];
+                        if (st.job < 0) continue;
+                        const int n0 = s * W;
+                        uint32_t yr[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) yr[i] = 0u;
+#pragma unroll
+                        for (int c8 = 0; c8 < 4; ++c8)
+                            if (c8 < nch) {
+                                const int b = 8 * c8;
+                                tmem_ld8(tz + n0 + b, yr[b], yr[b + 1], yr[b + 2], yr[b + 3], yr[b + 4], yr[b + 5],
+                                         yr[b + 6], yr[b + 7]);
+                            }
+                        tmem_wait_ld32(yr);
+#pragma unroll
+                        for (int k = 0; k < 32; k += 2) {
+                            if (k < Px) {
+                                float2 y = make_float2(__uint_as_float(yr[k]), __uint_as_float(yr[k + 1]));
+                                if (use_res) {
+                                    y.x += resr[(size_t)(n0 + k) * H + j];
+                                    if (k + 1 < Px) y.y += resr[(size_t)(n0 + k + 1) * H + j];
+                                }
+                                const float2 x = gelu_bf16out2(y);
+                                *reinterpret_cast<uint16_t *>(xt + tile_off(n0 + k)) = op_bits<F16>(x.x);
+                                if (k + 1 < Px) *reinterpret_cast<uint16_t *>(xt + tile_off(n0 + k + 1)) = op_bits<F16>(x.y);
+                            }
+                        }
+                    }
+                }
+                fence_proxy_async();
+                tc_before();
+                mbar_arrive(e2m);
+            }
+
+            // ---- readout: masked 16-way softmax of every patch of the row
+            wait_m2e();
+            if ((warp & 3) == 0 && ok) {
+                const int ri = warp >> 2;
+                const float bo = A.theta[A.tl.bo + (lane & 15)];
+                const int pc_lane = __popc(lane & 15);
+                for (int s = ri; s < S; s += NH) {
+                    Slot2 &st = M.slot[s];
+                    if (st.job < 0) continue;
+                    const int n0 = s * W, r = st.row;
+                    int up = st.n_up;
+                    float rsum = 0.0f;
+                    for (int c8 = 0; c8 < nch; ++c8) {
+                        uint32_t lr[8];
+                        tmem_ld8(tlg + n0 + 8 * c8, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], lr[6], lr[7]);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                                     : "+r"(lr[0]), "+r"(lr[1]), "+r"(lr[2]), "+r"(lr[3]), "+r"(lr[4]), "+r"(lr[5]),
+                                       "+r"(lr[6]), "+r"(lr[7])::"memory");
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int k = 8 * c8 + i;
+                            if (k >= Px) break;
+                            const int v = st.v[k];
+                            const int down = 2 * r * Lx + 4 * k - up;
+                            const bool allowed =
+                                !A.u1 || (up + pc_lane <= N / 2 && down + 4 - pc_lane <= N / 2);
+                            const float lg = __uint_as_float(lr[i]) + bo;
+                            float m = allowed ? lg : -INFINITY;
+#pragma unroll
+                            for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o, 16));
+                            float e = allowed ? __expf(lg - m) : 0.0f;
+#pragma unroll
+                            for (int o = 8; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o, 16);
+                            float lp = allowed ? lg - m - __logf(e) : -INFINITY;
+                            lp = __shfl_sync(0xffffffffu, lp, v);
+                            const int t = r * Px + k;
+                            float d = lp;
+                            if (A.mode == 1) d = lp - A.logp_ref[(size_t)st.sample * Np + t];
+                            else if (A.logp_out && lane == 0) A.logp_out[(size_t)st.sample * Np + t] = lp;
+                            rsum += d;
+                            up += __popc(v);
+                        }
+                    }
+                    if (lane == 0) {
+                        st.acc += rsum;
+                        if (r + 1 >= Py) A.out[st.job] = 0.5f * st.acc;
+                    }
+                    __syncwarp();
+                }
+            }
+            tc_before();
+            if (epi_bar_or(H, !ok)) {
+                ok = false;
+                break;
+            }
+            if (!*(volatile int *)&M.go_flag[(row_it + 1) & 1]) break;
+        }
+        if (!ok) {
+            M.abort_flag = 1;
+            set_status(A.status, PSR_ETIMEOUT);
+        }
+        if (j == 0 && hv_armed > 0 && !mbar_wait(hvb, (hv_armed - 1) & 1)) set_status(A.status, PSR_ETIMEOUT);
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+template <int H>
+size_t fwd2d_tc_smem(int R) {
+    return sizeof(Misc2) + 1024 + 2 * (size_t)(H / 64) * 16384 + (size_t)R * kSlice;
+}
+
+template <int H, bool F16>
+cudaError_t launch_h(const Fwd2TcArgs &a, int grid, cudaStream_t stream) {
+    const size_t smem = fwd2d_tc_smem<H>(a.R);
+    cudaError_t e =
+        cudaFuncSetAttribute(fwd2d_tc_kernel<H, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fwd2d_tc_kernel<H, F16><<<grid, H + 64, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// Weight slices in MMA order: 128 rows (units 128 g ..) x 64 inputs (64 kc ..)
+// of one matrix, 128-byte swizzle (16-byte chunk c of row m at c ^ (m & 7)).
+template <bool F16>
+__global__ void pack2d_tc_kernel(const float *__restrict__ theta, T2Layout tl, Sched2 sc,
+                                 uint8_t *__restrict__ wimg) {
+    const int H = tl.H;
+    const int64_t total = (int64_t)sc.n * 1024;
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(id >> 10), m = (int)((id >> 3) & 127), c = (int)(id & 7);
+        const int ty = sc.type[i], l = sc.l[i], unit = 128 * sc.g[i] + m, k0 = 64 * sc.kc[i] + 8 * c;
+        const int din = l == 0 ? 32 : H;
+        uint32_t w[4];
+#pragma unroll
+        for (int e2 = 0; e2 < 4; ++e2) {
+            float v2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = k0 + 2 * e2 + h;
+                float v = 0.0f;
+                switch (ty) {
+                    case kMtWz: if (k < din) v = theta[tl.Wz[l] + (int64_t)unit * din + k]; break;
+                    case kMtWhx: if (k < din) v = theta[tl.Wh[l] + (int64_t)unit * (din + H) + k]; break;
+                    case kMtWhv: v = theta[tl.Wh[l] + (int64_t)unit * (din + H) + din + k]; break;
+                    case kMtC: v = theta[tl.C[l] + (int64_t)unit * H + k]; break;
+                    case kMtD: if (k < din) v = theta[tl.D[l] + (int64_t)unit * din + k]; break;
+                    default: if (unit < 16) v = theta[tl.Wo + (int64_t)unit * H + k]; break;
+                }
+                v2[h] = v;
+            }
+            w[e2] = op_pack<F16>(v2[0], v2[1]);
+        }
+        *reinterpret_cast<uint4 *>(wimg + (size_t)i * kSlice + m * 128 + ((c ^ (m & 7)) << 4)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+}  // namespace
+
+// Slices of one row step, in the order the MMA thread consumes them, with
+// the synchronisation each needs first.
+Sched2 fwd2d_tc_schedule(int nL, int H) {
+    Sched2 sc{};
+    const int NH = H / 128, KC = H / 64;
+    int n = 0;
+    auto add = [&](int ty, int l, int g, int kc, int fl) {
+        sc.type[n] = (uint8_t)ty;
+        sc.l[n] = (uint8_t)l;
+        sc.g[n] = (uint8_t)g;
+        sc.kc[n] = (uint8_t)kc;
+        sc.flags[n] = (uint8_t)fl;
+        ++n;
+    };
+    for (int l = 0; l < nL; ++l) {
+        const int kin = l == 0 ? 1 : KC;
+        // projections: W_z x, W_hx x (x ready), then W_hv h_V (image loaded)
+        for (int g = 0; g < NH; ++g) {
+            for (int kc = 0; kc < kin; ++kc) {
+                int fl = 0;
+                if (g == 0 && kc == 0) fl = (l == 0) ? kSchedWaitX : (kSchedCommit | kSchedWaitX);
+                add(kMtWz, l, g, kc, fl);
+            }
+            for (int kc = 0; kc < kin; ++kc) add(kMtWhx, l, g, kc, 0);
+        }
+        for (int g = 0; g < NH; ++g)
+            for (int kc = 0; kc < KC; ++kc) add(kMtWhv, l, g, kc, (g == 0 && kc == 0) ? kSchedWaitHv : 0);
+        // output map: D x + C h (the scan has written h)
+        for (int g = 0; g < NH; ++g) {
+            for (int kc = 0; kc < kin; ++kc)
+                add(kMtD, l, g, kc, (g == 0 && kc == 0) ? (kSchedCommit | kSchedWaitX) : 0);
+            for (int kc = 0; kc < KC; ++kc) add(kMtC, l, g, kc, 0);
+        }
+    }
+    for (int kc = 0; kc < KC; ++kc) add(kMtWo, 0, 0, kc, kc == 0 ? (kSchedCommit | kSchedWaitX) : 0);
+    sc.n = n;
+    return sc;
+}
+
+bool fwd2d_tc_supported(int nL, int H, int Lx) {
+    return (H == 128 || H == 256) && nL >= 1 && nL <= kMaxLayers && Lx >= 2 && Lx <= 64 &&
+           fwd2d_tc_schedule(nL, H).n <= kSchedMax;
+}
+
+void fwd2d_tc_geometry(int Lx, int *W, int *S) {
+    const int Px = Lx / 2;
+    *W = 8 * ((Px + 7) / 8);
+    *S = kCols / *W;
+    if (*S > kMaxSlots) *S = kMaxSlots;
+}
+
+size_t fwd2d_tc_image_bytes(int H, int Lx) {
+    int W, S;
+    fwd2d_tc_geometry(Lx, &W, &S);
+    return (size_t)(H / 64) * W * 128;
+}
+
+size_t fwd2d_tc_weight_bytes(int nL, int H) { return (size_t)fwd2d_tc_schedule(nL, H).n * kSlice; }
+
+size_t fwd2d_tc_ckpt_bytes(int nL, int H, int Lx, int Ly) {
+    return (size_t)(Ly / 2) * nL * fwd2d_tc_image_bytes(H, Lx);
+}
+
+size_t fwd2d_tc_scratch_bytes(int nL, int H, int Lx, int grid) {
+    int W, S;
+    fwd2d_tc_geometry(Lx, &W, &S);
+    return (size_t)grid * S * nL * fwd2d_tc_image_bytes(H, Lx);
+}
+
+size_t fwd2d_tc_res_floats(int H, int grid) { return (size_t)grid * 2 * kCols * H; }
+
+cudaError_t launch_pack2d_tc(const float *theta, const T2Layout &tl, bool f16, uint8_t *wimg,
+                             cudaStream_t stream) {
+    const Sched2 sc = fwd2d_tc_schedule(tl.nL, tl.H);
+    const int64_t total = (int64_t)sc.n * 1024;
+    const int blocks = (int)((total + 255) / 256);
+    if (f16) pack2d_tc_kernel<true><<<blocks, 256, 0, stream>>>(theta, tl, sc, wimg);
+    else pack2d_tc_kernel<false><<<blocks, 256, 0, stream>>>(theta, tl, sc, wimg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd2d_tc(Fwd2TcArgs a, int grid, cudaStream_t stream) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int H = a.tl.H;
+    fwd2d_tc_geometry(a.Lx, &a.W, &a.S);
+    a.sched = fwd2d_tc_schedule(a.tl.nL, H);
+    a.n_slices = a.sched.n;
+    const size_t base = (H == 256) ? fwd2d_tc_smem<256>(0) : fwd2d_tc_smem<128>(0);
+    if ((size_t)optin < base + 2 * kSlice) return cudaErrorInvalidConfiguration;
+    int R = (int)(((size_t)optin - base) / kSlice);
+    a.R = R > kMaxRing ? kMaxRing : R;
+    if (grid < 1) grid = 1;
+    switch (H) {
+        case 128: return a.f16 ? launch_h<128, true>(a, grid, stream) : launch_h<128, false>(a, grid, stream);
+        case 256: return a.f16 ? launch_h<256, true>(a, grid, stream) : launch_h<256, false>(a, grid, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace psr

@@ -223,6 +223,58 @@ struct T2Layout {
     int64_t total;
 };
 T2Layout t2_layout(int nL, int H);
+
+// Two-dimensional patched minGRU on the tensor cores (psr_fwd2d_tc.cu):
+// FP16 or BF16 operands, FP32 accumulation, gates, scan, GELU and softmax; hidden
+// 128 or 256, Lx <= 64.  The weights are streamed as 16 KB slices in MMA
+// order (launch_pack2d_tc writes them); Sched2 lists, per slice, the matrix,
+// layer, unit half, K chunk and the synchronisation before it.
+enum { kMtWz = 0, kMtWhx = 1, kMtWhv = 2, kMtC = 3, kMtD = 4, kMtWo = 5 };
+enum { kSchedCommit = 1, kSchedWaitX = 2, kSchedWaitHv = 4 };
+constexpr int kSchedMax = 320;
+struct Sched2 {
+    int n;
+    uint8_t type[kSchedMax], l[kSchedMax], g[kSchedMax], kc[kSchedMax], flags[kSchedMax];
+};
+Sched2 fwd2d_tc_schedule(int nL, int H);
+// Jobs as in Fwd2Group; the row checkpoints are 16-bit h_V images:
+// img_out / img_in [n][Py][nL][fwd2d_tc_image_bytes] (mode 0 writes them when
+// img_out is set; mode 1 reads img_in).  scratch: fwd2d_tc_scratch_bytes,
+// res: fwd2d_tc_res_floats, zero_img: fwd2d_tc_image_bytes of zeros.
+struct Fwd2TcArgs {
+    int mode, Lx, Ly, u1;
+    int f16;            // operands FP16 (1) or BF16 (0)
+    int64_t n_jobs;
+    const int64_t *n_jobs_dev;
+    const uint8_t *spins;
+    const int32_t *entries;
+    const uint8_t *img_in;
+    uint8_t *img_out;
+    uint8_t *scratch;
+    const uint8_t *zero_img;
+    float *res;
+    const float *logp_ref;
+    float *out;
+    float *logp_out;
+    const float *theta;
+    T2Layout tl;
+    const uint8_t *wimg;
+    unsigned long long *job_counter;
+    int *status;
+    // set by launch_fwd2d_tc
+    int W, S, R, n_slices;
+    Sched2 sched;
+};
+bool fwd2d_tc_supported(int nL, int H, int Lx);
+void fwd2d_tc_geometry(int Lx, int *W, int *S);
+size_t fwd2d_tc_image_bytes(int H, int Lx);
+size_t fwd2d_tc_weight_bytes(int nL, int H);
+size_t fwd2d_tc_ckpt_bytes(int nL, int H, int Lx, int Ly);   // per sample
+size_t fwd2d_tc_scratch_bytes(int nL, int H, int Lx, int grid);
+size_t fwd2d_tc_res_floats(int H, int grid);
+cudaError_t launch_pack2d_tc(const float *theta, const T2Layout &tl, bool f16, uint8_t *wimg,
+                             cudaStream_t stream);
+cudaError_t launch_fwd2d_tc(Fwd2TcArgs a, int grid, cudaStream_t stream);
 // Reverse-mode gradient of the 2D model over n samples from the forward's
 // row checkpoints; grad_rows: [n][P] (dout == NULL) or [grid][P] partial
 // sums of dout_i O_k(s_i).  scratch: grid * bwd2d_scratch_floats_per_cta.

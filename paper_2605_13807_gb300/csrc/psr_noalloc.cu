@@ -111,6 +111,7 @@ extern "C" int psr_logpsi_noalloc(const psr_params *params, const uint8_t *spins
     if (nL < 1 || nL > kMaxLayers) return PSR_EINVAL;
     if (H != 32 && H != 64 && H != 128) return PSR_EINVAL;
     if (params->u1_mask != 0 && params->u1_mask != 1) return PSR_EINVAL;
+    if (params->precision == PSR_FP16) return PSR_EUNSUPPORTED;
     if (params->precision != PSR_FP32 && params->precision != PSR_BF16) return PSR_EINVAL;
     if (n < 1 || L < 1 || n > ((int64_t)1 << 31)) return PSR_EINVAL;
     if (params->u1_mask && (L % 2)) return PSR_EINVAL;

@@ -87,7 +87,7 @@ def test_rejected_shapes_and_precision():
         B.psr2d_logpsi(B.make_params(theta, 3, 32), s2, 66, 2, out)
     assert ei.value.code == B.PSR_EUNSUPPORTED
     s3 = torch.zeros((2, 16), dtype=torch.uint8, device="cuda")
-    with pytest.raises(B.PsrError) as ei:
+    with pytest.raises(B.PsrError) as ei:  # tensor-core path: hidden 128 or 256 only
         B.psr2d_logpsi(B.make_params(theta, 3, 32, False, "bf16"), s3, 4, 4, out)
     assert ei.value.code == B.PSR_EUNSUPPORTED
 

@@ -2,7 +2,7 @@
 
 The BF16 path's GELU uses erf from Abramowitz & Stegun, Handbook of
 Mathematical Functions, formula 7.1.28 (|error| <= 3e-7 for u >= 0).  The
-coefficients are read from the kernel source and the formula is checked
+coefficients are read from the kernels' shared header and the formula is checked
 against that published bound, so a mistyped coefficient fails here.
 """
 import os
@@ -12,7 +12,7 @@ import numpy as np
 from scipy.special import erf
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "paper_2605_13807_gb300", "csrc", "psr_fwd_bf16.cu")
+SRC = os.path.join(ROOT, "paper_2605_13807_gb300", "csrc", "psr_bf16_math.cuh")
 
 
 def _gelu_fit():
