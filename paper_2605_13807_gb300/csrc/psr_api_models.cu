@@ -71,6 +71,7 @@ cudaError_t tc2_run(psr_context *ctx, const Fwd2Jobs &jb, bool f16, const float 
     a.wimg = t.wimg;
     a.job_counter = jb.job_counter;
     a.status = jb.status;
+    if (jb.g.n_jobs >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;  // job indices are 32-bit
     int W, S;
     fwd2d_tc_geometry(a.Lx, &W, &S);
     int64_t grid = (jb.g.n_jobs + S - 1) / S;
@@ -333,6 +334,7 @@ int psr2d_local_energy(const psr_params *params, const uint8_t *samples, int64_t
     const int W = (int)words_per_row(N);
     const int nb = bond_count(Lx, Ly, ham->pbc);
     const int64_t cap = n * max_entries_per_sample(ham);
+    if (params->precision != PSR_FP32 && cap >= ((int64_t)1 << 31)) return PSR_EUNSUPPORTED;
     const size_t ckpt = fwd2d_checkpoint_floats(nL, H, Lx);
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
                d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
@@ -463,6 +465,7 @@ int sym2d_run(const psr_params *params, const uint8_t *samples, int64_t n, int32
     const int W = (int)words_per_row(N);
     const int nb = eloc ? bond_count(L, L, ham->pbc) : 0;
     const int64_t cap = eloc ? n * max_entries_per_sample(ham) : 0;
+    if (params->precision != PSR_FP32 && cap >= ((int64_t)1 << 31)) return PSR_EUNSUPPORTED;
     const size_t ckpt = fwd2d_checkpoint_floats(nL, H, L);
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
                d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;

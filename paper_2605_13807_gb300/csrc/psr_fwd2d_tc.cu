@@ -71,22 +71,24 @@ __device__ __forceinline__ uint64_t kdesc(uint32_t addr) {
 }
 __device__ __forceinline__ uint64_t kstep(int kk) { return (uint64_t)((kk * 32) >> 4); }
 
+constexpr int kEpi = 512;  // epilogue threads: 512 / H per hidden unit
+
 struct Slot2 {
-    long long job;        // -1: needs a job, -2: none left
+    int job;              // -1: needs a job, -2: none left (a launch holds < 2^31 jobs)
     int sample, p, q;     // configuration (p, q: flipped sites or -1)
     int row, r0, n_up;    // current patch row, first row, up spins before it
     float acc;            // sum of log P (mode 0) or of its differences (mode 1)
-    uint8_t v[32];        // patch values of the current row, path order
-    uint8_t vprev[32];    // previous row's values by column
+    float part[4];        // the row's readout sums, per 8-column chunk
+    uint8_t v[32];        // patch values of the current row, by column
+    uint8_t vprev[32];    // previous row's values, by column
 };
 
 struct Misc2 {
     uint64_t full[kMaxRing], empty[kMaxRing];
-    uint64_t e2m, m2e, hv, go[2];
+    uint64_t e2m, m2e, hv, imgw, go[2];
     uint32_t tmem_base;
     int abort_flag;
     int go_flag[2];
-    int pad_;
     Slot2 slot[kMaxSlots];
 };
 
@@ -117,9 +119,12 @@ __device__ __forceinline__ int patch_value(const uint8_t *s, int Lx, int pi, int
     return v;
 }
 
+// Barrier of the epilogue threads (hardware named barrier 1).
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory"); }
+
 // Barrier of the epilogue threads that also ORs a flag over them, so that
 // every epilogue thread takes the same exit.
-__device__ __forceinline__ bool epi_bar_or(int nthreads, bool v) {
+__device__ __forceinline__ bool epi_bar_or(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
@@ -127,10 +132,19 @@ __device__ __forceinline__ bool epi_bar_or(int nthreads, bool v) {
         "bar.red.or.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v), "r"(nthreads)
+        : "r"((uint32_t)v), "r"(kEpi)
         : "memory");
     return r != 0;
 }
+
+// Bulk copy shared -> global (bulk-group completion).
+__device__ __forceinline__ void bulk_s2g(void *dst, uint32_t src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Operand bits of an FP32 value, rounded to nearest: FP16 (values beyond the
 // largest finite FP16 saturate to it) or BF16.
@@ -145,24 +159,50 @@ __device__ __forceinline__ uint32_t op_pack(float lo, float hi) {
     return (uint32_t)op_bits<F16>(lo) | ((uint32_t)op_bits<F16>(hi) << 16);
 }
 
+// 16 columns (two 8-column TMEM loads) of this thread's lane, columns beyond
+// `nc8` chunks left untouched.
+__device__ __forceinline__ void tmem_ld_cols16(uint32_t taddr, int nc8, uint32_t (&r)[16]) {
+    tmem_ld8(taddr, r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7]);
+    if (nc8 > 1) tmem_ld8(taddr + 8, r[8], r[9], r[10], r[11], r[12], r[13], r[14], r[15]);
+}
+
 template <int H, bool F16>
-__global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_constant__ Fwd2TcArgs A) {
+__global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_constant__ Fwd2TcArgs A) {
     constexpr int NH = H / 128;     // unit halves (M tiles)
     constexpr int KC = H / 64;      // K chunks of a hidden-size input
-    constexpr int NW = H / 32;      // epilogue warps
+    constexpr int CG = kEpi / H;    // epilogue threads per unit (column groups)
+    constexpr int NW = kEpi / 32;   // epilogue warps
     constexpr uint32_t kTileBytes = KC * 16384u;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Misc2 &M = *reinterpret_cast<Misc2 *>(smem_raw);
     uint8_t *tiles = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + sizeof(Misc2) + 1023) & ~uintptr_t(1023));
-    uint8_t *xt = tiles;                    // layer input x (K-major rows = columns)
+    uint8_t *xt = tiles;                    // layer input x (K-major rows = site columns)
     uint8_t *ht = tiles + kTileBytes;       // h_V, then the layer's states h
     uint8_t *ring = tiles + 2 * kTileBytes; // weight slices
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int R = A.R, S = A.S, W = A.W, Lx = A.Lx, Ly = A.Ly, Px = Lx >> 1, Py = Ly >> 1;
     const int nL = A.tl.nL, N = Lx * Ly, Np = Px * Py;
+    const int nch = W >> 3;  // 8-column chunks of a slot
     const uint32_t img_bytes = (uint32_t)KC * (uint32_t)W * 128u;  // one layer's h_V image of a slot
     const volatile int *ab = &M.abort_flag;
+    uint8_t *scratch = A.scratch + (size_t)blockIdx.x * S * nL * img_bytes;
+
+    // h_V image of layer l for slot s's current row (source) and for its next
+    // row (destination; null after the job's last row)
+    auto img_src = [&](const Slot2 &st, int s, int l) -> const uint8_t * {
+        if (st.row == st.r0) {
+            if (st.r0 == 0) return A.zero_img;
+            return A.img_in + (((size_t)st.sample * Py + st.r0) * nL + l) * img_bytes;
+        }
+        if (A.img_out) return A.img_out + (((size_t)st.sample * Py + st.row) * nL + l) * img_bytes;
+        return scratch + ((size_t)s * nL + l) * img_bytes;
+    };
+    auto img_dst = [&](const Slot2 &st, int s, int l) -> uint8_t * {
+        if (st.row + 1 >= Py) return nullptr;
+        if (A.img_out) return A.img_out + (((size_t)st.sample * Py + st.row + 1) * nL + l) * img_bytes;
+        return scratch + ((size_t)s * nL + l) * img_bytes;
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&M.tmem_base))
@@ -174,9 +214,10 @@ __global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_consta
             mbar_init(smem_u32(&M.full[i]), 1);
             mbar_init(smem_u32(&M.empty[i]), 1);
         }
-        mbar_init(smem_u32(&M.e2m), H);
+        mbar_init(smem_u32(&M.e2m), 1);
         mbar_init(smem_u32(&M.m2e), 1);
         mbar_init(smem_u32(&M.hv), 1);
+        mbar_init(smem_u32(&M.imgw), 1);
         mbar_init(smem_u32(&M.go[0]), 1);
         mbar_init(smem_u32(&M.go[1]), 1);
         M.abort_flag = 0;
@@ -199,25 +240,30 @@ __global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_consta
     if (tid == 0) mbar_arrive(smem_u32(&M.go[0]));  // row step 0 runs
     __syncthreads();
     const long long njobs = A.mode == 1 ? (long long)*A.n_jobs_dev : (long long)A.n_jobs;
-    const uint32_t e2m = smem_u32(&M.e2m), m2e = smem_u32(&M.m2e), hvb = smem_u32(&M.hv);
+    const uint32_t e2m = smem_u32(&M.e2m), m2e = smem_u32(&M.m2e), hvb = smem_u32(&M.hv),
+                   imgw = smem_u32(&M.imgw);
 
     if (warp == NW) {
         // ------------------------------------------------ producer: weight stream
         if (lane == 0 && !M.abort_flag) {
-            uint32_t q = 0;
+            uint32_t q = 0, slot = 0, round = 0;  // slices issued; ring slot and pass over the ring
+            const uint32_t fb = smem_u32(&M.full[0]), ebar = smem_u32(&M.empty[0]), rb = smem_u32(ring);
             for (uint32_t row = 0;; ++row) {
                 if (!wait_ab(smem_u32(&M.go[row & 1]), (row >> 1) & 1, ab)) break;
                 if (!*(volatile int *)&M.go_flag[row & 1]) break;
                 bool ok = true;
-                for (int i = 0; i < A.n_slices; ++i, ++q) {
-                    const uint32_t slot = q % (uint32_t)R, use = q / (uint32_t)R;
-                    if (use > 0 && !wait_ab(smem_u32(&M.empty[slot]), (use - 1) & 1, ab)) {
+                const uint8_t *src = A.wimg;
+                for (int i = 0; i < A.n_slices; ++i, ++q, src += kSlice) {
+                    if (round > 0 && !wait_ab(ebar + 8 * slot, (round - 1) & 1, ab)) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_tx(smem_u32(&M.full[slot]), kSlice);
-                    bulk_g2s(smem_u32(ring + slot * kSlice), A.wimg + (size_t)i * kSlice, kSlice,
-                             smem_u32(&M.full[slot]));
+                    mbar_arrive_tx(fb + 8 * slot, kSlice);
+                    bulk_g2s(rb + slot * kSlice, src, kSlice, fb + 8 * slot);
+                    if (++slot == (uint32_t)R) {
+                        slot = 0;
+                        ++round;
+                    }
                 }
                 if (!ok) break;
             }
@@ -230,10 +276,13 @@ __global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_consta
             if (*ab) set_status(A.status, PSR_ETIMEOUT);
         }
     } else if (warp == NW + 1) {
-        // ------------------------------------------------ MMA issue
+        // ------------------------------------------------ MMA issue, h_V image stores
         if (lane == 0 && !M.abort_flag) {
-            uint32_t q = 0, pe = 0, ph = 0;
-            const uint32_t xa = smem_u32(xt), ha = smem_u32(ht), ra = smem_u32(ring);
+            // slices consumed; ring slot and the full barriers' phase; e2m and
+            // h_V barrier phases
+            uint32_t q = 0, slot = 0, fph = 0, pe = 0, ph = 0;
+            const uint32_t ha = smem_u32(ht), fb = smem_u32(&M.full[0]), ebar = smem_u32(&M.empty[0]);
+            const uint64_t xd = kdesc(smem_u32(xt)), hd = kdesc(ha), rd = kdesc(smem_u32(ring));
             bool ok = true;
             for (uint32_t row = 0; ok; ++row) {
                 if (!wait_ab(smem_u32(&M.go[row & 1]), (row >> 1) & 1, ab)) {
@@ -242,39 +291,59 @@ __global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_consta
                 }
                 if (!*(volatile int *)&M.go_flag[row & 1]) break;
                 for (int i = 0; i < A.n_slices; ++i, ++q) {
-                    const uint8_t ty = A.sched.type[i], g = A.sched.g[i], kc = A.sched.kc[i],
-                                  fl = A.sched.flags[i];
-                    if (fl & kSchedCommit) mma_commit(m2e);
-                    if (fl & kSchedWaitX) {
-                        if (!wait_ab(e2m, pe, ab)) { ok = false; break; }
-                        pe ^= 1u;
-                        tc_after();
+                    const uint32_t op = A.sched.op[i];
+                    if (op & 0x00FF0000u) {
+                        const uint32_t fl = (op >> 16) & 0xFFu;
+                        if (fl & kSchedCommit) {
+                            bulk_wait_read();  // the h tile may be overwritten once this commit lands
+                            mma_commit(m2e);
+                        }
+                        if (fl & kSchedWaitX) {
+                            if (!wait_ab(e2m, pe, ab)) { ok = false; break; }
+                            pe ^= 1u;
+                            tc_after();
+                        }
+                        if (fl & kSchedStoreH) {
+                            // the scan has written h: it is the next row's h_V of layer l
+                            const int l = (int)((op >> 24) & 0xFu);
+                            for (int s = 0; s < S; ++s) {
+                                const Slot2 &st = M.slot[s];
+                                if (st.job < 0) continue;
+                                uint8_t *dst = img_dst(st, s, l);
+                                if (!dst) continue;
+                                for (int c = 0; c < KC; ++c)
+                                    bulk_s2g(dst + (size_t)c * W * 128, ha + c * 16384 + s * W * 128,
+                                             (uint32_t)W * 128u);
+                            }
+                            bulk_commit();
+                        }
+                        if (fl & kSchedWaitHv) {
+                            if (!wait_ab(hvb, ph, ab)) { ok = false; break; }
+                            ph ^= 1u;
+                        }
                     }
-                    if (fl & kSchedWaitHv) {
-                        if (!wait_ab(hvb, ph, ab)) { ok = false; break; }
-                        ph ^= 1u;
+                    // the weight slice has landed (bulk-copy transactions)
+                    if (!wait_ab(fb + 8 * slot, fph, ab)) { ok = false; break; }
+                    const uint64_t ad = rd + (uint64_t)(slot * (kSlice >> 4));
+                    const uint64_t bd = ((op & (1u << 10)) ? hd : xd) + (uint64_t)(((op >> 12) & 3u) * (16384u >> 4));
+                    const uint32_t d = tmem + (op & 0x3FFu);
+                    mma_ss<idesc2<F16>()>(d, ad, bd, (op >> 11) & 1u);
+                    mma_ss<idesc2<F16>()>(d, ad + kstep(1), bd + kstep(1), 1u);
+                    mma_ss<idesc2<F16>()>(d, ad + kstep(2), bd + kstep(2), 1u);
+                    mma_ss<idesc2<F16>()>(d, ad + kstep(3), bd + kstep(3), 1u);
+                    mma_commit(ebar + 8 * slot);
+                    if (++slot == (uint32_t)R) {
+                        slot = 0;
+                        fph ^= 1u;
                     }
-                    const uint32_t slot = q % (uint32_t)R;
-                    if (!wait_ab(smem_u32(&M.full[slot]), (q / (uint32_t)R) & 1, ab)) { ok = false; break; }
-                    tc_after();
-                    uint32_t dcol, b;
-                    bool acc;
-                    switch (ty) {
-                        case kMtWz: dcol = 128u * g; b = xa; acc = kc > 0; break;
-                        case kMtWhx: dcol = 128u * (NH + g); b = xa; acc = kc > 0; break;
-                        case kMtWhv: dcol = 128u * (NH + g); b = ha; acc = true; break;
-                        case kMtD: dcol = 128u * g; b = xa; acc = kc > 0; break;
-                        case kMtC: dcol = 128u * g; b = ha; acc = true; break;
-                        default: dcol = 128u * NH; b = xa; acc = kc > 0; break;  // readout
-                    }
-                    const uint64_t ad = kdesc(ra + slot * kSlice), bd = kdesc(b + (uint32_t)kc * 16384u);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        mma_ss<idesc2<F16>()>(tmem + dcol, ad + kstep(kk), bd + kstep(kk), (acc || kk > 0) ? 1u : 0u);
-                    mma_commit(smem_u32(&M.empty[slot]));
                 }
-                if (ok) mma_commit(m2e);  // logits of the row
+                if (!ok) break;
+                // the row's image stores are complete before its successor reads them
+                bulk_wait_all();
+                mbar_arrive(imgw);
+                mma_commit(m2e);  // logits of the row
             }
+            bulk_wait_all();
             // the MMAs of the last slices complete before the CTA may exit
             const uint32_t last = q < (uint32_t)R ? q : (uint32_t)R;
             for (uint32_t t = 0; t < last; ++t) {
@@ -287,45 +356,27 @@ __global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_consta
             }
         }
     } else {
-        // ------------------------------------------------ epilogue (thread j = unit j)
-        const int j = tid, g = j >> 7;
-        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        // ------------------------------------------------ epilogue
+        // warp w reads tensor-memory lanes 32 (w & 3) ..; warpgroup w >> 2
+        // takes unit half g and column group cg (slots s = cg, cg + CG, ...)
+        const int q4 = warp & 3, wg = warp >> 2, g = wg % NH, cg = wg / NH;
+        const int j = 128 * g + 32 * q4 + lane;  // hidden unit
+        const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
         const uint32_t tz = tmem + lane_off + 128u * g;          // z, then y
         const uint32_t tcc = tmem + lane_off + 128u * (NH + g);  // c
-        const uint32_t tlg = tmem + lane_off + 128u * NH;        // logits (lanes 0..15)
-        // unit j's place in a K-major tile row and in a slot image row
+        const uint32_t tlg = tmem + lane_off + 128u * NH;        // logits (lanes 32 q4 + 0..15)
+        // unit j's place in a K-major tile row
         const uint32_t kreg = (uint32_t)(j >> 6) * 16384u;
         const int ch = (j & 63) >> 3;
         const uint32_t eb = (uint32_t)(j & 7) * 2u;
         auto tile_off = [&](int n) -> uint32_t {
             return kreg + (uint32_t)n * 128u + ((uint32_t)(ch ^ (n & 7)) << 4) + eb;
         };
-        const uint32_t ireg = (uint32_t)(j >> 6) * (uint32_t)W * 128u;
-        auto img_off = [&](int r) -> uint32_t {
-            return ireg + (uint32_t)r * 128u + ((uint32_t)(ch ^ (r & 7)) << 4) + eb;
-        };
-        const int nch = W >> 3;
-        uint8_t *scratch = A.scratch + (size_t)blockIdx.x * S * nL * img_bytes;
         float *res = A.res + (size_t)blockIdx.x * 2 * kCols * H;
-        uint32_t pm = 0;       // m2e phase
-        uint32_t hv_armed = 0; // h_V loads issued (thread 0)
+        uint32_t pm = 0;        // m2e phase
+        uint32_t hv_armed = 0;  // h_V loads issued (thread 0)
         bool ok = !M.abort_flag;
 
-        // h_V image of layer l for slot s's current row (source) and for its
-        // next row (destination, null after the last row)
-        auto img_src = [&](const Slot2 &st, int s, int l) -> const uint8_t * {
-            if (st.row == st.r0) {
-                if (st.r0 == 0) return A.zero_img;
-                return A.img_in + (((size_t)st.sample * Py + st.r0) * nL + l) * img_bytes;
-            }
-            if (A.img_out) return A.img_out + (((size_t)st.sample * Py + st.row) * nL + l) * img_bytes;
-            return scratch + ((size_t)s * nL + l) * img_bytes;
-        };
-        auto img_dst = [&](const Slot2 &st, int s, int l) -> uint8_t * {
-            if (st.row + 1 >= Py) return nullptr;
-            if (A.img_out) return A.img_out + (((size_t)st.sample * Py + st.row + 1) * nL + l) * img_bytes;
-            return scratch + ((size_t)s * nL + l) * img_bytes;
-        };
         // thread 0: bulk copies of every active slot's h_V image of layer l
         auto issue_hv = [&](int l) {
             uint32_t bytes = 0;
@@ -342,93 +393,112 @@ __global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_consta
             }
             ++hv_armed;
         };
+        // One thread polls the MMA thread's barrier and a named barrier
+        // releases the others (hundreds of pollers would contend for the
+        // shared memory the tensor core reads its operands from); the
+        // epilogue's signal is one arrival after a named barrier.
         auto wait_m2e = [&]() {
-            bool w = ok && wait_ab(m2e, pm, ab);
-            w = __all_sync(0xffffffffu, w);
-            if (!w && ok) {
+            bool w = true;
+            if (tid == 0) w = ok && wait_ab(m2e, pm, ab);
+            const bool bad = epi_bar_or(!w || !ok);
+            if (bad && ok && tid == 0) {
                 M.abort_flag = 1;
                 set_status(A.status, PSR_ETIMEOUT);
             }
-            ok = ok && w;
+            ok = ok && !bad;
             pm ^= 1u;
             tc_after();
         };
+        auto arrive_e2m = [&]() {
+            fence_proxy_async();  // this thread's tile writes, before the MMAs read them
+            tc_before();
+            epi_bar();
+            if (tid == 0) mbar_arrive(e2m);
+        };
+        // the previous row's readout sums into the job's total (fixed order),
+        // and the job's log psi after its last row (slot s, its warp)
+        auto fold = [&](int s) {
+            Slot2 &st = M.slot[s];
+            if (lane == 0 && st.job >= 0) {
+                float a = st.acc;
+                for (int c = 0; c < nch; ++c) a += st.part[c];
+                st.acc = a;
+                if (st.row + 1 >= Py) A.out[st.job] = 0.5f * a;
+            }
+            __syncwarp();
+        };
 
         for (uint32_t row_it = 0; ok; ++row_it) {
-            // ---- slot update: finished or empty slots take the next job; the
-            // others advance one patch row
+            // ---- slot update (warp s for slot s): finished or empty slots
+            // take the next job, the others advance one patch row
             for (int s = warp; s < S; s += NW) {
                 Slot2 &st = M.slot[s];
-                const long long job = st.job;
+                if (row_it > 0) fold(s);
+                const int job = st.job;
                 if (job == -2) continue;
+                const uint8_t *sp;
+                int r;
                 if (job == -1 || st.row + 1 >= Py) {
                     unsigned long long nj = 0;
                     if (lane == 0) nj = atomicAdd(A.job_counter, 1ull);
                     nj = __shfl_sync(0xffffffffu, nj, 0);
-                    __syncwarp();
                     if ((long long)nj >= njobs) {
                         if (lane == 0) st.job = -2;
                         __syncwarp();
                         continue;
                     }
-                    int sample = (int)nj, p = -1, q = -1, r0 = 0;
+                    int sample = (int)nj, p = -1, qq = -1, r0 = 0;
                     if (A.mode == 1) {
                         const int32_t *e = A.entries + 3 * nj;
                         sample = e[0];
                         p = e[1];
-                        q = e[2];
+                        qq = e[2];
                         r0 = (p / Lx) >> 1;
                     }
-                    const uint8_t *sp = A.spins + (size_t)sample * N;
+                    sp = A.spins + (size_t)sample * N;
                     int up = 0;
                     for (int t = lane; t < 2 * r0 * Lx; t += 32) up += sp[t] & 1;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(0xffffffffu, up, o);
                     if (lane < Px) {
                         if (r0 > 0) st.vprev[lane] = (uint8_t)patch_value(sp, Lx, lane, r0 - 1, -1, -1);
-                        const int pi = (r0 & 1) ? Px - 1 - lane : lane;
-                        st.v[lane] = (uint8_t)patch_value(sp, Lx, pi, r0, p, q);
+                        st.v[lane] = (uint8_t)patch_value(sp, Lx, lane, r0, p, qq);
                     }
                     if (lane == 0) {
-                        st.job = (long long)nj;
+                        st.job = (int)nj;
                         st.sample = sample;
                         st.p = p;
-                        st.q = q;
+                        st.q = qq;
                         st.row = r0;
                         st.r0 = r0;
                         st.n_up = up;
                         st.acc = 0.0f;
                     }
-                    __syncwarp();
+                    r = r0;
                 } else {
-                    const int r = st.row;
-                    int old = 0, pc = 0;
+                    r = st.row + 1;
+                    sp = A.spins + (size_t)st.sample * N;
+                    int pc = 0;
                     if (lane < Px) {
-                        old = st.v[lane];
+                        const int old = st.v[lane];
                         pc = __popc(old);
+                        st.vprev[lane] = (uint8_t)old;
+                        st.v[lane] = (uint8_t)patch_value(sp, Lx, lane, r, st.p, st.q);
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, o);
-                    __syncwarp();
-                    const uint8_t *sp = A.spins + (size_t)st.sample * N;
-                    if (lane < Px) {
-                        st.vprev[(r & 1) ? Px - 1 - lane : lane] = (uint8_t)old;
-                        const int pi = ((r + 1) & 1) ? Px - 1 - lane : lane;
-                        st.v[lane] = (uint8_t)patch_value(sp, Lx, pi, r + 1, st.p, st.q);
-                    }
-                    __syncwarp();
                     if (lane == 0) {
                         st.n_up += pc;
-                        st.row = r + 1;
+                        st.row = r;
                     }
-                    __syncwarp();
                 }
+                __syncwarp();
             }
-            if (epi_bar_or(H, !ok || *ab)) {
+            if (epi_bar_or(!ok || *ab)) {
                 ok = false;
                 break;
             }
-            if (j == 0) {
+            if (tid == 0) {
                 // does a row step follow this one?
                 bool more = false;
                 for (int s = 0; s < S; ++s)
@@ -436,193 +506,215 @@ __global__ void __launch_bounds__(H + 64, 1) fwd2d_tc_kernel(const __grid_consta
                 if (!more) more = (long long)atomicAdd(A.job_counter, 0ull) < njobs;
                 M.go_flag[(row_it + 1) & 1] = more ? 1 : 0;
                 mbar_arrive(smem_u32(&M.go[(row_it + 1) & 1]));
-                issue_hv(0);
+                // the previous row's image stores are complete
+                if (row_it > 0 && !wait_ab(imgw, (row_it - 1) & 1, ab)) {
+                    ok = false;
+                    M.abort_flag = 1;
+                    set_status(A.status, PSR_ETIMEOUT);
+                }
+                if (ok) issue_hv(0);
             }
             // ---- layer-0 input: one-hot (v_H, v_V) of every column, K chunk 0
-            constexpr uint32_t kOne = F16 ? 0x3C00u : 0x3F80u;  // 1.0
-            for (int id = j; id < kCols * 8; id += H) {
-                const int n = id >> 3, c = id & 7, s = n / W, k = n - s * W;
-                int vh = -1, vv = -1;
-                if (s < S && k < Px) {
-                    const Slot2 &st = M.slot[s];
-                    if (st.job >= 0) {
-                        if (k > 0) vh = st.v[k - 1];
-                        if (st.row > 0) vv = 16 + st.vprev[(st.row & 1) ? Px - 1 - k : k];
+            {
+                constexpr uint32_t kOne = F16 ? 0x3C00u : 0x3F80u;  // 1.0
+                for (int id = tid; id < kCols * 8; id += kEpi) {
+                    const int n = id >> 3, c = id & 7, s = n / W, i = n - s * W;
+                    int vh = -1, vv = -1;
+                    if (s < S && i < Px) {
+                        const Slot2 &st = M.slot[s];
+                        if (st.job >= 0) {
+                            const bool odd = st.row & 1;
+                            // the previous patch on the path: column i - 1 (even rows) or i + 1
+                            if (odd ? (i + 1 < Px) : (i > 0)) vh = st.v[odd ? i + 1 : i - 1];
+                            if (st.row > 0) vv = 16 + st.vprev[i];
+                        }
                     }
-                }
-                uint32_t w4[4];
+                    uint32_t w4[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int e0 = 8 * c + 2 * i, e1 = e0 + 1;
-                    const uint32_t lo = (e0 == vh || e0 == vv) ? kOne : 0u;
-                    const uint32_t hi = (e1 == vh || e1 == vv) ? kOne : 0u;
-                    w4[i] = lo | (hi << 16);
+                    for (int e = 0; e < 4; ++e) {
+                        const int e0 = 8 * c + 2 * e, e1 = e0 + 1;
+                        const uint32_t lo = (e0 == vh || e0 == vv) ? kOne : 0u;
+                        const uint32_t hi = (e1 == vh || e1 == vv) ? kOne : 0u;
+                        w4[e] = lo | (hi << 16);
+                    }
+                    *reinterpret_cast<uint4 *>(xt + n * 128 + ((c ^ (n & 7)) << 4)) =
+                        make_uint4(w4[0], w4[1], w4[2], w4[3]);
                 }
-                *reinterpret_cast<uint4 *>(xt + n * 128 + ((c ^ (n & 7)) << 4)) =
-                    make_uint4(w4[0], w4[1], w4[2], w4[3]);
             }
-            fence_proxy_async();
-            mbar_arrive(e2m);
+            arrive_e2m();
 
             for (int l = 0; l < nL; ++l) {
-                // ---- gates and scan along each slot's row
+                // ---- gates and scan along each slot's row (path order)
                 wait_m2e();
                 {
                     const float hbz = 0.5f * A.theta[A.tl.bz[l] + j], bh = A.theta[A.tl.bh[l] + j];
                     const float2 hbz2 = make_float2(hbz, hbz), bh2 = make_float2(bh, bh);
                     const bool keep_res = (l >= 1) && (l + 1 < nL);
                     float *resw = res + (size_t)(l & 1) * kCols * H;
-                    for (int s = 0; s < S; ++s) {
+                    for (int s = cg; s < S; s += CG) {
                         const Slot2 &st = M.slot[s];
                         if (st.job < 0) continue;
                         const int n0 = s * W;
-                        uint32_t zr[32], cr[32];
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) zr[i] = cr[i] = 0u;
-#pragma unroll
-                        for (int c8 = 0; c8 < 4; ++c8)
-                            if (c8 < nch) {
-                                const int b = 8 * c8;
-                                tmem_ld8(tz + n0 + b, zr[b], zr[b + 1], zr[b + 2], zr[b + 3], zr[b + 4], zr[b + 5],
-                                         zr[b + 6], zr[b + 7]);
-                                tmem_ld8(tcc + n0 + b, cr[b], cr[b + 1], cr[b + 2], cr[b + 3], cr[b + 4], cr[b + 5],
-                                         cr[b + 6], cr[b + 7]);
-                            }
-                        tmem_wait_ld32x2(zr, cr);
-                        uint8_t *dst = img_dst(st, s, l);
+                        const bool odd = st.row & 1;
                         float h = 0.0f;  // the row starts from h_H = 0
+                        // two 16-column halves, in path order
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int half = odd ? 1 - hh : hh;
+                            const int c0 = 16 * half;
+                            if (c0 >= Px) continue;
+                            const int nc8 = nch - 2 * half;
+                            uint32_t zr[16], cr[16];
+                            tmem_ld_cols16(tz + n0 + c0, nc8, zr);
+                            tmem_ld_cols16(tcc + n0 + c0, nc8, cr);
+                            tmem_wait_ld16x2(zr, cr);
+                            float av[16], bv[16];
 #pragma unroll
-                        for (int k = 0; k < 32; k += 2) {
-                            if (k < Px) {
-                                float2 a, bb;
+                            for (int k = 0; k < 16; k += 2) {
+                                float2 a2, b2;
                                 gates2(make_float2(__uint_as_float(zr[k]), __uint_as_float(zr[k + 1])),
-                                       make_float2(__uint_as_float(cr[k]), __uint_as_float(cr[k + 1])), hbz2, bh2, a,
-                                       bb);
-                                h = fmaf(a.x, h, bb.x);
-                                const float h0 = h;
-                                h = fmaf(a.y, h, bb.y);
-                                const float h1 = h;
-                                *reinterpret_cast<uint16_t *>(ht + tile_off(n0 + k)) = op_bits<F16>(h0);
-                                if (dst) *reinterpret_cast<uint16_t *>(dst + img_off(Px - 1 - k)) = op_bits<F16>(h0);
-                                if (keep_res) resw[(size_t)(n0 + k) * H + j] = h0;
-                                if (k + 1 < Px) {
-                                    *reinterpret_cast<uint16_t *>(ht + tile_off(n0 + k + 1)) = op_bits<F16>(h1);
-                                    if (dst)
-                                        *reinterpret_cast<uint16_t *>(dst + img_off(Px - 2 - k)) = op_bits<F16>(h1);
-                                    if (keep_res) resw[(size_t)(n0 + k + 1) * H + j] = h1;
+                                       make_float2(__uint_as_float(cr[k]), __uint_as_float(cr[k + 1])), hbz2, bh2, a2,
+                                       b2);
+                                av[k] = a2.x;
+                                av[k + 1] = a2.y;
+                                bv[k] = b2.x;
+                                bv[k + 1] = b2.y;
+                            }
+                            if (!odd) {
+#pragma unroll
+                                for (int k = 0; k < 16; ++k) {
+                                    if (c0 + k < Px) {
+                                        h = fmaf(av[k], h, bv[k]);
+                                        *reinterpret_cast<uint16_t *>(ht + tile_off(n0 + c0 + k)) = op_bits<F16>(h);
+                                        if (keep_res) resw[(size_t)(n0 + c0 + k) * H + j] = h;
+                                    }
+                                }
+                            } else {
+#pragma unroll
+                                for (int k = 15; k >= 0; --k) {
+                                    if (c0 + k < Px) {
+                                        h = fmaf(av[k], h, bv[k]);
+                                        *reinterpret_cast<uint16_t *>(ht + tile_off(n0 + c0 + k)) = op_bits<F16>(h);
+                                        if (keep_res) resw[(size_t)(n0 + c0 + k) * H + j] = h;
+                                    }
                                 }
                             }
                         }
                     }
                 }
-                fence_proxy_async();
-                fence_proxy_async_global();
-                tc_before();
-                mbar_arrive(e2m);
+                arrive_e2m();
 
                 // ---- output map: x = GELU(y + residual)
                 wait_m2e();
-                if (j == 0 && l + 1 < nL && ok) issue_hv(l + 1);
+                if (tid == 0 && l + 1 < nL && ok) issue_hv(l + 1);
                 {
                     const bool use_res = (l >= 2);
                     const float *resr = res + (size_t)((l - 1) & 1) * kCols * H;
-                    for (int s = 0; s < S; ++s) {
+                    for (int s = cg; s < S; s += CG) {
                         const Slot2 &st = M.slot[s];
                         if (st.job < 0) continue;
                         const int n0 = s * W;
-                        uint32_t yr[32];
+                        for (int half = 0; half < 2; ++half) {
+                            const int c0 = 16 * half;
+                            if (c0 >= Px) continue;
+                            uint32_t yr[16];
+                            tmem_ld_cols16(tz + n0 + c0, nch - 2 * half, yr);
+                            float rv[16];
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) yr[i] = 0u;
+                            for (int k = 0; k < 16; ++k)
+                                rv[k] = (use_res && c0 + k < Px) ? resr[(size_t)(n0 + c0 + k) * H + j] : 0.0f;
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(yr, 0)::"memory");
 #pragma unroll
-                        for (int c8 = 0; c8 < 4; ++c8)
-                            if (c8 < nch) {
-                                const int b = 8 * c8;
-                                tmem_ld8(tz + n0 + b, yr[b], yr[b + 1], yr[b + 2], yr[b + 3], yr[b + 4], yr[b + 5],
-                                         yr[b + 6], yr[b + 7]);
-                            }
-                        tmem_wait_ld32(yr);
-#pragma unroll
-                        for (int k = 0; k < 32; k += 2) {
-                            if (k < Px) {
-                                float2 y = make_float2(__uint_as_float(yr[k]), __uint_as_float(yr[k + 1]));
-                                if (use_res) {
-                                    y.x += resr[(size_t)(n0 + k) * H + j];
-                                    if (k + 1 < Px) y.y += resr[(size_t)(n0 + k + 1) * H + j];
+                            for (int k = 0; k < 16; k += 2) {
+                                if (c0 + k < Px) {
+                                    const float2 x = gelu_bf16out2(make_float2(__uint_as_float(yr[k]) + rv[k],
+                                                                               __uint_as_float(yr[k + 1]) + rv[k + 1]));
+                                    *reinterpret_cast<uint16_t *>(xt + tile_off(n0 + c0 + k)) = op_bits<F16>(x.x);
+                                    if (c0 + k + 1 < Px)
+                                        *reinterpret_cast<uint16_t *>(xt + tile_off(n0 + c0 + k + 1)) = op_bits<F16>(x.y);
                                 }
-                                const float2 x = gelu_bf16out2(y);
-                                *reinterpret_cast<uint16_t *>(xt + tile_off(n0 + k)) = op_bits<F16>(x.x);
-                                if (k + 1 < Px) *reinterpret_cast<uint16_t *>(xt + tile_off(n0 + k + 1)) = op_bits<F16>(x.y);
                             }
                         }
                     }
                 }
-                fence_proxy_async();
-                tc_before();
-                mbar_arrive(e2m);
+                arrive_e2m();
             }
 
-            // ---- readout: masked 16-way softmax of every patch of the row
+            // ---- readout: masked 16-way softmax of every patch of the row;
+            // warp w takes 8 columns (slot w / nch, chunk w % nch)
             wait_m2e();
-            if ((warp & 3) == 0 && ok) {
-                const int ri = warp >> 2;
-                const float bo = A.theta[A.tl.bo + (lane & 15)];
-                const int pc_lane = __popc(lane & 15);
-                for (int s = ri; s < S; s += NH) {
-                    Slot2 &st = M.slot[s];
-                    if (st.job < 0) continue;
-                    const int n0 = s * W, r = st.row;
-                    int up = st.n_up;
-                    float rsum = 0.0f;
-                    for (int c8 = 0; c8 < nch; ++c8) {
-                        uint32_t lr[8];
-                        tmem_ld8(tlg + n0 + 8 * c8, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], lr[6], lr[7]);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;"
-                                     : "+r"(lr[0]), "+r"(lr[1]), "+r"(lr[2]), "+r"(lr[3]), "+r"(lr[4]), "+r"(lr[5]),
-                                       "+r"(lr[6]), "+r"(lr[7])::"memory");
+            if (ok && warp < S * nch) {
+                const int s = warp / nch, c8 = warp - s * nch;
+                Slot2 &st = M.slot[s];
+                if (st.job >= 0) {
+                    const int r = st.row, n0 = s * W, i0 = 8 * c8;
+                    const bool odd = r & 1;
+                    const float bo = A.theta[A.tl.bo + (lane & 15)];
+                    const int pc_lane = __popc(lane & 15);
+                    // up spins of the row's patches before path position `lane`
+                    int upx;
+                    {
+                        const int c = odd ? Px - 1 - lane : lane;  // column at path position lane
+                        const int pc = lane < Px ? __popc(st.v[c]) : 0;
+                        int incl = pc;
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int k = 8 * c8 + i;
-                            if (k >= Px) break;
-                            const int v = st.v[k];
-                            const int down = 2 * r * Lx + 4 * k - up;
-                            const bool allowed =
-                                !A.u1 || (up + pc_lane <= N / 2 && down + 4 - pc_lane <= N / 2);
-                            const float lg = __uint_as_float(lr[i]) + bo;
-                            float m = allowed ? lg : -INFINITY;
-#pragma unroll
-                            for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o, 16));
-                            float e = allowed ? __expf(lg - m) : 0.0f;
-#pragma unroll
-                            for (int o = 8; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o, 16);
-                            float lp = allowed ? lg - m - __logf(e) : -INFINITY;
-                            lp = __shfl_sync(0xffffffffu, lp, v);
-                            const int t = r * Px + k;
-                            float d = lp;
-                            if (A.mode == 1) d = lp - A.logp_ref[(size_t)st.sample * Np + t];
-                            else if (A.logp_out && lane == 0) A.logp_out[(size_t)st.sample * Np + t] = lp;
-                            rsum += d;
-                            up += __popc(v);
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += t;
                         }
+                        upx = incl - pc;
                     }
-                    if (lane == 0) {
-                        st.acc += rsum;
-                        if (r + 1 >= Py) A.out[st.job] = 0.5f * st.acc;
+                    float ref = 0.0f;
+                    if (A.mode == 1 && lane < 8 && i0 + lane < Px) {
+                        const int i = i0 + lane, k = odd ? Px - 1 - i : i;
+                        ref = A.logp_ref[(size_t)st.sample * Np + r * Px + k];
                     }
-                    __syncwarp();
+                    uint32_t lr[8];
+                    tmem_ld8(tlg + n0 + i0, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], lr[6], lr[7]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                                 : "+r"(lr[0]), "+r"(lr[1]), "+r"(lr[2]), "+r"(lr[3]), "+r"(lr[4]), "+r"(lr[5]),
+                                   "+r"(lr[6]), "+r"(lr[7])::"memory");
+                    float rsum = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int i = i0 + e;
+                        if (i >= Px) break;
+                        const int k = odd ? Px - 1 - i : i, v = st.v[i];
+                        const int up = st.n_up + __shfl_sync(0xffffffffu, upx, k);
+                        const int down = 2 * r * Lx + 4 * k - up;
+                        const bool allowed = !A.u1 || (up + pc_lane <= N / 2 && down + 4 - pc_lane <= N / 2);
+                        const float lg = __uint_as_float(lr[e]) + bo;
+                        float m = allowed ? lg : -INFINITY;
+#pragma unroll
+                        for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o, 16));
+                        float ex = allowed ? __expf(lg - m) : 0.0f;
+#pragma unroll
+                        for (int o = 8; o > 0; o >>= 1) ex += __shfl_xor_sync(0xffffffffu, ex, o, 16);
+                        float lp = allowed ? lg - m - __logf(ex) : -INFINITY;
+                        lp = __shfl_sync(0xffffffffu, lp, v);
+                        const float rf = __shfl_sync(0xffffffffu, ref, e);
+                        float d = lp;
+                        if (A.mode == 1) d = lp - rf;
+                        else if (A.logp_out && lane == 0) A.logp_out[(size_t)st.sample * Np + r * Px + k] = lp;
+                        rsum += d;
+                    }
+                    if (lane == 0) st.part[c8] = rsum;
                 }
             }
             tc_before();
-            if (epi_bar_or(H, !ok)) {
+            if (epi_bar_or(!ok)) {
                 ok = false;
                 break;
             }
-            if (!*(volatile int *)&M.go_flag[(row_it + 1) & 1]) break;
+            if (!*(volatile int *)&M.go_flag[(row_it + 1) & 1]) {
+                for (int s = warp; s < S; s += NW) fold(s);
+                break;
+            }
         }
         if (!ok) {
             M.abort_flag = 1;
             set_status(A.status, PSR_ETIMEOUT);
         }
-        if (j == 0 && hv_armed > 0 && !mbar_wait(hvb, (hv_armed - 1) & 1)) set_status(A.status, PSR_ETIMEOUT);
+        if (tid == 0 && hv_armed > 0 && !mbar_wait(hvb, (hv_armed - 1) & 1)) set_status(A.status, PSR_ETIMEOUT);
     }
     tc_before();
     __syncthreads();
@@ -643,7 +735,7 @@ cudaError_t launch_h(const Fwd2TcArgs &a, int grid, cudaStream_t stream) {
     cudaError_t e =
         cudaFuncSetAttribute(fwd2d_tc_kernel<H, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fwd2d_tc_kernel<H, F16><<<grid, H + 64, smem, stream>>>(a);
+    fwd2d_tc_kernel<H, F16><<<grid, kEpi + 64, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -673,7 +765,9 @@ __global__ void pack2d_tc_kernel(const float *__restrict__ theta, T2Layout tl, S
                     case kMtWhv: v = theta[tl.Wh[l] + (int64_t)unit * (din + H) + din + k]; break;
                     case kMtC: v = theta[tl.C[l] + (int64_t)unit * H + k]; break;
                     case kMtD: if (k < din) v = theta[tl.D[l] + (int64_t)unit * din + k]; break;
-                    default: if (unit < 16) v = theta[tl.Wo + (int64_t)unit * H + k]; break;
+                    default:  // W_o in rows 32 q + o of every lane quarter q
+                        if ((unit & 31) < 16) v = theta[tl.Wo + (int64_t)(unit & 31) * H + k];
+                        break;
                 }
                 v2[h] = v;
             }
@@ -697,7 +791,21 @@ Sched2 fwd2d_tc_schedule(int nL, int H) {
         sc.l[n] = (uint8_t)l;
         sc.g[n] = (uint8_t)g;
         sc.kc[n] = (uint8_t)kc;
+        if (ty == kMtD && g == 0 && kc == 0) fl |= kSchedStoreH;  // the scan's h is the next row's h_V
         sc.flags[n] = (uint8_t)fl;
+        // accumulator column (z / y of half g: 128 g; c: 128 (NH + g); logits:
+        // 128 NH), B tile, accumulate flag
+        uint32_t dcol = 0, from_h = 0, acc = 0;
+        switch (ty) {
+            case kMtWz: dcol = 128u * g; acc = kc > 0; break;
+            case kMtWhx: dcol = 128u * (NH + g); acc = kc > 0; break;
+            case kMtWhv: dcol = 128u * (NH + g); from_h = 1; acc = 1; break;
+            case kMtD: dcol = 128u * g; acc = kc > 0; break;
+            case kMtC: dcol = 128u * g; from_h = 1; acc = 1; break;
+            default: dcol = 128u * NH; acc = kc > 0; break;
+        }
+        sc.op[n] = dcol | (from_h << 10) | (acc << 11) | ((uint32_t)kc << 12) | ((uint32_t)fl << 16) |
+                   ((uint32_t)l << 24);
         ++n;
     };
     for (int l = 0; l < nL; ++l) {

@@ -230,11 +230,15 @@ T2Layout t2_layout(int nL, int H);
 // order (launch_pack2d_tc writes them); Sched2 lists, per slice, the matrix,
 // layer, unit half, K chunk and the synchronisation before it.
 enum { kMtWz = 0, kMtWhx = 1, kMtWhv = 2, kMtC = 3, kMtD = 4, kMtWo = 5 };
-enum { kSchedCommit = 1, kSchedWaitX = 2, kSchedWaitHv = 4 };
+enum { kSchedCommit = 1, kSchedWaitX = 2, kSchedWaitHv = 4, kSchedStoreH = 8 };
 constexpr int kSchedMax = 320;
+// op[i], what the MMA thread needs of slice i: bits 0-9 accumulator column,
+// bit 10 B operand from the h tile (else x), bit 11 accumulate from the
+// first K step, bits 12-13 K chunk, bits 16-23 flags, bits 24-27 layer.
 struct Sched2 {
     int n;
     uint8_t type[kSchedMax], l[kSchedMax], g[kSchedMax], kc[kSchedMax], flags[kSchedMax];
+    uint32_t op[kSchedMax];
 };
 Sched2 fwd2d_tc_schedule(int nL, int H);
 // Jobs as in Fwd2Group; the row checkpoints are 16-bit h_V images:
