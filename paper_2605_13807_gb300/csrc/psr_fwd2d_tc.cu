@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                         if (fl & kSchedWaitHv) {
                             if (!wait_ab(hvb, ph, ab)) { ok = false; break; }
                             ph ^= 1u;
+                            tc_after();
                         }
                     }
                     // the weight slice has landed (bulk-copy transactions)
@@ -369,8 +370,12 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
         const uint32_t kreg = (uint32_t)(j >> 6) * 16384u;
         const int ch = (j & 63) >> 3;
         const uint32_t eb = (uint32_t)(j & 7) * 2u;
-        auto tile_off = [&](int n) -> uint32_t {
-            return kreg + (uint32_t)n * 128u + ((uint32_t)(ch ^ (n & 7)) << 4) + eb;
+        // unit j's element of tile row nb + k, nb a multiple of 8 (so the
+        // 16-byte chunk's swizzle phase is k & 7)
+        const uint32_t eoff = kreg + eb, sw = (uint32_t)ch << 4;
+        auto tile_st = [&](uint8_t *tile, int nb, int k, uint16_t v) {
+            *reinterpret_cast<uint16_t *>(tile + eoff + (uint32_t)nb * 128u + (sw ^ ((uint32_t)(k & 7) << 4)) +
+                                          (uint32_t)k * 128u) = v;
         };
         float *res = A.res + (size_t)blockIdx.x * 2 * kCols * H;
         uint32_t pm = 0;        // m2e phase
@@ -584,7 +589,7 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                                 for (int k = 0; k < 16; ++k) {
                                     if (c0 + k < Px) {
                                         h = fmaf(av[k], h, bv[k]);
-                                        *reinterpret_cast<uint16_t *>(ht + tile_off(n0 + c0 + k)) = op_bits<F16>(h);
+                                        tile_st(ht, n0 + c0, k, op_bits<F16>(h));
                                         if (keep_res) resw[(size_t)(n0 + c0 + k) * H + j] = h;
                                     }
                                 }
@@ -593,7 +598,7 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                                 for (int k = 15; k >= 0; --k) {
                                     if (c0 + k < Px) {
                                         h = fmaf(av[k], h, bv[k]);
-                                        *reinterpret_cast<uint16_t *>(ht + tile_off(n0 + c0 + k)) = op_bits<F16>(h);
+                                        tile_st(ht, n0 + c0, k, op_bits<F16>(h));
                                         if (keep_res) resw[(size_t)(n0 + c0 + k) * H + j] = h;
                                     }
                                 }
@@ -628,9 +633,9 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                                 if (c0 + k < Px) {
                                     const float2 x = gelu_bf16out2(make_float2(__uint_as_float(yr[k]) + rv[k],
                                                                                __uint_as_float(yr[k + 1]) + rv[k + 1]));
-                                    *reinterpret_cast<uint16_t *>(xt + tile_off(n0 + c0 + k)) = op_bits<F16>(x.x);
+                                    tile_st(xt, n0 + c0, k, op_bits<F16>(x.x));
                                     if (c0 + k + 1 < Px)
-                                        *reinterpret_cast<uint16_t *>(xt + tile_off(n0 + c0 + k + 1)) = op_bits<F16>(x.y);
+                                        tile_st(xt, n0 + c0, k + 1, op_bits<F16>(x.y));
                                 }
                             }
                         }
@@ -798,8 +803,8 @@ Sched2 fwd2d_tc_schedule(int nL, int H) {
         uint32_t dcol = 0, from_h = 0, acc = 0;
         switch (ty) {
             case kMtWz: dcol = 128u * g; acc = kc > 0; break;
-            case kMtWhx: dcol = 128u * (NH + g); acc = kc > 0; break;
-            case kMtWhv: dcol = 128u * (NH + g); from_h = 1; acc = 1; break;
+            case kMtWhx: dcol = 128u * (NH + g); acc = 1; break;
+            case kMtWhv: dcol = 128u * (NH + g); from_h = 1; acc = kc > 0; break;
             case kMtD: dcol = 128u * g; acc = kc > 0; break;
             case kMtC: dcol = 128u * g; from_h = 1; acc = 1; break;
             default: dcol = 128u * NH; acc = kc > 0; break;
@@ -810,17 +815,19 @@ Sched2 fwd2d_tc_schedule(int nL, int H) {
     };
     for (int l = 0; l < nL; ++l) {
         const int kin = l == 0 ? 1 : KC;
-        // projections: W_z x, W_hx x (x ready), then W_hv h_V (image loaded)
-        for (int g = 0; g < NH; ++g) {
-            for (int kc = 0; kc < kin; ++kc) {
+        // projections: W_hv h_V first (it needs only the h_V image, so above
+        // layer 0 it runs while the epilogue computes the layer input), then
+        // W_z x and W_hx x once x is ready
+        for (int g = 0; g < NH; ++g)
+            for (int kc = 0; kc < KC; ++kc) {
                 int fl = 0;
-                if (g == 0 && kc == 0) fl = (l == 0) ? kSchedWaitX : (kSchedCommit | kSchedWaitX);
-                add(kMtWz, l, g, kc, fl);
+                if (g == 0 && kc == 0) fl = (l == 0) ? kSchedWaitHv : (kSchedCommit | kSchedWaitHv);
+                add(kMtWhv, l, g, kc, fl);
             }
+        for (int g = 0; g < NH; ++g) {
+            for (int kc = 0; kc < kin; ++kc) add(kMtWz, l, g, kc, (g == 0 && kc == 0) ? kSchedWaitX : 0);
             for (int kc = 0; kc < kin; ++kc) add(kMtWhx, l, g, kc, 0);
         }
-        for (int g = 0; g < NH; ++g)
-            for (int kc = 0; kc < KC; ++kc) add(kMtWhv, l, g, kc, (g == 0 && kc == 0) ? kSchedWaitHv : 0);
         // output map: D x + C h (the scan has written h)
         for (int g = 0; g < NH; ++g) {
             for (int kc = 0; kc < kin; ++kc)

@@ -195,6 +195,11 @@ __device__ __forceinline__ void tmem_wait_ld16x2(uint32_t (&a)[16], uint32_t (&b
 __device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(a, 0), PSR_P16(a, 16)::"memory");
 }
+__device__ __forceinline__ void tmem_wait_ld16x4(uint32_t (&a)[16], uint32_t (&b)[16], uint32_t (&c)[16],
+                                                 uint32_t (&d)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : PSR_P16(a, 0), PSR_P16(b, 0), PSR_P16(c, 0), PSR_P16(d, 0)::"memory");
+}
 __device__ __forceinline__ void tmem_wait_ld32x2(uint32_t (&a)[32], uint32_t (&b)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : PSR_P16(a, 0), PSR_P16(a, 16), PSR_P16(b, 0), PSR_P16(b, 16)::"memory");
