@@ -82,8 +82,8 @@ def parse():
                     help="samples of the sample-only run (default: the workload's samples)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="only the mixed-lattice batch leg")
-    ap.add_argument("--samples-2d", type=int, default=32,
-                    help="samples of the 2D patched-model leg (52x52, FP32)")
+    ap.add_argument("--samples-2d", type=int, default=64,
+                    help="samples of the 2D patched-model leg (52x52; FP16 tensor cores, FP32 on 8 of them)")
     ap.add_argument("--scan-only", action="store_true",
                     help="only the standalone scan measurement (profiling runs)")
     ap.add_argument("--scan-n", type=int, default=0,
@@ -399,58 +399,77 @@ def flops_per_patch_2d(H):
     return 2 * H * H * 12
 
 
-def model2d_leg(Lx, Ly, n, dev, reps=2, H=256):
+def model2d_leg(Lx, Ly, n, dev, reps=2, H=256, n32=8):
     """The paper's 2D patched minGRU at its 52x52 configuration (3 layers,
-    d_h = 256, 2x2 patches; FP32 CUDA cores): log psi of n samples plus E_loc
-    over all their connected configurations, in the headline metric's unit
-    (configuration x spin site, logical)."""
+    d_h = 256, 2x2 patches): log psi of n samples plus E_loc over all their
+    connected configurations, in the headline metric's unit (configuration x
+    spin site, logical), on the tensor cores (FP16 operands, FP32
+    accumulation, gates, scan and softmax); the FP32 CUDA-core path of the
+    same model on n32 of the samples for comparison."""
     import torch
 
     from paper_2605_13807_gb300 import api, binding as B, inputs
     ham = B.make_hamiltonian("heisenberg", Lx, Ly, False, True, 1.0, 0.0)
-    cfg = api.ModelConfig(N_LAYERS, H, True, "fp32")
     theta = torch.from_numpy(inputs.glorot_params2d(N_LAYERS, H, seed=0)).to(dev)
-    spins = torch.from_numpy(rank_samples(0, n, Lx, Ly)).to(dev)
     N, Px, Py = Lx * Ly, Lx // 2, Ly // 2
-    _, ent, _ = api.connected(spins, ham)
-    E = int(ent.shape[0])
-    r0 = (ent[:, 1].to(torch.int64) // Lx) // 2
-    evaluated = n * Px * Py + int(((Py - r0) * Px).sum().item())
-    lp = torch.empty(n, dtype=torch.float32, device=dev)
-    el = torch.empty(n, dtype=torch.float32, device=dev)
-    st = torch.empty(3, dtype=torch.float64, device=dev)
-
-    def step():
-        api.logpsi2d(theta, spins, cfg, Lx, Ly, out=lp)
-        api.local_energy2d(theta, spins, cfg, ham, out=el, stats=st)
-
-    step()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        step()
-    e1.record()
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / reps
     ctx = B.context()
-    B.psr_context_set_profiling(ctx, True)
-    api.local_energy2d(theta, spins, cfg, ham, out=el, stats=st)
-    conn_ms = B.psr_context_stage_ms(ctx)["fwd_connected"]
-    conn_patches = evaluated - n * Px * Py
-    achieved = conn_patches * flops_per_patch_2d(H) / (conn_ms / 1e3) / 1e12
-    return {"model": "2D patched minGRU (2x2 patches, vertical h_V coupling), FP32 CUDA cores",
+
+    def run(prec, m):
+        cfg = api.ModelConfig(N_LAYERS, H, True, prec)
+        spins = torch.from_numpy(rank_samples(0, m, Lx, Ly)).to(dev)
+        _, ent, _ = api.connected(spins, ham)
+        E = int(ent.shape[0])
+        r0 = (ent[:, 1].to(torch.int64) // Lx) // 2
+        evaluated = m * Px * Py + int(((Py - r0) * Px).sum().item())
+        lp = torch.empty(m, dtype=torch.float32, device=dev)
+        el = torch.empty(m, dtype=torch.float32, device=dev)
+        st = torch.empty(3, dtype=torch.float64, device=dev)
+
+        def step():
+            api.logpsi2d(theta, spins, cfg, Lx, Ly, out=lp)
+            api.local_energy2d(theta, spins, cfg, ham, out=el, stats=st)
+
+        step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            step()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        B.psr_context_set_profiling(ctx, True)
+        api.local_energy2d(theta, spins, cfg, ham, out=el, stats=st)
+        conn_ms = B.psr_context_stage_ms(ctx)["fwd_connected"]
+        B.psr_context_set_profiling(ctx, False)
+        conn_patches = evaluated - m * Px * Py
+        achieved = conn_patches * flops_per_patch_2d(H) / (conn_ms / 1e3) / 1e12
+        return {"samples": m, "connected": E, "value": (m + E) * N / (ms / 1e3), "unit": UNIT,
+                "ms_per_step": ms, "evaluated_patches_per_step": evaluated, "connected_launch_ms": conn_ms,
+                "achieved_tflops": achieved, "energy_per_site": float(st[0].item()) / N}
+
+    tc = run("fp16", n)
+    pk, src = measured_peaks()
+    peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+    f32 = run("fp32", min(n32, n))
+    return {"model": "2D patched minGRU (2x2 patches, vertical h_V coupling), tcgen05 tensor cores "
+                     "(FP16 operands, FP32 accumulation, gates, scan, softmax)",
             "lattice": f"{Lx}x{Ly} OBC", "hidden": H, "layers": N_LAYERS, "samples": n,
-            "connected": E,
-            "value": (n + E) * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "evaluated_patches_per_step": evaluated,
-            "roofline": {"kernel": "fwd2d_f32_kernel (connected configurations)", "bound": "alu",
-                         "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_SIMT_TFLOPS,
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+            "connected": tc["connected"], "value": tc["value"], "unit": UNIT, "ms_per_step": tc["ms_per_step"],
+            "evaluated_patches_per_step": tc["evaluated_patches_per_step"],
+            "energy_per_site": tc["energy_per_site"],
+            "roofline": {"kernel": "fwd2d_tc_kernel (connected configurations)", "bound": "tensor",
+                         "achieved": tc["achieved_tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": tc["achieved_tflops"] / peak,
+                         "peak_source": f"{src} dense BF16 tensor rate, sustained (FP16 runs at the same rate)",
                          "traffic": None, "flops_per_unit": flops_per_patch_2d(H),
-                         "launch_ms": conn_ms}}
+                         "launch_ms": tc["connected_launch_ms"]},
+            "fp32_cuda_cores": {"samples": f32["samples"], "value": f32["value"], "unit": UNIT,
+                                "ms_per_step": f32["ms_per_step"], "achieved_tflops": f32["achieved_tflops"],
+                                "frac_of_fp32_simt_peak": f32["achieved_tflops"] / FP32_SIMT_TFLOPS,
+                                "energy_per_site": f32["energy_per_site"]},
+            "speedup_vs_fp32": tc["value"] / f32["value"]}
 
 
 # FLOPs per evaluated site of the deep LRU (3 layers, hidden H): layer 0:
@@ -678,7 +697,7 @@ def vmc_leg(dev, L=10, n=1024, reps=3):
                     "energy_per_site": float(out["stats"][0].item()) / N}
     # the paper's 2D patched minGRU (hidden 128 here: its gradient kernel
     # keeps a row's tiles in shared memory up to that width)
-    cfg2 = api.ModelConfig(N_LAYERS, HIDDEN, True, "fp32")
+    cfg2 = api.ModelConfig(N_LAYERS, HIDDEN, True, "fp16")
     th2 = torch.from_numpy(inputs.glorot_params2d(N_LAYERS, HIDDEN, seed=0)).to(dev)
     u2 = torch.rand((n, N // 4), generator=g, device=dev)
     adam = api.Adam(th2.numel(), dev, lr=1e-3)
@@ -691,7 +710,8 @@ def vmc_leg(dev, L=10, n=1024, reps=3):
         out = api.vmc_step2d(th2, cfg2, ham, u2, adam, theta_out=th2)
     e1.record()
     e1.synchronize()
-    res["model2d"] = {"ms_per_step": e0.elapsed_time(e1) / reps, "precision": "FP32",
+    res["model2d"] = {"ms_per_step": e0.elapsed_time(e1) / reps,
+                      "precision": "FP16 tensor-core E_loc forward; FP32 sampling and gradient",
                       "energy_per_site": float(out["stats"][0].item()) / N}
     return res
 
@@ -705,15 +725,16 @@ def paper2d_leg(dev, sizes=(10, 20), n=200, reps=2, warmup=1):
     """One on-device VMC step of the 2D patched minGRU at the paper's 2D
     configuration (3 layers, d_h = 256, 2x2 patches, c4v symmetrisation,
     200 samples, Heisenberg OBC with zero magnetisation): exact sampling,
-    symmetrised E_loc (8 images), the gradient over the 8 images, Adam;
-    FP32 CUDA cores."""
+    symmetrised E_loc (8 images; the tensor-core forward, FP16 operands), the
+    gradient over the 8 images, Adam (sampling and gradient FP32 CUDA cores)."""
     import torch
 
     from paper_2605_13807_gb300 import api, binding as B, inputs
     H = 256
-    cfg = api.ModelConfig(N_LAYERS, H, True, "fp32")
+    cfg = api.ModelConfig(N_LAYERS, H, True, "fp16")
     res = {"model": "2D patched minGRU, c4v-symmetrised VMC step", "hidden": H, "layers": N_LAYERS,
-           "samples": n, "precision": "FP32", "paper_step_s_A100": {}}
+           "samples": n, "precision": "FP16 tensor-core E_loc forward; FP32 sampling, image weights, gradient",
+           "paper_step_s_A100": {}}
     g = torch.Generator(device=dev)
     g.manual_seed(7)
     for L in sizes:
