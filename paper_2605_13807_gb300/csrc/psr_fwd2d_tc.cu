@@ -85,10 +85,11 @@ struct Slot2 {
 
 struct Misc2 {
     uint64_t full[kMaxRing], empty[kMaxRing];
-    uint64_t e2m, m2e, hv, imgw, go[2];
+    uint64_t e2m[2], m2e[2], hv, imgw, go[2];  // e2m, m2e: per unit half
     uint32_t tmem_base;
     int abort_flag;
     int go_flag[2];
+    uint32_t hv_armed;                           // h_V image loads issued
     Slot2 slot[kMaxSlots];
 };
 
@@ -119,23 +120,27 @@ __device__ __forceinline__ int patch_value(const uint8_t *s, int Lx, int pi, int
     return v;
 }
 
-// Barrier of the epilogue threads (hardware named barrier 1).
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory"); }
+// Named barrier `id` of `n` threads.
+__device__ __forceinline__ void named_bar(uint32_t id, uint32_t n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
-// Barrier of the epilogue threads that also ORs a flag over them, so that
-// every epilogue thread takes the same exit.
-__device__ __forceinline__ bool epi_bar_or(bool v) {
+// Named barrier that also ORs a flag over its threads, so that they all
+// take the same exit.
+__device__ __forceinline__ bool named_bar_or(uint32_t id, uint32_t n, bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v), "r"(kEpi)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
         : "memory");
     return r != 0;
 }
+// all epilogue threads (barrier 1)
+__device__ __forceinline__ bool epi_bar_or(bool v) { return named_bar_or(1, kEpi, v); }
 
 // Bulk copy shared -> global (bulk-group completion).
 __device__ __forceinline__ void bulk_s2g(void *dst, uint32_t src, uint32_t bytes) {
@@ -214,8 +219,11 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
             mbar_init(smem_u32(&M.full[i]), 1);
             mbar_init(smem_u32(&M.empty[i]), 1);
         }
-        mbar_init(smem_u32(&M.e2m), 1);
-        mbar_init(smem_u32(&M.m2e), 1);
+        for (int g = 0; g < 2; ++g) {
+            mbar_init(smem_u32(&M.e2m[g]), 1);
+            mbar_init(smem_u32(&M.m2e[g]), 1);
+        }
+        M.hv_armed = 0;
         mbar_init(smem_u32(&M.hv), 1);
         mbar_init(smem_u32(&M.imgw), 1);
         mbar_init(smem_u32(&M.go[0]), 1);
@@ -240,8 +248,7 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
     if (tid == 0) mbar_arrive(smem_u32(&M.go[0]));  // row step 0 runs
     __syncthreads();
     const long long njobs = A.mode == 1 ? (long long)*A.n_jobs_dev : (long long)A.n_jobs;
-    const uint32_t e2m = smem_u32(&M.e2m), m2e = smem_u32(&M.m2e), hvb = smem_u32(&M.hv),
-                   imgw = smem_u32(&M.imgw);
+    const uint32_t hvb = smem_u32(&M.hv), imgw = smem_u32(&M.imgw);
 
     if (warp == NW) {
         // ------------------------------------------------ producer: weight stream
@@ -280,7 +287,9 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
         if (lane == 0 && !M.abort_flag) {
             // slices consumed; ring slot and the full barriers' phase; e2m and
             // h_V barrier phases
-            uint32_t q = 0, slot = 0, fph = 0, pe = 0, ph = 0;
+            uint32_t q = 0, slot = 0, fph = 0, pe0 = 0, pe1 = 0, ph = 0;
+            const uint32_t e2m0 = smem_u32(&M.e2m[0]), e2m1 = smem_u32(&M.e2m[1]), m2e0 = smem_u32(&M.m2e[0]),
+                           m2e1 = smem_u32(&M.m2e[1]);
             const uint32_t ha = smem_u32(ht), fb = smem_u32(&M.full[0]), ebar = smem_u32(&M.empty[0]);
             const uint64_t xd = kdesc(smem_u32(xt)), hd = kdesc(ha), rd = kdesc(smem_u32(ring));
             bool ok = true;
@@ -294,13 +303,19 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                     const uint32_t op = A.sched.op[i];
                     if (op & 0x00FF0000u) {
                         const uint32_t fl = (op >> 16) & 0xFFu;
-                        if (fl & kSchedCommit) {
+                        if (fl & (kSchedC0 | kSchedC1)) {
                             bulk_wait_read();  // the h tile may be overwritten once this commit lands
-                            mma_commit(m2e);
+                            if (fl & kSchedC0) mma_commit(m2e0);
+                            if (fl & kSchedC1) mma_commit(m2e1);
                         }
-                        if (fl & kSchedWaitX) {
-                            if (!wait_ab(e2m, pe, ab)) { ok = false; break; }
-                            pe ^= 1u;
+                        if (fl & kSchedW0) {
+                            if (!wait_ab(e2m0, pe0, ab)) { ok = false; break; }
+                            pe0 ^= 1u;
+                            tc_after();
+                        }
+                        if (fl & kSchedW1) {
+                            if (!wait_ab(e2m1, pe1, ab)) { ok = false; break; }
+                            pe1 ^= 1u;
                             tc_after();
                         }
                         if (fl & kSchedStoreH) {
@@ -342,7 +357,8 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                 // the row's image stores are complete before its successor reads them
                 bulk_wait_all();
                 mbar_arrive(imgw);
-                mma_commit(m2e);  // logits of the row
+                mma_commit(m2e0);  // logits of the row
+                if (NH == 2) mma_commit(m2e1);
             }
             bulk_wait_all();
             // the MMAs of the last slices complete before the CTA may exit
@@ -378,9 +394,12 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                                           (uint32_t)k * 128u) = v;
         };
         float *res = A.res + (size_t)blockIdx.x * 2 * kCols * H;
-        uint32_t pm = 0;        // m2e phase
-        uint32_t hv_armed = 0;  // h_V loads issued (thread 0)
+        uint32_t pm = 0;  // m2e phase of this thread's unit half
         bool ok = !M.abort_flag;
+        // this unit half's barriers, named barrier (2 + g) and leader thread
+        const uint32_t e2m = smem_u32(&M.e2m[g]), m2e = smem_u32(&M.m2e[g]);
+        const uint32_t hbar = 2u + (uint32_t)g, hcount = (uint32_t)(kEpi / NH);
+        const bool leader = tid == 128 * g;
 
         // thread 0: bulk copies of every active slot's h_V image of layer l
         auto issue_hv = [&](int l) {
@@ -396,7 +415,7 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                     bulk_g2s(smem_u32(ht + kc * 16384 + s * W * 128), src + (size_t)kc * W * 128, (uint32_t)W * 128u,
                              hvb);
             }
-            ++hv_armed;
+            ++M.hv_armed;
         };
         // One thread polls the MMA thread's barrier and a named barrier
         // releases the others (hundreds of pollers would contend for the
@@ -404,9 +423,9 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
         // epilogue's signal is one arrival after a named barrier.
         auto wait_m2e = [&]() {
             bool w = true;
-            if (tid == 0) w = ok && wait_ab(m2e, pm, ab);
-            const bool bad = epi_bar_or(!w || !ok);
-            if (bad && ok && tid == 0) {
+            if (leader) w = ok && wait_ab(m2e, pm, ab);
+            const bool bad = named_bar_or(hbar, hcount, !w || !ok);
+            if (bad && ok && leader) {
                 M.abort_flag = 1;
                 set_status(A.status, PSR_ETIMEOUT);
             }
@@ -417,8 +436,8 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
         auto arrive_e2m = [&]() {
             fence_proxy_async();  // this thread's tile writes, before the MMAs read them
             tc_before();
-            epi_bar();
-            if (tid == 0) mbar_arrive(e2m);
+            named_bar(hbar, hcount);
+            if (leader) mbar_arrive(e2m);
         };
         // the previous row's readout sums into the job's total (fixed order),
         // and the job's log psi after its last row (slot s, its warp)
@@ -610,7 +629,9 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
 
                 // ---- output map: x = GELU(y + residual)
                 wait_m2e();
-                if (tid == 0 && l + 1 < nL && ok) issue_hv(l + 1);
+                // the last half's output map is committed: every MMA reading
+                // the h tile is complete, the next layer's h_V may land in it
+                if (leader && g == NH - 1 && l + 1 < nL && ok) issue_hv(l + 1);
                 {
                     const bool use_res = (l >= 2);
                     const float *resr = res + (size_t)((l - 1) & 1) * kCols * H;
@@ -719,7 +740,7 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
             M.abort_flag = 1;
             set_status(A.status, PSR_ETIMEOUT);
         }
-        if (tid == 0 && hv_armed > 0 && !mbar_wait(hvb, (hv_armed - 1) & 1)) set_status(A.status, PSR_ETIMEOUT);
+        if (tid == 0 && M.hv_armed > 0 && !mbar_wait(hvb, (M.hv_armed - 1) & 1)) set_status(A.status, PSR_ETIMEOUT);
     }
     tc_before();
     __syncthreads();
@@ -796,7 +817,6 @@ Sched2 fwd2d_tc_schedule(int nL, int H) {
         sc.l[n] = (uint8_t)l;
         sc.g[n] = (uint8_t)g;
         sc.kc[n] = (uint8_t)kc;
-        if (ty == kMtD && g == 0 && kc == 0) fl |= kSchedStoreH;  // the scan's h is the next row's h_V
         sc.flags[n] = (uint8_t)fl;
         // accumulator column (z / y of half g: 128 g; c: 128 (NH + g); logits:
         // 128 NH), B tile, accumulate flag
@@ -813,29 +833,44 @@ Sched2 fwd2d_tc_schedule(int nL, int H) {
                    ((uint32_t)l << 24);
         ++n;
     };
+    const int HL = NH - 1;                                       // last unit half
+    const int kC[2] = {kSchedC0, kSchedC1}, kW[2] = {kSchedW0, kSchedW1};
+    const int wall = NH == 2 ? (kSchedW0 | kSchedW1) : kSchedW0;  // both halves' epilogues
     for (int l = 0; l < nL; ++l) {
         const int kin = l == 0 ? 1 : KC;
-        // projections: W_hv h_V first (it needs only the h_V image, so above
-        // layer 0 it runs while the epilogue computes the layer input), then
-        // W_z x and W_hx x once x is ready
+        // W_hv h_V needs only the h_V image of the layer: above layer 0 it
+        // runs while the epilogue computes the layer input (after the last
+        // half's output map of layer l - 1 has been committed)
         for (int g = 0; g < NH; ++g)
             for (int kc = 0; kc < KC; ++kc) {
                 int fl = 0;
-                if (g == 0 && kc == 0) fl = (l == 0) ? kSchedWaitHv : (kSchedCommit | kSchedWaitHv);
+                if (g == 0 && kc == 0) fl = kSchedWaitHv | (l > 0 ? kC[HL] : 0);
                 add(kMtWhv, l, g, kc, fl);
             }
+        // W_z x, W_hx x once x is complete; half g's projections are
+        // committed (its scan may start) before half g + 1's are issued
         for (int g = 0; g < NH; ++g) {
-            for (int kc = 0; kc < kin; ++kc) add(kMtWz, l, g, kc, (g == 0 && kc == 0) ? kSchedWaitX : 0);
+            for (int kc = 0; kc < kin; ++kc) {
+                int fl = 0;
+                if (kc == 0) fl = (g == 0) ? wall : kC[g - 1];
+                add(kMtWz, l, g, kc, fl);
+            }
             for (int kc = 0; kc < kin; ++kc) add(kMtWhx, l, g, kc, 0);
         }
-        // output map: D x + C h (the scan has written h)
-        for (int g = 0; g < NH; ++g) {
-            for (int kc = 0; kc < kin; ++kc)
-                add(kMtD, l, g, kc, (g == 0 && kc == 0) ? (kSchedCommit | kSchedWaitX) : 0);
-            for (int kc = 0; kc < KC; ++kc) add(kMtC, l, g, kc, 0);
-        }
+        // D x of half g once half g's scan has consumed z; C h once every
+        // half's scan has written h (then h is also stored as the next row's
+        // h_V); half g's output map committed before half g + 1's C
+        for (int g = 0; g < NH; ++g)
+            for (int kc = 0; kc < kin; ++kc) {
+                int fl = 0;
+                if (kc == 0) fl = (g == 0 ? kC[HL] : 0) | kW[g] | (g == HL ? kSchedStoreH : 0);
+                add(kMtD, l, g, kc, fl);
+            }
+        for (int g = 0; g < NH; ++g)
+            for (int kc = 0; kc < KC; ++kc) add(kMtC, l, g, kc, (kc == 0 && g > 0) ? kC[g - 1] : 0);
     }
-    for (int kc = 0; kc < KC; ++kc) add(kMtWo, 0, 0, kc, kc == 0 ? (kSchedCommit | kSchedWaitX) : 0);
+    // readout once both halves' layer input of the readout (x) is complete
+    for (int kc = 0; kc < KC; ++kc) add(kMtWo, 0, 0, kc, kc == 0 ? (kC[HL] | wall) : 0);
     sc.n = n;
     return sc;
 }

@@ -230,7 +230,10 @@ T2Layout t2_layout(int nL, int H);
 // order (launch_pack2d_tc writes them); Sched2 lists, per slice, the matrix,
 // layer, unit half, K chunk and the synchronisation before it.
 enum { kMtWz = 0, kMtWhx = 1, kMtWhv = 2, kMtC = 3, kMtD = 4, kMtWo = 5 };
-enum { kSchedCommit = 1, kSchedWaitX = 2, kSchedWaitHv = 4, kSchedStoreH = 8 };
+// Synchronisation before a slice, in this order: commit the MMAs so far to
+// unit half 0's / 1's epilogue, wait for half 0's / 1's epilogue, store the
+// h tile as the next row's h_V images, wait for the h_V image of the layer.
+enum { kSchedC0 = 1, kSchedC1 = 2, kSchedW0 = 4, kSchedW1 = 8, kSchedStoreH = 16, kSchedWaitHv = 32 };
 constexpr int kSchedMax = 320;
 // op[i], what the MMA thread needs of slice i: bits 0-9 accumulator column,
 // bit 10 B operand from the h tile (else x), bit 11 accumulate from the
