@@ -90,6 +90,8 @@ def parse():
                     help="sequences of the scan-only run (default: the workload's samples)")
     ap.add_argument("--scan-tile", default="",
                     help="units,chunk: fixed tile shape of the scan-only run (default: autotuned)")
+    ap.add_argument("--model2d-only", action="store_true",
+                    help="only the 2D patched-model leg (52x52, --samples-2d samples)")
     ap.add_argument("--paper2d-only", action="store_true",
                     help="only the 2D VMC step at the paper's 2D configuration")
     ap.add_argument("--paper2d-sizes", default="10,20",
@@ -765,6 +767,17 @@ def paper2d_sizes(args):
     return tuple(int(x) for x in args.paper2d_sizes.split(",") if x)
 
 
+def run_model2d_only(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    res = model2d_leg(52, 52, args.samples_2d, torch.device("cuda", 0))
+    print(json.dumps({"model2d": res}), flush=True)
+    return 0
+
+
 def run_paper2d_only(args):
     import torch
 
@@ -1088,6 +1101,8 @@ def main():
         return run_scan_only(args)
     if args.paper2d_only:
         return run_paper2d_only(args)
+    if args.model2d_only:
+        return run_model2d_only(args)
     if args.mixed_only:
         return run_mixed_only(args)
     if args.depth_only:
