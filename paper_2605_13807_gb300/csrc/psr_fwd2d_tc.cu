@@ -163,14 +163,6 @@ template <bool F16>
 __device__ __forceinline__ uint32_t op_pack(float lo, float hi) {
     return (uint32_t)op_bits<F16>(lo) | ((uint32_t)op_bits<F16>(hi) << 16);
 }
-// The same two roundings in one packed conversion (lo in the low half).
-template <bool F16>
-__device__ __forceinline__ uint32_t op_pack_fast(float lo, float hi) {
-    uint32_t r;
-    if (F16) asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
-}
 
 // 16 columns (two 8-column TMEM loads) of this thread's lane, columns beyond
 // `nc8` chunks left untouched.
@@ -353,10 +345,8 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                     const uint32_t d = tmem + (op & 0x3FFu);
                     mma_ss<idesc2<F16>()>(d, ad, bd, (op >> 11) & 1u);
                     mma_ss<idesc2<F16>()>(d, ad + kstep(1), bd + kstep(1), 1u);
-                    if (!(op & (1u << 14))) {
-                        mma_ss<idesc2<F16>()>(d, ad + kstep(2), bd + kstep(2), 1u);
-                        mma_ss<idesc2<F16>()>(d, ad + kstep(3), bd + kstep(3), 1u);
-                    }
+                    mma_ss<idesc2<F16>()>(d, ad + kstep(2), bd + kstep(2), 1u);
+                    mma_ss<idesc2<F16>()>(d, ad + kstep(3), bd + kstep(3), 1u);
                     mma_commit(ebar + 8 * slot);
                     if (++slot == (uint32_t)R) {
                         slot = 0;
@@ -613,38 +603,22 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                                 bv[k] = b2.x;
                                 bv[k + 1] = b2.y;
                             }
-                            // two sites per step, one packed conversion for both
                             if (!odd) {
 #pragma unroll
-                                for (int k = 0; k < 16; k += 2) {
+                                for (int k = 0; k < 16; ++k) {
                                     if (c0 + k < Px) {
-                                        const float h0 = fmaf(av[k], h, bv[k]);
-                                        const bool v1 = c0 + k + 1 < Px;
-                                        h = v1 ? fmaf(av[k + 1], h0, bv[k + 1]) : h0;
-                                        const uint32_t pr = op_pack_fast<F16>(h0, h);
-                                        tile_st(ht, n0 + c0, k, (uint16_t)(pr & 0xFFFFu));
-                                        if (keep_res) resw[(size_t)(n0 + c0 + k) * H + j] = h0;
-                                        if (v1) {
-                                            tile_st(ht, n0 + c0, k + 1, (uint16_t)(pr >> 16));
-                                            if (keep_res) resw[(size_t)(n0 + c0 + k + 1) * H + j] = h;
-                                        }
+                                        h = fmaf(av[k], h, bv[k]);
+                                        tile_st(ht, n0 + c0, k, op_bits<F16>(h));
+                                        if (keep_res) resw[(size_t)(n0 + c0 + k) * H + j] = h;
                                     }
                                 }
                             } else {
 #pragma unroll
-                                for (int k = 15; k >= 1; k -= 2) {
-                                    // sites k, then k - 1 (path order runs down the columns)
-                                    const bool v0 = c0 + k < Px;
-                                    if (c0 + k - 1 < Px) {
-                                        const float h0 = v0 ? fmaf(av[k], h, bv[k]) : h;
-                                        h = fmaf(av[k - 1], h0, bv[k - 1]);
-                                        const uint32_t pr = op_pack_fast<F16>(h0, h);
-                                        if (v0) {
-                                            tile_st(ht, n0 + c0, k, (uint16_t)(pr & 0xFFFFu));
-                                            if (keep_res) resw[(size_t)(n0 + c0 + k) * H + j] = h0;
-                                        }
-                                        tile_st(ht, n0 + c0, k - 1, (uint16_t)(pr >> 16));
-                                        if (keep_res) resw[(size_t)(n0 + c0 + k - 1) * H + j] = h;
+                                for (int k = 15; k >= 0; --k) {
+                                    if (c0 + k < Px) {
+                                        h = fmaf(av[k], h, bv[k]);
+                                        tile_st(ht, n0 + c0, k, op_bits<F16>(h));
+                                        if (keep_res) resw[(size_t)(n0 + c0 + k) * H + j] = h;
                                     }
                                 }
                             }
@@ -680,9 +654,9 @@ __global__ void __launch_bounds__(kEpi + 64, 1) fwd2d_tc_kernel(const __grid_con
                                 if (c0 + k < Px) {
                                     const float2 x = gelu_bf16out2(make_float2(__uint_as_float(yr[k]) + rv[k],
                                                                                __uint_as_float(yr[k + 1]) + rv[k + 1]));
-                                    const uint32_t pr = op_pack_fast<F16>(x.x, x.y);
-                                    tile_st(xt, n0 + c0, k, (uint16_t)(pr & 0xFFFFu));
-                                    if (c0 + k + 1 < Px) tile_st(xt, n0 + c0, k + 1, (uint16_t)(pr >> 16));
+                                    tile_st(xt, n0 + c0, k, op_bits<F16>(x.x));
+                                    if (c0 + k + 1 < Px)
+                                        tile_st(xt, n0 + c0, k + 1, op_bits<F16>(x.y));
                                 }
                             }
                         }
@@ -855,11 +829,8 @@ Sched2 fwd2d_tc_schedule(int nL, int H) {
             case kMtC: dcol = 128u * g; from_h = 1; acc = 1; break;
             default: dcol = 128u * NH; acc = kc > 0; break;
         }
-        // layer 0's W_z, W_hx, D act on the 32-entry one-hot pair: the upper
-        // half of their 64-wide K chunk is zero and its two K steps are skipped
-        const uint32_t half_k = (l == 0 && (ty == kMtWz || ty == kMtWhx || ty == kMtD)) ? 1u : 0u;
-        sc.op[n] = dcol | (from_h << 10) | (acc << 11) | ((uint32_t)kc << 12) | (half_k << 14) |
-                   ((uint32_t)fl << 16) | ((uint32_t)l << 24);
+        sc.op[n] = dcol | (from_h << 10) | (acc << 11) | ((uint32_t)kc << 12) | ((uint32_t)fl << 16) |
+                   ((uint32_t)l << 24);
         ++n;
     };
     const int HL = NH - 1;                                       // last unit half

@@ -237,8 +237,7 @@ enum { kSchedC0 = 1, kSchedC1 = 2, kSchedW0 = 4, kSchedW1 = 8, kSchedStoreH = 16
 constexpr int kSchedMax = 320;
 // op[i], what the MMA thread needs of slice i: bits 0-9 accumulator column,
 // bit 10 B operand from the h tile (else x), bit 11 accumulate from the
-// first K step, bits 12-13 K chunk, bit 14 only the first 32 inputs are
-// non-zero, bits 16-23 flags, bits 24-27 layer.
+// first K step, bits 12-13 K chunk, bits 16-23 flags, bits 24-27 layer.
 struct Sched2 {
     int n;
     uint8_t type[kSchedMax], l[kSchedMax], g[kSchedMax], kc[kSchedMax], flags[kSchedMax];
