@@ -452,6 +452,9 @@ def model2d_leg(Lx, Ly, n, dev, reps=2, H=256, n32=8):
                 "achieved_tflops": achieved, "energy_per_site": float(st[0].item()) / N}
 
     tc = run("fp16", n)
+    bpu = profiled_traffic_per_unit("fwd2d_tc_connected_52x52.md", "psr_fwd2d_tc.cu",
+                                    "dram bytes per evaluated patch")
+    conn_patches = tc["evaluated_patches_per_step"] - n * (Lx // 2) * (Ly // 2)
     pk, src = measured_peaks()
     peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
     f32 = run("fp32", min(n32, n))
@@ -465,7 +468,10 @@ def model2d_leg(Lx, Ly, n, dev, reps=2, H=256, n32=8):
                          "achieved": tc["achieved_tflops"], "peak": peak, "unit": "TFLOP/s",
                          "frac": tc["achieved_tflops"] / peak,
                          "peak_source": f"{src} dense BF16 tensor rate, sustained (FP16 runs at the same rate)",
-                         "traffic": None, "flops_per_unit": flops_per_patch_2d(H),
+                         "traffic": (bpu * conn_patches) if bpu is not None else None,
+                         "traffic_source": "DRAM bytes per evaluated patch of the committed ncu "
+                                           "summary (4-sample capture) x the launch's evaluated patches",
+                         "flops_per_unit": flops_per_patch_2d(H),
                          "launch_ms": tc["connected_launch_ms"]},
             "fp32_cuda_cores": {"samples": f32["samples"], "value": f32["value"], "unit": UNIT,
                                 "ms_per_step": f32["ms_per_step"], "achieved_tflops": f32["achieved_tflops"],
