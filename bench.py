@@ -92,6 +92,10 @@ def parse():
                     help="units,chunk: fixed tile shape of the scan-only run (default: autotuned)")
     ap.add_argument("--model2d-only", action="store_true",
                     help="only the 2D patched-model leg (52x52, --samples-2d samples)")
+    ap.add_argument("--lru-only", action="store_true",
+                    help="only the deep 1D LRU leg (TFIM chain N = 256, --samples-lru samples)")
+    ap.add_argument("--samples-lru", type=int, default=1024,
+                    help="samples of the deep 1D LRU leg")
     ap.add_argument("--paper2d-only", action="store_true",
                     help="only the 2D VMC step at the paper's 2D configuration")
     ap.add_argument("--paper2d-sizes", default="10,20",
@@ -487,93 +491,116 @@ def lru_flops_per_site(H):
     return 8 * H * H + 2 * 12 * H * H
 
 
-def lru_leg(dev, N=256, H=64, n=1024, reps=3):
+def lru_leg(dev, N=256, H=64, n=1024, reps=3, n32=None):
     """The paper's deep 1D LRU on the 1D TFIM (Table IV configuration: 3
     layers, d = d_h = 64, N = 256 OBC, 1024 samples, h = 1): log psi + E_loc
-    over every site flip, FP32 CUDA cores; then the gradient's reverse pass
-    and one full VMC step (sampling, E_loc, gradient, Adam) on the same
-    configuration."""
+    over every site flip on the tensor cores (FP16 operands, FP32
+    accumulation, complex scan, GLU and readout) and on the FP32 CUDA cores;
+    then the gradient's reverse pass and one full VMC step (sampling, E_loc,
+    gradient, Adam) at both precisions (sampling and gradient run in FP32 in
+    both)."""
     import torch
 
     from paper_2605_13807_gb300 import api, binding as B, inputs
     ham = B.make_hamiltonian("tfim", N, 1, False, True, 1.0, 1.0)
-    cfg = api.ModelConfig(N_LAYERS, H, False, "fp32")
     theta = torch.from_numpy(inputs.lru_params(N_LAYERS, H, seed=0)).to(dev)
     spins = torch.from_numpy(inputs.random_spins(2000, n, N)).to(dev)
     lp = torch.empty(n, dtype=torch.float32, device=dev)
     el = torch.empty(n, dtype=torch.float32, device=dev)
     st = torch.empty(3, dtype=torch.float64, device=dev)
     E = n * N
-
-    def step():
-        api.logpsi_lru(theta, spins, cfg, out=lp)
-        api.local_energy_lru(theta, spins, cfg, ham, out=el, stats=st)
-
-    step()
-    torch.cuda.synchronize()
+    ctx = B.context()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        step()
-    e1.record()
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    ctx = B.context()
-    B.psr_context_set_profiling(ctx, True)
-    api.local_energy_lru(theta, spins, cfg, ham, out=el, stats=st)
-    conn_ms = B.psr_context_stage_ms(ctx)["fwd_connected"]
     # sites evaluated by the connected forward: each flip at p resumes at its chunk
     p = torch.arange(N, device=dev)
     conn_sites = n * int((N - (p // 32) * 32).sum().item())
-    achieved = conn_sites * lru_flops_per_site(H) / (conn_ms / 1e3) / 1e12
-    # reverse-mode gradient (dout-weighted sum) and one full VMC step
-    w = torch.full((n,), 1.0 / n, dtype=torch.float32, device=dev)
-    api.grad_lru(theta, spins, cfg, dout=w)
-    bwd_ms = B.psr_context_stage_ms(ctx)["bwd"]
-    B.psr_context_set_profiling(ctx, False)
-    g = torch.Generator(device=dev)
-    g.manual_seed(6)
-    u = torch.rand((n, N), generator=g, device=dev)
-    adam = api.Adam(theta.numel(), dev, lr=1e-3)
-    th = theta.clone()  # updated in place by every step
-    api.vmc_step_lru(th, cfg, ham, u, adam, theta_out=th)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        out = api.vmc_step_lru(th, cfg, ham, u, adam, theta_out=th)
-    e1.record()
-    e1.synchronize()
-    vmc_ms = e0.elapsed_time(e1) / reps
-    # the same step at shorter chains, beside the paper's Table I step times
-    # (1x H100, same model and sample count; context, not a target)
-    by_n = {}
-    for Nc in (32, 64, 128):
-        ham_c = B.make_hamiltonian("tfim", Nc, 1, False, True, 1.0, 1.0)
-        u_c = torch.rand((n, Nc), generator=g, device=dev)
-        th_c = theta.clone()
-        adam_c = api.Adam(theta.numel(), dev, lr=1e-3)
-        api.vmc_step_lru(th_c, cfg, ham_c, u_c, adam_c, theta_out=th_c)
+
+    def timed(fn):
+        fn()
         torch.cuda.synchronize()
         e0.record()
         for _ in range(reps):
-            api.vmc_step_lru(th_c, cfg, ham_c, u_c, adam_c, theta_out=th_c)
+            fn()
         e1.record()
         e1.synchronize()
-        by_n[str(Nc)] = e0.elapsed_time(e1) / reps
-    by_n[str(N)] = vmc_ms
-    return {"model": "deep 1D LRU (complex diagonal recurrence + GLU), FP32 CUDA cores",
-            "grad_bwd_ms": bwd_ms, "vmc_step_ms": vmc_ms, "vmc_step_ms_by_N": by_n,
+        return e0.elapsed_time(e1) / reps
+
+    def run(prec):
+        cfg = api.ModelConfig(N_LAYERS, H, False, prec)
+
+        def step():
+            api.logpsi_lru(theta, spins, cfg, out=lp)
+            api.local_energy_lru(theta, spins, cfg, ham, out=el, stats=st)
+
+        ms = timed(step)
+        B.psr_context_set_profiling(ctx, True)
+        api.local_energy_lru(theta, spins, cfg, ham, out=el, stats=st)
+        conn_ms = B.psr_context_stage_ms(ctx)["fwd_connected"]
+        B.psr_context_set_profiling(ctx, False)
+        achieved = conn_sites * lru_flops_per_site(H) / (conn_ms / 1e3) / 1e12
+        g = torch.Generator(device=dev)
+        g.manual_seed(6)
+        u = torch.rand((n, N), generator=g, device=dev)
+        adam = api.Adam(theta.numel(), dev, lr=1e-3)
+        th = theta.clone()  # updated in place by every step
+        out = {}
+
+        def vmc():
+            out.update(api.vmc_step_lru(th, cfg, ham, u, adam, theta_out=th))
+
+        vmc_ms = timed(vmc)
+        # the same step at shorter chains, beside the paper's Table I step
+        # times (1x H100, same model and sample count; context, not a target)
+        by_n = {}
+        for Nc in (32, 64, 128):
+            ham_c = B.make_hamiltonian("tfim", Nc, 1, False, True, 1.0, 1.0)
+            u_c = torch.rand((n, Nc), generator=g, device=dev)
+            th_c = theta.clone()
+            adam_c = api.Adam(theta.numel(), dev, lr=1e-3)
+            by_n[str(Nc)] = timed(lambda: api.vmc_step_lru(th_c, cfg, ham_c, u_c, adam_c, theta_out=th_c))
+        by_n[str(N)] = vmc_ms
+        return {"value": (n + E) * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                "connected_launch_ms": conn_ms, "achieved_tflops": achieved,
+                "energy_per_site": float(st[0].item()) / N, "vmc_step_ms": vmc_ms,
+                "vmc_step_ms_by_N": by_n, "vmc_energy_per_site": float(out["stats"][0].item()) / N}
+
+    tc = run("fp16")
+    f32 = run("fp32")
+    # reverse-mode gradient (dout-weighted sum), FP32
+    w = torch.full((n,), 1.0 / n, dtype=torch.float32, device=dev)
+    B.psr_context_set_profiling(ctx, True)
+    api.grad_lru(theta, spins, api.ModelConfig(N_LAYERS, H, False, "fp32"), dout=w)
+    bwd_ms = B.psr_context_stage_ms(ctx)["bwd"]
+    B.psr_context_set_profiling(ctx, False)
+    bpu = profiled_traffic_per_unit("lru_tc_connected_tfim256.md", "psr_lru_tc.cu",
+                                    "dram bytes per evaluated site")
+    pk, src = measured_peaks()
+    peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+    return {"model": "deep 1D LRU (complex diagonal recurrence + GLU), tcgen05 tensor cores "
+                     "(FP16 operands, FP32 accumulation, complex scan, GLU, readout)",
+            "grad_bwd_ms": bwd_ms, "vmc_step_ms": tc["vmc_step_ms"], "vmc_step_ms_by_N": tc["vmc_step_ms_by_N"],
             "paper_step_ms_H100_by_N": {"32": 28, "64": 71, "128": 260, "256": 900},
-            "vmc_energy_per_site": float(out["stats"][0].item()) / N,
+            "vmc_energy_per_site": tc["vmc_energy_per_site"],
             "workload": f"tfim_chain_{N}_obc_{n}_samples", "hidden": H, "connected": E,
-            "value": (n + E) * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "roofline": {"kernel": "lru_f32_kernel (connected configurations)", "bound": "alu",
-                         "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_SIMT_TFLOPS,
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                         "traffic": None, "flops_per_unit": lru_flops_per_site(H),
-                         "launch_ms": conn_ms}}
+            "value": tc["value"], "unit": UNIT, "ms_per_step": tc["ms_per_step"],
+            "energy_per_site": tc["energy_per_site"],
+            "roofline": {"kernel": "lru_tc_kernel (connected configurations)", "bound": "tensor",
+                         "achieved": tc["achieved_tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": tc["achieved_tflops"] / peak,
+                         "peak_source": f"{src} dense BF16 tensor rate, sustained (FP16 runs at the same rate)",
+                         "traffic": (bpu * conn_sites) if bpu is not None else None,
+                         "traffic_source": "DRAM bytes per evaluated site of the committed ncu summary "
+                                           "x the launch's evaluated sites",
+                         "flops_per_unit": lru_flops_per_site(H), "launch_ms": tc["connected_launch_ms"]},
+            "fp32_cuda_cores": {"value": f32["value"], "unit": UNIT, "ms_per_step": f32["ms_per_step"],
+                                "connected_launch_ms": f32["connected_launch_ms"],
+                                "achieved_tflops": f32["achieved_tflops"],
+                                "frac_of_fp32_simt_peak": f32["achieved_tflops"] / FP32_SIMT_TFLOPS,
+                                "energy_per_site": f32["energy_per_site"],
+                                "vmc_step_ms": f32["vmc_step_ms"], "vmc_step_ms_by_N": f32["vmc_step_ms_by_N"],
+                                "vmc_energy_per_site": f32["vmc_energy_per_site"]},
+            "speedup_vs_fp32": tc["value"] / f32["value"]}
 
 
 # The mixed persistent batch: 2D Heisenberg 16x16, 24x24, 32x32 (open, zero
@@ -781,6 +808,16 @@ def run_model2d_only(args):
     torch.cuda.set_device(0)
     res = model2d_leg(52, 52, args.samples_2d, torch.device("cuda", 0))
     print(json.dumps({"model2d": res}), flush=True)
+    return 0
+
+
+def run_lru_only(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"lru": lru_leg(torch.device("cuda", 0), n=args.samples_lru)}), flush=True)
     return 0
 
 
@@ -1051,7 +1088,7 @@ def run_mine(args):
     if not args.no_2d and rank == 0:
         line["model2d"] = model2d_leg(Lx, Ly, min(args.samples_2d, n), dev)
     if not args.no_lru and rank == 0:
-        line["lru"] = lru_leg(dev)
+        line["lru"] = lru_leg(dev, n=args.samples_lru)
     if not args.no_mixed and rank == 0:
         line["mixed_batch"] = mixed_leg(dev)
     if not args.no_vmc and rank == 0:
@@ -1109,6 +1146,8 @@ def main():
         return run_paper2d_only(args)
     if args.model2d_only:
         return run_model2d_only(args)
+    if args.lru_only:
+        return run_lru_only(args)
     if args.mixed_only:
         return run_mixed_only(args)
     if args.depth_only:

@@ -621,7 +621,8 @@ int check_params_lru(const psr_params *p, int64_t n, int32_t L) {
     if (p->precision != PSR_FP32 && p->precision != PSR_BF16 && p->precision != PSR_FP16) return PSR_EINVAL;
     if (n < 1 || L < 1 || n > (int64_t)1 << 31) return PSR_EINVAL;
     if (p->u1_mask && (L % 2)) return PSR_EINVAL;
-    if (p->precision != PSR_FP32) return PSR_EUNSUPPORTED;
+    // FP16 / BF16: the forward evaluations (log psi, E_loc) on the tensor cores
+    if (p->precision != PSR_FP32 && !lru_tc_supported(p->n_layers, p->hidden)) return PSR_EUNSUPPORTED;
     return PSR_OK;
 }
 
@@ -637,10 +638,13 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
     const bool eloc = ham != nullptr;
     const int nb = eloc ? bond_count(ham->Lx, ham->Ly, ham->pbc) : 0;
     const int64_t cap = eloc ? n * max_entries_per_sample(ham) : 0;
+    const bool tc = params->precision != PSR_FP32, f16 = params->precision == PSR_FP16;
+    if (tc && cap >= ((int64_t)1 << 31)) return PSR_EUNSUPPORTED;  // 32-bit job indices
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
                d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
     float *theta_ws = nullptr, *out_ws = nullptr, *pk = nullptr, *lpsi = nullptr, *logp = nullptr,
-          *carries = nullptr, *delta = nullptr;
+          *carries = nullptr, *delta = nullptr, *xres = nullptr;
+    uint8_t *wimg = nullptr;
     double *stats_ws = nullptr;
     uint8_t *s_ws = nullptr;
     uint64_t *bits = nullptr;
@@ -654,6 +658,10 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
         pk = c.get<float>(f.total);
         bits = c.get<uint64_t>((size_t)n * W);
         counters = c.get<unsigned long long>(2);
+        if (tc) {
+            wimg = c.get<uint8_t>(lru_tc_weight_bytes(nL));
+            xres = c.get<float>(lru_tc_xres_floats(ctx->num_sms));
+        }
         if (eloc) {
             b.bonds = c.get<int32_t>(2 * (size_t)nb + 2);
             b.counts = c.get<int64_t>(n);
@@ -684,9 +692,28 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
     {
         StageScope sc(ctx, PSR_STAGE_PACK);
         PSR_TRY(launch_pack_theta_lru(theta, f, pk, st));
+        if (tc) PSR_TRY(launch_pack_lru_tc(pk, f, f16, wimg, st));
         PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));
         PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
     }
+    // the FP32 kernel, or the tensor-core one (one job per slot, 4 slots per CTA)
+    auto run = [&](const FwdJobs &jb) -> cudaError_t {
+        if (!tc) return launch_lru_f32(jb, pk, f, ctx->num_sms, st);
+        LruTcArgs a{};
+        a.mode = jb.mode;
+        a.nL = nL;
+        a.f16 = f16 ? 1 : 0;
+        a.g = jb.g[0];
+        a.f = f;
+        a.pk = pk;
+        a.wimg = wimg;
+        a.xres = xres;
+        a.job_counter = jb.job_counter;
+        a.status = jb.status;
+        int64_t grid = (jb.g[0].n_jobs + 3) / 4;
+        if (grid > ctx->num_sms) grid = ctx->num_sms;
+        return launch_lru_tc(a, (int)(grid < 1 ? 1 : grid), st);
+    };
     HamDev hd{};
     if (eloc) {
         StageScope sc(ctx, PSR_STAGE_GENERATOR);
@@ -707,7 +734,7 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
     js.status = ctx->status;
     {
         StageScope sc(ctx, PSR_STAGE_FWD_SAMPLES);
-        PSR_TRY(launch_lru_f32(js, pk, f, ctx->num_sms, st));
+        PSR_TRY(run(js));
     }
     if (eloc) {
         FwdJobs jc = js;
@@ -723,7 +750,7 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
         jc.job_counter = counters + 1;
         if (cap > 0) {
             StageScope sc(ctx, PSR_STAGE_FWD_CONNECTED);
-            PSR_TRY(launch_lru_f32(jc, pk, f, ctx->num_sms, st));
+            PSR_TRY(run(jc));
         }
         StageScope sc(ctx, PSR_STAGE_GATHER);
         PSR_TRY(launch_eloc_gather(b.offsets, delta, b.diag, hd.coeff, n, o, st));

@@ -1,0 +1,673 @@
+// Forward of the paper's deep 1D LRU ansatz (Sec. II.B Eq. lru, Sec. II.G 1D
+// residual, Sec. III.B: each layer an LRU followed by a single-layer GLU) on
+// the tensor cores, hidden d = d_h = 64 (the paper's Table IV width): FP16
+// (or BF16) operands, FP32 accumulation in tensor memory, FP32 complex scan,
+// GLU, residual and readout.
+//
+// The model is the one psr_lru.cu evaluates in FP32:
+//   h_t = lambda h_{t-1} + e^gamma (B u_t),   y_t = Re(C h_t) + D u_t,
+//   x_t = (W_a y_t + b_a) sigmoid(W_g y_t + b_g) + [l >= 1] u_t,
+// with the two-logit readout.  Its dense products become three MMAs per
+// layer, each with an M = 128 weight operand (A, K-major, 128-byte swizzle)
+// and the sites as B (N = 128 columns):
+//   [B_re; B_im] u   rows 2j, 2j + 1 = unit j's real / imaginary part
+//   [C_re, -C_im] [h_re; h_im]   rows j < 64 (rows 64.. zero), K = 128
+//   [W_a; W_g] y     rows 2j, 2j + 1 = unit j's W_a / W_g row
+// and the readout w_d x with w_d in row 32 q of every lane quarter q.  Layer
+// 0's input is one-hot (Sec. II.F), so its B u and D u are lookups.
+//
+// Work layout, as in the 2D tensor-core forward: one persistent CTA per SM
+// with 128 site columns in 4 slots of one 32-site chunk each; slot s is
+// warpgroup s of the epilogue, each slot holds one job (a sample, or a
+// connected configuration resumed at the chunk of its first flipped site
+// from the sample's FP32 complex chunk carries) and advances one chunk per
+// step, taking the next job from a counter when its sequence ends.  The
+// weights (12 slices of 16 KB per chunk step at 3 layers) stream from L2
+// through a ring of slices (producer thread); one thread issues the MMAs.
+// The complex carries of a slot stay in the registers of its warpgroup.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "psr_bf16_math.cuh"
+#include "psr_device.cuh"
+#include "psr_internal.cuh"
+#include "psr_tc.cuh"
+
+namespace psr {
+
+namespace {
+
+using namespace tc;
+using namespace bf16m;
+
+constexpr int kH = 64;              // hidden width of this kernel
+constexpr int kCh = 32;             // sites per chunk (slot width)
+constexpr int kSl = 4;              // slots (one per epilogue warpgroup)
+constexpr int kColsL = kCh * kSl;   // MMA N
+constexpr uint32_t kSliceL = 16384; // 128 rows x 64 inputs, 16-bit
+constexpr int kMaxRingL = 12;
+constexpr int kEpiL = 512;          // epilogue threads
+
+// tensor-memory regions (columns): B u, y, GLU, readout
+enum { kTmP = 0, kTmY = 128, kTmG = 256, kTmO = 384 };
+// B operand tiles (byte offsets inside the tile block): x (K = 64), h (K =
+// 128: h_re then h_im), y (K = 64)
+enum { kTileX = 0, kTileH = 16384, kTileY = 3 * 16384 };
+constexpr uint32_t kTilesBytes = 4 * 16384;
+
+template <bool F16>
+constexpr uint32_t idesc_l() {
+    return (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) | (0u << 15) | (0u << 16) |
+           ((uint32_t)(kColsL >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ uint64_t kdesc_l(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(1024u >> 4) << 16) |
+           ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+struct SlotL {
+    int job;              // -1: needs a job, -2: none left
+    int sample, p, q;     // configuration (p, q: flipped sites or -1)
+    int c, c0, nch;       // current chunk, first chunk, chunks of the sequence
+    int n_up;             // up spins before the current chunk
+    int first;            // 1 in the job's first chunk (carries to load)
+    float acc;            // sum of log P (mode 0) or of its differences (mode 1)
+};
+
+struct MiscL {
+    uint64_t full[kMaxRingL], empty[kMaxRingL];
+    uint64_t e2m, m2e, go[2];
+    uint32_t tmem_base;
+    int abort_flag;
+    int go_flag[2];
+    SlotL slot[kSl];
+};
+
+__device__ __forceinline__ bool wait_abl(uint32_t bar, uint32_t parity, const volatile int *ab) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u && (*ab || globaltimer() - t0 > kWaitNs)) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool bar_or_l(uint32_t id, uint32_t n, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+template <bool F16>
+__device__ __forceinline__ uint16_t op16(float x) {
+    if (F16) return __half_as_ushort(__float2half_rn(fminf(fmaxf(x, -65504.0f), 65504.0f)));
+    const __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<const uint16_t *>(&b);
+}
+
+// op word of a slice: bits 0-8 accumulator column, bits 9-10 B tile (0 x,
+// 1 h, 2 y), bit 11 K chunk, bit 12 accumulate from the first K step, bit
+// 13 commit the MMAs so far to the epilogue first, bit 14 wait for the
+// epilogue first.
+enum { kLopC = 1u << 13, kLopW = 1u << 14 };
+
+template <bool F16>
+__global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_constant__ LruTcArgs A) {
+    constexpr int NW = kEpiL / 32;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    MiscL &M = *reinterpret_cast<MiscL *>(smem_raw);
+    uint8_t *tiles = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + sizeof(MiscL) + 1023) & ~uintptr_t(1023));
+    uint8_t *ring = tiles + kTilesBytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = A.R, nL = A.nL;
+    const FwdGroup &G = A.g;
+    const int N = G.N;
+    const volatile int *ab = &M.abort_flag;
+    const float *pk = A.pk;
+    const LruLayout &f = A.f;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&M.tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < R; ++i) {
+            mbar_init(smem_u32(&M.full[i]), 1);
+            mbar_init(smem_u32(&M.empty[i]), 1);
+        }
+        mbar_init(smem_u32(&M.e2m), 1);
+        mbar_init(smem_u32(&M.m2e), 1);
+        mbar_init(smem_u32(&M.go[0]), 1);
+        mbar_init(smem_u32(&M.go[1]), 1);
+        M.abort_flag = 0;
+        M.go_flag[0] = 1;
+        M.go_flag[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < kSl) {
+        M.slot[tid].job = -1;
+        M.slot[tid].acc = 0.0f;
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = M.tmem_base;
+    if (tmem != 0) {
+        if (tid == 0) set_status(A.status, PSR_EDEVICE);
+        M.abort_flag = 1;
+    }
+    if (tid == 0) mbar_arrive(smem_u32(&M.go[0]));
+    __syncthreads();
+    const long long njobs = A.mode == 1 ? (long long)*G.n_jobs_dev : (long long)G.n_jobs;
+    const uint32_t e2m = smem_u32(&M.e2m), m2e = smem_u32(&M.m2e);
+
+    if (warp == NW) {
+        // ------------------------------------------------ producer: weight stream
+        if (lane == 0 && !M.abort_flag) {
+            uint32_t q = 0, slot = 0, round = 0;
+            const uint32_t fb = smem_u32(&M.full[0]), ebar = smem_u32(&M.empty[0]), rb = smem_u32(ring);
+            for (uint32_t row = 0;; ++row) {
+                if (!wait_abl(smem_u32(&M.go[row & 1]), (row >> 1) & 1, ab)) break;
+                if (!*(volatile int *)&M.go_flag[row & 1]) break;
+                bool ok = true;
+                const uint8_t *src = A.wimg;
+                for (int i = 0; i < A.n_slices; ++i, ++q, src += kSliceL) {
+                    if (round > 0 && !wait_abl(ebar + 8 * slot, (round - 1) & 1, ab)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_tx(fb + 8 * slot, kSliceL);
+                    bulk_g2s(rb + slot * kSliceL, src, kSliceL, fb + 8 * slot);
+                    if (++slot == (uint32_t)R) {
+                        slot = 0;
+                        ++round;
+                    }
+                }
+                if (!ok) break;
+            }
+            const uint32_t last = q < (uint32_t)R ? q : (uint32_t)R;
+            for (uint32_t t = 0; t < last; ++t) {
+                const uint32_t qq = q - 1 - t;
+                if (!mbar_wait(smem_u32(&M.full[qq % R]), (qq / R) & 1)) set_status(A.status, PSR_ETIMEOUT);
+            }
+            if (*ab) set_status(A.status, PSR_ETIMEOUT);
+        }
+    } else if (warp == NW + 1) {
+        // ------------------------------------------------ MMA issue
+        if (lane == 0 && !M.abort_flag) {
+            uint32_t q = 0, slot = 0, fph = 0, pe = 0;
+            const uint32_t fb = smem_u32(&M.full[0]), ebar = smem_u32(&M.empty[0]);
+            const uint64_t tdesc0 = kdesc_l(smem_u32(tiles)), rd = kdesc_l(smem_u32(ring));
+            bool ok = true;
+            for (uint32_t row = 0; ok; ++row) {
+                if (!wait_abl(smem_u32(&M.go[row & 1]), (row >> 1) & 1, ab)) {
+                    ok = false;
+                    break;
+                }
+                if (!*(volatile int *)&M.go_flag[row & 1]) break;
+                for (int i = 0; i < A.n_slices; ++i, ++q) {
+                    const uint32_t op = A.op[i];
+                    if (op & kLopC) mma_commit(m2e);
+                    if (op & kLopW) {
+                        if (!wait_abl(e2m, pe, ab)) { ok = false; break; }
+                        pe ^= 1u;
+                        tc_after();
+                    }
+                    if (!wait_abl(fb + 8 * slot, fph, ab)) { ok = false; break; }
+                    const uint32_t tile = (op >> 9) & 3u;
+                    const uint32_t boff = (tile == 0 ? (uint32_t)kTileX : tile == 1 ? (uint32_t)kTileH : (uint32_t)kTileY) +
+                                          ((op >> 11) & 1u) * 16384u;
+                    const uint64_t ad = rd + (uint64_t)(slot * (kSliceL >> 4)), bd = tdesc0 + (uint64_t)(boff >> 4);
+                    const uint32_t d = tmem + (op & 0x1FFu);
+                    mma_ss<idesc_l<F16>()>(d, ad, bd, (op >> 12) & 1u);
+                    mma_ss<idesc_l<F16>()>(d, ad + 2, bd + 2, 1u);
+                    mma_ss<idesc_l<F16>()>(d, ad + 4, bd + 4, 1u);
+                    mma_ss<idesc_l<F16>()>(d, ad + 6, bd + 6, 1u);
+                    mma_commit(ebar + 8 * slot);
+                    if (++slot == (uint32_t)R) {
+                        slot = 0;
+                        fph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(m2e);  // readout of the chunk step
+            }
+            const uint32_t last = q < (uint32_t)R ? q : (uint32_t)R;
+            for (uint32_t t = 0; t < last; ++t) {
+                const uint32_t qq = q - 1 - t;
+                if (!mbar_wait(smem_u32(&M.empty[qq % R]), (qq / R) & 1)) set_status(A.status, PSR_ETIMEOUT);
+            }
+            if (!ok) {
+                M.abort_flag = 1;
+                set_status(A.status, PSR_ETIMEOUT);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        // warpgroup s = slot s (columns 32 s ..); warp w reads TMEM lanes
+        // 32 (w & 3) + lane = row r of every accumulator
+        const int s = warp >> 2, q4 = warp & 3, r = 32 * q4 + lane;
+        const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
+        const uint32_t tP = tmem + lane_off + kTmP + kCh * s, tY = tmem + lane_off + kTmY + kCh * s,
+                       tG = tmem + lane_off + kTmG + kCh * s, tO = tmem + lane_off + kTmO + kCh * s;
+        const int j = r >> 1;        // unit of rows 2j, 2j + 1 (B u, GLU)
+        const bool odd_r = r & 1;
+        // element k of tile row n (K-major, 128-byte swizzle), K chunk kc
+        auto tile_st = [&](uint32_t tile, int kc, int n, int k, uint16_t v) {
+            *reinterpret_cast<uint16_t *>(tiles + tile + kc * 16384 + n * 128 +
+                                          ((((k >> 3) ^ (n & 7))) << 4) + (k & 7) * 2) = v;
+        };
+        float *xres = A.xres + (size_t)blockIdx.x * kColsL * kH;  // FP32 layer input [column][unit]
+        float cre[kMaxLayers], cim[kMaxLayers];  // this slot's complex carries of unit j
+#pragma unroll
+        for (int l = 0; l < kMaxLayers; ++l) cre[l] = cim[l] = 0.0f;
+        uint32_t pm = 0;
+        bool ok = !M.abort_flag;
+
+        auto wait_m2e = [&]() {
+            bool w = true;
+            if (tid == 0) w = ok && wait_abl(m2e, pm, ab);
+            const bool bad = bar_or_l(1, kEpiL, !w || !ok);
+            if (bad && ok && tid == 0) {
+                M.abort_flag = 1;
+                set_status(A.status, PSR_ETIMEOUT);
+            }
+            ok = ok && !bad;
+            pm ^= 1u;
+            tc_after();
+        };
+        auto arrive_e2m = [&]() {
+            fence_proxy_async();
+            tc_before();
+            asm volatile("bar.sync 1, %0;" ::"r"(kEpiL) : "memory");
+            if (tid == 0) mbar_arrive(e2m);
+        };
+        // the 32 sites' 32-bit spins of the slot's current chunk: cur (bit t =
+        // s_{t0+t}) and prevbits (bit t = s_{t0+t-1}, 0 at the first site)
+        auto chunk_spins = [&](const SlotL &st, uint32_t &cur, uint32_t &prevbits) {
+            const uint64_t *row = G.bits + (int64_t)st.sample * G.W;
+            uint32_t prev;
+            chunk_bits32(row, st.c * kCh, st.p, st.q, cur, prev);
+            const int nvalid = min(kCh, N - st.c * kCh);
+            if (nvalid < 32) cur &= (1u << nvalid) - 1u;
+            prevbits = (cur << 1) | prev;
+        };
+        // carry of layer l entering the slot's chunk (stored as the chunk's
+        // checkpoint in mode 0)
+        auto carry_in = [&](int l, const SlotL &st, float &zr, float &zi) {
+            zr = zi = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kMaxLayers; ++k)
+                if (k == l) { zr = cre[k]; zi = cim[k]; }
+            if (st.first) {
+                zr = zi = 0.0f;
+                if (A.mode == 1 && st.c0 > 0) {
+                    const float *cin = G.carries_in + (((int64_t)st.sample * st.nch + st.c0) * nL + l) * 2 * kH;
+                    zr = cin[j];
+                    zi = cin[kH + j];
+                }
+            }
+            if (G.carries_out && !odd_r) {
+                float *co = G.carries_out + (((int64_t)st.sample * st.nch + st.c) * nL + l) * 2 * kH;
+                co[j] = zr;
+                co[kH + j] = zi;
+            }
+        };
+        auto carry_out = [&](int l, float zr, float zi) {
+#pragma unroll
+            for (int k = 0; k < kMaxLayers; ++k)
+                if (k == l) { cre[k] = zr; cim[k] = zi; }
+        };
+        // h_t = lambda h_{t-1} + e^gamma P_t over 16 sites (c0 .. c0 + 15) of
+        // the slot; this thread's part of h (real: row 2j, imaginary: row
+        // 2j + 1) to the h tile
+        auto scan16 = [&](int c0, const float (&pr)[16], const float (&pi)[16], float lr, float li, float g, float &zr,
+                          float &zi) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const float nr = fmaf(lr, zr, fmaf(-li, zi, g * pr[t]));
+                const float ni = fmaf(lr, zi, fmaf(li, zr, g * pi[t]));
+                zr = nr;
+                zi = ni;
+                tile_st(kTileH, odd_r ? 1 : 0, kCh * s + c0 + t, j, op16<F16>(odd_r ? zi : zr));
+            }
+        };
+
+        for (uint32_t row_it = 0; ok; ++row_it) {
+            // ---- slot update (warp 4 s: slot s)
+            if (q4 == 0 && lane == 0) {
+                SlotL &st = M.slot[s];
+                if (row_it > 0 && st.job >= 0 && st.c + 1 >= st.nch) {
+                    G.out[st.job] = 0.5f * st.acc;  // the job's last chunk is done
+                }
+                if (st.job != -2) {
+                    if (st.job == -1 || st.c + 1 >= st.nch) {
+                        const unsigned long long nj = atomicAdd(A.job_counter, 1ull);
+                        if ((long long)nj >= njobs) {
+                            st.job = -2;
+                        } else {
+                            int sample = (int)nj, p = -1, q = -1, c0 = 0;
+                            if (A.mode == 1) {
+                                const int32_t *e = G.entries + 3 * nj;
+                                sample = e[0];
+                                p = e[1];
+                                q = e[2];
+                                c0 = p / kCh;
+                            }
+                            st.job = (int)nj;
+                            st.sample = sample;
+                            st.p = p;
+                            st.q = q;
+                            st.c0 = c0;
+                            st.c = c0;
+                            st.nch = (N + kCh - 1) / kCh;
+                            st.first = 1;
+                            st.acc = 0.0f;
+                            st.n_up = G.u1 ? count_up_before(G.bits + (int64_t)sample * G.W, c0 * kCh) : 0;
+                        }
+                    } else {
+                        uint32_t cur, pb;
+                        chunk_spins(st, cur, pb);
+                        st.n_up += __popc(cur);
+                        st.c += 1;
+                        st.first = 0;
+                    }
+                }
+            }
+            if (bar_or_l(1, kEpiL, !ok || *ab)) {
+                ok = false;
+                break;
+            }
+            if (tid == 0) {
+                bool more = false;
+                for (int k = 0; k < kSl; ++k)
+                    if (M.slot[k].job >= 0 && M.slot[k].c + 1 < M.slot[k].nch) more = true;
+                if (!more) more = (long long)atomicAdd(A.job_counter, 0ull) < njobs;
+                M.go_flag[(row_it + 1) & 1] = more ? 1 : 0;
+                mbar_arrive(smem_u32(&M.go[(row_it + 1) & 1]));
+            }
+            const SlotL &st = M.slot[s];
+            const bool act = st.job >= 0;
+            uint32_t cur = 0, pb = 0;
+            if (act) chunk_spins(st, cur, pb);
+            const int t0 = act ? st.c * kCh : 0;
+
+            // ---- layer 0: B u and D u are lookups of the one-hot input
+            if (act) {
+                const float br0 = pk[f.BreT[0] + j], br1 = pk[f.BreT[0] + kH + j];
+                const float bi0 = pk[f.BimT[0] + j], bi1 = pk[f.BimT[0] + kH + j];
+                const float lr = pk[f.lre[0] + j], li = pk[f.lim[0] + j], g = pk[f.gam[0] + j];
+                float zr, zi;
+                carry_in(0, st, zr, zi);
+#pragma unroll 1
+                for (int hh = 0; hh < 2; ++hh) {
+                    float pr[16], pi[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const int tc = 16 * hh + t;
+                        const bool first = (t0 + tc == 0), sb = (pb >> tc) & 1u;
+                        pr[t] = first ? 0.0f : (sb ? br1 : br0);
+                        pi[t] = first ? 0.0f : (sb ? bi1 : bi0);
+                    }
+                    scan16(16 * hh, pr, pi, lr, li, g, zr, zi);
+                }
+                carry_out(0, zr, zi);
+            }
+            arrive_e2m();
+
+            for (int l = 0; l < nL; ++l) {
+                if (l > 0) {
+                    // ---- B u from the MMA: rows 2j (re), 2j + 1 (im)
+                    wait_m2e();
+                    if (act) {
+                        const float lr = pk[f.lre[l] + j], li = pk[f.lim[l] + j], g = pk[f.gam[l] + j];
+                        float zr, zi;
+                        carry_in(l, st, zr, zi);
+#pragma unroll 1
+                        for (int hh = 0; hh < 2; ++hh) {
+                            uint32_t v[16];
+                            tmem_ld16(tP + 16 * hh, v);
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
+                            float pr[16], pi[16];
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                const float mine = __uint_as_float(v[t]);
+                                const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                                pr[t] = odd_r ? other : mine;
+                                pi[t] = odd_r ? mine : other;
+                            }
+                            scan16(16 * hh, pr, pi, lr, li, g, zr, zi);
+                        }
+                        carry_out(l, zr, zi);
+                    }
+                    arrive_e2m();
+                }
+                // ---- y = Re(C h) + D u (rows j < 64)
+                wait_m2e();
+                if (act) {
+                    uint32_t v[32];
+                    tmem_ld32(tY, v);
+                    tmem_wait_ld32(v);
+                    if (r < kH) {
+                        const int u = r;
+                        if (l == 0) {
+                            const float d0 = pk[f.D[0] + u], d1 = pk[f.D[0] + kH + u];
+#pragma unroll
+                            for (int t = 0; t < kCh; ++t) {
+                                const bool first = (t0 + t == 0), sb = (pb >> t) & 1u;
+                                const float y = __uint_as_float(v[t]) + (first ? 0.0f : (sb ? d1 : d0));
+                                tile_st(kTileY, 0, kCh * s + t, u, op16<F16>(y));
+                            }
+                        } else {
+                            const float du = pk[f.D[l] + u];
+#pragma unroll
+                            for (int t = 0; t < kCh; ++t) {
+                                const float y = fmaf(du, xres[(size_t)(kCh * s + t) * kH + u], __uint_as_float(v[t]));
+                                tile_st(kTileY, 0, kCh * s + t, u, op16<F16>(y));
+                            }
+                        }
+                    }
+                }
+                arrive_e2m();
+                // ---- GLU: rows 2j (W_a y), 2j + 1 (W_g y); even sites by the
+                // thread of row 2j, odd sites by the thread of row 2j + 1
+                wait_m2e();
+                {
+                    const float ba = pk[f.ba[l] + j], bg = pk[f.bg[l] + j];
+#pragma unroll 1
+                    for (int hh = 0; hh < 2 && act; ++hh) {
+                        uint32_t v[16];
+                        tmem_ld16(tG + 16 * hh, v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            const float mine = __uint_as_float(v[t]);
+                            const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                            // even sites by the thread of row 2j, odd sites by row 2j + 1
+                            if ((t & 1) != (int)odd_r) continue;
+                            const float a = (odd_r ? other : mine) + ba, gg = (odd_r ? mine : other) + bg;
+                            const int tc = 16 * hh + t;
+                            float *xr = xres + (size_t)(kCh * s + tc) * kH + j;
+                            const float x = a * (0.5f + 0.5f * tanh_approx(0.5f * gg)) + (l >= 1 ? *xr : 0.0f);
+                            *xr = x;
+                            tile_st(kTileX, 0, kCh * s + tc, j, op16<F16>(x));
+                        }
+                    }
+                }
+                arrive_e2m();
+            }
+
+            // ---- readout: d_t = w_d x_t + b_d in row 0 of the first lane
+            // quarter; site t by lane t
+            wait_m2e();
+            if (q4 == 0 && act) {
+                uint32_t v[32];
+                tmem_ld32(tO, v);
+                tmem_wait_ld32(v);
+                {
+                    float dv = 0.0f;
+#pragma unroll
+                    for (int t = 0; t < kCh; ++t) {
+                        const float x = __shfl_sync(0xffffffffu, __uint_as_float(v[t]), 0);
+                        if (t == lane) dv = x;
+                    }
+                    const int t = lane, tt = t0 + t;
+                    float lp = 0.0f;
+                    if (tt < N) {
+                        const float d = dv + pk[f.bd];
+                        const int sv = (cur >> t) & 1u;
+                        const int nu = st.n_up + __popc(cur & ((1u << t) - 1u));
+                        lp = site_logp_fast(d, sv, u1_forced(G.u1, N, tt, nu));
+                        if (A.mode == 0 && G.logp_out) G.logp_out[(int64_t)st.sample * N + tt] = lp;
+                        if (A.mode == 1) lp -= G.logp_ref[(int64_t)st.sample * N + tt];
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+                    if (lane == 0) M.slot[s].acc += lp;
+                }
+            }
+            tc_before();
+            if (bar_or_l(1, kEpiL, !ok)) {
+                ok = false;
+                break;
+            }
+            if (!*(volatile int *)&M.go_flag[(row_it + 1) & 1]) {
+                if (q4 == 0 && lane == 0) {
+                    SlotL &sf = M.slot[s];
+                    if (sf.job >= 0) G.out[sf.job] = 0.5f * sf.acc;
+                }
+                break;
+            }
+        }
+        if (!ok) {
+            M.abort_flag = 1;
+            set_status(A.status, PSR_ETIMEOUT);
+        }
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// Weight slices (128 rows x 64 inputs) in the MMA thread's order, from the
+// packed FP32 matrices (transposed: M^T[k][j]).
+struct LruKinds {
+    int n;
+    uint8_t kind[kLruSchedMax];
+};
+
+template <bool F16>
+__global__ void pack_lru_tc_kernel(const float *__restrict__ pk, LruLayout f, LruKinds kd,
+                                   uint8_t *__restrict__ wimg) {
+    constexpr int H = kH;
+    const int64_t total = (int64_t)kd.n * 1024;
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(id >> 10), m = (int)((id >> 3) & 127), c = (int)(id & 7);
+        const int code = kd.kind[i], ty = code >> 4, l = code & 15;
+        uint32_t w[4];
+#pragma unroll
+        for (int e2 = 0; e2 < 4; ++e2) {
+            float v2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 8 * c + 2 * e2 + h;
+                float v = 0.0f;
+                switch (ty) {
+                    case 0: v = pk[((m & 1) ? f.BimT[l] : f.BreT[l]) + (int64_t)k * H + (m >> 1)]; break;  // B
+                    case 1: if (m < H) v = pk[f.CreT[l] + (int64_t)k * H + m]; break;                      // C_re
+                    case 2: if (m < H) v = -pk[f.CimT[l] + (int64_t)k * H + m]; break;                     // -C_im
+                    case 3: v = pk[((m & 1) ? f.WgT[l] : f.WaT[l]) + (int64_t)k * H + (m >> 1)]; break;   // W_a, W_g
+                    default: if ((m & 31) == 0) v = pk[f.wd + k]; break;                                  // w_d
+                }
+                v2[h] = v;
+            }
+            w[e2] = (uint32_t)op16<F16>(v2[0]) | ((uint32_t)op16<F16>(v2[1]) << 16);
+        }
+        *reinterpret_cast<uint4 *>(wimg + (size_t)i * kSliceL + m * 128 + ((c ^ (m & 7)) << 4)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+}  // namespace
+
+// Slices of one chunk step and the MMA thread's op words (see kLopC/kLopW);
+// kind[i] = matrix type << 4 | layer.
+int lru_tc_schedule(int nL, uint8_t *kind, uint32_t *op) {
+    int n = 0;
+    auto add = [&](int ty, int l, uint32_t dcol, uint32_t tile, uint32_t kc, uint32_t acc, uint32_t fl) {
+        kind[n] = (uint8_t)(ty << 4 | l);
+        op[n] = dcol | (tile << 9) | (kc << 11) | (acc << 12) | fl;
+        ++n;
+    };
+    for (int l = 0; l < nL; ++l) {
+        if (l > 0)  // B u (after the previous GLU; x ready)
+            add(0, l, kTmP, 0, 0, 0, kLopC | kLopW);
+        // Re(C h): wait for the scan (after committing B u above layer 0)
+        add(1, l, kTmY, 1, 0, 0, (l > 0 ? kLopC : 0) | kLopW);
+        add(2, l, kTmY, 1, 1, 1, 0);
+        // GLU: y ready
+        add(3, l, kTmG, 2, 0, 0, kLopC | kLopW);
+    }
+    add(4, 0, kTmO, 0, 0, 0, kLopC | kLopW);  // readout: x of the last layer ready
+    return n;
+}
+
+bool lru_tc_supported(int nL, int H) { return H == kH && nL >= 1 && nL <= kMaxLayers && 4 * nL <= kLruSchedMax; }
+
+size_t lru_tc_weight_bytes(int nL) { return (size_t)(4 * nL) * kSliceL; }
+
+size_t lru_tc_xres_floats(int grid) { return (size_t)grid * kColsL * kH; }
+
+cudaError_t launch_pack_lru_tc(const float *pk, const LruLayout &f, bool f16, uint8_t *wimg, cudaStream_t stream) {
+    LruKinds kd{};
+    uint32_t op[kLruSchedMax];
+    kd.n = lru_tc_schedule(f.nL, kd.kind, op);
+    const int blocks = (int)(((int64_t)kd.n * 1024 + 255) / 256);
+    if (f16) pack_lru_tc_kernel<true><<<blocks, 256, 0, stream>>>(pk, f, kd, wimg);
+    else pack_lru_tc_kernel<false><<<blocks, 256, 0, stream>>>(pk, f, kd, wimg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lru_tc(LruTcArgs a, int grid, cudaStream_t stream) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    uint8_t kind[kLruSchedMax];
+    a.n_slices = lru_tc_schedule(a.nL, kind, a.op);
+    const size_t base = sizeof(MiscL) + 1024 + kTilesBytes;
+    if ((size_t)optin < base + 2 * kSliceL) return cudaErrorInvalidConfiguration;
+    int R = (int)(((size_t)optin - base) / kSliceL);
+    a.R = R > kMaxRingL ? kMaxRingL : R;
+    const size_t smem = base + (size_t)a.R * kSliceL;
+    if (grid < 1) grid = 1;
+    if (a.f16) {
+        e = cudaFuncSetAttribute(lru_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        lru_tc_kernel<true><<<grid, kEpiL + 64, smem, stream>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(lru_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        lru_tc_kernel<false><<<grid, kEpiL + 64, smem, stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace psr

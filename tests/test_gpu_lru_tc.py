@@ -1,0 +1,129 @@
+"""GPU deep 1D LRU on the tensor cores (precisions "fp16" and "bf16", hidden
+64: psr_lru_logpsi and psr_lru_local_energy through lru_tc_kernel, 16-bit
+operands with FP32 accumulation, complex scan, GLU and readout) against the
+FP64 oracle of the same model (Sec. II.B Eq. lru, Sec. II.G, Sec. III.B).
+
+Tolerances, the stated bounds of the 16-bit path:
+  log psi : |d| <= 2e-2 + 2e-5 |log psi|
+  E_loc   : |d| <= 1e-3 (|diag| + |E_loc - diag|)
+FP16 operands meet both.  BF16 operands are held to twice the log psi bound
+and three times the E_loc bound (2.1e-3 measured on the 256-site TFIM
+chain): regression bounds, as for the 2D model's BF16 path.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2605_13807_gb300 import api, binding as B, inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    yield
+
+
+H = 64
+
+
+def _theta(oracle_mod, nL, seed, kind):
+    P = oracle_mod.param_count_lru(nL, H)
+    assert P == api.param_count_lru(nL, H)
+    if kind == "ring":
+        th = inputs.lru_params(nL, H, seed=seed)
+    else:  # every entry random (biases, nu, theta and gamma included)
+        th = ((2.0 * inputs.uniform(seed, (P,)) - 1.0) / np.sqrt(H)).astype(np.float32)
+    return th
+
+
+def _spins(seed, n, N, u1):
+    return inputs.zero_magnetisation_spins(seed, n, N) if u1 else inputs.random_spins(seed, n, N)
+
+
+@pytest.mark.parametrize("N,nL,u1,kind", [(16, 3, False, "random"), (100, 3, True, "ring"),
+                                          (256, 3, False, "ring"), (37, 2, False, "random"),
+                                          (70, 1, True, "random"), (34, 3, True, "ring")])
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_logpsi_lru_tc_matches_oracle(oracle_mod, N, nL, u1, kind, prec):
+    theta = _theta(oracle_mod, nL, 700 + N + nL, kind)
+    s = _spins(701, 40, N, u1)
+    cfg = api.ModelConfig(nL, H, u1, prec)
+    got = api.logpsi_lru(torch.from_numpy(theta).cuda(), torch.from_numpy(s).cuda(), cfg)
+    api.sync()
+    ref = oracle_mod.logpsi_lru(theta.astype(np.float64), nL, H, s, u1=u1)
+    got = got.cpu().numpy().astype(np.float64)
+    scale = 1.0 if prec == "fp16" else 2.0
+    assert np.all(np.isfinite(got) == np.isfinite(ref))
+    fin = np.isfinite(ref)
+    err = np.abs(got[fin] - ref[fin])
+    assert np.all(err <= scale * (2e-2 + 2e-5 * np.abs(ref[fin]))), (err.max(), np.abs(ref).max())
+
+
+@pytest.mark.parametrize("kind,N,pbc,u1,hf", [(1, 16, False, False, 1.0), (1, 16, True, False, 1.0),
+                                              (0, 20, False, True, 0.0), (1, 256, False, False, 1.0),
+                                              (0, 66, True, True, 0.0)])
+@pytest.mark.parametrize("prec,tol", [("fp16", 1e-3), ("bf16", 3e-3)])
+def test_local_energy_lru_tc_matches_oracle(oracle_mod, kind, N, pbc, u1, hf, prec, tol):
+    nL = 3
+    theta = _theta(oracle_mod, nL, 710 + N, "ring")
+    n = 3 if N >= 256 else 12
+    s = _spins(711, n, N, u1)
+    ham = B.make_hamiltonian(kind, N, 1, pbc, True, 1.0, hf)
+    cfg = api.ModelConfig(nL, H, u1, prec)
+    e, st = api.local_energy_lru(torch.from_numpy(theta).cuda(), torch.from_numpy(s).cuda(), cfg, ham)
+    api.sync()
+    ref = oracle_mod.local_energy_lru(theta.astype(np.float64), nL, H, s, kind, N, 1, pbc=pbc,
+                                      marshall=True, J=1.0, h=hf, u1=u1)
+    _, _, diag = oracle_mod.connected(kind, N, 1, pbc, s)
+    scale = np.abs(diag) + np.abs(ref - diag)
+    err = np.abs(e.cpu().numpy() - ref)
+    assert np.all(err <= tol * scale), (err / scale).max()
+    m, _, _ = oracle_mod.stats(e.cpu().numpy().astype(np.float64))
+    assert abs(st[0].item() - m) <= 1e-9 * max(1.0, abs(m))
+
+
+def test_lru_tc_many_jobs_and_determinism():
+    """More sequences than the CTAs hold slots (4 per CTA), so slots take new
+    jobs mid-launch; within the 16-bit bound of the (oracle-checked) FP32
+    path, and two runs bitwise equal."""
+    N, nL, n = 96, 3, 3000
+    theta = torch.from_numpy(inputs.lru_params(nL, H, seed=4)).cuda()
+    s = torch.from_numpy(_spins(721, n, N, True)).cuda()
+    a = api.logpsi_lru(theta, s, api.ModelConfig(nL, H, True, "fp16"))
+    b = api.logpsi_lru(theta, s, api.ModelConfig(nL, H, True, "fp16"))
+    r = api.logpsi_lru(theta, s, api.ModelConfig(nL, H, True, "fp32"))
+    api.sync()
+    assert torch.equal(a, b)
+    err = (a.double() - r.double()).abs()
+    assert torch.all(err <= 2e-2 + 2e-5 * r.double().abs())
+
+
+def test_lru_vmc_step_fp16_local_energies(oracle_mod):
+    """The LRU VMC step at precision fp16: samples and gradient from the FP32
+    path, local energies from the tensor-core forward, within the E_loc
+    bound of the oracle."""
+    N, nL, n = 32, 3, 64
+    theta = inputs.lru_params(nL, H, seed=5)
+    ham = B.make_hamiltonian("tfim", N, 1, False, True, 1.0, 1.0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(9)
+    u = torch.rand((n, N), generator=g, device="cuda")
+    th = torch.from_numpy(theta).cuda()
+    outs = {}
+    for prec in ("fp32", "fp16"):
+        adam = api.Adam(th.numel(), th.device, lr=1e-3)
+        outs[prec] = api.vmc_step_lru(th, api.ModelConfig(nL, H, False, prec), ham, u, adam)
+    api.sync()
+    assert torch.equal(outs["fp32"]["spins"], outs["fp16"]["spins"])
+    s = outs["fp16"]["spins"].cpu().numpy()
+    ref = oracle_mod.local_energy_lru(theta.astype(np.float64), nL, H, s, 1, N, 1, pbc=False, marshall=True,
+                                      J=1.0, h=1.0, u1=False)
+    _, _, diag = oracle_mod.connected(1, N, 1, False, s)
+    e = outs["fp16"]["eloc"].cpu().numpy()
+    assert np.all(np.abs(e - ref) <= 1e-3 * (np.abs(diag) + np.abs(ref - diag)))
