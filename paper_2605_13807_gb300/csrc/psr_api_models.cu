@@ -643,7 +643,7 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
     const bool d_theta = is_device_ptr(params->theta), d_s = is_device_ptr(samples),
                d_out = is_device_ptr(out), d_stats = stats ? is_device_ptr(stats) : true;
     float *theta_ws = nullptr, *out_ws = nullptr, *pk = nullptr, *lpsi = nullptr, *logp = nullptr,
-          *carries = nullptr, *delta = nullptr, *xres = nullptr;
+          *carries = nullptr, *delta = nullptr;
     uint8_t *wimg = nullptr;
     double *stats_ws = nullptr;
     uint8_t *s_ws = nullptr;
@@ -658,10 +658,7 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
         pk = c.get<float>(f.total);
         bits = c.get<uint64_t>((size_t)n * W);
         counters = c.get<unsigned long long>(2);
-        if (tc) {
-            wimg = c.get<uint8_t>(lru_tc_weight_bytes(nL));
-            xres = c.get<float>(lru_tc_xres_floats(ctx->num_sms));
-        }
+        if (tc) wimg = c.get<uint8_t>(lru_tc_weight_bytes(nL));
         if (eloc) {
             b.bonds = c.get<int32_t>(2 * (size_t)nb + 2);
             b.counts = c.get<int64_t>(n);
@@ -707,7 +704,6 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
         a.f = f;
         a.pk = pk;
         a.wimg = wimg;
-        a.xres = xres;
         a.job_counter = jb.job_counter;
         a.status = jb.status;
         int64_t grid = (jb.g[0].n_jobs + 3) / 4;

@@ -316,9 +316,9 @@ int64_t param_count_lru(int nL, int H);
 constexpr int kChunkLru = 32;
 // Deep LRU on the tensor cores (psr_lru_tc.cu), hidden 64: FP16 or BF16
 // operands, FP32 accumulation, complex scan, GLU and readout.  Jobs and the
-// FP32 complex chunk carries as for launch_lru_f32 (group 0 of g only); xres:
-// lru_tc_xres_floats(grid) of scratch; wimg: lru_tc_weight_bytes(nL), written
-// by launch_pack_lru_tc from the packed FP32 matrices.
+// FP32 complex chunk carries as for launch_lru_f32 (group 0 of g only); wimg:
+// lru_tc_weight_bytes(nL), written by launch_pack_lru_tc from the packed FP32
+// matrices.
 constexpr int kLruSchedMax = 36;
 struct LruTcArgs {
     int mode, nL, f16;
@@ -326,7 +326,6 @@ struct LruTcArgs {
     LruLayout f;
     const float *pk;
     const uint8_t *wimg;
-    float *xres;
     unsigned long long *job_counter;
     int *status;
     // set by launch_lru_tc
@@ -335,7 +334,6 @@ struct LruTcArgs {
 };
 bool lru_tc_supported(int nL, int H);
 size_t lru_tc_weight_bytes(int nL);
-size_t lru_tc_xres_floats(int grid);
 cudaError_t launch_pack_lru_tc(const float *pk, const LruLayout &f, bool f16, uint8_t *wimg, cudaStream_t stream);
 cudaError_t launch_lru_tc(LruTcArgs a, int grid, cudaStream_t stream);
 cudaError_t launch_pack_theta_lru(const float *theta, const LruLayout &f, float *packed,

@@ -11,10 +11,14 @@
 // layer, each with an M = 128 weight operand (A, K-major, 128-byte swizzle)
 // and the sites as B (N = 128 columns):
 //   [B_re; B_im] u   rows 2j, 2j + 1 = unit j's real / imaginary part
-//   [C_re, -C_im] [h_re; h_im]   rows j < 64 (rows 64.. zero), K = 128
+//   [C_re, -C_im] [h_re; h_im]   rows 2j, 2j + 1 both unit j's, K = 128
 //   [W_a; W_g] y     rows 2j, 2j + 1 = unit j's W_a / W_g row
 // and the readout w_d x with w_d in row 32 q of every lane quarter q.  Layer
-// 0's input is one-hot (Sec. II.F), so its B u and D u are lookups.
+// 0's input is one-hot (Sec. II.F), so its B u and D u are lookups.  The
+// thread pair of rows 2j, 2j + 1 shares unit j: both run its complex scan
+// over the chunk, and the y and GLU epilogues split the sites by parity
+// (even sites: row 2j), so the FP32 layer input u_t that D u and the residual
+// need stays in the registers of the thread that made it.
 //
 // Work layout, as in the 2D tensor-core forward: one persistent CTA per SM
 // with 128 site columns in 4 slots of one 32-site chunk each; slot s is
@@ -48,6 +52,7 @@ constexpr int kColsL = kCh * kSl;   // MMA N
 constexpr uint32_t kSliceL = 16384; // 128 rows x 64 inputs, 16-bit
 constexpr int kMaxRingL = 12;
 constexpr int kEpiL = 512;          // epilogue threads
+constexpr int kMaxLL = 4;           // layers (complex carries held in registers)
 
 // tensor-memory regions (columns): B u, y, GLU, readout
 enum { kTmP = 0, kTmY = 128, kTmG = 256, kTmO = 384 };
@@ -55,6 +60,10 @@ enum { kTmP = 0, kTmY = 128, kTmG = 256, kTmO = 384 };
 // 128: h_re then h_im), y (K = 64)
 enum { kTileX = 0, kTileH = 16384, kTileY = 3 * 16384 };
 constexpr uint32_t kTilesBytes = 4 * 16384;
+// per-unit constants of each layer in shared memory, [layer][kind][unit]:
+// lambda (re, im), e^gamma, D (one-hot rows 0, 1 at layer 0; the diagonal
+// above), b_a, b_g, and layer 0's one-hot B u (re, im for inputs 0, 1)
+enum { kCLre, kCLim, kCGam, kCD0, kCD1, kCBa, kCBg, kCBr0, kCBr1, kCBi0, kCBi1, kCst };
 
 template <bool F16>
 constexpr uint32_t idesc_l() {
@@ -74,6 +83,7 @@ struct SlotL {
     int n_up;             // up spins before the current chunk
     int first;            // 1 in the job's first chunk (carries to load)
     float acc;            // sum of log P (mode 0) or of its differences (mode 1)
+    uint32_t cur, pb;     // spins of the current chunk and of the sites before (chunk_bits32)
 };
 
 struct MiscL {
@@ -129,6 +139,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
     uint8_t *tiles = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + sizeof(MiscL) + 1023) & ~uintptr_t(1023));
     uint8_t *ring = tiles + kTilesBytes;
+    float *cst = reinterpret_cast<float *>(ring + (size_t)A.R * kSliceL);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int R = A.R, nL = A.nL;
     const FwdGroup &G = A.g;
@@ -159,6 +170,24 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
     if (tid < kSl) {
         M.slot[tid].job = -1;
         M.slot[tid].acc = 0.0f;
+    }
+    for (int i = tid; i < nL * kCst * kH; i += blockDim.x) {
+        const int u = i % kH, k = (i / kH) % kCst, l = i / (kH * kCst);
+        int64_t o = -1;
+        switch (k) {
+            case kCLre: o = f.lre[l] + u; break;
+            case kCLim: o = f.lim[l] + u; break;
+            case kCGam: o = f.gam[l] + u; break;
+            case kCD0: o = f.D[l] + u; break;
+            case kCD1: o = l == 0 ? f.D[0] + kH + u : -1; break;
+            case kCBa: o = f.ba[l] + u; break;
+            case kCBg: o = f.bg[l] + u; break;
+            case kCBr0: o = l == 0 ? f.BreT[0] + u : -1; break;
+            case kCBr1: o = l == 0 ? f.BreT[0] + kH + u : -1; break;
+            case kCBi0: o = l == 0 ? f.BimT[0] + u : -1; break;
+            default: o = l == 0 ? f.BimT[0] + kH + u : -1; break;
+        }
+        cst[i] = o >= 0 ? pk[o] : 0.0f;
     }
     tc_before();
     __syncthreads();
@@ -269,10 +298,11 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             *reinterpret_cast<uint16_t *>(tiles + tile + kc * 16384 + n * 128 +
                                           ((((k >> 3) ^ (n & 7))) << 4) + (k & 7) * 2) = v;
         };
-        float *xres = A.xres + (size_t)blockIdx.x * kColsL * kH;  // FP32 layer input [column][unit]
-        float cre[kMaxLayers], cim[kMaxLayers];  // this slot's complex carries of unit j
+        auto C = [&](int l, int k) { return cst[(l * kCst + k) * kH + j]; };
+        float xr[kCh / 2];  // FP32 layer input of unit j at the sites 2i + odd_r of the chunk
+        float cre[kMaxLL], cim[kMaxLL];  // this slot's complex carries of unit j
 #pragma unroll
-        for (int l = 0; l < kMaxLayers; ++l) cre[l] = cim[l] = 0.0f;
+        for (int l = 0; l < kMaxLL; ++l) cre[l] = cim[l] = 0.0f;
         uint32_t pm = 0;
         bool ok = !M.abort_flag;
 
@@ -309,16 +339,8 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
         auto carry_in = [&](int l, const SlotL &st, float &zr, float &zi) {
             zr = zi = 0.0f;
 #pragma unroll
-            for (int k = 0; k < kMaxLayers; ++k)
+            for (int k = 0; k < kMaxLL; ++k)
                 if (k == l) { zr = cre[k]; zi = cim[k]; }
-            if (st.first) {
-                zr = zi = 0.0f;
-                if (A.mode == 1 && st.c0 > 0) {
-                    const float *cin = G.carries_in + (((int64_t)st.sample * st.nch + st.c0) * nL + l) * 2 * kH;
-                    zr = cin[j];
-                    zi = cin[kH + j];
-                }
-            }
             if (G.carries_out && !odd_r) {
                 float *co = G.carries_out + (((int64_t)st.sample * st.nch + st.c) * nL + l) * 2 * kH;
                 co[j] = zr;
@@ -327,7 +349,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
         };
         auto carry_out = [&](int l, float zr, float zi) {
 #pragma unroll
-            for (int k = 0; k < kMaxLayers; ++k)
+            for (int k = 0; k < kMaxLL; ++k)
                 if (k == l) { cre[k] = zr; cim[k] = zi; }
         };
         // h_t = lambda h_{t-1} + e^gamma P_t over 16 sites (c0 .. c0 + 15) of
@@ -376,13 +398,19 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                             st.first = 1;
                             st.acc = 0.0f;
                             st.n_up = G.u1 ? count_up_before(G.bits + (int64_t)sample * G.W, c0 * kCh) : 0;
+                            uint32_t cur, pb;
+                            chunk_spins(st, cur, pb);
+                            st.cur = cur;
+                            st.pb = pb;
                         }
                     } else {
-                        uint32_t cur, pb;
-                        chunk_spins(st, cur, pb);
-                        st.n_up += __popc(cur);
+                        st.n_up += __popc(st.cur);
                         st.c += 1;
                         st.first = 0;
+                        uint32_t cur, pb;
+                        chunk_spins(st, cur, pb);
+                        st.cur = cur;
+                        st.pb = pb;
                     }
                 }
             }
@@ -401,14 +429,31 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             const SlotL &st = M.slot[s];
             const bool act = st.job >= 0;
             uint32_t cur = 0, pb = 0;
-            if (act) chunk_spins(st, cur, pb);
+            if (act) {
+                cur = st.cur;
+                pb = st.pb;
+            }
             const int t0 = act ? st.c * kCh : 0;
+            // carries entering the job's first chunk (zero, or the sample's
+            // checkpoint in mode 1), all layers' loads in flight at once
+            if (act && st.first) {
+                const bool ld = A.mode == 1 && st.c0 > 0;
+                const float *cin = G.carries_in + ((int64_t)st.sample * st.nch + st.c0) * nL * 2 * kH;
+#pragma unroll
+                for (int k = 0; k < kMaxLL; ++k) {
+                    cre[k] = (ld && k < nL) ? cin[k * 2 * kH + j] : 0.0f;
+                    cim[k] = (ld && k < nL) ? cin[k * 2 * kH + kH + j] : 0.0f;
+                }
+            }
+            // log P of the reference configuration at this lane's site (mode 1
+            // readout), loaded ahead of the step
+            float lref = 0.0f;
+            if (A.mode == 1 && q4 == 0 && act && t0 + lane < N) lref = G.logp_ref[(int64_t)st.sample * N + t0 + lane];
 
             // ---- layer 0: B u and D u are lookups of the one-hot input
             if (act) {
-                const float br0 = pk[f.BreT[0] + j], br1 = pk[f.BreT[0] + kH + j];
-                const float bi0 = pk[f.BimT[0] + j], bi1 = pk[f.BimT[0] + kH + j];
-                const float lr = pk[f.lre[0] + j], li = pk[f.lim[0] + j], g = pk[f.gam[0] + j];
+                const float br0 = C(0, kCBr0), br1 = C(0, kCBr1), bi0 = C(0, kCBi0), bi1 = C(0, kCBi1);
+                const float lr = C(0, kCLre), li = C(0, kCLim), g = C(0, kCGam);
                 float zr, zi;
                 carry_in(0, st, zr, zi);
 #pragma unroll 1
@@ -432,7 +477,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                     // ---- B u from the MMA: rows 2j (re), 2j + 1 (im)
                     wait_m2e();
                     if (act) {
-                        const float lr = pk[f.lre[l] + j], li = pk[f.lim[l] + j], g = pk[f.gam[l] + j];
+                        const float lr = C(l, kCLre), li = C(l, kCLim), g = C(l, kCGam);
                         float zr, zi;
                         carry_in(l, st, zr, zi);
 #pragma unroll 1
@@ -454,29 +499,27 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                     }
                     arrive_e2m();
                 }
-                // ---- y = Re(C h) + D u (rows j < 64)
+                // ---- y = Re(C h) + D u: unit j at the sites of this row's parity
                 wait_m2e();
                 if (act) {
-                    uint32_t v[32];
-                    tmem_ld32(tY, v);
-                    tmem_wait_ld32(v);
-                    if (r < kH) {
-                        const int u = r;
-                        if (l == 0) {
-                            const float d0 = pk[f.D[0] + u], d1 = pk[f.D[0] + kH + u];
+                    const float d0 = C(l, kCD0), d1 = C(l, kCD1);
 #pragma unroll
-                            for (int t = 0; t < kCh; ++t) {
+                    for (int hh = 0; hh < 2; ++hh) {
+                        uint32_t v[16];
+                        tmem_ld16(tY + 16 * hh, v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int ii = 8 * hh + i, t = 2 * ii + (odd_r ? 1 : 0);
+                            const float c = __uint_as_float(odd_r ? v[2 * i + 1] : v[2 * i]);
+                            float y;
+                            if (l == 0) {
                                 const bool first = (t0 + t == 0), sb = (pb >> t) & 1u;
-                                const float y = __uint_as_float(v[t]) + (first ? 0.0f : (sb ? d1 : d0));
-                                tile_st(kTileY, 0, kCh * s + t, u, op16<F16>(y));
+                                y = c + (first ? 0.0f : (sb ? d1 : d0));
+                            } else {
+                                y = fmaf(d0, xr[ii], c);
                             }
-                        } else {
-                            const float du = pk[f.D[l] + u];
-#pragma unroll
-                            for (int t = 0; t < kCh; ++t) {
-                                const float y = fmaf(du, xres[(size_t)(kCh * s + t) * kH + u], __uint_as_float(v[t]));
-                                tile_st(kTileY, 0, kCh * s + t, u, op16<F16>(y));
-                            }
+                            tile_st(kTileY, 0, kCh * s + t, j, op16<F16>(y));
                         }
                     }
                 }
@@ -484,25 +527,24 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                 // ---- GLU: rows 2j (W_a y), 2j + 1 (W_g y); even sites by the
                 // thread of row 2j, odd sites by the thread of row 2j + 1
                 wait_m2e();
-                {
-                    const float ba = pk[f.ba[l] + j], bg = pk[f.bg[l] + j];
-#pragma unroll 1
-                    for (int hh = 0; hh < 2 && act; ++hh) {
+                if (act) {
+                    const float ba = C(l, kCBa), bg = C(l, kCBg);
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
                         uint32_t v[16];
                         tmem_ld16(tG + 16 * hh, v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
 #pragma unroll
-                        for (int t = 0; t < 16; ++t) {
-                            const float mine = __uint_as_float(v[t]);
-                            const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                            // even sites by the thread of row 2j, odd sites by row 2j + 1
-                            if ((t & 1) != (int)odd_r) continue;
-                            const float a = (odd_r ? other : mine) + ba, gg = (odd_r ? mine : other) + bg;
-                            const int tc = 16 * hh + t;
-                            float *xr = xres + (size_t)(kCh * s + tc) * kH + j;
-                            const float x = a * (0.5f + 0.5f * tanh_approx(0.5f * gg)) + (l >= 1 ? *xr : 0.0f);
-                            *xr = x;
-                            tile_st(kTileX, 0, kCh * s + tc, j, op16<F16>(x));
+                        for (int i = 0; i < 8; ++i) {
+                            // row 2j holds W_a y, row 2j + 1 W_g y: each sends its
+                            // partner the value at the partner's site
+                            const float ve = __uint_as_float(v[2 * i]), vo = __uint_as_float(v[2 * i + 1]);
+                            const float other = __shfl_xor_sync(0xffffffffu, odd_r ? ve : vo, 1);
+                            const float a = (odd_r ? other : ve) + ba, gg = (odd_r ? vo : other) + bg;
+                            const int ii = 8 * hh + i;
+                            const float x = a * (0.5f + 0.5f * tanh_approx(0.5f * gg)) + (l >= 1 ? xr[ii] : 0.0f);
+                            xr[ii] = x;
+                            tile_st(kTileX, 0, kCh * s + 2 * ii + (odd_r ? 1 : 0), j, op16<F16>(x));
                         }
                     }
                 }
@@ -531,7 +573,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                         const int nu = st.n_up + __popc(cur & ((1u << t) - 1u));
                         lp = site_logp_fast(d, sv, u1_forced(G.u1, N, tt, nu));
                         if (A.mode == 0 && G.logp_out) G.logp_out[(int64_t)st.sample * N + tt] = lp;
-                        if (A.mode == 1) lp -= G.logp_ref[(int64_t)st.sample * N + tt];
+                        if (A.mode == 1) lp -= lref;
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
@@ -590,8 +632,8 @@ __global__ void pack_lru_tc_kernel(const float *__restrict__ pk, LruLayout f, Lr
                 float v = 0.0f;
                 switch (ty) {
                     case 0: v = pk[((m & 1) ? f.BimT[l] : f.BreT[l]) + (int64_t)k * H + (m >> 1)]; break;  // B
-                    case 1: if (m < H) v = pk[f.CreT[l] + (int64_t)k * H + m]; break;                      // C_re
-                    case 2: if (m < H) v = -pk[f.CimT[l] + (int64_t)k * H + m]; break;                     // -C_im
+                    case 1: v = pk[f.CreT[l] + (int64_t)k * H + (m >> 1)]; break;                          // C_re
+                    case 2: v = -pk[f.CimT[l] + (int64_t)k * H + (m >> 1)]; break;                         // -C_im
                     case 3: v = pk[((m & 1) ? f.WgT[l] : f.WaT[l]) + (int64_t)k * H + (m >> 1)]; break;   // W_a, W_g
                     default: if ((m & 31) == 0) v = pk[f.wd + k]; break;                                  // w_d
                 }
@@ -628,11 +670,9 @@ int lru_tc_schedule(int nL, uint8_t *kind, uint32_t *op) {
     return n;
 }
 
-bool lru_tc_supported(int nL, int H) { return H == kH && nL >= 1 && nL <= kMaxLayers && 4 * nL <= kLruSchedMax; }
+bool lru_tc_supported(int nL, int H) { return H == kH && nL >= 1 && nL <= kMaxLL && 4 * nL <= kLruSchedMax; }
 
 size_t lru_tc_weight_bytes(int nL) { return (size_t)(4 * nL) * kSliceL; }
-
-size_t lru_tc_xres_floats(int grid) { return (size_t)grid * kColsL * kH; }
 
 cudaError_t launch_pack_lru_tc(const float *pk, const LruLayout &f, bool f16, uint8_t *wimg, cudaStream_t stream) {
     LruKinds kd{};
@@ -652,7 +692,7 @@ cudaError_t launch_lru_tc(LruTcArgs a, int grid, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     uint8_t kind[kLruSchedMax];
     a.n_slices = lru_tc_schedule(a.nL, kind, a.op);
-    const size_t base = sizeof(MiscL) + 1024 + kTilesBytes;
+    const size_t base = sizeof(MiscL) + 1024 + kTilesBytes + (size_t)a.nL * kCst * kH * sizeof(float);
     if ((size_t)optin < base + 2 * kSliceL) return cudaErrorInvalidConfiguration;
     int R = (int)(((size_t)optin - base) / kSliceL);
     a.R = R > kMaxRingL ? kMaxRingL : R;

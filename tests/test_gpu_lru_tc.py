@@ -127,3 +127,14 @@ def test_lru_vmc_step_fp16_local_energies(oracle_mod):
     _, _, diag = oracle_mod.connected(1, N, 1, False, s)
     e = outs["fp16"]["eloc"].cpu().numpy()
     assert np.all(np.abs(e - ref) <= 1e-3 * (np.abs(diag) + np.abs(ref - diag)))
+
+
+def test_lru_tc_rejects_unsupported_shapes():
+    """The 16-bit path holds hidden 64 and up to 4 layers; other shapes at
+    fp16 or bf16 return PSR_EUNSUPPORTED (FP32 takes them)."""
+    for nL, Hh in ((5, 64), (3, 128)):
+        theta = torch.from_numpy(inputs.lru_params(nL, Hh, seed=1)).cuda()
+        s = torch.from_numpy(_spins(731, 4, 16, False)).cuda()
+        with pytest.raises(B.PsrError) as ei:
+            api.logpsi_lru(theta, s, api.ModelConfig(nL, Hh, False, "fp16"))
+        assert ei.value.code == B.PSR_EUNSUPPORTED
