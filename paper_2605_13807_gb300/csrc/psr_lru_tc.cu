@@ -61,9 +61,9 @@ enum { kTmP = 0, kTmY = 128, kTmG = 256, kTmO = 384 };
 enum { kTileX = 0, kTileH = 16384, kTileY = 3 * 16384 };
 constexpr uint32_t kTilesBytes = 4 * 16384;
 // per-unit constants of each layer in shared memory, [layer][kind][unit]:
-// lambda (re, im), e^gamma, D (one-hot rows 0, 1 at layer 0; the diagonal
-// above), b_a, b_g, and layer 0's one-hot B u (re, im for inputs 0, 1)
-enum { kCLre, kCLim, kCGam, kCD0, kCD1, kCBa, kCBg, kCBr0, kCBr1, kCBi0, kCBi1, kCst };
+// lambda (re, im), D (one-hot rows 0, 1 at layer 0; the diagonal above),
+// b_a, b_g, and layer 0's one-hot e^gamma B u (re, im for inputs 0, 1)
+enum { kCLre, kCLim, kCD0, kCD1, kCBa, kCBg, kCBr0, kCBr1, kCBi0, kCBi1, kCst };
 
 template <bool F16>
 constexpr uint32_t idesc_l() {
@@ -118,11 +118,17 @@ __device__ __forceinline__ bool bar_or_l(uint32_t id, uint32_t n, bool v) {
     return r != 0;
 }
 
+// FP32 -> 16-bit operand, round to nearest even; FP16 saturates at +-65504
 template <bool F16>
 __device__ __forceinline__ uint16_t op16(float x) {
-    if (F16) return __half_as_ushort(__float2half_rn(fminf(fmaxf(x, -65504.0f), 65504.0f)));
-    const __nv_bfloat16 b = __float2bfloat16_rn(x);
-    return *reinterpret_cast<const uint16_t *>(&b);
+    uint16_t h;
+    if (F16) asm("cvt.rn.satfinite.f16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    else asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    return h;
+}
+
+__device__ __forceinline__ void sts16(uint32_t a, uint16_t v) {
+    asm volatile("st.shared.b16 [%0], %1;" ::"r"(a), "h"(v));
 }
 
 // op word of a slice: bits 0-8 accumulator column, bits 9-10 B tile (0 x,
@@ -177,7 +183,6 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
         switch (k) {
             case kCLre: o = f.lre[l] + u; break;
             case kCLim: o = f.lim[l] + u; break;
-            case kCGam: o = f.gam[l] + u; break;
             case kCD0: o = f.D[l] + u; break;
             case kCD1: o = l == 0 ? f.D[0] + kH + u : -1; break;
             case kCBa: o = f.ba[l] + u; break;
@@ -187,7 +192,8 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             case kCBi0: o = l == 0 ? f.BimT[0] + u : -1; break;
             default: o = l == 0 ? f.BimT[0] + kH + u : -1; break;
         }
-        cst[i] = o >= 0 ? pk[o] : 0.0f;
+        // layer 0's one-hot B u lookups carry the factor e^gamma
+        cst[i] = o >= 0 ? (k >= kCBr0 ? pk[f.gam[0] + u] * pk[o] : pk[o]) : 0.0f;
     }
     tc_before();
     __syncthreads();
@@ -293,13 +299,20 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                        tG = tmem + lane_off + kTmG + kCh * s, tO = tmem + lane_off + kTmO + kCh * s;
         const int j = r >> 1;        // unit of rows 2j, 2j + 1 (B u, GLU)
         const bool odd_r = r & 1;
-        // element k of tile row n (K-major, 128-byte swizzle), K chunk kc
-        auto tile_st = [&](uint32_t tile, int kc, int n, int k, uint16_t v) {
-            *reinterpret_cast<uint16_t *>(tiles + tile + kc * 16384 + n * 128 +
-                                          ((((k >> 3) ^ (n & 7))) << 4) + (k & 7) * 2) = v;
+        // Element k of row n of a B tile (K-major, 128-byte swizzle: the
+        // 16-byte group k >> 3 of row n sits at group (k >> 3) ^ (n & 7)).
+        // tb(tile, kc, nb, k) is the address of element k of row nb; element
+        // k of row nb + dt is at (tb ^ ((dt & 7) << 4)) + 128 dt whenever the
+        // low three bits of nb and dt share no bit (no carry into the group).
+        const uint32_t tiles_s = smem_u32(tiles);
+        auto tb = [&](uint32_t tile, int kc, int nb, int k) -> uint32_t {
+            return tiles_s + tile + (uint32_t)kc * 16384u + (uint32_t)nb * 128u +
+                   ((uint32_t)((k >> 3) ^ (nb & 7)) << 4) + (uint32_t)(k & 7) * 2u;
         };
+        auto tst = [&](uint32_t b, int dt, uint16_t v) { sts16((b ^ ((uint32_t)(dt & 7) << 4)) + 128u * dt, v); };
         auto C = [&](int l, int k) { return cst[(l * kCst + k) * kH + j]; };
         float xr[kCh / 2];  // FP32 layer input of unit j at the sites 2i + odd_r of the chunk
+        const float bd = pk[f.bd];
         float cre[kMaxLL], cim[kMaxLL];  // this slot's complex carries of unit j
 #pragma unroll
         for (int l = 0; l < kMaxLL; ++l) cre[l] = cim[l] = 0.0f;
@@ -352,18 +365,22 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             for (int k = 0; k < kMaxLL; ++k)
                 if (k == l) { cre[k] = zr; cim[k] = zi; }
         };
-        // h_t = lambda h_{t-1} + e^gamma P_t over 16 sites (c0 .. c0 + 15) of
-        // the slot; this thread's part of h (real: row 2j, imaginary: row
-        // 2j + 1) to the h tile
-        auto scan16 = [&](int c0, const float (&pr)[16], const float (&pi)[16], float lr, float li, float g, float &zr,
-                          float &zi) {
+        // h_t = lambda h_{t-1} + e^gamma B u_t over 16 sites (c0 .. c0 + 15)
+        // of the slot, on this thread's part m of h (real part: row 2j,
+        // imaginary part: row 2j + 1) and the partner's part o:
+        //   m' = Re(lambda) m + sl Im(lambda) o + pm,  o' = Re(lambda) o - sl Im(lambda) m + po
+        // with sl = -1 on row 2j and +1 on row 2j + 1, pm/po the two parts of
+        // e^gamma B u_t; m to the h tile (K chunk 0: real, 1: imaginary)
+        auto scan16 = [&](int c0, const float (&pm)[16], const float (&po)[16], float lr, float lis, float &m,
+                          float &o) {
+            const uint32_t b = tb(kTileH, odd_r ? 1 : 0, kCh * s + c0, j);
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
-                const float nr = fmaf(lr, zr, fmaf(-li, zi, g * pr[t]));
-                const float ni = fmaf(lr, zi, fmaf(li, zr, g * pi[t]));
-                zr = nr;
-                zi = ni;
-                tile_st(kTileH, odd_r ? 1 : 0, kCh * s + c0 + t, j, op16<F16>(odd_r ? zi : zr));
+                const float nm = fmaf(lr, m, fmaf(lis, o, pm[t]));
+                const float no = fmaf(lr, o, fmaf(-lis, m, po[t]));
+                m = nm;
+                o = no;
+                tst(b, t, op16<F16>(m));
             }
         };
 
@@ -453,22 +470,25 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             // ---- layer 0: B u and D u are lookups of the one-hot input
             if (act) {
                 const float br0 = C(0, kCBr0), br1 = C(0, kCBr1), bi0 = C(0, kCBi0), bi1 = C(0, kCBi1);
-                const float lr = C(0, kCLre), li = C(0, kCLim), g = C(0, kCGam);
+                const float pm0 = odd_r ? bi0 : br0, pm1 = odd_r ? bi1 : br1;
+                const float po0 = odd_r ? br0 : bi0, po1 = odd_r ? br1 : bi1;
+                const float lr = C(0, kCLre), lis = odd_r ? C(0, kCLim) : -C(0, kCLim);
                 float zr, zi;
                 carry_in(0, st, zr, zi);
+                float m = odd_r ? zi : zr, o = odd_r ? zr : zi;
 #pragma unroll 1
                 for (int hh = 0; hh < 2; ++hh) {
-                    float pr[16], pi[16];
+                    float pm[16], po[16];
 #pragma unroll
                     for (int t = 0; t < 16; ++t) {
                         const int tc = 16 * hh + t;
                         const bool first = (t0 + tc == 0), sb = (pb >> tc) & 1u;
-                        pr[t] = first ? 0.0f : (sb ? br1 : br0);
-                        pi[t] = first ? 0.0f : (sb ? bi1 : bi0);
+                        pm[t] = first ? 0.0f : (sb ? pm1 : pm0);
+                        po[t] = first ? 0.0f : (sb ? po1 : po0);
                     }
-                    scan16(16 * hh, pr, pi, lr, li, g, zr, zi);
+                    scan16(16 * hh, pm, po, lr, lis, m, o);
                 }
-                carry_out(0, zr, zi);
+                carry_out(0, odd_r ? o : m, odd_r ? m : o);
             }
             arrive_e2m();
 
@@ -477,25 +497,24 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                     // ---- B u from the MMA: rows 2j (re), 2j + 1 (im)
                     wait_m2e();
                     if (act) {
-                        const float lr = C(l, kCLre), li = C(l, kCLim), g = C(l, kCGam);
+                        const float lr = C(l, kCLre), lis = odd_r ? C(l, kCLim) : -C(l, kCLim);
                         float zr, zi;
                         carry_in(l, st, zr, zi);
+                        float m = odd_r ? zi : zr, o = odd_r ? zr : zi;
 #pragma unroll 1
                         for (int hh = 0; hh < 2; ++hh) {
                             uint32_t v[16];
                             tmem_ld16(tP + 16 * hh, v);
                             asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
-                            float pr[16], pi[16];
+                            float pm[16], po[16];
 #pragma unroll
                             for (int t = 0; t < 16; ++t) {
-                                const float mine = __uint_as_float(v[t]);
-                                const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                                pr[t] = odd_r ? other : mine;
-                                pi[t] = odd_r ? mine : other;
+                                pm[t] = __uint_as_float(v[t]);
+                                po[t] = __shfl_xor_sync(0xffffffffu, pm[t], 1);
                             }
-                            scan16(16 * hh, pr, pi, lr, li, g, zr, zi);
+                            scan16(16 * hh, pm, po, lr, lis, m, o);
                         }
-                        carry_out(l, zr, zi);
+                        carry_out(l, odd_r ? o : m, odd_r ? m : o);
                     }
                     arrive_e2m();
                 }
@@ -503,6 +522,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                 wait_m2e();
                 if (act) {
                     const float d0 = C(l, kCD0), d1 = C(l, kCD1);
+                    const uint32_t by = tb(kTileY, 0, kCh * s + (odd_r ? 1 : 0), j);
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
                         uint32_t v[16];
@@ -519,7 +539,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                             } else {
                                 y = fmaf(d0, xr[ii], c);
                             }
-                            tile_st(kTileY, 0, kCh * s + t, j, op16<F16>(y));
+                            tst(by, 2 * ii, op16<F16>(y));
                         }
                     }
                 }
@@ -529,6 +549,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                 wait_m2e();
                 if (act) {
                     const float ba = C(l, kCBa), bg = C(l, kCBg);
+                    const uint32_t bx = tb(kTileX, 0, kCh * s + (odd_r ? 1 : 0), j);
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
                         uint32_t v[16];
@@ -544,7 +565,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                             const int ii = 8 * hh + i;
                             const float x = a * (0.5f + 0.5f * tanh_approx(0.5f * gg)) + (l >= 1 ? xr[ii] : 0.0f);
                             xr[ii] = x;
-                            tile_st(kTileX, 0, kCh * s + 2 * ii + (odd_r ? 1 : 0), j, op16<F16>(x));
+                            tst(bx, 2 * ii, op16<F16>(x));
                         }
                     }
                 }
@@ -568,7 +589,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                     const int t = lane, tt = t0 + t;
                     float lp = 0.0f;
                     if (tt < N) {
-                        const float d = dv + pk[f.bd];
+                        const float d = dv + bd;
                         const int sv = (cur >> t) & 1u;
                         const int nu = st.n_up + __popc(cur & ((1u << t) - 1u));
                         lp = site_logp_fast(d, sv, u1_forced(G.u1, N, tt, nu));
@@ -631,7 +652,9 @@ __global__ void pack_lru_tc_kernel(const float *__restrict__ pk, LruLayout f, Lr
                 const int k = 8 * c + 2 * e2 + h;
                 float v = 0.0f;
                 switch (ty) {
-                    case 0: v = pk[((m & 1) ? f.BimT[l] : f.BreT[l]) + (int64_t)k * H + (m >> 1)]; break;  // B
+                    case 0:  // e^gamma B
+                        v = pk[f.gam[l] + (m >> 1)] * pk[((m & 1) ? f.BimT[l] : f.BreT[l]) + (int64_t)k * H + (m >> 1)];
+                        break;
                     case 1: v = pk[f.CreT[l] + (int64_t)k * H + (m >> 1)]; break;                          // C_re
                     case 2: v = -pk[f.CimT[l] + (int64_t)k * H + (m >> 1)]; break;                         // -C_im
                     case 3: v = pk[((m & 1) ? f.WgT[l] : f.WaT[l]) + (int64_t)k * H + (m >> 1)]; break;   // W_a, W_g
