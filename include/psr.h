@@ -463,7 +463,16 @@ int psr2d_sym_local_energy(const psr_params *params, const uint8_t *samples, int
  * B_re[H][din], B_im[H][din], C_re[H][H], C_im[H][H], D ([H][2] at layer 0,
  * else [H]), W_a[H][H], b_a[H], W_g[H][H], b_g[H] (din = 2 at layer 0, else
  * H), then W_o[2][H], b_o[2]; 16 H^2 + 25 H + 2 values for three layers.
- * Computed in FP32 on CUDA cores (PSR_EUNSUPPORTED for PSR_BF16, PSR_FP16). */
+ * Precision: PSR_FP32 computes in FP32 on CUDA cores (hidden 32, 64 or 128,
+ * up to 8 layers).  PSR_FP16 and PSR_BF16 run psr_lru_logpsi and
+ * psr_lru_local_energy on the tensor cores at hidden 64 with 1 to 4 layers:
+ * the products e^gamma B u, Re(C h) and [W_a; W_g] y and the readout with
+ * 16-bit operands (FP16 or BF16) and FP32 accumulation; the complex scan,
+ * D u, GLU, residual, softmax and sums in FP32.  Bounds of the 16-bit path
+ * against the exact model: |d log psi| <= 2e-2 + 2e-5 |log psi| and E_loc
+ * within 1e-3 (|diag| + |E_loc - diag|) with FP16 operands (BF16: about
+ * twice that).  Other shapes at 16-bit precision return PSR_EUNSUPPORTED;
+ * psr_lru_sample and psr_lru_grad compute in FP32 at every precision. */
 int psr_lru_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
 
 int psr_lru_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, float *out);
@@ -560,7 +569,9 @@ int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian,
 /* One VMC step of the LRU ansatz on the device, as psr_vmc_step without
  * symmetrisation: exact samples from uniforms [n][N] (psr_lru_sample),
  * E_loc (psr_lru_local_energy), the energy gradient by psr_lru_grad, Adam.
- * Same array rules as psr_vmc_step. */
+ * At PSR_FP16 / PSR_BF16 the local energies come from the tensor-core
+ * forward; samples and gradient are FP32.  Same array rules as
+ * psr_vmc_step. */
 int psr_lru_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, const float *uniforms,
                      int64_t n, const psr_adam *adam, float *theta_out, uint8_t *spins_out,
                      float *eloc_out, double *stats_out, float *grad_out);

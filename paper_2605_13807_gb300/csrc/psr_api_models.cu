@@ -693,7 +693,7 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
         PSR_TRY(launch_bitpack(sp, n, N, W, bits, ctx->status, st));
         PSR_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
     }
-    // the FP32 kernel, or the tensor-core one (one job per slot, 4 slots per CTA)
+    // the FP32 kernel, or the tensor-core one (one job per slot, 8 slots per CTA)
     auto run = [&](const FwdJobs &jb) -> cudaError_t {
         if (!tc) return launch_lru_f32(jb, pk, f, ctx->num_sms, st);
         LruTcArgs a{};
@@ -706,7 +706,7 @@ int lru_run(const psr_params *params, const uint8_t *samples, int64_t n, int32_t
         a.wimg = wimg;
         a.job_counter = jb.job_counter;
         a.status = jb.status;
-        int64_t grid = (jb.g[0].n_jobs + 3) / 4;
+        int64_t grid = (jb.g[0].n_jobs + 7) / 8;
         if (grid > ctx->num_sms) grid = ctx->num_sms;
         return launch_lru_tc(a, (int)(grid < 1 ? 1 : grid), st);
     };

@@ -47,19 +47,20 @@ using namespace bf16m;
 
 constexpr int kH = 64;              // hidden width of this kernel
 constexpr int kCh = 32;             // sites per chunk (slot width)
-constexpr int kSl = 4;              // slots (one per epilogue warpgroup)
-constexpr int kColsL = kCh * kSl;   // MMA N
+constexpr int kSl = 4;              // slots per group (one per epilogue warpgroup)
+constexpr int kGroups = 2;          // slot groups, a chunk step apart in phase
 constexpr uint32_t kSliceL = 16384; // 128 rows x 64 inputs, 16-bit
 constexpr int kMaxRingL = 12;
 constexpr int kEpiL = 512;          // epilogue threads
 constexpr int kMaxLL = 4;           // layers (complex carries held in registers)
 
-// tensor-memory regions (columns): B u, y, GLU, readout
-enum { kTmP = 0, kTmY = 128, kTmG = 256, kTmO = 384 };
-// B operand tiles (byte offsets inside the tile block): x (K = 64), h (K =
-// 128: h_re then h_im), y (K = 64)
-enum { kTileX = 0, kTileH = 16384, kTileY = 3 * 16384 };
-constexpr uint32_t kTilesBytes = 4 * 16384;
+// Tensor memory (columns): group g's accumulator at 128 g (B u, y, GLU and
+// readout in turn: each MMA starts after the epilogue has read the previous
+// one); warpgroup s's FP32 layer input u_t of group g at 256 + 32 s + 16 g.
+// Shared memory: group g's B operand tile at 32 KB g, used in turn by x
+// (K = 64), h (K = 128: h_re, then h_im) and y (K = 64).
+constexpr uint32_t kTileG = 2 * 16384;
+constexpr uint32_t kTilesBytes = kGroups * kTileG;
 // per-unit constants of each layer in shared memory, [layer][kind][unit]:
 // lambda (re, im), D (one-hot rows 0, 1 at layer 0; the diagonal above),
 // b_a, b_g, and layer 0's one-hot e^gamma B u (re, im for inputs 0, 1)
@@ -68,7 +69,7 @@ enum { kCLre, kCLim, kCD0, kCD1, kCBa, kCBg, kCBr0, kCBr1, kCBi0, kCBi1, kCst };
 template <bool F16>
 constexpr uint32_t idesc_l() {
     return (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) | (0u << 15) | (0u << 16) |
-           ((uint32_t)(kColsL >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+           ((uint32_t)((kCh * kSl) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ uint64_t kdesc_l(uint32_t addr) {
@@ -88,11 +89,11 @@ struct SlotL {
 
 struct MiscL {
     uint64_t full[kMaxRingL], empty[kMaxRingL];
-    uint64_t e2m, m2e, go[2];
+    uint64_t e2m[kGroups], m2e[kGroups], go[2];
     uint32_t tmem_base;
     int abort_flag;
     int go_flag[2];
-    SlotL slot[kSl];
+    SlotL slot[kGroups * kSl];
 };
 
 __device__ __forceinline__ bool wait_abl(uint32_t bar, uint32_t parity, const volatile int *ab) {
@@ -131,11 +132,10 @@ __device__ __forceinline__ void sts16(uint32_t a, uint16_t v) {
     asm volatile("st.shared.b16 [%0], %1;" ::"r"(a), "h"(v));
 }
 
-// op word of a slice: bits 0-8 accumulator column, bits 9-10 B tile (0 x,
-// 1 h, 2 y), bit 11 K chunk, bit 12 accumulate from the first K step, bit
-// 13 commit the MMAs so far to the epilogue first, bit 14 wait for the
-// epilogue first.
-enum { kLopC = 1u << 13, kLopW = 1u << 14 };
+// op word of a slice: bit 0 K chunk of the B tile, bit 1 accumulate from the
+// first K step, bit 2 last slice of its stage (commit to the epilogue).
+// Every stage starts after an epilogue arrival of the same group.
+enum { kLopKc = 1u, kLopAcc = 2u, kLopEnd = 4u };
 
 template <bool F16>
 __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_constant__ LruTcArgs A) {
@@ -164,8 +164,10 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             mbar_init(smem_u32(&M.full[i]), 1);
             mbar_init(smem_u32(&M.empty[i]), 1);
         }
-        mbar_init(smem_u32(&M.e2m), 1);
-        mbar_init(smem_u32(&M.m2e), 1);
+        for (int g = 0; g < kGroups; ++g) {
+            mbar_init(smem_u32(&M.e2m[g]), 1);
+            mbar_init(smem_u32(&M.m2e[g]), 1);
+        }
         mbar_init(smem_u32(&M.go[0]), 1);
         mbar_init(smem_u32(&M.go[1]), 1);
         M.abort_flag = 0;
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
         M.go_flag[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < kSl) {
+    if (tid < kGroups * kSl) {
         M.slot[tid].job = -1;
         M.slot[tid].acc = 0.0f;
     }
@@ -206,7 +208,6 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
     if (tid == 0) mbar_arrive(smem_u32(&M.go[0]));
     __syncthreads();
     const long long njobs = A.mode == 1 ? (long long)*G.n_jobs_dev : (long long)G.n_jobs;
-    const uint32_t e2m = smem_u32(&M.e2m), m2e = smem_u32(&M.m2e);
 
     if (warp == NW) {
         // ------------------------------------------------ producer: weight stream
@@ -241,8 +242,11 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
         }
     } else if (warp == NW + 1) {
         // ------------------------------------------------ MMA issue
+        // Each stage (the slices up to one marked kLopEnd) runs for group 0,
+        // then for group 1, each after that group's epilogue arrival; the
+        // stage's ring slots are released after group 1's MMAs.
         if (lane == 0 && !M.abort_flag) {
-            uint32_t q = 0, slot = 0, fph = 0, pe = 0;
+            uint32_t q = 0, pe0 = 0, pe1 = 0;
             const uint32_t fb = smem_u32(&M.full[0]), ebar = smem_u32(&M.empty[0]);
             const uint64_t tdesc0 = kdesc_l(smem_u32(tiles)), rd = kdesc_l(smem_u32(ring));
             bool ok = true;
@@ -252,32 +256,42 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                     break;
                 }
                 if (!*(volatile int *)&M.go_flag[row & 1]) break;
-                for (int i = 0; i < A.n_slices; ++i, ++q) {
-                    const uint32_t op = A.op[i];
-                    if (op & kLopC) mma_commit(m2e);
-                    if (op & kLopW) {
-                        if (!wait_abl(e2m, pe, ab)) { ok = false; break; }
+                for (int i = 0; i < A.n_slices && ok;) {
+                    int ns = 1;
+                    while (!(A.op[i + ns - 1] & kLopEnd)) ++ns;
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g) {
+                        if (!ok) break;
+                        uint32_t &pe = g ? pe1 : pe0;
+                        if (!wait_abl(smem_u32(&M.e2m[g]), pe, ab)) {
+                            ok = false;
+                            break;
+                        }
                         pe ^= 1u;
                         tc_after();
+                        for (int k = 0; k < ns; ++k) {
+                            const uint32_t qq = q + k, sl = qq % R;
+                            if (g == 0 && !wait_abl(fb + 8 * sl, (qq / R) & 1, ab)) {
+                                ok = false;
+                                break;
+                            }
+                            const uint32_t op = A.op[i + k];
+                            const uint64_t ad = rd + (uint64_t)(sl * (kSliceL >> 4)),
+                                           bd = tdesc0 + (uint64_t)((g * kTileG + (op & kLopKc) * 16384u) >> 4);
+                            const uint32_t d = tmem + 128u * g;
+                            mma_ss<idesc_l<F16>()>(d, ad, bd, (op & kLopAcc) ? 1u : 0u);
+                            mma_ss<idesc_l<F16>()>(d, ad + 2, bd + 2, 1u);
+                            mma_ss<idesc_l<F16>()>(d, ad + 4, bd + 4, 1u);
+                            mma_ss<idesc_l<F16>()>(d, ad + 6, bd + 6, 1u);
+                        }
+                        if (!ok) break;
+                        mma_commit(smem_u32(&M.m2e[g]));
                     }
-                    if (!wait_abl(fb + 8 * slot, fph, ab)) { ok = false; break; }
-                    const uint32_t tile = (op >> 9) & 3u;
-                    const uint32_t boff = (tile == 0 ? (uint32_t)kTileX : tile == 1 ? (uint32_t)kTileH : (uint32_t)kTileY) +
-                                          ((op >> 11) & 1u) * 16384u;
-                    const uint64_t ad = rd + (uint64_t)(slot * (kSliceL >> 4)), bd = tdesc0 + (uint64_t)(boff >> 4);
-                    const uint32_t d = tmem + (op & 0x1FFu);
-                    mma_ss<idesc_l<F16>()>(d, ad, bd, (op >> 12) & 1u);
-                    mma_ss<idesc_l<F16>()>(d, ad + 2, bd + 2, 1u);
-                    mma_ss<idesc_l<F16>()>(d, ad + 4, bd + 4, 1u);
-                    mma_ss<idesc_l<F16>()>(d, ad + 6, bd + 6, 1u);
-                    mma_commit(ebar + 8 * slot);
-                    if (++slot == (uint32_t)R) {
-                        slot = 0;
-                        fph ^= 1u;
-                    }
+                    if (!ok) break;
+                    for (int k = 0; k < ns; ++k) mma_commit(ebar + 8 * ((q + k) % R));
+                    q += ns;
+                    i += ns;
                 }
-                if (!ok) break;
-                mma_commit(m2e);  // readout of the chunk step
             }
             const uint32_t last = q < (uint32_t)R ? q : (uint32_t)R;
             for (uint32_t t = 0; t < last; ++t) {
@@ -291,37 +305,41 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
         }
     } else {
         // ------------------------------------------------ epilogue
-        // warpgroup s = slot s (columns 32 s ..); warp w reads TMEM lanes
-        // 32 (w & 3) + lane = row r of every accumulator
+        // warpgroup s = slot s of each group (columns 32 s ..); warp w reads
+        // TMEM lanes 32 (w & 3) + lane = row r of every accumulator
         const int s = warp >> 2, q4 = warp & 3, r = 32 * q4 + lane;
         const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-        const uint32_t tP = tmem + lane_off + kTmP + kCh * s, tY = tmem + lane_off + kTmY + kCh * s,
-                       tG = tmem + lane_off + kTmG + kCh * s, tO = tmem + lane_off + kTmO + kCh * s;
-        const int j = r >> 1;        // unit of rows 2j, 2j + 1 (B u, GLU)
+        const int j = r >> 1;        // unit of rows 2j, 2j + 1
         const bool odd_r = r & 1;
+        auto C = [&](int l, int k) { return cst[(l * kCst + k) * kH + j]; };
+        // accumulator columns of this thread's slot in group g; its layer input
+        auto tacc = [&](int g) { return tmem + lane_off + 128u * g + (uint32_t)(kCh * s); };
+        auto tres = [&](int g) { return tmem + lane_off + 256u + (uint32_t)(32 * s + 16 * g); };
         // Element k of row n of a B tile (K-major, 128-byte swizzle: the
         // 16-byte group k >> 3 of row n sits at group (k >> 3) ^ (n & 7)).
-        // tb(tile, kc, nb, k) is the address of element k of row nb; element
-        // k of row nb + dt is at (tb ^ ((dt & 7) << 4)) + 128 dt whenever the
-        // low three bits of nb and dt share no bit (no carry into the group).
+        // tb(g, kc, nb, k) is the address of element k of row nb of group g's
+        // tile; element k of row nb + dt is at (tb ^ ((dt & 7) << 4)) + 128 dt
+        // whenever the low three bits of nb and dt share no bit.
         const uint32_t tiles_s = smem_u32(tiles);
-        auto tb = [&](uint32_t tile, int kc, int nb, int k) -> uint32_t {
-            return tiles_s + tile + (uint32_t)kc * 16384u + (uint32_t)nb * 128u +
+        auto tb = [&](int g, int kc, int nb, int k) -> uint32_t {
+            return tiles_s + (uint32_t)g * kTileG + (uint32_t)kc * 16384u + (uint32_t)nb * 128u +
                    ((uint32_t)((k >> 3) ^ (nb & 7)) << 4) + (uint32_t)(k & 7) * 2u;
         };
         auto tst = [&](uint32_t b, int dt, uint16_t v) { sts16((b ^ ((uint32_t)(dt & 7) << 4)) + 128u * dt, v); };
-        auto C = [&](int l, int k) { return cst[(l * kCst + k) * kH + j]; };
-        float xr[kCh / 2];  // FP32 layer input of unit j at the sites 2i + odd_r of the chunk
         const float bd = pk[f.bd];
-        float cre[kMaxLL], cim[kMaxLL];  // this slot's complex carries of unit j
+        float cre[kGroups][kMaxLL], cim[kGroups][kMaxLL];  // complex carries of unit j, per group
 #pragma unroll
-        for (int l = 0; l < kMaxLL; ++l) cre[l] = cim[l] = 0.0f;
-        uint32_t pm = 0;
+        for (int g = 0; g < kGroups; ++g)
+#pragma unroll
+            for (int l = 0; l < kMaxLL; ++l) cre[g][l] = cim[g][l] = 0.0f;
+        float lref[kGroups] = {0.0f, 0.0f};
+        uint32_t pm0 = 0, pm1 = 0;
         bool ok = !M.abort_flag;
 
-        auto wait_m2e = [&]() {
+        auto wait_m2e = [&](int g) {
+            uint32_t &pm = g ? pm1 : pm0;
             bool w = true;
-            if (tid == 0) w = ok && wait_abl(m2e, pm, ab);
+            if (tid == 0) w = ok && wait_abl(smem_u32(&M.m2e[g]), pm, ab);
             const bool bad = bar_or_l(1, kEpiL, !w || !ok);
             if (bad && ok && tid == 0) {
                 M.abort_flag = 1;
@@ -331,11 +349,191 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             pm ^= 1u;
             tc_after();
         };
-        auto arrive_e2m = [&]() {
+        auto arrive_e2m = [&](int g) {
             fence_proxy_async();
             tc_before();
             asm volatile("bar.sync 1, %0;" ::"r"(kEpiL) : "memory");
-            if (tid == 0) mbar_arrive(e2m);
+            if (tid == 0) mbar_arrive(smem_u32(&M.e2m[g]));
+        };
+        // carry of layer l entering the slot's chunk (stored as the chunk's
+        // checkpoint in mode 0)
+        auto carry_in = [&](int g, int l, const SlotL &st, float &zr, float &zi) {
+            zr = zi = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kMaxLL; ++k)
+                if (k == l) { zr = cre[g][k]; zi = cim[g][k]; }
+            if (G.carries_out && !odd_r) {
+                float *co = G.carries_out + (((int64_t)st.sample * st.nch + st.c) * nL + l) * 2 * kH;
+                co[j] = zr;
+                co[kH + j] = zi;
+            }
+        };
+        auto carry_out = [&](int g, int l, float zr, float zi) {
+#pragma unroll
+            for (int k = 0; k < kMaxLL; ++k)
+                if (k == l) { cre[g][k] = zr; cim[g][k] = zi; }
+        };
+        // h_t = lambda h_{t-1} + e^gamma B u_t over 16 sites (c0 .. c0 + 15)
+        // of the slot, on this thread's part m of h (real part: row 2j,
+        // imaginary part: row 2j + 1) and the partner's part o:
+        //   m' = Re(lambda) m + sl Im(lambda) o + pm,  o' = Re(lambda) o - sl Im(lambda) m + po
+        // with sl = -1 on row 2j and +1 on row 2j + 1, pm/po the two parts of
+        // e^gamma B u_t; m to the h tile (K chunk 0: real, 1: imaginary)
+        auto scan16 = [&](int g, int c0, const float (&pm)[16], const float (&po)[16], float lr, float lis, float &m,
+                          float &o) {
+            const uint32_t b = tb(g, odd_r ? 1 : 0, kCh * s + c0, j);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const float nm = fmaf(lr, m, fmaf(lis, o, pm[t]));
+                const float no = fmaf(lr, o, fmaf(-lis, m, po[t]));
+                m = nm;
+                o = no;
+                tst(b, t, op16<F16>(m));
+            }
+        };
+        // ---- the complex scan of layer l over the slot's chunk: B u from a
+        // lookup of the one-hot input (layer 0) or from the MMA (rows 2j: re,
+        // 2j + 1: im)
+        auto scan_stage = [&](int g, int l) {
+            const SlotL &st = M.slot[s + kSl * g];
+            if (st.job < 0) return;
+            const uint32_t pb = st.pb;
+            const int t0 = st.c * kCh;
+            const float lr = C(l, kCLre), lis = odd_r ? C(l, kCLim) : -C(l, kCLim);
+            float zr, zi;
+            carry_in(g, l, st, zr, zi);
+            float m = odd_r ? zi : zr, o = odd_r ? zr : zi;
+            if (l == 0) {
+                const float br0 = C(0, kCBr0), br1 = C(0, kCBr1), bi0 = C(0, kCBi0), bi1 = C(0, kCBi1);
+                const float pm0_ = odd_r ? bi0 : br0, pm1_ = odd_r ? bi1 : br1;
+                const float po0_ = odd_r ? br0 : bi0, po1_ = odd_r ? br1 : bi1;
+#pragma unroll 1
+                for (int hh = 0; hh < 2; ++hh) {
+                    float pm[16], po[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const int tc = 16 * hh + t;
+                        const bool first = (t0 + tc == 0), sb = (pb >> tc) & 1u;
+                        pm[t] = first ? 0.0f : (sb ? pm1_ : pm0_);
+                        po[t] = first ? 0.0f : (sb ? po1_ : po0_);
+                    }
+                    scan16(g, 16 * hh, pm, po, lr, lis, m, o);
+                }
+            } else {
+#pragma unroll 1
+                for (int hh = 0; hh < 2; ++hh) {
+                    uint32_t v[16];
+                    tmem_ld16(tacc(g) + 16 * hh, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
+                    float pm[16], po[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        pm[t] = __uint_as_float(v[t]);
+                        po[t] = __shfl_xor_sync(0xffffffffu, pm[t], 1);
+                    }
+                    scan16(g, 16 * hh, pm, po, lr, lis, m, o);
+                }
+            }
+            carry_out(g, l, odd_r ? o : m, odd_r ? m : o);
+        };
+        // ---- y = Re(C h) + D u: unit j at the sites of this row's parity
+        auto y_stage = [&](int g, int l) {
+            const SlotL &st = M.slot[s + kSl * g];
+            if (st.job < 0) return;
+            const uint32_t pb = st.pb;
+            const int t0 = st.c * kCh;
+            const float d0 = C(l, kCD0), d1 = C(l, kCD1);
+            const uint32_t by = tb(g, 0, kCh * s + (odd_r ? 1 : 0), j);
+            uint32_t v0[16], v1[16], xv[16];
+            tmem_ld16(tacc(g), v0);
+            tmem_ld16(tacc(g) + 16, v1);
+            if (l > 0) {
+                tmem_ld16(tres(g), xv);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v0, 0), PSR_P16(v1, 0), PSR_P16(xv, 0)::"memory");
+            } else {
+                tmem_wait_ld16x2(v0, v1);
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int ii = 8 * hh + i, t = 2 * ii + (odd_r ? 1 : 0);
+                    const uint32_t cv = hh ? (odd_r ? v1[2 * i + 1] : v1[2 * i]) : (odd_r ? v0[2 * i + 1] : v0[2 * i]);
+                    const float c = __uint_as_float(cv);
+                    float y;
+                    if (l == 0) {
+                        const bool first = (t0 + t == 0), sb = (pb >> t) & 1u;
+                        y = c + (first ? 0.0f : (sb ? d1 : d0));
+                    } else {
+                        y = fmaf(d0, __uint_as_float(xv[ii]), c);
+                    }
+                    tst(by, 2 * ii, op16<F16>(y));
+                }
+            }
+        };
+        // ---- GLU: rows 2j (W_a y), 2j + 1 (W_g y); the new layer input x
+        // (+ the residual above layer 0) to the x tile and to tensor memory
+        auto glu_stage = [&](int g, int l) {
+            const SlotL &st = M.slot[s + kSl * g];
+            if (st.job < 0) return;
+            const float ba = C(l, kCBa), bg = C(l, kCBg);
+            const uint32_t bx = tb(g, 0, kCh * s + (odd_r ? 1 : 0), j);
+            uint32_t v0[16], v1[16], xv[16];
+            tmem_ld16(tacc(g), v0);
+            tmem_ld16(tacc(g) + 16, v1);
+            if (l > 0) {
+                tmem_ld16(tres(g), xv);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v0, 0), PSR_P16(v1, 0), PSR_P16(xv, 0)::"memory");
+            } else {
+                tmem_wait_ld16x2(v0, v1);
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    // each thread sends its partner the value at the partner's site
+                    const float ve = __uint_as_float(hh ? v1[2 * i] : v0[2 * i]),
+                                vo = __uint_as_float(hh ? v1[2 * i + 1] : v0[2 * i + 1]);
+                    const float other = __shfl_xor_sync(0xffffffffu, odd_r ? ve : vo, 1);
+                    const float a = (odd_r ? other : ve) + ba, gg = (odd_r ? vo : other) + bg;
+                    const int ii = 8 * hh + i;
+                    const float x = a * (0.5f + 0.5f * tanh_approx(0.5f * gg)) + (l >= 1 ? __uint_as_float(xv[ii]) : 0.0f);
+                    xv[ii] = __float_as_uint(x);
+                    tst(bx, 2 * ii, op16<F16>(x));
+                }
+            }
+            tmem_st16(tres(g), xv);
+            tmem_wait_st();
+        };
+        // ---- readout: d_t = w_d x_t + b_d in row 0 of the first lane
+        // quarter; site t by lane t
+        auto readout = [&](int g) {
+            const SlotL &st = M.slot[s + kSl * g];
+            if (q4 != 0 || st.job < 0) return;
+            const uint32_t cur = st.cur;
+            const int t0 = st.c * kCh;
+            uint32_t v[32];
+            tmem_ld32(tacc(g), v);
+            tmem_wait_ld32(v);
+            float dv = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kCh; ++t) {
+                const float x = __shfl_sync(0xffffffffu, __uint_as_float(v[t]), 0);
+                if (t == lane) dv = x;
+            }
+            const int t = lane, tt = t0 + t;
+            float lp = 0.0f;
+            if (tt < N) {
+                const float d = dv + bd;
+                const int sv = (cur >> t) & 1u;
+                const int nu = st.n_up + __popc(cur & ((1u << t) - 1u));
+                lp = site_logp_fast(d, sv, u1_forced(G.u1, N, tt, nu));
+                if (A.mode == 0 && G.logp_out) G.logp_out[(int64_t)st.sample * N + tt] = lp;
+                if (A.mode == 1) lp -= lref[g];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+            if (lane == 0) M.slot[s + kSl * g].acc += lp;
         };
         // the 32 sites' 32-bit spins of the slot's current chunk: cur (bit t =
         // s_{t0+t}) and prevbits (bit t = s_{t0+t-1}, 0 at the first site)
@@ -347,47 +545,11 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             if (nvalid < 32) cur &= (1u << nvalid) - 1u;
             prevbits = (cur << 1) | prev;
         };
-        // carry of layer l entering the slot's chunk (stored as the chunk's
-        // checkpoint in mode 0)
-        auto carry_in = [&](int l, const SlotL &st, float &zr, float &zi) {
-            zr = zi = 0.0f;
-#pragma unroll
-            for (int k = 0; k < kMaxLL; ++k)
-                if (k == l) { zr = cre[k]; zi = cim[k]; }
-            if (G.carries_out && !odd_r) {
-                float *co = G.carries_out + (((int64_t)st.sample * st.nch + st.c) * nL + l) * 2 * kH;
-                co[j] = zr;
-                co[kH + j] = zi;
-            }
-        };
-        auto carry_out = [&](int l, float zr, float zi) {
-#pragma unroll
-            for (int k = 0; k < kMaxLL; ++k)
-                if (k == l) { cre[k] = zr; cim[k] = zi; }
-        };
-        // h_t = lambda h_{t-1} + e^gamma B u_t over 16 sites (c0 .. c0 + 15)
-        // of the slot, on this thread's part m of h (real part: row 2j,
-        // imaginary part: row 2j + 1) and the partner's part o:
-        //   m' = Re(lambda) m + sl Im(lambda) o + pm,  o' = Re(lambda) o - sl Im(lambda) m + po
-        // with sl = -1 on row 2j and +1 on row 2j + 1, pm/po the two parts of
-        // e^gamma B u_t; m to the h tile (K chunk 0: real, 1: imaginary)
-        auto scan16 = [&](int c0, const float (&pm)[16], const float (&po)[16], float lr, float lis, float &m,
-                          float &o) {
-            const uint32_t b = tb(kTileH, odd_r ? 1 : 0, kCh * s + c0, j);
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const float nm = fmaf(lr, m, fmaf(lis, o, pm[t]));
-                const float no = fmaf(lr, o, fmaf(-lis, m, po[t]));
-                m = nm;
-                o = no;
-                tst(b, t, op16<F16>(m));
-            }
-        };
 
         for (uint32_t row_it = 0; ok; ++row_it) {
-            // ---- slot update (warp 4 s: slot s)
-            if (q4 == 0 && lane == 0) {
-                SlotL &st = M.slot[s];
+            // ---- slot update (lanes 0, 1 of warp 4 s: slots s, 4 + s)
+            if (q4 == 0 && lane < kGroups) {
+                SlotL &st = M.slot[s + kSl * lane];
                 if (row_it > 0 && st.job >= 0 && st.c + 1 >= st.nch) {
                     G.out[st.job] = 0.5f * st.acc;  // the job's last chunk is done
                 }
@@ -437,169 +599,69 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             }
             if (tid == 0) {
                 bool more = false;
-                for (int k = 0; k < kSl; ++k)
+                for (int k = 0; k < kGroups * kSl; ++k)
                     if (M.slot[k].job >= 0 && M.slot[k].c + 1 < M.slot[k].nch) more = true;
                 if (!more) more = (long long)atomicAdd(A.job_counter, 0ull) < njobs;
                 M.go_flag[(row_it + 1) & 1] = more ? 1 : 0;
                 mbar_arrive(smem_u32(&M.go[(row_it + 1) & 1]));
             }
-            const SlotL &st = M.slot[s];
-            const bool act = st.job >= 0;
-            uint32_t cur = 0, pb = 0;
-            if (act) {
-                cur = st.cur;
-                pb = st.pb;
-            }
-            const int t0 = act ? st.c * kCh : 0;
-            // carries entering the job's first chunk (zero, or the sample's
-            // checkpoint in mode 1), all layers' loads in flight at once
-            if (act && st.first) {
-                const bool ld = A.mode == 1 && st.c0 > 0;
-                const float *cin = G.carries_in + ((int64_t)st.sample * st.nch + st.c0) * nL * 2 * kH;
 #pragma unroll
-                for (int k = 0; k < kMaxLL; ++k) {
-                    cre[k] = (ld && k < nL) ? cin[k * 2 * kH + j] : 0.0f;
-                    cim[k] = (ld && k < nL) ? cin[k * 2 * kH + kH + j] : 0.0f;
-                }
-            }
-            // log P of the reference configuration at this lane's site (mode 1
-            // readout), loaded ahead of the step
-            float lref = 0.0f;
-            if (A.mode == 1 && q4 == 0 && act && t0 + lane < N) lref = G.logp_ref[(int64_t)st.sample * N + t0 + lane];
-
-            // ---- layer 0: B u and D u are lookups of the one-hot input
-            if (act) {
-                const float br0 = C(0, kCBr0), br1 = C(0, kCBr1), bi0 = C(0, kCBi0), bi1 = C(0, kCBi1);
-                const float pm0 = odd_r ? bi0 : br0, pm1 = odd_r ? bi1 : br1;
-                const float po0 = odd_r ? br0 : bi0, po1 = odd_r ? br1 : bi1;
-                const float lr = C(0, kCLre), lis = odd_r ? C(0, kCLim) : -C(0, kCLim);
-                float zr, zi;
-                carry_in(0, st, zr, zi);
-                float m = odd_r ? zi : zr, o = odd_r ? zr : zi;
-#pragma unroll 1
-                for (int hh = 0; hh < 2; ++hh) {
-                    float pm[16], po[16];
+            for (int g = 0; g < kGroups; ++g) {
+                const SlotL &st = M.slot[s + kSl * g];
+                const bool act = st.job >= 0;
+                const int t0 = act ? st.c * kCh : 0;
+                // carries entering the job's first chunk (zero, or the
+                // sample's checkpoint in mode 1), all layers' loads at once
+                if (act && st.first) {
+                    const bool ld = A.mode == 1 && st.c0 > 0;
+                    const float *cin = G.carries_in + ((int64_t)st.sample * st.nch + st.c0) * nL * 2 * kH;
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const int tc = 16 * hh + t;
-                        const bool first = (t0 + tc == 0), sb = (pb >> tc) & 1u;
-                        pm[t] = first ? 0.0f : (sb ? pm1 : pm0);
-                        po[t] = first ? 0.0f : (sb ? po1 : po0);
+                    for (int k = 0; k < kMaxLL; ++k) {
+                        cre[g][k] = (ld && k < nL) ? cin[k * 2 * kH + j] : 0.0f;
+                        cim[g][k] = (ld && k < nL) ? cin[k * 2 * kH + kH + j] : 0.0f;
                     }
-                    scan16(16 * hh, pm, po, lr, lis, m, o);
                 }
-                carry_out(0, odd_r ? o : m, odd_r ? m : o);
+                // log P of the reference configuration at this lane's site
+                // (mode 1 readout), loaded ahead of the step
+                lref[g] = 0.0f;
+                if (A.mode == 1 && q4 == 0 && act && t0 + lane < N)
+                    lref[g] = G.logp_ref[(int64_t)st.sample * N + t0 + lane];
             }
-            arrive_e2m();
 
+            // ---- the layers: every stage for group 0, then for group 1, so
+            // that one group's MMAs run while the other's epilogue works
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) {
+                scan_stage(g, 0);
+                arrive_e2m(g);
+            }
+#pragma unroll 1
             for (int l = 0; l < nL; ++l) {
                 if (l > 0) {
-                    // ---- B u from the MMA: rows 2j (re), 2j + 1 (im)
-                    wait_m2e();
-                    if (act) {
-                        const float lr = C(l, kCLre), lis = odd_r ? C(l, kCLim) : -C(l, kCLim);
-                        float zr, zi;
-                        carry_in(l, st, zr, zi);
-                        float m = odd_r ? zi : zr, o = odd_r ? zr : zi;
-#pragma unroll 1
-                        for (int hh = 0; hh < 2; ++hh) {
-                            uint32_t v[16];
-                            tmem_ld16(tP + 16 * hh, v);
-                            asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
-                            float pm[16], po[16];
 #pragma unroll
-                            for (int t = 0; t < 16; ++t) {
-                                pm[t] = __uint_as_float(v[t]);
-                                po[t] = __shfl_xor_sync(0xffffffffu, pm[t], 1);
-                            }
-                            scan16(16 * hh, pm, po, lr, lis, m, o);
-                        }
-                        carry_out(l, odd_r ? o : m, odd_r ? m : o);
-                    }
-                    arrive_e2m();
-                }
-                // ---- y = Re(C h) + D u: unit j at the sites of this row's parity
-                wait_m2e();
-                if (act) {
-                    const float d0 = C(l, kCD0), d1 = C(l, kCD1);
-                    const uint32_t by = tb(kTileY, 0, kCh * s + (odd_r ? 1 : 0), j);
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        uint32_t v[16];
-                        tmem_ld16(tY + 16 * hh, v);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int ii = 8 * hh + i, t = 2 * ii + (odd_r ? 1 : 0);
-                            const float c = __uint_as_float(odd_r ? v[2 * i + 1] : v[2 * i]);
-                            float y;
-                            if (l == 0) {
-                                const bool first = (t0 + t == 0), sb = (pb >> t) & 1u;
-                                y = c + (first ? 0.0f : (sb ? d1 : d0));
-                            } else {
-                                y = fmaf(d0, xr[ii], c);
-                            }
-                            tst(by, 2 * ii, op16<F16>(y));
-                        }
+                    for (int g = 0; g < kGroups; ++g) {
+                        wait_m2e(g);
+                        scan_stage(g, l);
+                        arrive_e2m(g);
                     }
                 }
-                arrive_e2m();
-                // ---- GLU: rows 2j (W_a y), 2j + 1 (W_g y); even sites by the
-                // thread of row 2j, odd sites by the thread of row 2j + 1
-                wait_m2e();
-                if (act) {
-                    const float ba = C(l, kCBa), bg = C(l, kCBg);
-                    const uint32_t bx = tb(kTileX, 0, kCh * s + (odd_r ? 1 : 0), j);
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        uint32_t v[16];
-                        tmem_ld16(tG + 16 * hh, v);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" : PSR_P16(v, 0)::"memory");
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            // row 2j holds W_a y, row 2j + 1 W_g y: each sends its
-                            // partner the value at the partner's site
-                            const float ve = __uint_as_float(v[2 * i]), vo = __uint_as_float(v[2 * i + 1]);
-                            const float other = __shfl_xor_sync(0xffffffffu, odd_r ? ve : vo, 1);
-                            const float a = (odd_r ? other : ve) + ba, gg = (odd_r ? vo : other) + bg;
-                            const int ii = 8 * hh + i;
-                            const float x = a * (0.5f + 0.5f * tanh_approx(0.5f * gg)) + (l >= 1 ? xr[ii] : 0.0f);
-                            xr[ii] = x;
-                            tst(bx, 2 * ii, op16<F16>(x));
-                        }
-                    }
+                for (int g = 0; g < kGroups; ++g) {
+                    wait_m2e(g);
+                    y_stage(g, l);
+                    arrive_e2m(g);
                 }
-                arrive_e2m();
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g) {
+                    wait_m2e(g);
+                    glu_stage(g, l);
+                    arrive_e2m(g);
+                }
             }
-
-            // ---- readout: d_t = w_d x_t + b_d in row 0 of the first lane
-            // quarter; site t by lane t
-            wait_m2e();
-            if (q4 == 0 && act) {
-                uint32_t v[32];
-                tmem_ld32(tO, v);
-                tmem_wait_ld32(v);
-                {
-                    float dv = 0.0f;
 #pragma unroll
-                    for (int t = 0; t < kCh; ++t) {
-                        const float x = __shfl_sync(0xffffffffu, __uint_as_float(v[t]), 0);
-                        if (t == lane) dv = x;
-                    }
-                    const int t = lane, tt = t0 + t;
-                    float lp = 0.0f;
-                    if (tt < N) {
-                        const float d = dv + bd;
-                        const int sv = (cur >> t) & 1u;
-                        const int nu = st.n_up + __popc(cur & ((1u << t) - 1u));
-                        lp = site_logp_fast(d, sv, u1_forced(G.u1, N, tt, nu));
-                        if (A.mode == 0 && G.logp_out) G.logp_out[(int64_t)st.sample * N + tt] = lp;
-                        if (A.mode == 1) lp -= lref;
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
-                    if (lane == 0) M.slot[s].acc += lp;
-                }
+            for (int g = 0; g < kGroups; ++g) {
+                wait_m2e(g);
+                readout(g);
             }
             tc_before();
             if (bar_or_l(1, kEpiL, !ok)) {
@@ -607,8 +669,8 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                 break;
             }
             if (!*(volatile int *)&M.go_flag[(row_it + 1) & 1]) {
-                if (q4 == 0 && lane == 0) {
-                    SlotL &sf = M.slot[s];
+                if (q4 == 0 && lane < kGroups) {
+                    SlotL &sf = M.slot[s + kSl * lane];
                     if (sf.job >= 0) G.out[sf.job] = 0.5f * sf.acc;
                 }
                 break;
@@ -671,25 +733,22 @@ __global__ void pack_lru_tc_kernel(const float *__restrict__ pk, LruLayout f, Lr
 
 }  // namespace
 
-// Slices of one chunk step and the MMA thread's op words (see kLopC/kLopW);
-// kind[i] = matrix type << 4 | layer.
+// Slices of one chunk step and the MMA thread's op words (kLopKc, kLopAcc,
+// kLopEnd); kind[i] = matrix type << 4 | layer.
 int lru_tc_schedule(int nL, uint8_t *kind, uint32_t *op) {
     int n = 0;
-    auto add = [&](int ty, int l, uint32_t dcol, uint32_t tile, uint32_t kc, uint32_t acc, uint32_t fl) {
+    auto add = [&](int ty, int l, uint32_t fl) {
         kind[n] = (uint8_t)(ty << 4 | l);
-        op[n] = dcol | (tile << 9) | (kc << 11) | (acc << 12) | fl;
+        op[n] = fl;
         ++n;
     };
     for (int l = 0; l < nL; ++l) {
-        if (l > 0)  // B u (after the previous GLU; x ready)
-            add(0, l, kTmP, 0, 0, 0, kLopC | kLopW);
-        // Re(C h): wait for the scan (after committing B u above layer 0)
-        add(1, l, kTmY, 1, 0, 0, (l > 0 ? kLopC : 0) | kLopW);
-        add(2, l, kTmY, 1, 1, 1, 0);
-        // GLU: y ready
-        add(3, l, kTmG, 2, 0, 0, kLopC | kLopW);
+        if (l > 0) add(0, l, kLopEnd);  // e^gamma B u: after the previous GLU (x ready)
+        add(1, l, 0);                   // Re(C h), K chunk 0 (h_re): after the scan
+        add(2, l, kLopKc | kLopAcc | kLopEnd);
+        add(3, l, kLopEnd);             // [W_a; W_g] y: y ready
     }
-    add(4, 0, kTmO, 0, 0, 0, kLopC | kLopW);  // readout: x of the last layer ready
+    add(4, 0, kLopEnd);  // readout: x of the last layer ready
     return n;
 }
 

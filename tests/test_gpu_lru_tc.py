@@ -89,7 +89,7 @@ def test_local_energy_lru_tc_matches_oracle(oracle_mod, kind, N, pbc, u1, hf, pr
 
 
 def test_lru_tc_many_jobs_and_determinism():
-    """More sequences than the CTAs hold slots (4 per CTA), so slots take new
+    """More sequences than the CTAs hold slots (8 per CTA), so slots take new
     jobs mid-launch; within the 16-bit bound of the (oracle-checked) FP32
     path, and two runs bitwise equal."""
     N, nL, n = 96, 3, 3000
