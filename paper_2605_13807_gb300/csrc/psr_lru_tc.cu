@@ -18,17 +18,19 @@
 // thread pair of rows 2j, 2j + 1 shares unit j: both run its complex scan
 // over the chunk, and the y and GLU epilogues split the sites by parity
 // (even sites: row 2j), so the FP32 layer input u_t that D u and the residual
-// need stays in the registers of the thread that made it.
+// need stays with the thread that made it (in its tensor-memory lane).
 //
-// Work layout, as in the 2D tensor-core forward: one persistent CTA per SM
-// with 128 site columns in 4 slots of one 32-site chunk each; slot s is
-// warpgroup s of the epilogue, each slot holds one job (a sample, or a
-// connected configuration resumed at the chunk of its first flipped site
-// from the sample's FP32 complex chunk carries) and advances one chunk per
-// step, taking the next job from a counter when its sequence ends.  The
-// weights (12 slices of 16 KB per chunk step at 3 layers) stream from L2
-// through a ring of slices (producer thread); one thread issues the MMAs.
-// The complex carries of a slot stay in the registers of its warpgroup.
+// Work layout: one persistent CTA per SM with two groups of 4 slots; a slot
+// holds one 32-site chunk of one job (a sample, or a connected configuration
+// resumed at the chunk of its first flipped site from the sample's FP32
+// complex chunk carries), advances one chunk per step and takes the next job
+// from a counter when its sequence ends.  Warpgroup s serves slot s of both
+// groups; every stage of a chunk step (scan, y, GLU per layer, readout) runs
+// for group 0 and then for group 1, so one group's MMAs (N = 128: its 4
+// slots) run while the epilogue works on the other group.  The weights (12
+// slices of 16 KB per chunk step at 3 layers) stream from L2 through a ring
+// of slices (producer thread), each slice serving both groups; one thread
+// issues the MMAs.  The complex carries of the slots stay in shared memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
         (reinterpret_cast<uintptr_t>(smem_raw) + sizeof(MiscL) + 1023) & ~uintptr_t(1023));
     uint8_t *ring = tiles + kTilesBytes;
     float *cst = reinterpret_cast<float *>(ring + (size_t)A.R * kSliceL);
+    float *car = cst + A.nL * kCst * kH;  // complex carries [slot][layer][re, im][unit]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int R = A.R, nL = A.nL;
     const FwdGroup &G = A.g;
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             mbar_init(smem_u32(&M.empty[i]), 1);
         }
         for (int g = 0; g < kGroups; ++g) {
-            mbar_init(smem_u32(&M.e2m[g]), 1);
+            mbar_init(smem_u32(&M.e2m[g]), kEpiL / 32);  // one arrival per epilogue warp
             mbar_init(smem_u32(&M.m2e[g]), 1);
         }
         mbar_init(smem_u32(&M.go[0]), 1);
@@ -327,41 +330,42 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
         };
         auto tst = [&](uint32_t b, int dt, uint16_t v) { sts16((b ^ ((uint32_t)(dt & 7) << 4)) + 128u * dt, v); };
         const float bd = pk[f.bd];
-        float cre[kGroups][kMaxLL], cim[kGroups][kMaxLL];  // complex carries of unit j, per group
-#pragma unroll
-        for (int g = 0; g < kGroups; ++g)
-#pragma unroll
-            for (int l = 0; l < kMaxLL; ++l) cre[g][l] = cim[g][l] = 0.0f;
+        auto carp = [&](int g, int l) { return car + ((s + kSl * g) * kMaxLL + l) * 2 * kH + j; };
         float lref[kGroups] = {0.0f, 0.0f};
         uint32_t pm0 = 0, pm1 = 0;
         bool ok = !M.abort_flag;
 
+        // Inside a chunk step the epilogue warps synchronise with the MMA
+        // thread only: each warp waits for the group's MMAs (lane 0 polls,
+        // the warp takes its answer) and arrives on the group's e2m barrier
+        // once its tensor-memory reads and tile stores are done.  A warp whose
+        // wait expires sets the abort flag, which ends every other wait, and
+        // all warps meet at the step's closing barrier.
         auto wait_m2e = [&](int g) {
             uint32_t &pm = g ? pm1 : pm0;
-            bool w = true;
-            if (tid == 0) w = ok && wait_abl(smem_u32(&M.m2e[g]), pm, ab);
-            const bool bad = bar_or_l(1, kEpiL, !w || !ok);
-            if (bad && ok && tid == 0) {
+            bool w = false;
+            if (lane == 0) w = ok && wait_abl(smem_u32(&M.m2e[g]), pm, ab);
+            w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
+            if (!w && ok && lane == 0) {
                 M.abort_flag = 1;
                 set_status(A.status, PSR_ETIMEOUT);
             }
-            ok = ok && !bad;
+            ok = ok && w;
             pm ^= 1u;
             tc_after();
         };
         auto arrive_e2m = [&](int g) {
             fence_proxy_async();
             tc_before();
-            asm volatile("bar.sync 1, %0;" ::"r"(kEpiL) : "memory");
-            if (tid == 0) mbar_arrive(smem_u32(&M.e2m[g]));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&M.e2m[g]));
         };
         // carry of layer l entering the slot's chunk (stored as the chunk's
         // checkpoint in mode 0)
         auto carry_in = [&](int g, int l, const SlotL &st, float &zr, float &zi) {
-            zr = zi = 0.0f;
-#pragma unroll
-            for (int k = 0; k < kMaxLL; ++k)
-                if (k == l) { zr = cre[g][k]; zi = cim[g][k]; }
+            const float *cp = carp(g, l);
+            zr = cp[0];
+            zi = cp[kH];
             if (G.carries_out && !odd_r) {
                 float *co = G.carries_out + (((int64_t)st.sample * st.nch + st.c) * nL + l) * 2 * kH;
                 co[j] = zr;
@@ -369,9 +373,11 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             }
         };
         auto carry_out = [&](int g, int l, float zr, float zi) {
-#pragma unroll
-            for (int k = 0; k < kMaxLL; ++k)
-                if (k == l) { cre[g][k] = zr; cim[g][k] = zi; }
+            if (!odd_r) {
+                float *cp = carp(g, l);
+                cp[0] = zr;
+                cp[kH] = zi;
+            }
         };
         // h_t = lambda h_{t-1} + e^gamma B u_t over 16 sites (c0 .. c0 + 15)
         // of the slot, on this thread's part m of h (real part: row 2j,
@@ -612,13 +618,15 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                 const int t0 = act ? st.c * kCh : 0;
                 // carries entering the job's first chunk (zero, or the
                 // sample's checkpoint in mode 1), all layers' loads at once
-                if (act && st.first) {
+                if (act && st.first && !odd_r) {
                     const bool ld = A.mode == 1 && st.c0 > 0;
                     const float *cin = G.carries_in + ((int64_t)st.sample * st.nch + st.c0) * nL * 2 * kH;
 #pragma unroll
                     for (int k = 0; k < kMaxLL; ++k) {
-                        cre[g][k] = (ld && k < nL) ? cin[k * 2 * kH + j] : 0.0f;
-                        cim[g][k] = (ld && k < nL) ? cin[k * 2 * kH + kH + j] : 0.0f;
+                        if (k >= nL) break;
+                        float *cp = carp(g, k);
+                        cp[0] = ld ? cin[k * 2 * kH + j] : 0.0f;
+                        cp[kH] = ld ? cin[k * 2 * kH + kH + j] : 0.0f;
                     }
                 }
                 // log P of the reference configuration at this lane's site
@@ -627,12 +635,13 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                 if (A.mode == 1 && q4 == 0 && act && t0 + lane < N)
                     lref[g] = G.logp_ref[(int64_t)st.sample * N + t0 + lane];
             }
+            __syncwarp();  // the carries written by the even lanes, before both lanes read them
 
             // ---- the layers: every stage for group 0, then for group 1, so
             // that one group's MMAs run while the other's epilogue works
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) {
-                scan_stage(g, 0);
+                if (ok) scan_stage(g, 0);
                 arrive_e2m(g);
             }
 #pragma unroll 1
@@ -641,27 +650,27 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
 #pragma unroll
                     for (int g = 0; g < kGroups; ++g) {
                         wait_m2e(g);
-                        scan_stage(g, l);
+                        if (ok) scan_stage(g, l);
                         arrive_e2m(g);
                     }
                 }
 #pragma unroll
                 for (int g = 0; g < kGroups; ++g) {
                     wait_m2e(g);
-                    y_stage(g, l);
+                    if (ok) y_stage(g, l);
                     arrive_e2m(g);
                 }
 #pragma unroll
                 for (int g = 0; g < kGroups; ++g) {
                     wait_m2e(g);
-                    glu_stage(g, l);
+                    if (ok) glu_stage(g, l);
                     arrive_e2m(g);
                 }
             }
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) {
                 wait_m2e(g);
-                readout(g);
+                if (ok) readout(g);
             }
             tc_before();
             if (bar_or_l(1, kEpiL, !ok)) {
@@ -774,7 +783,8 @@ cudaError_t launch_lru_tc(LruTcArgs a, int grid, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     uint8_t kind[kLruSchedMax];
     a.n_slices = lru_tc_schedule(a.nL, kind, a.op);
-    const size_t base = sizeof(MiscL) + 1024 + kTilesBytes + (size_t)a.nL * kCst * kH * sizeof(float);
+    const size_t base = sizeof(MiscL) + 1024 + kTilesBytes + (size_t)a.nL * kCst * kH * sizeof(float) +
+                        (size_t)kGroups * kSl * kMaxLL * 2 * kH * sizeof(float);
     if ((size_t)optin < base + 2 * kSliceL) return cudaErrorInvalidConfiguration;
     int R = (int)(((size_t)optin - base) / kSliceL);
     a.R = R > kMaxRingL ? kMaxRingL : R;
