@@ -86,6 +86,7 @@ struct SlotL {
     int n_up;             // up spins before the current chunk
     int first;            // 1 in the job's first chunk (carries to load)
     float acc;            // sum of log P (mode 0) or of its differences (mode 1)
+    float part[4];        // the last chunk's sums over sites 8 q .. 8 q + 7 (warp q4 = q)
     uint32_t cur, pb;     // spins of the current chunk and of the sites before (chunk_bits32)
 };
 
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
     if (tid < kGroups * kSl) {
         M.slot[tid].job = -1;
         M.slot[tid].acc = 0.0f;
+        for (int q = 0; q < 4; ++q) M.slot[tid].part[q] = 0.0f;
     }
     for (int i = tid; i < nL * kCst * kH; i += blockDim.x) {
         const int u = i % kH, k = (i / kH) % kCst, l = i / (kH * kCst);
@@ -511,25 +513,28 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             tmem_st16(tres(g), xv);
             tmem_wait_st();
         };
-        // ---- readout: d_t = w_d x_t + b_d in row 0 of the first lane
-        // quarter; site t by lane t
+        // ---- readout: d_t = w_d x_t + b_d in row 32 q4 of every lane
+        // quarter (lane 0 of each warp); warp q4 takes sites 8 q4 .. 8 q4 + 7,
+        // site 8 q4 + i by lane i, and leaves its sum in the slot's part[q4]
         auto readout = [&](int g) {
-            const SlotL &st = M.slot[s + kSl * g];
-            if (q4 != 0 || st.job < 0) return;
+            SlotL &st = M.slot[s + kSl * g];
+            if (st.job < 0) return;
             const uint32_t cur = st.cur;
             const int t0 = st.c * kCh;
-            uint32_t v[32];
-            tmem_ld32(tacc(g), v);
-            tmem_wait_ld32(v);
+            uint32_t v0, v1, v2, v3, v4, v5, v6, v7;
+            tmem_ld8(tacc(g) + 8 * q4, v0, v1, v2, v3, v4, v5, v6, v7);
+            asm volatile("tcgen05.wait::ld.sync.aligned;"
+                         : "+r"(v0), "+r"(v1), "+r"(v2), "+r"(v3), "+r"(v4), "+r"(v5), "+r"(v6), "+r"(v7)::"memory");
+            const uint32_t vv[8] = {v0, v1, v2, v3, v4, v5, v6, v7};
             float dv = 0.0f;
 #pragma unroll
-            for (int t = 0; t < kCh; ++t) {
-                const float x = __shfl_sync(0xffffffffu, __uint_as_float(v[t]), 0);
-                if (t == lane) dv = x;
+            for (int i = 0; i < 8; ++i) {
+                const float x = __shfl_sync(0xffffffffu, __uint_as_float(vv[i]), 0);
+                if (i == lane) dv = x;
             }
-            const int t = lane, tt = t0 + t;
+            const int t = 8 * q4 + lane, tt = t0 + t;
             float lp = 0.0f;
-            if (tt < N) {
+            if (lane < 8 && tt < N) {
                 const float d = dv + bd;
                 const int sv = (cur >> t) & 1u;
                 const int nu = st.n_up + __popc(cur & ((1u << t) - 1u));
@@ -538,8 +543,14 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                 if (A.mode == 1) lp -= lref[g];
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
-            if (lane == 0) M.slot[s + kSl * g].acc += lp;
+            for (int o = 4; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+            if (lane == 0) st.part[q4] = lp;
+        };
+        // adds the last chunk's four partial sums to the job's sum, in a
+        // fixed order
+        auto fold = [&](SlotL &st) {
+            st.acc += (st.part[0] + st.part[1]) + (st.part[2] + st.part[3]);
+            st.part[0] = st.part[1] = st.part[2] = st.part[3] = 0.0f;
         };
         // the 32 sites' 32-bit spins of the slot's current chunk: cur (bit t =
         // s_{t0+t}) and prevbits (bit t = s_{t0+t-1}, 0 at the first site)
@@ -556,6 +567,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             // ---- slot update (lanes 0, 1 of warp 4 s: slots s, 4 + s)
             if (q4 == 0 && lane < kGroups) {
                 SlotL &st = M.slot[s + kSl * lane];
+                fold(st);
                 if (row_it > 0 && st.job >= 0 && st.c + 1 >= st.nch) {
                     G.out[st.job] = 0.5f * st.acc;  // the job's last chunk is done
                 }
@@ -632,8 +644,8 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
                 // log P of the reference configuration at this lane's site
                 // (mode 1 readout), loaded ahead of the step
                 lref[g] = 0.0f;
-                if (A.mode == 1 && q4 == 0 && act && t0 + lane < N)
-                    lref[g] = G.logp_ref[(int64_t)st.sample * N + t0 + lane];
+                if (A.mode == 1 && act && lane < 8 && t0 + 8 * q4 + lane < N)
+                    lref[g] = G.logp_ref[(int64_t)st.sample * N + t0 + 8 * q4 + lane];
             }
             __syncwarp();  // the carries written by the even lanes, before both lanes read them
 
@@ -680,6 +692,7 @@ __global__ void __launch_bounds__(kEpiL + 64, 1) lru_tc_kernel(const __grid_cons
             if (!*(volatile int *)&M.go_flag[(row_it + 1) & 1]) {
                 if (q4 == 0 && lane < kGroups) {
                     SlotL &sf = M.slot[s + kSl * lane];
+                    fold(sf);
                     if (sf.job >= 0) G.out[sf.job] = 0.5f * sf.acc;
                 }
                 break;
