@@ -65,6 +65,25 @@ def test_logpsi_lru_tc_matches_oracle(oracle_mod, N, nL, u1, kind, prec):
     assert np.all(err <= scale * (2e-2 + 2e-5 * np.abs(ref[fin]))), (err.max(), np.abs(ref).max())
 
 
+@pytest.mark.parametrize("N,nL,u1", [(1, 3, False), (2, 3, True), (33, 2, False), (64, 4, True), (31, 4, False)])
+def test_logpsi_lru_tc_edge_sizes(oracle_mod, N, nL, u1):
+    """Degenerate and boundary chains on the tensor-core path: a single site,
+    the smallest zero-magnetisation chain, one site past a chunk, an exact
+    multiple of the chunk, and the deepest supported model (4 layers)."""
+    theta = _theta(oracle_mod, nL, 740 + N + nL, "random")
+    s = _spins(741, 24, N, u1)
+    ref = oracle_mod.logpsi_lru(theta.astype(np.float64), nL, H, s, u1=u1)
+    for prec, scale in (("fp16", 1.0), ("bf16", 2.0)):
+        got = api.logpsi_lru(torch.from_numpy(theta).cuda(), torch.from_numpy(s).cuda(),
+                             api.ModelConfig(nL, H, u1, prec))
+        api.sync()
+        got = got.cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(got) == np.isfinite(ref))
+        fin = np.isfinite(ref)
+        err = np.abs(got[fin] - ref[fin])
+        assert np.all(err <= scale * (2e-2 + 2e-5 * np.abs(ref[fin]))), (prec, err.max())
+
+
 @pytest.mark.parametrize("kind,N,pbc,u1,hf", [(1, 16, False, False, 1.0), (1, 16, True, False, 1.0),
                                               (0, 20, False, True, 0.0), (1, 256, False, False, 1.0),
                                               (0, 66, True, True, 0.0)])
