@@ -10,10 +10,11 @@
 // with the two-logit readout.  Its dense products become three MMAs per
 // layer, each with an M = 128 weight operand (A, K-major, 128-byte swizzle)
 // and the sites as B (N = 128 columns):
-//   [B_re; B_im] u   rows 2j, 2j + 1 = unit j's real / imaginary part
+//   e^gamma [B_re; B_im] u   rows 2j, 2j + 1 = unit j's real / imaginary part
 //   [C_re, -C_im] [h_re; h_im]   rows 2j, 2j + 1 both unit j's, K = 128
 //   [W_a; W_g] y     rows 2j, 2j + 1 = unit j's W_a / W_g row
-// and the readout w_d x with w_d in row 32 q of every lane quarter q.  Layer
+// and the readout w_d x with w_d in row 32 q of every lane quarter q (each
+// warp reads it from its lane 0 and takes 8 of the chunk's sites).  Layer
 // 0's input is one-hot (Sec. II.F), so its B u and D u are lookups.  The
 // thread pair of rows 2j, 2j + 1 shares unit j: both run its complex scan
 // over the chunk, and the y and GLU epilogues split the sites by parity
@@ -54,7 +55,7 @@ constexpr int kGroups = 2;          // slot groups, a chunk step apart in phase
 constexpr uint32_t kSliceL = 16384; // 128 rows x 64 inputs, 16-bit
 constexpr int kMaxRingL = 12;
 constexpr int kEpiL = 512;          // epilogue threads
-constexpr int kMaxLL = 4;           // layers (complex carries held in registers)
+constexpr int kMaxLL = 4;           // layers (rows of the slots' carries in shared memory)
 
 // Tensor memory (columns): group g's accumulator at 128 g (B u, y, GLU and
 // readout in turn: each MMA starts after the epilogue has read the previous
