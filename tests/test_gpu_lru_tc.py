@@ -65,11 +65,13 @@ def test_logpsi_lru_tc_matches_oracle(oracle_mod, N, nL, u1, kind, prec):
     assert np.all(err <= scale * (2e-2 + 2e-5 * np.abs(ref[fin]))), (err.max(), np.abs(ref).max())
 
 
-@pytest.mark.parametrize("N,nL,u1", [(1, 3, False), (2, 3, True), (33, 2, False), (64, 4, True), (31, 4, False)])
+@pytest.mark.parametrize("N,nL,u1", [(1, 3, False), (2, 3, True), (33, 2, False), (64, 4, True), (31, 4, False),
+                                     (1000, 3, True)])
 def test_logpsi_lru_tc_edge_sizes(oracle_mod, N, nL, u1):
     """Degenerate and boundary chains on the tensor-core path: a single site,
     the smallest zero-magnetisation chain, one site past a chunk, an exact
-    multiple of the chunk, and the deepest supported model (4 layers)."""
+    multiple of the chunk, the deepest supported model (4 layers), and a
+    1000-site chain (32 chunks, ragged last chunk)."""
     theta = _theta(oracle_mod, nL, 740 + N + nL, "random")
     s = _spins(741, 24, N, u1)
     ref = oracle_mod.logpsi_lru(theta.astype(np.float64), nL, H, s, u1=u1)
