@@ -112,6 +112,41 @@ def test_many_jobs_slot_refill_and_determinism():
     _lp_close(a.cpu().numpy(), r.cpu().numpy().astype(np.float64))
 
 
+def test_52x52_tc_at_the_benchmark_size(oracle_mod):
+    """The benchmark's 2D workload in its own launch shape (52x52 open
+    Heisenberg, 3 layers, d_h = 256, zero magnetisation, 64 Neel-like
+    samples of seed 1000, Glorot theta seed 0, FP16 operands): E_loc of
+    sampled rows (first, middle, last) of the 64-sample launch equals the
+    combination of full tensor-core forwards of their connected
+    configurations, and sampled log psi values agree with the oracle."""
+    Lx = Ly = 52
+    nL, H, n = 3, 256, 64
+    theta = inputs.glorot_params2d(nL, H, seed=0)
+    s = inputs.neel_like_spins(1000, n, Lx, Ly)
+    ham = B.make_hamiltonian("heisenberg", Lx, Ly, False, True, 1.0, 0.0)
+    cfg = api.ModelConfig(nL, H, True, "fp16")
+    th = torch.from_numpy(theta).cuda()
+    e, _ = api.local_energy2d(th, torch.from_numpy(s).cuda(), cfg, ham)
+    pick = [0, n // 2, n - 1]
+    sub = s[pick]
+    offsets, entries, diag = oracle_mod.connected(0, Lx, Ly, False, sub)
+    flipped = np.repeat(sub, np.diff(offsets), axis=0)
+    rows = np.arange(flipped.shape[0])
+    flipped[rows, entries[:, 1]] ^= 1
+    flipped[rows, entries[:, 2]] ^= 1
+    lp_s = api.logpsi2d(th, torch.from_numpy(sub).cuda(), cfg, Lx, Ly).cpu().numpy().astype(np.float64)
+    lp_f = api.logpsi2d(th, torch.from_numpy(flipped).cuda(), cfg, Lx, Ly).cpu().numpy().astype(np.float64)
+    api.sync()
+    full = np.array([diag[i] - 0.5 * np.sum(np.exp(lp_f[offsets[i]:offsets[i + 1]] - lp_s[i]))
+                     for i in range(len(pick))])
+    scale = np.abs(diag) + np.abs(full - diag)
+    assert np.all(np.abs(e.cpu().numpy()[pick] - full) <= 1e-4 * scale)
+    q = np.random.default_rng(2).choice(flipped.shape[0], 2, replace=False)
+    ref = oracle_mod.logpsi2d(theta.astype(np.float64), nL, H, Lx, Ly, np.concatenate([sub[:2], flipped[q]]),
+                              u1=True)
+    _lp_close(np.concatenate([lp_s[:2], lp_f[q]]), ref)
+
+
 def test_52x52_tc_resume_equals_full_forwards(oracle_mod):
     """The paper's 52x52 configuration (3 layers, d_h = 256, zero
     magnetisation; FP16 operands): E_loc of two samples, whose connected

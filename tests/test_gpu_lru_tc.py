@@ -109,6 +109,32 @@ def test_local_energy_lru_tc_matches_oracle(oracle_mod, kind, N, pbc, u1, hf, pr
     assert abs(st[0].item() - m) <= 1e-9 * max(1.0, abs(m))
 
 
+def test_lru_tc_at_the_benchmark_size(oracle_mod):
+    """The benchmark's LRU workload in its own launch shape (TFIM chain N =
+    256, OBC, h = 1, 1024 samples, ring parameters seed 0, FP16 operands):
+    log psi of every sample, and E_loc of sampled rows (first, middle, last),
+    against the oracle."""
+    N, nL, n = 256, 3, 1024
+    theta = inputs.lru_params(nL, H, seed=0)
+    s = inputs.random_spins(2000, n, N)
+    ham = B.make_hamiltonian("tfim", N, 1, False, True, 1.0, 1.0)
+    cfg = api.ModelConfig(nL, H, False, "fp16")
+    th, sp = torch.from_numpy(theta).cuda(), torch.from_numpy(s).cuda()
+    lp = api.logpsi_lru(th, sp, cfg)
+    e, _ = api.local_energy_lru(th, sp, cfg, ham)
+    api.sync()
+    ref = oracle_mod.logpsi_lru(theta.astype(np.float64), nL, H, s, u1=False)
+    err = np.abs(lp.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= 2e-2 + 2e-5 * np.abs(ref)), err.max()
+    pick = [0, n // 2, n - 1]
+    sub = s[pick]
+    eref = oracle_mod.local_energy_lru(theta.astype(np.float64), nL, H, sub, 1, N, 1, pbc=False, marshall=True,
+                                       J=1.0, h=1.0, u1=False)
+    _, _, diag = oracle_mod.connected(1, N, 1, False, sub)
+    got = e.cpu().numpy()[pick]
+    assert np.all(np.abs(got - eref) <= 1e-3 * (np.abs(diag) + np.abs(eref - diag))), (got, eref)
+
+
 def test_lru_tc_many_jobs_and_determinism():
     """More sequences than the CTAs hold slots (8 per CTA), so slots take new
     jobs mid-launch; within the 16-bit bound of the (oracle-checked) FP32
