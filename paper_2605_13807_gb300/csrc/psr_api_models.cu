@@ -797,13 +797,17 @@ int psr_lru_sample(const psr_params *params, const float *uniforms, int64_t n, i
     const bool d_theta = is_device_ptr(params->theta), d_u = is_device_ptr(uniforms),
                d_s = is_device_ptr(spins), d_lp = logpsi ? is_device_ptr(logpsi) : true;
     float *theta_ws = nullptr, *u_ws = nullptr, *lp_ws = nullptr, *pk = nullptr;
-    uint8_t *s_ws = nullptr;
+    uint8_t *s_ws = nullptr, *wimg = nullptr;
+    // 16-bit precision: the tensor-core sampler (the conditionals of the
+    // tensor-core forward) where it holds the model; FP32 otherwise
+    const bool tc = params->precision != PSR_FP32 && lru_tc_sample_supported(nL, H);
     auto carve = [&](Carver &c) {
         theta_ws = c.get<float>(d_theta ? 0 : P);
         u_ws = c.get<float>(d_u ? 0 : (size_t)n * N);
         s_ws = c.get<uint8_t>(d_s ? 0 : (size_t)n * N);
         lp_ws = c.get<float>(d_lp ? 0 : n);
         pk = c.get<float>(f.total);
+        if (tc) wimg = c.get<uint8_t>(lru_tc_weight_bytes(nL));
     };
     Carver sz;
     carve(sz);
@@ -817,6 +821,25 @@ int psr_lru_sample(const psr_params *params, const float *uniforms, int64_t n, i
     if ((rc = stage_in(uniforms, u_ws, (size_t)n * N, d_u, st, &uu)) != PSR_OK) return rc;
     uint8_t *so = d_s ? spins : s_ws;
     float *lo = logpsi ? (d_lp ? logpsi : lp_ws) : nullptr;
+    if (tc) {
+        const bool f16 = params->precision == PSR_FP16;
+        reset_stages(ctx);
+        {
+            StageScope sc(ctx, PSR_STAGE_PACK);
+            PSR_TRY(launch_pack_theta_lru(theta, f, pk, st));
+            PSR_TRY(launch_pack_lru_tc(pk, f, f16, wimg, st));
+        }
+        {
+            StageScope sc(ctx, PSR_STAGE_SAMPLE);
+            PSR_TRY(launch_sample_lru_tc(pk, f, f16, wimg, uu, n, N, params->u1_mask, so, lo, ctx->status,
+                                         ctx->num_sms, st));
+        }
+        if (!d_s) PSR_TRY(cudaMemcpyAsync(spins, s_ws, (size_t)n * N, cudaMemcpyDeviceToHost, st));
+        if (logpsi && !d_lp)
+            PSR_TRY(cudaMemcpyAsync(logpsi, lp_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+        if (!d_theta || !d_u || !d_s || !d_lp) return take_status(ctx);
+        return PSR_OK;
+    }
     // samples per CTA: measured by the autotuner when it is on; otherwise
     // the most that still gives every SM a CTA (weights are read once per
     // CTA and site, so more samples per CTA read less)
