@@ -550,6 +550,8 @@ def lru_leg(dev, N=256, H=64, n=1024, reps=3, n32=None):
             out.update(api.vmc_step_lru(th, cfg, ham, u, adam, theta_out=th))
 
         vmc_ms = timed(vmc)
+        # the exact sampler alone (1024 samples of the chain)
+        sample_ms = timed(lambda: api.sample_lru(theta, u, cfg))
         # the same step at shorter chains, beside the paper's Table I step
         # times (1x H100, same model and sample count; context, not a target)
         by_n = {}
@@ -562,7 +564,7 @@ def lru_leg(dev, N=256, H=64, n=1024, reps=3, n32=None):
         by_n[str(N)] = vmc_ms
         return {"value": (n + E) * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                 "connected_launch_ms": conn_ms, "achieved_tflops": achieved,
-                "energy_per_site": float(st[0].item()) / N, "vmc_step_ms": vmc_ms,
+                "energy_per_site": float(st[0].item()) / N, "vmc_step_ms": vmc_ms, "sample_ms": sample_ms,
                 "vmc_step_ms_by_N": by_n, "vmc_energy_per_site": float(out["stats"][0].item()) / N}
 
     tc = run("fp16")
@@ -580,6 +582,7 @@ def lru_leg(dev, N=256, H=64, n=1024, reps=3, n32=None):
     return {"model": "deep 1D LRU (complex diagonal recurrence + GLU), tcgen05 tensor cores "
                      "(FP16 operands, FP32 accumulation, complex scan, GLU, readout)",
             "grad_bwd_ms": bwd_ms, "vmc_step_ms": tc["vmc_step_ms"], "vmc_step_ms_by_N": tc["vmc_step_ms_by_N"],
+            "sample_ms": tc["sample_ms"],
             "paper_step_ms_H100_by_N": {"32": 28, "64": 71, "128": 260, "256": 900},
             "vmc_energy_per_site": tc["vmc_energy_per_site"],
             "workload": f"tfim_chain_{N}_obc_{n}_samples", "hidden": H, "connected": E,
@@ -599,6 +602,7 @@ def lru_leg(dev, N=256, H=64, n=1024, reps=3, n32=None):
                                 "frac_of_fp32_simt_peak": f32["achieved_tflops"] / FP32_SIMT_TFLOPS,
                                 "energy_per_site": f32["energy_per_site"],
                                 "vmc_step_ms": f32["vmc_step_ms"], "vmc_step_ms_by_N": f32["vmc_step_ms_by_N"],
+                                "sample_ms": f32["sample_ms"],
                                 "vmc_energy_per_site": f32["vmc_energy_per_site"]},
             "speedup_vs_fp32": tc["value"] / f32["value"]}
 

@@ -471,8 +471,10 @@ int psr2d_sym_local_energy(const psr_params *params, const uint8_t *samples, int
  * D u, GLU, residual, softmax and sums in FP32.  Bounds of the 16-bit path
  * against the exact model: |d log psi| <= 2e-2 + 2e-5 |log psi| and E_loc
  * within 1e-3 (|diag| + |E_loc - diag|) with FP16 operands (BF16: about
- * twice that).  Other shapes at 16-bit precision return PSR_EUNSUPPORTED;
- * psr_lru_sample and psr_lru_grad compute in FP32 at every precision. */
+ * twice that).  Other shapes at 16-bit precision return PSR_EUNSUPPORTED.
+ * psr_lru_sample at 16-bit precision draws from the conditionals of that
+ * tensor-core model (up to 3 layers; 4 layers draw in FP32); psr_lru_grad
+ * computes in FP32 at every precision. */
 int psr_lru_param_count(int32_t n_layers, int32_t hidden, int64_t *P);
 
 int psr_lru_logpsi(const psr_params *params, const uint8_t *spins, int64_t n, int32_t L, float *out);
@@ -486,9 +488,12 @@ int psr_lru_local_energy(const psr_params *params, const uint8_t *samples, int64
 /* Exact samples of |psi|^2 of the LRU ansatz from uniforms [n][L] (float,
  * host or device): s_t = 1 iff u_t < P(s_t = 1 | s_<t), the forced value at
  * sites the zero-magnetisation mask fixes (Sec. II.A).  spins: uint8 [n][L]
- * out; logpsi: float [n] out (NULL to skip).  FP32; the result does not
- * depend on how samples are grouped into CTAs.  Requirements as
- * psr_lru_logpsi. */
+ * out; logpsi: float [n] out (NULL to skip).  PSR_FP32: FP32 on CUDA cores.
+ * PSR_FP16 / PSR_BF16 at hidden 64 with 1 to 3 layers: on the tensor cores,
+ * the conditionals of the 16-bit model psr_lru_logpsi evaluates at that
+ * precision (a draw can differ from the FP32 one only where u_t lies within
+ * the 16-bit rounding of P).  The result does not depend on how samples are
+ * grouped into CTAs.  Requirements as psr_lru_logpsi. */
 int psr_lru_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t L, uint8_t *spins,
                    float *logpsi);
 
@@ -569,9 +574,9 @@ int psr2d_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian,
 /* One VMC step of the LRU ansatz on the device, as psr_vmc_step without
  * symmetrisation: exact samples from uniforms [n][N] (psr_lru_sample),
  * E_loc (psr_lru_local_energy), the energy gradient by psr_lru_grad, Adam.
- * At PSR_FP16 / PSR_BF16 the local energies come from the tensor-core
- * forward; samples and gradient are FP32.  Same array rules as
- * psr_vmc_step. */
+ * At PSR_FP16 / PSR_BF16 the samples and the local energies come from the
+ * tensor cores (the sampler at up to 3 layers); the gradient is FP32.  Same
+ * array rules as psr_vmc_step. */
 int psr_lru_vmc_step(const psr_params *params, const psr_hamiltonian *hamiltonian, const float *uniforms,
                      int64_t n, const psr_adam *adam, float *theta_out, uint8_t *spins_out,
                      float *eloc_out, double *stats_out, float *grad_out);
