@@ -388,6 +388,16 @@ def sample_leg(theta, n, N, dev, reps=2):
     avg = sum(ms) / len(ms)
     flops = n * N * MMA_FLOPS_PER_SITE
     achieved = flops / (avg / 1e3) / 1e12
+    # the same draws' model at BF16: the tensor-core sampler (blocks of 32
+    # samples as MMA columns; the chain of a site's MMA stages bounds it)
+    cfg16 = api.ModelConfig(N_LAYERS, HIDDEN, True, "bf16")
+    api.sample(theta, u, cfg16, spins=s, logpsi=lp)
+    ms16 = []
+    for _ in range(reps):
+        api.sample(theta, u, cfg16, spins=s, logpsi=lp)
+        ms16.append(B.psr_context_stage_ms(ctx)["sample"])
+    api.sync()
+    avg16 = sum(ms16) / len(ms16)
     del u, s, lp
     return {"kernel": "sample_kernel (psr_sample, exact autoregressive sampler, FP32)",
             "samples": n, "sites": N, "samples_per_cta": per_cta, "tuned": tuned, "ms": avg,
@@ -395,7 +405,10 @@ def sample_leg(theta, n, N, dev, reps=2):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                         "traffic": None, "flops_per_unit": MMA_FLOPS_PER_SITE}}
+                         "traffic": None, "flops_per_unit": MMA_FLOPS_PER_SITE},
+            "bf16_tensor_cores": {"kernel": "sample_tc_kernel (BF16 operands, FP32 gates, scan, readout)",
+                                  "ms": avg16, "value": n * N / (avg16 / 1e3), "unit": "sample-sites/s",
+                                  "speedup_vs_fp32": avg / avg16}}
 
 
 # FLOPs per evaluated patch of the 2D patched minGRU (3 layers, hidden H):
@@ -704,7 +717,7 @@ def vmc_leg(dev, L=10, n=1024, reps=3):
     """One full on-device VMC step (exact sampling, E_loc, energy gradient,
     Adam; the paper's definition of a training step, Sec. III.A) for the
     chain model on the 10x10 Heisenberg lattice (hidden 128, 3 layers, BF16
-    E_loc, FP32 sampling and gradient), without and with c4v
+    sampling and E_loc on the tensor cores, FP32 gradient), without and with c4v
     symmetrisation (8 images per configuration)."""
     import torch
 
@@ -718,7 +731,7 @@ def vmc_leg(dev, L=10, n=1024, reps=3):
     u = torch.rand((n, N), generator=g, device=dev)
     us = torch.rand(n, generator=g, device=dev)
     res = {"workload": f"heisenberg_{L}x{L}_obc_{n}_samples", "hidden": HIDDEN,
-           "layers": N_LAYERS, "precision": "BF16 E_loc, FP32 sampling and gradient"}
+           "layers": N_LAYERS, "precision": "BF16 sampling and E_loc (tensor cores), FP32 gradient"}
     for sym in (False, True):
         adam = api.Adam(theta.numel(), dev, lr=1e-3)
         th = theta.clone()  # updated in place by every step

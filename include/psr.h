@@ -310,9 +310,14 @@ int psr_scan_tile_for(psr_context *ctx, int64_t n, int32_t N, int32_t H, psr_sca
  * of sample i is s_t = 1 iff uniforms[i][t] < P(s_t = 1 | s_<t) (with
  * u1_mask, the forced value where the mask forces one).  spins: uint8
  * [n][L] output in sequence order; logpsi: float [n] output (log psi of the
- * drawn sample) or NULL.  Computed in FP32 for both precisions.  The result
- * does not depend on how samples are grouped into CTAs (a tile shape the
- * autotuner chooses), so equal uniforms give equal samples.
+ * drawn sample) or NULL.  PSR_FP32: FP32 on CUDA cores.  PSR_BF16 at the
+ * BF16 forward's shape (hidden 128, 3 layers): on the tensor cores, the
+ * conditionals of the BF16 model psr_logpsi evaluates (BF16 operands, FP32
+ * gates, scan and readout; a draw can differ from the exact model's only
+ * where u lies within the BF16 error of P); other BF16 shapes draw in FP32.
+ * The result does not depend on how samples are grouped into CTAs (a tile
+ * shape the autotuner chooses, or blocks of 32 on the tensor cores), so
+ * equal uniforms give equal samples.
  * PSR_EINVAL: what psr_logpsi rejects, or null uniforms / spins. */
 int psr_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t L,
                uint8_t *spins, float *logpsi);

@@ -253,7 +253,8 @@ int psr_scan_tile_for(psr_context *ctx, int64_t n, int32_t N, int32_t H, psr_sca
 int psr_sample(const psr_params *params, const float *uniforms, int64_t n, int32_t L,
                uint8_t *spins, float *logpsi) {
     int rc = check_params(params, n, L);
-    if (rc == PSR_EUNSUPPORTED && params->precision == PSR_BF16) rc = PSR_OK;  // FP32 either way
+    // BF16 shapes the tensor-core sampler does not hold draw in FP32
+    if (rc == PSR_EUNSUPPORTED && params->precision == PSR_BF16) rc = PSR_OK;
     if (rc != PSR_OK) return rc;
     if (!uniforms || !spins) return PSR_EINVAL;
     psr_context *ctx = params->ctx;
@@ -265,13 +266,17 @@ int psr_sample(const psr_params *params, const float *uniforms, int64_t n, int32
     const size_t cells = (size_t)n * L;
 
     float *theta_ws = nullptr, *u_ws = nullptr, *lp_ws = nullptr, *pk = nullptr;
-    uint8_t *s_ws = nullptr;
+    uint8_t *s_ws = nullptr, *wimg = nullptr;
+    // BF16 at the BF16 forward's shape: the tensor-core sampler (the
+    // conditionals of the BF16 model); FP32 otherwise
+    const bool tc = params->precision == PSR_BF16 && sample_tc_supported(nL, H);
     auto carve = [&](Carver &c) {
         theta_ws = c.get<float>(d_theta ? 0 : tl.total);
         u_ws = c.get<float>(d_u ? 0 : cells);
         s_ws = c.get<uint8_t>(d_s ? 0 : cells);
         lp_ws = c.get<float>(d_lp ? 0 : n);
         pk = c.get<float>(fl.total);
+        if (tc) wimg = c.get<uint8_t>(sample_tc_weight_bytes());
     };
     Carver sz;
     carve(sz);
@@ -286,6 +291,22 @@ int psr_sample(const psr_params *params, const float *uniforms, int64_t n, int32
     uint8_t *so = d_s ? spins : s_ws;
     float *lo = logpsi ? (d_lp ? logpsi : lp_ws) : nullptr;
 
+    if (tc) {
+        reset_stages(ctx);
+        {
+            StageScope sc(ctx, PSR_STAGE_PACK);
+            PSR_TRY(launch_pack_theta_f32(theta, tl, fl, pk, st));
+        }
+        {
+            StageScope sc(ctx, PSR_STAGE_SAMPLE);
+            PSR_TRY(launch_sample_tc(pk, fl, wimg, uu, n, L, params->u1_mask, so, lo, ctx->status, ctx->num_sms, st));
+        }
+        if (!d_s) PSR_TRY(cudaMemcpyAsync(spins, s_ws, cells, cudaMemcpyDeviceToHost, st));
+        if (logpsi && !d_lp)
+            PSR_TRY(cudaMemcpyAsync(logpsi, lp_ws, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+        if (!d_theta || !d_u || !d_s || !d_lp) return take_status(ctx);
+        return PSR_OK;
+    }
     // samples per CTA: forced by nothing, tuned, or the default
     const int64_t key2 = (int64_t)nL * 1024 + H;
     int per_cta = 8;

@@ -336,6 +336,15 @@ bool lru_tc_supported(int nL, int H);
 size_t lru_tc_weight_bytes(int nL);
 cudaError_t launch_pack_lru_tc(const float *pk, const LruLayout &f, bool f16, uint8_t *wimg, cudaStream_t stream);
 cudaError_t launch_lru_tc(LruTcArgs a, int grid, cudaStream_t stream);
+// Exact sampler of the chain minGRU on the tensor cores (psr_sample_tc.cu),
+// hidden 128, 3 layers, BF16 operands: packs its weight image (wimg:
+// sample_tc_weight_bytes()) from the FP32-packed parameters, then draws
+// blocks of 32 samples; spins [n][N] and (if logpsi) log psi [n] out.
+bool sample_tc_supported(int nL, int H);
+size_t sample_tc_weight_bytes();
+cudaError_t launch_sample_tc(const float *pk, const F32Layout &fl, uint8_t *wimg, const float *unif, int64_t n,
+                             int N, int u1, uint8_t *out, float *logpsi, int *status, int num_sms,
+                             cudaStream_t stream);
 // Exact sampler of the deep LRU on the tensor cores (psr_sample_lru_tc.cu),
 // hidden 64, 1 to 3 layers: blocks of 32 samples, weights from the image
 // launch_pack_lru_tc wrote (resident in shared memory), FP16 or BF16
