@@ -504,14 +504,14 @@ def lru_flops_per_site(H):
     return 8 * H * H + 2 * 12 * H * H
 
 
-def lru_leg(dev, N=256, H=64, n=1024, reps=3, n32=None):
+def lru_leg(dev, N=256, H=64, n=1024, reps=3):
     """The paper's deep 1D LRU on the 1D TFIM (Table IV configuration: 3
     layers, d = d_h = 64, N = 256 OBC, 1024 samples, h = 1): log psi + E_loc
     over every site flip on the tensor cores (FP16 operands, FP32
     accumulation, complex scan, GLU and readout) and on the FP32 CUDA cores;
-    then the gradient's reverse pass and one full VMC step (sampling, E_loc,
-    gradient, Adam) at both precisions (sampling and gradient run in FP32 in
-    both)."""
+    then the gradient's reverse pass, the exact sampler, and one full VMC
+    step (sampling, E_loc, gradient, Adam) at both precisions (at FP16 the
+    sampler and E_loc run on the tensor cores, the gradient in FP32)."""
     import torch
 
     from paper_2605_13807_gb300 import api, binding as B, inputs
